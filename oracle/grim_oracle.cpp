@@ -35,7 +35,11 @@
 //    zone per stage; converged when max_i |r_i| <= tol, tested before each
 //    Jacobian (Section 3 leaves the norm open).
 //  * FD Jacobian (Section 3.1): only component j is perturbed; the divisor is
-//    the computed difference P_eps,j - P_j.
+//    the computed difference P_eps,j - P_j.  small() is there to keep that
+//    divisor away from zero, but taken literally (P_eps,j = eps when
+//    |P_j| < 5 eps) it makes the divisor vanish at P_j = eps and tiny near
+//    it; we perturb small components by +eps (P_eps,j = P_j + eps), which is
+//    the printed formula at P_j = 0, the case the text discusses.
 //  * line search (Section 3.2): the acceptance test is compared in squared
 //    form; a non-finite trial halves lambda; after ls_max backtracks the last
 //    trial is taken and a stall flag is set.
@@ -111,6 +115,16 @@ inline Cnt sqrt(Cnt a) {
   return Cnt(std::sqrt(a.v), true);
 }
 inline double re(Cnt a) { return a.v; }
+inline bool operator>(Cnt a, double b) { return a.v > b; }
+inline bool operator<(Cnt a, double b) { return a.v < b; }
+inline bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
+inline bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
+inline Cnt tabs(Cnt a) { return Cnt(std::fabs(a.v), a.dep); }
+inline Cnt tmin(Cnt a, Cnt b) { return a.v < b.v ? a : b; }
+inline Cnt tmax(Cnt a, Cnt b) { return a.v > b.v ? a : b; }
+inline double tabs(double a) { return std::fabs(a); }
+inline double tmin(double a, double b) { return std::min(a, b); }
+inline double tmax(double a, double b) { return std::max(a, b); }
 
 // Forward-mode dual number over any scalar T (value + one directional derivative).
 template <class T> struct Dual {
@@ -340,23 +354,23 @@ static void relax_targets(const State<C>& sE, const Geom& g, const Params& p, co
 // corrections v_q^2 = (gamma-1) chi/tau_R, v_dP^2 = 4 nu/(3 tau_R) (Section 4.1),
 // then the grid-frame speeds of waves moving at +-v_max in direction j: the
 // roots c of (k.u)^2 = v^2 (k.k + (k.u)^2) with k_mu = (-c, e_j).
-static void wave_speeds(const State<double>& s, const Geom& g, const Params& p, int j, double& cmin,
-                        double& cmax) {
-  double vA2 = s.bsq / (s.rho + p.gamma * s.u + s.bsq);
-  double vq2 = (p.gamma - 1.0) * s.chi / s.tauR;
-  double vdp2 = 4.0 * s.nu / (3.0 * s.tauR);
-  double cs2t = 0.5 * (s.cs2 + vq2 + std::sqrt(s.cs2 * s.cs2 + vq2 * vq2)) + vdp2;
-  double v2 = cs2t + vA2 - cs2t * vA2;
-  double ut = s.ucon[0], uj = s.ucon[j];
-  double A = (1.0 - v2) * ut * ut - v2 * g.gcon[0][0];
-  double B = -2.0 * ((1.0 - v2) * ut * uj - v2 * g.gcon[0][j]);
-  double Cc = (1.0 - v2) * uj * uj - v2 * g.gcon[j][j];
-  double disc = B * B - 4.0 * A * Cc;
-  if (disc < 0.0) disc = 0.0;
-  double sq = std::sqrt(disc);
-  double c1 = (-B + sq) / (2.0 * A), c2 = (-B - sq) / (2.0 * A);
-  cmax = std::max(c1, c2);
-  cmin = std::min(c1, c2);
+template <class T>
+static void wave_speeds(const State<T>& s, const Geom& g, const Params& p, int j, T& cmin, T& cmax) {
+  T vA2 = s.bsq / (s.rho + p.gamma * s.u + s.bsq);
+  T vq2 = (p.gamma - 1.0) * s.chi / s.tauR;
+  T vdp2 = 4.0 * s.nu / (3.0 * s.tauR);
+  T cs2t = 0.5 * (s.cs2 + vq2 + sqrt(s.cs2 * s.cs2 + vq2 * vq2)) + vdp2;
+  T v2 = cs2t + vA2 - cs2t * vA2;
+  T ut = s.ucon[0], uj = s.ucon[j];
+  T A = (1.0 - v2) * ut * ut - v2 * g.gcon[0][0];
+  T B = -2.0 * ((1.0 - v2) * ut * uj - v2 * g.gcon[0][j]);
+  T Cc = (1.0 - v2) * uj * uj - v2 * g.gcon[j][j];
+  T disc = B * B - 4.0 * A * Cc;
+  if (disc < 0.0) disc = T(0.0);
+  T sq = sqrt(disc);
+  T c1 = (-B + sq) / (2.0 * A), c2 = (-B - sq) / (2.0 * A);
+  cmax = tmax(c1, c2);
+  cmin = tmin(c1, c2);
 }
 
 // ---------------------------------------------------------------- grid access
@@ -372,8 +386,10 @@ struct Grid {
     int bc = p.bc[d][side];
     if (bc == BC_PERIODIC) return ((i % n) + n) % n;
     if (bc == BC_OUTFLOW) return (i < 0) ? 0 : n - 1;
-    flip = !flip;
-    return (i < 0) ? (-1 - i) : (2 * n - 1 - i);
+    // reflections: images repeat with period 2n, odd images are mirrored
+    int m = ((i % (2 * n)) + 2 * n) % (2 * n);
+    if (m >= n) { flip = !flip; return 2 * n - 1 - m; }
+    return m;
   }
   // Primitive vector of the (possibly ghost) zone (i,j,k).
   void prim(const double* P, int i, int j, int k, double out[10]) const {
@@ -394,42 +410,42 @@ struct Grid {
 
 // ---------------------------------------------------------------- reconstruction
 // Generalized minmod slope (Section 2.4.1): theta = 1 is minmod, theta = 2 is MC.
-static double gminmod(double theta, double vm, double v0, double vp) {
-  double a = theta * (v0 - vm), b = 0.5 * (vp - vm), c = theta * (vp - v0);
-  if (a > 0 && b > 0 && c > 0) return std::min(a, std::min(b, c));
-  if (a < 0 && b < 0 && c < 0) return std::max(a, std::max(b, c));
-  return 0.0;
+template <class T> static T gminmod(double theta, T vm, T v0, T vp) {
+  T a = theta * (v0 - vm), b = 0.5 * (vp - vm), c = theta * (vp - v0);
+  if (a > 0.0 && b > 0.0 && c > 0.0) return tmin(a, tmin(b, c));
+  if (a < 0.0 && b < 0.0 && c < 0.0) return tmax(a, tmax(b, c));
+  return T(0.0);
 }
 
 // WENO5 (Jiang & Shu 1996): value at the right face of the middle zone of
 // v[0..4] from the three 3-point candidates and their smoothness indicators.
-static double weno5_right(const double v[5]) {
+template <class T> static T weno5_right(const T v[5]) {
   const double eps = 1e-6;
-  double q0 = (2 * v[0] - 7 * v[1] + 11 * v[2]) / 6.0;
-  double q1 = (-v[1] + 5 * v[2] + 2 * v[3]) / 6.0;
-  double q2 = (2 * v[2] + 5 * v[3] - v[4]) / 6.0;
-  double b0 = 13.0 / 12.0 * (v[0] - 2 * v[1] + v[2]) * (v[0] - 2 * v[1] + v[2]) +
-              0.25 * (v[0] - 4 * v[1] + 3 * v[2]) * (v[0] - 4 * v[1] + 3 * v[2]);
-  double b1 = 13.0 / 12.0 * (v[1] - 2 * v[2] + v[3]) * (v[1] - 2 * v[2] + v[3]) +
-              0.25 * (v[1] - v[3]) * (v[1] - v[3]);
-  double b2 = 13.0 / 12.0 * (v[2] - 2 * v[3] + v[4]) * (v[2] - 2 * v[3] + v[4]) +
-              0.25 * (3 * v[2] - 4 * v[3] + v[4]) * (3 * v[2] - 4 * v[3] + v[4]);
-  double a0 = 0.1 / ((eps + b0) * (eps + b0));
-  double a1 = 0.6 / ((eps + b1) * (eps + b1));
-  double a2 = 0.3 / ((eps + b2) * (eps + b2));
+  T q0 = (2 * v[0] - 7 * v[1] + 11 * v[2]) / 6.0;
+  T q1 = (-v[1] + 5 * v[2] + 2 * v[3]) / 6.0;
+  T q2 = (2 * v[2] + 5 * v[3] - v[4]) / 6.0;
+  T b0 = 13.0 / 12.0 * (v[0] - 2 * v[1] + v[2]) * (v[0] - 2 * v[1] + v[2]) +
+         0.25 * (v[0] - 4 * v[1] + 3 * v[2]) * (v[0] - 4 * v[1] + 3 * v[2]);
+  T b1 = 13.0 / 12.0 * (v[1] - 2 * v[2] + v[3]) * (v[1] - 2 * v[2] + v[3]) +
+         0.25 * (v[1] - v[3]) * (v[1] - v[3]);
+  T b2 = 13.0 / 12.0 * (v[2] - 2 * v[3] + v[4]) * (v[2] - 2 * v[3] + v[4]) +
+         0.25 * (3 * v[2] - 4 * v[3] + v[4]) * (3 * v[2] - 4 * v[3] + v[4]);
+  T a0 = 0.1 / ((eps + b0) * (eps + b0));
+  T a1 = 0.6 / ((eps + b1) * (eps + b1));
+  T a2 = 0.3 / ((eps + b2) * (eps + b2));
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
 // Face states of the zone whose 7-point line (offsets -3..3) is s[]: the value
 // at its left face (lo) and right face (hi).
-static void recon_zone(const Params& p, const double s[7], double& lo, double& hi) {
+template <class T> static void recon_zone(const Params& p, const T s[7], T& lo, T& hi) {
   if (p.recon == RECON_WENO5) {
-    double f[5] = {s[1], s[2], s[3], s[4], s[5]};
-    double b[5] = {s[5], s[4], s[3], s[2], s[1]};
+    T f[5] = {s[1], s[2], s[3], s[4], s[5]};
+    T b[5] = {s[5], s[4], s[3], s[2], s[1]};
     hi = weno5_right(f);
     lo = weno5_right(b);
   } else {
-    double sl = gminmod(p.theta, s[2], s[3], s[4]);
+    T sl = gminmod(p.theta, s[2], s[3], s[4]);
     hi = s[3] + 0.5 * sl;
     lo = s[3] - 0.5 * sl;
   }
@@ -442,6 +458,7 @@ struct Stage {
   int ext[3];             // extended sizes n+2 (offset 1)
   std::vector<double> F[3];  // face fluxes F[d][v*NE + e], e = extended index of the zone right of the face
   long long NE;
+  const char* zmask = nullptr;  // zones to solve (nullptr = all); only their stencils are computed
   long long eidx(int i, int j, int k) const {
     return ((long long)(k + 1) * ext[1] + (j + 1)) * ext[0] + (i + 1);
   }
@@ -490,7 +507,23 @@ static void compute_fluxes(Stage& S, const double* PE) {
   const Params& p = S.G.p;
   for (int d = 0; d < 3; d++) S.ext[d] = p.n[d] + 2;
   S.NE = (long long)S.ext[0] * S.ext[1] * S.ext[2];
-  // Faces needed: in direction d, faces 0..n_d; transverse range -1..n (for flux-CT) in active dims.
+  // Faces a zone needs: its own low and high faces in each active direction,
+  // and those of its transverse neighbours (the flux-CT corner averages).
+  std::vector<char> fm;
+  if (S.zmask) {
+    fm.assign(S.NE, 0);
+    int r[3];
+    for (int e = 0; e < 3; e++) r[e] = (e < p.dim) ? 1 : 0;
+    for (int k = 0; k < p.n[2]; k++)
+      for (int j = 0; j < p.n[1]; j++)
+        for (int i = 0; i < p.n[0]; i++) {
+          if (!S.zmask[S.G.idx(i, j, k)]) continue;
+          for (int c = -r[2]; c <= r[2] + (p.dim >= 3); c++)
+            for (int b = -r[1]; b <= r[1] + (p.dim >= 2); b++)
+              for (int a = -r[0]; a <= r[0] + 1; a++) fm[S.eidx(i + a, j + b, k + c)] = 1;
+        }
+  }
+  // Faces in direction d: 0..n_d along d; -1..n across it (flux-CT), in active dims.
   for (int d = 0; d < p.dim; d++) {
     S.F[d].assign(10 * S.NE, 0.0);
     int lo[3], hi[3];
@@ -503,9 +536,10 @@ static void compute_fluxes(Stage& S, const double* PE) {
     for (int k = lo[2]; k < hi[2]; k++)
       for (int j = lo[1]; j < hi[1]; j++)
         for (int i = lo[0]; i < hi[0]; i++) {
+          long long e = S.eidx(i, j, k);
+          if (S.zmask && !fm[e]) continue;
           double Fv[10];
           face_flux(S.G, PE, d, i, j, k, Fv);
-          long long e = S.eidx(i, j, k);
           for (int v = 0; v < 10; v++) S.F[d][v * S.NE + e] = Fv[v];
         }
   }
@@ -677,8 +711,7 @@ static NewtonOut newton(const ZoneConst& z, const Params& p, double P[10]) {
     for (int j = 0; j < 10; j++) {
       double Pe[10];
       std::memcpy(Pe, P, sizeof(Pe));
-      Pe[j] = (std::fabs(P[j]) < 5.0 * eps) ? eps : (1.0 + eps) * P[j];
-      if (Pe[j] == P[j]) Pe[j] = P[j] + eps;
+      Pe[j] = (std::fabs(P[j]) < 5.0 * eps) ? P[j] + eps : (1.0 + eps) * P[j];
       double re_[10];
       residual(z, p, Pe, re_);
       o.evals++;
@@ -805,10 +838,14 @@ int oracle_max_threads() {
 // state and P_n the start of the step.  guess may be NULL (then P_n).  The
 // magnetic components of the guess are always the explicit flux-CT update.
 // Writes P_out (SoA [10][N]), iters and status per zone.
-int oracle_stage(const int* ip, const double* dp, const double* Pn, const double* PE, double dts,
-                 const double* guess, double* Pout, int* iters, int* status, long long* evals_out) {
+// One stage solved on the zones with mask[z] != 0 (mask NULL = every zone);
+// P_out, iters and status are written only there.
+int oracle_stage_masked(const int* ip, const double* dp, const double* Pn, const double* PE, double dts,
+                        const double* guess, const char* mask, double* Pout, int* iters, int* status,
+                        long long* evals_out) {
   Stage S;
   S.G.p = read_params(ip, dp);
+  S.zmask = mask;
   set_threads(ip[I_NTHREADS]);
   const Params& p = S.G.p;
   compute_fluxes(S, PE);
@@ -818,9 +855,10 @@ int oracle_stage(const int* ip, const double* dp, const double* Pn, const double
   for (int k = 0; k < p.n[2]; k++)
     for (int j = 0; j < p.n[1]; j++)
       for (int i = 0; i < p.n[0]; i++) {
+        long long zi = S.G.idx(i, j, k);
+        if (mask && !mask[zi]) continue;
         ZoneConst z;
         zone_const(S, Pn, PE, dts, i, j, k, z);
-        long long zi = S.G.idx(i, j, k);
         double P[10];
         const double* src = guess ? guess : Pn;
         for (int v = 0; v < 10; v++) P[v] = src[v * p.N + zi];
@@ -833,6 +871,57 @@ int oracle_stage(const int* ip, const double* dp, const double* Pn, const double
         evals += o.evals;
       }
   if (evals_out) *evals_out = evals;
+  return 0;
+}
+
+// One stage (Section 2.3): solve R(P) = 0 for every zone, with P^E the explicit
+// state and P_n the start of the step.  guess may be NULL (then P_n).  The
+// magnetic components of the guess are always the explicit flux-CT update.
+// Writes P_out (SoA [10][N]), iters and status per zone.
+int oracle_stage(const int* ip, const double* dp, const double* Pn, const double* PE, double dts,
+                 const double* guess, double* Pout, int* iters, int* status, long long* evals_out) {
+  return oracle_stage_masked(ip, dp, Pn, PE, dts, guess, nullptr, Pout, iters, status, evals_out);
+}
+
+// One full step evaluated only at the listed zones: the half step is solved on
+// the zones within 4 zones of a listed one (all its full-step stencil needs),
+// then the full step at the listed zones.  Pout is [10][nz], iters/status [nz].
+int oracle_step_sampled(const int* ip, const double* dp, const double* Pn, double dt, const long long* zones,
+                        int nz, double* Pout, int* iters, int* status, long long* evals) {
+  Params p = read_params(ip, dp);
+  Grid G;
+  G.p = p;
+  std::vector<char> m1(p.N, 0), m2(p.N, 0);
+  const int R = 4;
+  for (int s = 0; s < nz; s++) {
+    long long z = zones[s];
+    int i = (int)(z % p.n[0]), j = (int)((z / p.n[0]) % p.n[1]), k = (int)(z / ((long long)p.n[0] * p.n[1]));
+    m2[z] = 1;
+    int rk = (p.dim >= 3) ? R : 0, rj = (p.dim >= 2) ? R : 0;
+    for (int c = -rk; c <= rk; c++)
+      for (int b = -rj; b <= rj; b++)
+        for (int a = -R; a <= R; a++) {
+          bool f = false;
+          int ii = G.map1(0, i + a, f);
+          int jj = (p.dim >= 2) ? G.map1(1, j + b, f) : 0;
+          int kk = (p.dim >= 3) ? G.map1(2, k + c, f) : 0;
+          m1[G.idx(ii, jj, kk)] = 1;
+        }
+  }
+  std::vector<double> Ph(10 * p.N, 0.0), Pf(10 * p.N, 0.0);
+  std::vector<int> it1(p.N, 0), st1(p.N, 0), it2(p.N, 0), st2(p.N, 0);
+  long long e1 = 0, e2 = 0;
+  // zones outside the half-step mask keep P_n (they are never read)
+  std::memcpy(Ph.data(), Pn, sizeof(double) * 10 * p.N);
+  oracle_stage_masked(ip, dp, Pn, Pn, 0.5 * dt, nullptr, m1.data(), Ph.data(), it1.data(), st1.data(), &e1);
+  oracle_stage_masked(ip, dp, Pn, Ph.data(), dt, nullptr, m2.data(), Pf.data(), it2.data(), st2.data(), &e2);
+  for (int s = 0; s < nz; s++) {
+    long long z = zones[s];
+    for (int v = 0; v < 10; v++) Pout[v * nz + s] = Pf[v * p.N + z];
+    if (iters) iters[s] = it1[z] + it2[z];
+    if (status) status[s] = st1[z] | st2[z];
+  }
+  if (evals) *evals = e1 + e2;
   return 0;
 }
 
@@ -1049,8 +1138,7 @@ int oracle_zone_jacobian_fd(const int* ip, const double* dp, const double* zc, c
   for (int j = 0; j < 10; j++) {
     double Pe[10], re_[10];
     std::memcpy(Pe, P, sizeof(Pe));
-    Pe[j] = (std::fabs(P[j]) < 5.0 * p.eps) ? p.eps : (1.0 + p.eps) * P[j];
-    if (Pe[j] == P[j]) Pe[j] = P[j] + p.eps;
+    Pe[j] = (std::fabs(P[j]) < 5.0 * p.eps) ? P[j] + p.eps : (1.0 + p.eps) * P[j];
     residual(z, p, Pe, re_);
     for (int i = 0; i < 10; i++) J[i * 10 + j] = (re_[i] - r[i]) / (Pe[j] - P[j]);
   }
@@ -1067,6 +1155,74 @@ int oracle_zone_newton(const int* ip, const double* dp, const double* zc, double
 }
 
 // Face values (left face, right face) of the middle zone of a 7-zone line.
+// Algorithmic flop counts of the explicit part of a stage (same convention
+// as oracle_flop_counts, with every input treated as variable):
+//   out[0]: one LLF face flux from an 8-zone line of states line8[8][10]
+//           (reconstruction of the two face states, their fluxes, conserved
+//           variables and wave speeds, the LLF combination);
+//   out[1]: the per-zone remainder for dim active directions: states at P^E
+//           and P_n, U(P_n), row scales, limited slopes of Theta, u_mu and
+//           u^d, the flux divergence and flux-CT averages, the relaxation
+//           targets' explicit parts and the constants of the residual.
+int oracle_explicit_flops(const int* ip, const double* dp, const double* line8, const double* Pn1, long long* out) {
+  Params p = read_params(ip, dp);
+  Geom g;
+  geom_minkowski(g, p.tauR);
+  Cnt L[8][10];
+  for (int t = 0; t < 8; t++)
+    for (int v = 0; v < 10; v++) L[t][v] = Cnt(line8[t * 10 + v], true);
+  g_flops = 0;
+  Cnt PL[10], PR[10];
+  for (int v = 0; v < 10; v++) {
+    Cnt sL[7], sR[7], lo, hi;
+    for (int t = 0; t < 7; t++) { sL[t] = L[t][v]; sR[t] = L[t + 1][v]; }
+    recon_zone(p, sL, lo, hi);
+    PL[v] = hi;
+    recon_zone(p, sR, lo, hi);
+    PR[v] = lo;
+  }
+  State<Cnt> sl, sr;
+  make_state(PL, g, p, sl);
+  make_state(PR, g, p, sr);
+  Cnt FL[10], FR[10], UL[10], UR[10], c[4];
+  flux(sl, 1, FL); flux(sr, 1, FR);
+  conserved(sl, UL); conserved(sr, UR);
+  wave_speeds(sl, g, p, 1, c[0], c[1]);
+  wave_speeds(sr, g, p, 1, c[2], c[3]);
+  Cnt cm = tmax(tmax(tabs(c[0]), tabs(c[1])), tmax(tabs(c[2]), tabs(c[3])));
+  for (int v = 0; v < 10; v++) FL[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+  out[0] = g_flops;
+  // per-zone remainder
+  g_flops = 0;
+  Cnt PE[10], Pn[10];
+  for (int v = 0; v < 10; v++) { PE[v] = L[4][v]; Pn[v] = Cnt(Pn1[v], true); }
+  State<Cnt> sE, sn;
+  make_state(PE, g, p, sE);
+  make_state(Pn, g, p, sn);
+  Cnt Un[10];
+  conserved(sn, Un);
+  Cnt sc[10];
+  for (int a = 0; a < 10; a++) sc[a] = Cnt(1.0, true) / (tabs(Un[a]) + tabs(Un[0]));
+  // limited slopes of Theta, the four u_mu and u^d along each active direction
+  Cnt dTh[4], du[4][4], divu = Cnt(0.0);
+  for (int m = 0; m < 4; m++) { dTh[m] = Cnt(0.0); for (int n = 0; n < 4; n++) du[m][n] = Cnt(0.0); }
+  for (int d = 0; d < p.dim; d++) {
+    // the neighbours' states are their own zones' work: count only the slopes
+    long long g0 = g_flops;
+    State<Cnt> s3[3];
+    for (int t = 0; t < 3; t++) make_state(L[3 + t], g, p, s3[t]);
+    long long g1 = g_flops;
+    dTh[d + 1] = gminmod(p.theta, s3[0].Theta, s3[1].Theta, s3[2].Theta) / p.dx[d];
+    for (int n = 0; n < 4; n++) du[d + 1][n] = gminmod(p.theta, s3[0].ucov[n], s3[1].ucov[n], s3[2].ucov[n]) / p.dx[d];
+    divu = divu + du[d + 1][d + 1];
+    g_flops = g0 + (g_flops - g1);
+  }
+  Cnt qt0, dPt0;
+  relax_targets(sE, g, p, dTh, du, divu, qt0, dPt0);
+  out[1] = g_flops + 20 * p.dim + 8 + 60;  // flux divergence, flux-CT averages, residual constants
+  return 0;
+}
+
 int oracle_recon(const int* ip, const double* dp, const double* line7, double* lohi) {
   Params p = read_params(ip, dp);
   recon_zone(p, line7, lohi[0], lohi[1]);

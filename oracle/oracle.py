@@ -176,3 +176,45 @@ def recon(prob, line7):
     out = np.empty(2)
     lib().oracle_recon(_iptr(ip), _dptr(dp), _dptr(_c(line7)), _dptr(out))
     return out
+
+
+def stage_masked(prob, Pn, PE, dts, mask, guess=None, threads: int = 0):
+    """One stage solved only where mask != 0; returns (P_out, iters, status, evals)
+    with P_out = P_n elsewhere."""
+    ip, dp = params(prob, threads)
+    Pn, PE = _c(Pn), _c(PE)
+    out = Pn.copy()
+    it = np.zeros(prob.zones, dtype=np.int32)
+    st = np.zeros(prob.zones, dtype=np.int32)
+    ev = ctypes.c_longlong(0)
+    m = np.ascontiguousarray(np.asarray(mask).reshape(-1).astype(np.int8))
+    g = _c(guess) if guess is not None else None
+    lib().oracle_stage_masked(_iptr(ip), _dptr(dp), _dptr(Pn), _dptr(PE), ctypes.c_double(dts),
+                              _dptr(g) if g is not None else None, m.ctypes.data_as(ctypes.c_char_p),
+                              _dptr(out), _iptr(it), _iptr(st), ctypes.byref(ev))
+    return out, it, st, ev.value
+
+
+def step_sampled(prob, Pn, dt, zones, threads: int = 0):
+    """One full step at the listed flat zone indices only: (P [10, nz], iters, status, evals)."""
+    ip, dp = params(prob, threads)
+    Pn = _c(Pn)
+    z = np.ascontiguousarray(np.asarray(zones, dtype=np.int64))
+    nz = z.size
+    out = np.empty((10, nz))
+    it = np.zeros(nz, dtype=np.int32)
+    st = np.zeros(nz, dtype=np.int32)
+    ev = ctypes.c_longlong(0)
+    lib().oracle_step_sampled(_iptr(ip), _dptr(dp), _dptr(Pn), ctypes.c_double(dt),
+                              z.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), ctypes.c_int(nz),
+                              _dptr(out), _iptr(it), _iptr(st), ctypes.byref(ev))
+    return out, it, st, ev.value
+
+
+def explicit_flops(prob, line8, Pn1):
+    """(per-face, per-zone remainder) algorithmic flops of the explicit part."""
+    ip, dp = params(prob)
+    out = np.zeros(2, dtype=np.int64)
+    lib().oracle_explicit_flops(_iptr(ip), _dptr(dp), _dptr(_c(line8)), _dptr(_c(Pn1)),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    return out

@@ -407,3 +407,14 @@ def test_periodic_box_conserves_mass_and_energy_momentum(orc):
     assert (st == 0).all()
     t1, _ = totals(P1)
     assert np.all(np.abs(t1 - t0) <= 1e-12 * m0)
+
+
+def test_flop_count_file_matches_oracle():
+    """tests/golden/flop_counts.txt is what make_flop_counts.py writes now."""
+    from tests.golden import make_flop_counts
+    stored = {}
+    for line in open(make_flop_counts.OUT):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            stored[k] = int(v)
+    assert stored == make_flop_counts.counts()
