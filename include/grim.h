@@ -1,0 +1,173 @@
+/*
+ * grim.h -- C ABI of the B300 (sm_103a) implicit extended-GRMHD zone step.
+ *
+ * The library implements the hot path of the scheme of Chandra, Foucart &
+ * Gammie (2017), "grim: a flexible, conservative scheme for relativistic
+ * fluid theories": the two-stage semi-implicit time step of Section 2.3 for
+ * the 10-field extended MHD system of Section 4, in which each zone's new
+ * primitive variables are found by driving the discrete residual R(P) of
+ * Eq. half_step_residual (and its full-step analogue, Eq. full_step) to zero
+ * with Newton iterations on a finite-difference Jacobian (Section 3.1) and a
+ * quadratic backtracking line search (Section 3.2).  Fluxes are local
+ * Lax-Friedrichs (Section 2.4.2) on generalized-minmod or WENO5 states
+ * (Section 2.4.1) with flux-CT for the magnetic field (Section 4.2).
+ *
+ * Conventions shared by every entry point:
+ *  - A state is a caller-owned DEVICE buffer of float64, structure of arrays
+ *    [10][n3][n2][n1] (X1 fastest), fields in the order rho, u, u^1, u^2,
+ *    u^3, B^1, B^2, B^3, q~, dP~, where q~ and dP~ are the rescaled heat flux
+ *    and pressure anisotropy of Eqs. q and dP.  Units G = c = 1.
+ *  - Every call is asynchronous on the stream given to grim_init and returns
+ *    0 on success or a negative GRIM_E* code; grim_strerror names it.  No call
+ *    traps, aborts or waits on the device.  Zones whose Newton solve does not
+ *    converge keep their last iterate and are counted in grim_stats.
+ *  - The library owns its scratch (stage constants, status bytes, counters),
+ *    allocated once by grim_init and freed by grim_destroy.
+ *  - Minkowski space, 2-D grids (dim = 2, n3 = 1) in this version.
+ */
+#ifndef GRIM_H
+#define GRIM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRIM_OK 0
+#define GRIM_EINVAL (-1)   /* bad argument or unsupported configuration */
+#define GRIM_ECUDA (-2)    /* a CUDA runtime call failed (message: grim_last_error) */
+#define GRIM_ENOMEM (-3)   /* device allocation failed */
+#define GRIM_ESIZE (-4)    /* a size is outside the limit of the entry point */
+
+#define GRIM_BC_PERIODIC 0
+#define GRIM_BC_OUTFLOW 1
+#define GRIM_BC_REFLECT 2
+
+#define GRIM_METRIC_MINKOWSKI 0
+
+#define GRIM_RECON_MC 0    /* generalized minmod, parameter theta (2 = MC, 1 = minmod) */
+#define GRIM_RECON_WENO5 1 /* Jiang & Shu WENO5 */
+
+#define GRIM_FP64 0        /* Jacobian, LU, residual all in float64 */
+#define GRIM_MIXED 1       /* Jacobian and LU in float32; residual, update and test in float64 */
+
+/* Grid (Section 2.1): uniform in X^i, dX^i = (x_end - x_start)/n_i. */
+typedef struct {
+  int dim, n1, n2, n3;
+  double x_start[3], x_end[3];
+  int bc[3][2]; /* GRIM_BC_* for the low and high side of each direction */
+} grim_grid;
+
+typedef struct {
+  int kind; /* GRIM_METRIC_MINKOWSKI */
+  double spin, h;
+} grim_metric;
+
+/* Physics (Section 4): gamma-law gas, closure chi = phi c_s^2 tau_R,
+ * nu = psi c_s^2 tau_R, switches for conduction, viscosity and the
+ * higher-order terms of Eqs. q_evol_eqn_rescaled and dP_evol_eqn_rescaled. */
+typedef struct {
+  double gamma, tau_R, phi, psi;
+  int conduction, viscosity, higher_order;
+  int recon;    /* GRIM_RECON_* */
+  double theta; /* generalized minmod parameter, also used for source slopes */
+} grim_physics;
+
+/* Nonlinear solver (Section 3).  Converged when max_a |r_a| <= tol with
+ * r_a = dt_s R_a / (|U_a(P_n)| + |U_0(P_n)|).  eps_fd: the finite-difference
+ * parameter epsilon of Section 3.1 (float64 Jacobian), eps_fd32 the same for
+ * the float32 Jacobian of GRIM_MIXED.  k_max: Newton updates per stage;
+ * ls_max: backtracks per line search. */
+typedef struct {
+  int precision; /* GRIM_FP64 or GRIM_MIXED */
+  double tol, eps_fd, eps_fd32;
+  int k_max, ls_max;
+} grim_solver;
+
+/* Counters accumulated over calls since the last grim_reset_stats. */
+typedef struct {
+  unsigned long long zones;     /* zone solves (one per zone per stage) */
+  unsigned long long failed;    /* zone solves that ended with a non-zero status */
+  unsigned long long iters;     /* Newton updates */
+  unsigned long long evals64;   /* float64 residual evaluations */
+  unsigned long long evals32;   /* float32 residual evaluations */
+  unsigned long long lu64;      /* float64 10x10 LU solves */
+  unsigned long long lu32;      /* float32 10x10 LU solves */
+  unsigned long long hist[32];  /* zone solves by number of Newton updates (31 = 31 or more) */
+  double max_res;               /* largest final max_a |r_a| over zone solves */
+  unsigned long long launches;  /* kernels launched by the library */
+} grim_stats;
+
+typedef struct grim_ctx grim_ctx;
+
+/* Create a context: validates the configuration, allocates the library's
+ * scratch for n1*n2*n3 zones on the current device, binds the CUDA stream
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Errors: GRIM_EINVAL (dim != 2, n3 != 1, sizes < 1, unsupported metric or
+ * reconstruction), GRIM_ENOMEM, GRIM_ECUDA.  *out is NULL on failure. */
+int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physics* phys,
+              const grim_solver* solver, void* stream, grim_ctx** out);
+
+/* One time step (Section 2.3): the half step P_n -> P_{n+1/2} with P^E = P_n
+ * and dt/2, then the full step P_n -> P_{n+1} with P^E = P_{n+1/2} and dt.
+ * P_in, P_out: device states; P_out may equal P_in.  The initial guess of
+ * each stage is P_n with B set to the explicit flux-CT update. */
+int grim_step(grim_ctx* ctx, const double* P_in, double* P_out, double dt);
+
+/* grim_step with HOST buffers: copies P_in_host to the device, steps, and
+ * copies the result to P_out_host (pinned host memory gives asynchronous
+ * copies); synchronises the stream before returning. */
+int grim_step_host(grim_ctx* ctx, const double* P_in_host, double* P_out_host, double dt);
+
+/* One stage: solve R(P) = 0 with explicit state P_E, start-of-step state P_n
+ * and stage time step dts (dt/2 for the half step, dt for the full step).
+ * guess: optional device state to start Newton from (NULL = P_n); its B
+ * components are replaced by the explicit flux-CT update.  Writes P_out and,
+ * if non-NULL, the per-zone Newton update count and status bits
+ * (1 max-iterations, 2 line-search stall, 4 singular, 8 non-finite,
+ * 16 inadmissible rho or u) to device byte arrays of n1*n2*n3 entries. */
+int grim_stage(grim_ctx* ctx, const double* P_n, const double* P_E, double dts, const double* guess,
+               double* P_out, unsigned char* iters, unsigned char* status);
+
+/* Residual of a stage at P_k (Eq. half_step_residual): scaled r_a when
+ * scaled != 0, else the raw R_a.  R_out: device state-shaped buffer. */
+int grim_residual(grim_ctx* ctx, const double* P_n, const double* P_E, double dts, const double* P_k,
+                  int scaled, double* R_out);
+
+/* Kernel classes reported by grim_kernel_times. */
+#define GRIM_K_EXPLICIT 0  /* reconstruction, fluxes, flux-CT, stage constants */
+#define GRIM_K_NEWTON64 1  /* Newton, float64 Jacobian */
+#define GRIM_K_NEWTON32 2  /* Newton, float32 Jacobian */
+#define GRIM_K_RESIDUAL 3  /* single residual evaluation */
+#define GRIM_K_COUNT 8
+
+/* Enable (1) or disable (0) per-kernel timing: CUDA events are recorded on
+ * the context's stream around every kernel launch, and their durations are
+ * accumulated per kernel class until read by grim_kernel_times. */
+int grim_profile(grim_ctx* ctx, int enable);
+
+/* Read and reset the accumulated per-kernel durations (milliseconds) and
+ * launch counts, arrays of GRIM_K_COUNT entries indexed by GRIM_K_*.
+ * Synchronises the stream. */
+int grim_kernel_times(grim_ctx* ctx, double* ms, unsigned long long* launches);
+
+/* Copy the accumulated counters to *out (synchronises the stream). */
+int grim_get_stats(grim_ctx* ctx, grim_stats* out);
+int grim_reset_stats(grim_ctx* ctx);
+
+/* Message of the last failing call on this context (static storage). */
+const char* grim_last_error(grim_ctx* ctx);
+const char* grim_strerror(int code);
+
+/* Free the context and its scratch (NULL is ignored). */
+void grim_destroy(grim_ctx* ctx);
+
+/* Measure the float64 and float32 FMA throughput of the current device with
+ * dependent FMA chains (no memory traffic): writes TFLOP/s (2 flops per
+ * FMA) to *fp64_tflops and *fp32_tflops.  Allocates and frees a small
+ * device buffer; synchronises the device. */
+int grim_peak_flops(double* fp64_tflops, double* fp32_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIM_H */

@@ -1,0 +1,193 @@
+"""Thin ctypes binding of libgrim.so (include/grim.h), argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; PyTorch provides
+device memory and streams.  The library is loaded on first use and a missing
+library is an error: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrim.so")
+
+GRIM_FP64, GRIM_MIXED = 0, 1
+
+_lib = None
+
+# Names every build of libgrim.so exports (the declarations of include/grim.h).
+EXPORTS = (
+    "grim_init", "grim_step", "grim_step_host", "grim_stage", "grim_residual", "grim_get_stats",
+    "grim_reset_stats", "grim_last_error", "grim_strerror", "grim_destroy", "grim_peak_flops",
+    "grim_profile", "grim_kernel_times",
+)
+KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual")
+
+
+class GrimGrid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+                ("x_start", ctypes.c_double * 3), ("x_end", ctypes.c_double * 3),
+                ("bc", (ctypes.c_int * 2) * 3)]
+
+
+class GrimMetric(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("spin", ctypes.c_double), ("h", ctypes.c_double)]
+
+
+class GrimPhysics(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("tau_R", ctypes.c_double), ("phi", ctypes.c_double),
+                ("psi", ctypes.c_double), ("conduction", ctypes.c_int), ("viscosity", ctypes.c_int),
+                ("higher_order", ctypes.c_int), ("recon", ctypes.c_int), ("theta", ctypes.c_double)]
+
+
+class GrimSolver(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("eps_fd", ctypes.c_double),
+                ("eps_fd32", ctypes.c_double), ("k_max", ctypes.c_int), ("ls_max", ctypes.c_int)]
+
+
+class GrimStats(ctypes.Structure):
+    _fields_ = [("zones", ctypes.c_ulonglong), ("failed", ctypes.c_ulonglong), ("iters", ctypes.c_ulonglong),
+                ("evals64", ctypes.c_ulonglong), ("evals32", ctypes.c_ulonglong), ("lu64", ctypes.c_ulonglong),
+                ("lu32", ctypes.c_ulonglong), ("hist", ctypes.c_ulonglong * 32), ("max_res", ctypes.c_double),
+                ("launches", ctypes.c_ulonglong)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
+        d["hist"] = list(self.hist)
+        return d
+
+
+def load():
+    """Load libgrim.so; raises if it is missing (build it with build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libgrim.so not found at {LIB_PATH}: build it first "
+                           "(python -m paper_1702_01106_b300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    lib.grim_init.argtypes = [ctypes.POINTER(GrimGrid), ctypes.POINTER(GrimMetric), ctypes.POINTER(GrimPhysics),
+                              ctypes.POINTER(GrimSolver), vp, ctypes.POINTER(vp)]
+    lib.grim_step.argtypes = [vp, vp, vp, dp]
+    lib.grim_step_host.argtypes = [vp, vp, vp, dp]
+    lib.grim_stage.argtypes = [vp, vp, vp, dp, vp, vp, vp, vp]
+    lib.grim_residual.argtypes = [vp, vp, vp, dp, vp, i, vp]
+    lib.grim_get_stats.argtypes = [vp, ctypes.POINTER(GrimStats)]
+    lib.grim_reset_stats.argtypes = [vp]
+    lib.grim_last_error.argtypes = [vp]
+    lib.grim_last_error.restype = ctypes.c_char_p
+    lib.grim_strerror.argtypes = [i]
+    lib.grim_strerror.restype = ctypes.c_char_p
+    lib.grim_destroy.argtypes = [vp]
+    lib.grim_destroy.restype = None
+    lib.grim_peak_flops.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
+    lib.grim_profile.argtypes = [vp, i]
+    lib.grim_kernel_times.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_ulonglong)]
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(t):
+    import torch
+    if t is not None and t.dtype != torch.float64:
+        raise ValueError("expected float64")
+    return _ptr(t)
+
+
+class Grim:
+    """One context of the library (grim_init ... grim_destroy)."""
+
+    def __init__(self, prob, precision: int = GRIM_FP64, stream=None, eps_fd32: float = 2.0 ** -12):
+        import torch
+        self.lib = load()
+        self.prob = prob
+        g = GrimGrid(prob.dim, prob.n[0], prob.n[1], prob.n[2],
+                     (ctypes.c_double * 3)(*prob.x_start), (ctypes.c_double * 3)(*prob.x_end),
+                     ((ctypes.c_int * 2) * 3)(*[(ctypes.c_int * 2)(*b) for b in prob.bc]))
+        m = GrimMetric(prob.metric, prob.spin, prob.h_mks)
+        ph = GrimPhysics(prob.gamma, prob.tau_R, prob.phi, prob.psi, int(prob.conduction), int(prob.viscosity),
+                         int(prob.higher_order), prob.recon, prob.theta)
+        sv = GrimSolver(precision, prob.tol, prob.eps_fd, eps_fd32, prob.k_max, prob.ls_max)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.grim_init(ctypes.byref(g), ctypes.byref(m), ctypes.byref(ph), ctypes.byref(sv),
+                                ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"grim_init failed: {self.lib.grim_strerror(rc).decode()}")
+        self.h = h
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} failed ({self.lib.grim_strerror(rc).decode()}): "
+                               f"{self.lib.grim_last_error(self.h).decode()}")
+
+    def step(self, P_in, P_out, dt: float):
+        self._check(self.lib.grim_step(self.h, _f64(P_in), _f64(P_out), dt), "grim_step")
+
+    def step_host(self, P_in_host, P_out_host, dt: float):
+        """grim_step on host tensors (pinned for asynchronous copies)."""
+        self._check(self.lib.grim_step_host(self.h, ctypes.c_void_p(P_in_host.data_ptr()),
+                                            ctypes.c_void_p(P_out_host.data_ptr()), dt), "grim_step_host")
+
+    def stage(self, P_n, P_E, dts: float, P_out, guess=None, iters=None, status=None):
+        self._check(self.lib.grim_stage(self.h, _f64(P_n), _f64(P_E), dts, _f64(guess), _f64(P_out),
+                                        _ptr(iters), _ptr(status)), "grim_stage")
+
+    def residual(self, P_n, P_E, dts: float, P_k, R_out, scaled: bool = True):
+        self._check(self.lib.grim_residual(self.h, _f64(P_n), _f64(P_E), dts, _f64(P_k), int(scaled),
+                                           _f64(R_out)), "grim_residual")
+
+    def stats(self) -> dict:
+        s = GrimStats()
+        self._check(self.lib.grim_get_stats(self.h, ctypes.byref(s)), "grim_get_stats")
+        return s.as_dict()
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.grim_profile(self.h, int(enable)), "grim_profile")
+
+    def kernel_times(self) -> dict:
+        """{class: (total ms, launches)} since the last read (synchronises)."""
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_ulonglong * 8)()
+        self._check(self.lib.grim_kernel_times(self.h, ms, n), "grim_kernel_times")
+        return {KERNEL_CLASSES[k]: (ms[k], n[k]) for k in range(len(KERNEL_CLASSES)) if n[k]}
+
+    def reset_stats(self):
+        self._check(self.lib.grim_reset_stats(self.h), "grim_reset_stats")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def peak_flops():
+    """(fp64, fp32) FMA throughput of the current device in TFLOP/s."""
+    lib = load()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = lib.grim_peak_flops(ctypes.byref(a), ctypes.byref(b))
+    if rc != 0:
+        raise RuntimeError(f"grim_peak_flops failed: {lib.grim_strerror(rc).decode()}")
+    return a.value, b.value

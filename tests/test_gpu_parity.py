@@ -1,0 +1,154 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Grids span several 16x16 tiles with ragged tails; the full-size workload is
+checked on sampled zones in the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+from paper_1702_01106_b300 import inputs
+from tests.gpu_helpers import rel_field_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _g(prob, precision=0):
+    from paper_1702_01106_b300.grim import Grim
+    return Grim(prob, precision=precision)
+
+
+def _t(P, dev):
+    return torch.from_numpy(np.ascontiguousarray(P)).to(dev)
+
+
+def _ragged_turbulent(n1=40, n2=24, tol=1e-14, **kw):
+    prob = inputs.turbulent_box_problem(32, tol=tol, **kw).with_(n=(n1, n2, 1))
+    P = inputs.turbulent_box_state(inputs.turbulent_box_problem(32).with_(n=(n1, n2, 1)))
+    return prob, P
+
+
+def test_residual_parity(dev, orc):
+    prob, Pn = _ragged_turbulent()
+    rng = np.random.default_rng(1)
+    PE = Pn * (1 + 1e-3 * rng.standard_normal(Pn.shape))
+    Pk = Pn * (1 + 1e-3 * rng.standard_normal(Pn.shape))
+    dts = 0.25 / 32
+    g = _g(prob)
+    R = torch.empty_like(_t(Pn, dev))
+    for scaled in (True, False):
+        g.residual(_t(Pn, dev), _t(PE, dev), dts, _t(Pk, dev), R, scaled=scaled)
+        ref = orc.residual(prob, Pn, PE, dts, Pk, scaled=scaled)
+        got = R.cpu().numpy()
+        if scaled:
+            assert np.abs(got - ref).max() < 1e-13
+        else:
+            err = np.abs(got - ref).reshape(10, -1).max(axis=1)
+            mag = np.abs(ref).reshape(10, -1).max(axis=1) + 1.0 / dts
+            assert np.all(err < 1e-12 * mag), err / mag
+
+
+@pytest.mark.parametrize("recon", [inputs.RECON_MC, inputs.RECON_WENO5])
+def test_stage_parity(dev, orc, recon):
+    prob, Pn = _ragged_turbulent(recon=recon)
+    dts = 0.25 / 32
+    g = _g(prob)
+    out = torch.empty_like(_t(Pn, dev))
+    it = torch.zeros(prob.zones, dtype=torch.uint8, device=dev)
+    st = torch.zeros(prob.zones, dtype=torch.uint8, device=dev)
+    g.stage(_t(Pn, dev), _t(Pn, dev), dts, out, iters=it, status=st)
+    ref, rit, rst, _ = orc.stage(prob, Pn, Pn, dts)
+    assert int(st.max()) == 0 and rst.max() == 0
+    assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
+    assert np.abs(it.cpu().numpy().astype(int) - rit).max() <= 1
+
+
+def test_one_step_linear_mode(dev, orc):
+    prob = inputs.linear_mode_problem(48, tol=1e-14)
+    P = inputs.linear_mode_state(prob, amp=1e-4, phase=inputs.linear_mode_phase(1))
+    dt = 0.5 / 48
+    g = _g(prob)
+    out = torch.empty_like(_t(P, dev))
+    g.step(_t(P, dev), out, dt)
+    ref, _, st, _ = orc.step(prob, P, dt)
+    assert st.max() == 0
+    assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
+    s = g.stats()
+    assert s["failed"] == 0 and s["zones"] == 2 * prob.zones
+
+
+def test_many_steps_turbulent(dev, orc):
+    """100 steps on a ragged grid: within 1e-9 per primitive."""
+    prob, P = _ragged_turbulent(40, 24, tol=1e-14)
+    dt = 0.5 / 40
+    g = _g(prob)
+    a = _t(P, dev)
+    b = torch.empty_like(a)
+    ref = P.copy()
+    for _ in range(100):
+        g.step(a, b, dt)
+        a, b = b, a
+        ref, _, st, _ = orc.step(prob, ref, dt)
+        assert st.max() == 0
+    assert rel_field_err(a.cpu().numpy(), ref).max() < 1e-9
+    assert g.stats()["failed"] == 0
+
+
+def test_in_place_step(dev, orc):
+    prob, P = _ragged_turbulent(24, 40)
+    g = _g(prob)
+    a = _t(P, dev)
+    g.step(a, a, 0.5 / 40)
+    ref, _, _, _ = orc.step(prob, P, 0.5 / 40)
+    assert rel_field_err(a.cpu().numpy(), ref).max() < 1e-12
+
+
+def test_mixed_precision_matches_fp64(dev, orc):
+    """FP32 Jacobian/LU, FP64 residual and test: at tol 1e-10 every zone
+    reaches max|r| <= 1e-10 and the primitives stay within 1e-9 of the FP64 oracle."""
+    prob, P = _ragged_turbulent(40, 24, tol=1e-10)
+    dt = 0.5 / 40
+    g = _g(prob, precision=1)
+    out = torch.empty_like(_t(P, dev))
+    g.step(_t(P, dev), out, dt)
+    s = g.stats()
+    assert s["failed"] == 0 and s["max_res"] <= 1e-10 and s["evals32"] > 0
+    ref, _, _, _ = orc.step(prob.with_(tol=1e-14), P, dt)
+    assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 17), (17, 1), (16, 16), (33, 17)])
+def test_small_and_degenerate_grids(dev, orc, shape):
+    prob, P = _ragged_turbulent(*shape, tol=1e-14)
+    g = _g(prob)
+    out = torch.empty_like(_t(P, dev))
+    g.step(_t(P, dev), out, 0.01)
+    ref, _, _, _ = orc.step(prob, P, 0.01)
+    assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
+
+
+def test_full_size_sampled_parity(dev, orc):
+    """The 1024^2 turbulent box in the benchmark's configuration (tol 1e-10):
+    sampled zones against the oracle, and the residual bound everywhere."""
+    prob = inputs.turbulent_box_problem(1024)
+    P = inputs.turbulent_box_state(prob)
+    dt = 0.5 / 1024
+    for precision in (0, 1):
+        g = _g(prob, precision)
+        out = torch.empty_like(_t(P, dev))
+        g.step(_t(P, dev), out, dt)
+        s = g.stats()
+        assert s["failed"] == 0 and s["max_res"] <= prob.tol
+        rng = np.random.default_rng(7 + precision)
+        zs = np.concatenate([rng.choice(prob.zones, 48, replace=False), [0, 1023, prob.zones - 1]])
+        ref, _, st, _ = orc.step_sampled(prob.with_(tol=1e-14), P, dt, zs)
+        got = out.cpu().numpy().reshape(10, -1)[:, zs]
+        assert rel_field_err(got, ref).max() < 1e-9
+        g.close()
