@@ -161,6 +161,32 @@ const char* grim_strerror(int code);
 /* Free the context and its scratch (NULL is ignored). */
 void grim_destroy(grim_ctx* ctx);
 
+/* Largest grid (n1*n2*n3 zones) grim_step_static accepts. */
+#define GRIM_STATIC_MAX_ZONES 65536
+
+/* One time step, as grim_step, that allocates no device memory.  (The paper
+ * has no counterpart; this is an interface for callers.)  It is meant for
+ * callers that cannot call cudaMalloc: host applications that own all device
+ * memory through their own pool, and loops that must not allocate after
+ * start-up because cudaMalloc can synchronise the device.
+ *  - Arguments: the configuration structs of grim_init, a cudaStream_t
+ *    (NULL = legacy default stream) and the caller's device states P_in and
+ *    P_out (layout as above; P_out may equal P_in).
+ *  - Scratch: the stage constants, half-step state, status bytes and
+ *    counters live in one static device array sized for
+ *    GRIM_STATIC_MAX_ZONES zones (about 23 MB), which every GPU that loads
+ *    the library holds until the process exits.  Larger grids return
+ *    GRIM_ESIZE without launching anything.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (other
+ *    streams, other threads) race and must be serialised by the caller.
+ *  - Returns 0, GRIM_EINVAL (bad configuration or pointer), GRIM_ESIZE or
+ *    GRIM_ECUDA; asynchronous on the stream like grim_step. */
+int grim_step_static(const grim_grid* grid, const grim_metric* metric, const grim_physics* phys,
+                     const grim_solver* solver, void* stream, const double* P_in, double* P_out, double dt);
+
 /* Measure the float64 and float32 FMA throughput of the current device with
  * dependent FMA chains (no memory traffic): writes TFLOP/s (2 flops per
  * FMA) to *fp64_tflops and *fp32_tflops.  Allocates and frees a small

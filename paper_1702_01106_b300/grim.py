@@ -22,8 +22,9 @@ _lib = None
 EXPORTS = (
     "grim_init", "grim_step", "grim_step_host", "grim_stage", "grim_residual", "grim_get_stats",
     "grim_reset_stats", "grim_last_error", "grim_strerror", "grim_destroy", "grim_peak_flops",
-    "grim_profile", "grim_kernel_times",
+    "grim_profile", "grim_kernel_times", "grim_step_static",
 )
+STATIC_MAX_ZONES = 65536
 KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual")
 
 
@@ -85,6 +86,8 @@ def load():
     lib.grim_destroy.argtypes = [vp]
     lib.grim_destroy.restype = None
     lib.grim_peak_flops.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
+    lib.grim_step_static.argtypes = [ctypes.POINTER(GrimGrid), ctypes.POINTER(GrimMetric),
+                                     ctypes.POINTER(GrimPhysics), ctypes.POINTER(GrimSolver), vp, vp, vp, dp]
     lib.grim_profile.argtypes = [vp, i]
     lib.grim_kernel_times.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_ulonglong)]
     _lib = lib
@@ -108,6 +111,30 @@ def _f64(t):
     return _ptr(t)
 
 
+def _config(prob, precision, eps_fd32):
+    g = GrimGrid(prob.dim, prob.n[0], prob.n[1], prob.n[2],
+                 (ctypes.c_double * 3)(*prob.x_start), (ctypes.c_double * 3)(*prob.x_end),
+                 ((ctypes.c_int * 2) * 3)(*[(ctypes.c_int * 2)(*b) for b in prob.bc]))
+    m = GrimMetric(prob.metric, prob.spin, prob.h_mks)
+    ph = GrimPhysics(prob.gamma, prob.tau_R, prob.phi, prob.psi, int(prob.conduction), int(prob.viscosity),
+                     int(prob.higher_order), prob.recon, prob.theta)
+    sv = GrimSolver(precision, prob.tol, prob.eps_fd, eps_fd32, prob.k_max, prob.ls_max)
+    return g, m, ph, sv
+
+
+def step_static(prob, P_in, P_out, dt: float, precision: int = GRIM_FP64, stream=None,
+                eps_fd32: float = 2.0 ** -12) -> int:
+    """grim_step_static: one step with the library's static scratch (no device
+    allocation), for callers that cannot call cudaMalloc.  Returns the C code."""
+    import torch
+    lib = load()
+    g, m, ph, sv = _config(prob, precision, eps_fd32)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return lib.grim_step_static(ctypes.byref(g), ctypes.byref(m), ctypes.byref(ph), ctypes.byref(sv),
+                                ctypes.c_void_p(stream.cuda_stream), _f64(P_in), _f64(P_out), dt)
+
+
 class Grim:
     """One context of the library (grim_init ... grim_destroy)."""
 
@@ -115,13 +142,7 @@ class Grim:
         import torch
         self.lib = load()
         self.prob = prob
-        g = GrimGrid(prob.dim, prob.n[0], prob.n[1], prob.n[2],
-                     (ctypes.c_double * 3)(*prob.x_start), (ctypes.c_double * 3)(*prob.x_end),
-                     ((ctypes.c_int * 2) * 3)(*[(ctypes.c_int * 2)(*b) for b in prob.bc]))
-        m = GrimMetric(prob.metric, prob.spin, prob.h_mks)
-        ph = GrimPhysics(prob.gamma, prob.tau_R, prob.phi, prob.psi, int(prob.conduction), int(prob.viscosity),
-                         int(prob.higher_order), prob.recon, prob.theta)
-        sv = GrimSolver(precision, prob.tol, prob.eps_fd, eps_fd32, prob.k_max, prob.ls_max)
+        g, m, ph, sv = _config(prob, precision, eps_fd32)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
