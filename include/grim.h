@@ -193,6 +193,14 @@ int grim_step_static(const grim_grid* grid, const grim_metric* metric, const gri
  * device buffer; synchronises the device. */
 int grim_peak_flops(double* fp64_tflops, double* fp32_tflops);
 
+/* Self-check of the float64 reciprocal the kernels use for finite-difference
+ * divisors and LU pivots (a Newton-Raphson refinement of the hardware
+ * approximation): over n seeded values spanning magnitudes 2^-300..2^300 of
+ * both signs, writes the largest relative difference from IEEE division to
+ * *max_rel_err.  Allocates and frees a small device buffer; synchronises the
+ * device. */
+int grim_math_selftest(int n, double* max_rel_err);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@ cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P
                           Counters* cnt, cudaStream_t st);
 cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, int scaled, double dts, double* R,
                             cudaStream_t st);
+cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cudaStream_t st);
 }  // namespace grim
 
 using grim::Params;
@@ -272,6 +273,17 @@ int grim_reset_stats(grim_ctx* ctx) {
   if (!ctx) return GRIM_EINVAL;
   GRIM_CUDA(cudaMemsetAsync(ctx->cnt, 0, sizeof(grim::Counters), ctx->stream), "stats reset");
   return GRIM_OK;
+}
+
+int grim_math_selftest(int n, double* max_rel_err) {
+  if (n < 1 || !max_rel_err) return GRIM_EINVAL;
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double)) != cudaSuccess) return GRIM_ENOMEM;
+  cudaError_t e = cudaMemset(d, 0, sizeof(double));
+  if (e == cudaSuccess) e = grim::launch_rcp_check(n, 12345ull, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(max_rel_err, d, sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? GRIM_OK : GRIM_ECUDA;
 }
 
 }  // extern "C"

@@ -2,44 +2,188 @@
 // (Section 3.1), 10x10 partial-pivot LU, quadratic backtracking line search
 // (Section 3.2), convergence test max_a |r_a| <= tol before each Jacobian.
 //
-// One thread owns one zone.  The Jacobian and right-hand side live in shared
-// memory (stride = block size, so a warp's accesses are conflict-free); the
-// state, the residual and the zone constants live in registers.
+// One thread owns one zone.  The zone constants, the Jacobian and the
+// right-hand side live in shared memory (stride = block size, so a warp's
+// accesses are conflict-free); the state, the residual and the cached
+// intermediates of the residual live in registers.
+//
+// The FP64 pipe bounds these kernels (B300: 1/58 of the FP32 rate), so the
+// residual is organised to spend as few float64 instructions as possible
+// without changing what it computes:
+//  * its intermediates are grouped by the primitives they depend on
+//    (thermodynamic: rho, u; kinematic: u^i; magnetic: B^i, u^i), so a
+//    finite-difference column recomputes only the groups its perturbed
+//    component touches, and only the residual rows that component can change
+//    (the others are exact zeros of the FD Jacobian);
+//  * five root operations per full evaluation (1/rho = rsqrt(rho)^2, ...);
+//  * divisors of the FD columns and the LU pivots use a Newton-Raphson
+//    reciprocal, comparisons of magnitudes use the integer order of the
+//    IEEE bit patterns, and eliminations with an exactly zero multiplier are
+//    skipped (a - 0*x = a).
 //
 // Precision variants:
 //   FP64  -- everything in double.
-//   MIXED -- the Jacobian (its 11 residual evaluations) and the LU in float;
+//   MIXED -- the Jacobian (its residual evaluations) and the LU in float;
 //            the residual of the iterate, the update, the line search and the
 //            convergence test in double (inexact Newton).
 #include "grim_dev.cuh"
 
 namespace grim {
 
-// Scaled residual r(P) of one zone from its constants kk (see grim_dev.cuh).
-template <typename T>
-__device__ __forceinline__ void zone_residual(const T* P, const T* kk, const Params& p, T* r) {
-  Pt<T> s;
-  point_state(P, p, s);
-  T row[4];
-  stress_row(s, 0, row);
-  T U[NV];
-  U[0] = s.rho * s.ut;
-  U[1] = row[0]; U[2] = row[1]; U[3] = row[2]; U[4] = row[3];
-  U[5] = P[5]; U[6] = P[6]; U[7] = P[7];
-  U[8] = s.qt * s.ut;
-  U[9] = s.dpt * s.ut;
+// ---------------------------------------------------------------- math helpers
+// Reciprocal by the Newton-Raphson iteration r <- r + r (1 - x r), started
+// from the hardware approximation and applied twice (quadratic convergence
+// takes its ~2^-20 relative error below 2^-53).  Checked against IEEE division
+// by grim_math_selftest.
+__device__ __forceinline__ double nr_rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float nr_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sqr_root(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqr_root(float x) { return sqrtf(x); }
+// |x| as an unsigned integer: ordered like |x| for every non-NaN value.
+__device__ __forceinline__ unsigned long long abits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned int abits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// ---------------------------------------------------------------- residual
+// Constants of the residual in the working precision.
+template <typename T> struct RC {
+  T gam, gm1, sphig, spsig;  // gamma, gamma - 1, sqrt(phi gamma), sqrt(psi gamma)
+  int cond, visc;
+};
+template <typename T> __device__ __forceinline__ RC<T> make_rc(const Params& p) {
+  RC<T> c;
+  c.gam = T(p.gamma);
+  c.gm1 = T(p.gamma - 1.0);
+  c.sphig = T(sqrt(p.phi * p.gamma));
+  c.spsig = T(sqrt(p.psi * p.gamma));
+  c.cond = p.cond;
+  c.visc = p.visc;
+  return c;
+}
+
+// Intermediates of the residual at one state, grouped by dependence.
+template <typename T> struct Z {
+  T rho, u, pg, theta, qs, ds, w0;   // thermodynamic group (rho, u)
+  T v[3], ut;                        // kinematic group (u^i): u^t = sqrt(1 + u.u)
+  T iut;
+  T B[3], bt, bc[3], bsq, bht, bh[3];  // magnetic group (B^i, u^i)
+  T qt, dpt;
+};
+
+// P_g = (gamma-1)u, Theta = P_g/rho, and the factors that turn q~, dP~ into
+// q = q~ Theta (phi c_s^2 rho)^(1/2) and dP = dP~ (psi c_s^2 P_g)^(1/2)
+// (Eqs. q, dP with chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R, and
+// c_s^2 = gamma P_g/(rho + gamma u)); w0 = rho + u + P_g.
+template <typename T> __device__ __forceinline__ void z_thermo(Z<T>& z, const RC<T>& c) {
+  const T pg = c.gm1 * z.u;
+  const T ra = rsq(z.rho);               // rho^(-1/2)
+  const T rb = rsq(z.rho + c.gam * z.u); // (rho + gamma u)^(-1/2)
+  z.pg = pg;
+  z.theta = pg * ra * ra;
+  z.qs = c.cond ? c.sphig * z.theta * sqr_root(pg) * (z.rho * ra) * rb : T(0);
+  z.ds = c.visc ? c.spsig * pg * rb : T(0);
+  z.w0 = z.rho + z.u + pg;
+}
+template <typename T> __device__ __forceinline__ void z_kin(Z<T>& z) {
+  const T s = T(1) + z.v[0] * z.v[0] + z.v[1] * z.v[1] + z.v[2] * z.v[2];
+  z.iut = rsq(s);
+  z.ut = s * z.iut;
+}
+// b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t, b^2, bhat = b/|b| (Section 4).
+template <typename T> __device__ __forceinline__ void z_mag(Z<T>& z) {
+  z.bt = z.B[0] * z.v[0] + z.B[1] * z.v[1] + z.B[2] * z.v[2];
 #pragma unroll
-  for (int a = 0; a < NV; a++) r[a] = kk[K_U + a] * U[a] + kk[K_C + a];
-  const T ul[4] = {-s.ut, s.uc[0], s.uc[1], s.uc[2]};
-  T e8 = kk[K_Q + 0] * s.qt + kk[K_Q + 1] * s.theta + kk[K_Q + 6] * s.ut;
-  T e9 = kk[K_D + 0] * s.dpt + kk[K_D + 5] * s.ut;
+  for (int i = 0; i < 3; i++) z.bc[i] = (z.B[i] + z.bt * z.v[i]) * z.iut;
+  z.bsq = z.bc[0] * z.bc[0] + z.bc[1] * z.bc[1] + z.bc[2] * z.bc[2] - z.bt * z.bt;
+  if (z.bsq > T(0)) {
+    const T ib = rsq(z.bsq);
+    z.bht = z.bt * ib;
 #pragma unroll
-  for (int m = 0; m < 4; m++) {
-    e8 += kk[K_Q + 2 + m] * ul[m];
-    e9 += kk[K_D + 1 + m] * ul[m];
+    for (int i = 0; i < 3; i++) z.bh[i] = z.bc[i] * ib;
+  } else {
+    z.bht = T(0);
+    z.bh[0] = z.bh[1] = z.bh[2] = T(0);
   }
-  r[8] += e8;
-  r[9] += e9;
+}
+template <typename T> __device__ __forceinline__ void z_load(Z<T>& z, const T* P, const RC<T>& c) {
+  z.rho = P[0]; z.u = P[1];
+  z.v[0] = P[2]; z.v[1] = P[3]; z.v[2] = P[4];
+  z.B[0] = P[5]; z.B[1] = P[6]; z.B[2] = P[7];
+  z.qt = P[8]; z.dpt = P[9];
+  z_thermo(z, c);
+  z_kin(z);
+  z_mag(z);
+}
+
+// Zone-constant accessors: shared memory at stride BS, or global at stride N.
+template <typename T, int BS> struct KSm {
+  const T* p;
+  __device__ __forceinline__ T operator()(int a) const { return p[a * BS]; }
+};
+struct KGl {
+  const double* p;
+  long long N;
+  __device__ __forceinline__ double operator()(int a) const { return __ldg(p + a * N); }
+};
+
+// Rows of the scaled residual (see grim_dev.cuh for the constants).
+// T^t_nu of Eq. fullSEtens: A u_nu - b^t b_nu + q (bhat^t u_nu + u^t bhat_nu)
+// - dP bhat^t bhat_nu + (p_t + dP/3) delta^t_nu with A = (w + dP/3) u^t,
+// w = rho + u + P_g + b^2, p_t = P_g + b^2/2; lowering flips the t component.
+template <typename T, class KA>
+__device__ __forceinline__ void r_T(const Z<T>& z, const KA& k, T out[4]) {
+  const T q = z.qt * z.qs, dp = z.dpt * z.ds;
+  const T third = dp * T(1.0 / 3.0);
+  const T A = (z.w0 + z.bsq + third) * z.ut;
+  const T qb = q * z.bht, dpb = dp * z.bht, qut = q * z.ut;
+  // nu = t: u_t = -u^t, b_t = -b^t, bhat_t = -bhat^t
+  const T Ttt = -A * z.ut + z.bt * z.bt - T(2) * qb * z.ut + dpb * z.bht + z.pg + T(0.5) * z.bsq + third;
+  out[0] = k(K_U + 1) * Ttt + k(K_C + 1);
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    const T Tti = A * z.v[i] - z.bt * z.bc[i] + qb * z.v[i] + qut * z.bh[i] - dpb * z.bh[i];
+    out[1 + i] = k(K_U + 2 + i) * Tti + k(K_C + 2 + i);
+  }
+}
+template <typename T, class KA> __device__ __forceinline__ T r_mass(const Z<T>& z, const KA& k) {
+  return k(K_U + 0) * (z.rho * z.ut) + k(K_C + 0);
+}
+template <typename T, class KA> __device__ __forceinline__ T r_field(const Z<T>& z, const KA& k, int i) {
+  return k(K_U + 5 + i) * z.B[i] + k(K_C + 5 + i);
+}
+template <typename T, class KA> __device__ __forceinline__ T r_heat(const Z<T>& z, const KA& k) {
+  T r = k(K_U + 8) * (z.qt * z.ut) + k(K_C + 8);
+  r += k(K_Q + 0) * z.qt + k(K_Q + 1) * z.theta + k(K_Q + 6) * z.ut;
+  r += -k(K_Q + 2) * z.ut + k(K_Q + 3) * z.v[0] + k(K_Q + 4) * z.v[1] + k(K_Q + 5) * z.v[2];
+  return r;
+}
+template <typename T, class KA> __device__ __forceinline__ T r_aniso(const Z<T>& z, const KA& k) {
+  T r = k(K_U + 9) * (z.dpt * z.ut) + k(K_C + 9);
+  r += k(K_D + 0) * z.dpt + k(K_D + 5) * z.ut;
+  r += -k(K_D + 1) * z.ut + k(K_D + 2) * z.v[0] + k(K_D + 3) * z.v[1] + k(K_D + 4) * z.v[2];
+  return r;
+}
+template <typename T, class KA> __device__ __forceinline__ void r_all(const Z<T>& z, const KA& k, T r[NV]) {
+  r[0] = r_mass(z, k);
+  r_T(z, k, r + 1);
+  r[5] = r_field(z, k, 0);
+  r[6] = r_field(z, k, 1);
+  r[7] = r_field(z, k, 2);
+  r[8] = r_heat(z, k);
+  r[9] = r_aniso(z, k);
 }
 
 // Perturbed component of the FD Jacobian (Section 3.1): (1 + eps) x, or
@@ -49,37 +193,94 @@ template <typename T> __device__ __forceinline__ T fd_step(T x, T eps) {
   return (fabs(x) < T(5) * eps) ? x + eps : (T(1) + eps) * x;
 }
 
+// Column C of the FD Jacobian, J_iC = (r_i(P_eps) - r_i(P)) / (P_eps,C - P_C),
+// written to shared memory (element (i, C) at Jc[(i*10 + C)*BS]).  Rows whose
+// residual cannot depend on component C are exact zeros.
+template <int C, typename T, int BS, class KA>
+__device__ __forceinline__ void fd_column(const Z<T>& z0, const T r[NV], const KA& k, const RC<T>& c, T eps,
+                                          T* Jc) {
+  Z<T> z = z0;
+  T pj;
+  if constexpr (C == 0) pj = z.rho;
+  else if constexpr (C == 1) pj = z.u;
+  else if constexpr (C <= 4) pj = z.v[C - 2];
+  else if constexpr (C <= 7) pj = z.B[C - 5];
+  else if constexpr (C == 8) pj = z.qt;
+  else pj = z.dpt;
+  const T pe = fd_step(pj, eps);
+  const T ih = nr_rcp(pe - pj);
+  if constexpr (C == 0) { z.rho = pe; z_thermo(z, c); }
+  else if constexpr (C == 1) { z.u = pe; z_thermo(z, c); }
+  else if constexpr (C <= 4) { z.v[C - 2] = pe; z_kin(z); z_mag(z); }
+  else if constexpr (C <= 7) { z.B[C - 5] = pe; z_mag(z); }
+  else if constexpr (C == 8) z.qt = pe;
+  else z.dpt = pe;
+  constexpr bool kin = (C >= 2 && C <= 4);
+  T re[NV];
+#pragma unroll
+  for (int i = 0; i < NV; i++) re[i] = r[i];
+  if constexpr (C == 0 || kin) re[0] = r_mass(z, k);
+  r_T(z, k, re + 1);
+  if constexpr (C >= 5 && C <= 7) re[C] = r_field(z, k, C - 5);
+  if constexpr (C <= 4 || C == 8) re[8] = r_heat(z, k);
+  if constexpr (kin || C == 9) re[9] = r_aniso(z, k);
+#pragma unroll
+  for (int i = 0; i < NV; i++) {
+    const bool dep = (i >= 1 && i <= 4) || (i == 0 && (C == 0 || kin)) || (i == C && C >= 5 && C <= 7) ||
+                     (i == 8 && (C <= 4 || C == 8)) || (i == 9 && (kin || C == 9));
+    Jc[(i * NV + C) * BS] = dep ? (re[i] - r[i]) * ih : T(0);
+  }
+}
+
+template <typename T, int BS, class KA>
+__device__ __forceinline__ void fd_jacobian(const Z<T>& z, const T r[NV], const KA& k, const RC<T>& c, T eps,
+                                            T* J) {
+  fd_column<0, T, BS>(z, r, k, c, eps, J);
+  fd_column<1, T, BS>(z, r, k, c, eps, J);
+  fd_column<2, T, BS>(z, r, k, c, eps, J);
+  fd_column<3, T, BS>(z, r, k, c, eps, J);
+  fd_column<4, T, BS>(z, r, k, c, eps, J);
+  fd_column<5, T, BS>(z, r, k, c, eps, J);
+  fd_column<6, T, BS>(z, r, k, c, eps, J);
+  fd_column<7, T, BS>(z, r, k, c, eps, J);
+  fd_column<8, T, BS>(z, r, k, c, eps, J);
+  fd_column<9, T, BS>(z, r, k, c, eps, J);
+}
+
 // Partial-pivot LU solve J x = b with J, b in shared memory at stride BS
 // (element (i,j) at J[(i*10+j)*BS], b[i] at b[i*BS]); x returned in registers.
 // Pivot: largest |a_ik|, lowest row on ties.  Returns false on a zero pivot.
 template <typename T, int BS>
 __device__ __forceinline__ bool lu_solve_smem(T* J, T* b, T x[NV]) {
+  T inv[NV];
 #pragma unroll
   for (int k = 0; k < NV; k++) {
     int piv = k;
-    T best = fabs(J[(k * NV + k) * BS]);
+    auto best = abits(J[(k * NV + k) * BS]);
 #pragma unroll
     for (int i = k + 1; i < NV; i++) {
-      T a = fabs(J[(i * NV + k) * BS]);
+      const auto a = abits(J[(i * NV + k) * BS]);
       if (a > best) { best = a; piv = i; }
     }
-    if (!(best > T(0))) return false;
+    if (best == 0) return false;
     if (piv != k) {
 #pragma unroll
       for (int c = k; c < NV; c++) {
-        T t = J[(k * NV + c) * BS];
+        const T t = J[(k * NV + c) * BS];
         J[(k * NV + c) * BS] = J[(piv * NV + c) * BS];
         J[(piv * NV + c) * BS] = t;
       }
-      T t = b[k * BS];
+      const T t = b[k * BS];
       b[k * BS] = b[piv * BS];
       b[piv * BS] = t;
     }
-    const T inv = T(1) / J[(k * NV + k) * BS];
+    inv[k] = nr_rcp(J[(k * NV + k) * BS]);
     const T bk = b[k * BS];
 #pragma unroll
     for (int i = k + 1; i < NV; i++) {
-      const T l = J[(i * NV + k) * BS] * inv;
+      const T a = J[(i * NV + k) * BS];
+      if (abits(a) == 0) continue;  // zero multiplier: row i is unchanged
+      const T l = a * inv[k];
 #pragma unroll
       for (int c = k + 1; c < NV; c++) J[(i * NV + c) * BS] -= l * J[(k * NV + c) * BS];
       b[i * BS] -= l * bk;
@@ -90,21 +291,21 @@ __device__ __forceinline__ bool lu_solve_smem(T* J, T* b, T x[NV]) {
     T acc = b[i * BS];
 #pragma unroll
     for (int c = i + 1; c < NV; c++) acc -= J[(i * NV + c) * BS] * x[c];
-    x[i] = acc / J[(i * NV + i) * BS];
+    x[i] = acc * inv[i];
   }
   return true;
 }
 
-__device__ __forceinline__ double max_abs10(const double* r) {
-  double m = 0.0;
+__device__ __forceinline__ unsigned long long max_abits10(const double* r) {
+  unsigned long long m = 0;
 #pragma unroll
-  for (int a = 0; a < NV; a++) m = fmax(m, fabs(r[a]));
+  for (int a = 0; a < NV; a++) m = max(m, abits(r[a]));
   return m;
 }
 __device__ __forceinline__ double sum_sq10(const double* r) {
   double f = 0.0;
 #pragma unroll
-  for (int a = 0; a < NV; a++) f += r[a] * r[a];
+  for (int a = 0; a < NV; a++) f = fma(r[a], r[a], f);
   return f;
 }
 
@@ -113,76 +314,49 @@ struct ZoneResult {
   double res;
 };
 
-// Newton on one zone, starting from P (updated in place).
+// Newton on one zone, starting from P (updated in place).  kd: the zone's
+// float64 constants in shared memory (stride BS); kf: their float copies.
 template <bool MIXED, int BS>
-__device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double* kk, double P[NV], void* smem_v) {
+__device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double* kd, const float* kf, double P[NV],
+                                                  void* jac) {
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0.0};
+  const RC<double> c64 = make_rc<double>(p);
+  const KSm<double, BS> k64{kd};
+  const unsigned long long tol_bits = abits(p.tol);
+  Z<double> z;
+  z_load(z, P, c64);
   double r[NV];
-  zone_residual<double>(P, kk, p, r);
+  r_all(z, k64, r);
   o.evals64++;
   double f = sum_sq10(r);
-  float kf[NK];
-  if (MIXED) {
-#pragma unroll
-    for (int a = 0; a < NK; a++) kf[a] = (float)kk[a];
-  }
   int k = 0;
   for (;;) {
-    if (!isfinite(f)) { o.status |= ST_NONFINITE; break; }
-    if (max_abs10(r) <= p.tol) break;
+    if (!finite_bits(f)) { o.status |= ST_NONFINITE; break; }
+    if (max_abits10(r) <= tol_bits) break;
     if (k >= p.kmax) { o.status |= ST_MAXIT; break; }
     double dP[NV];
     bool ok;
     if (!MIXED) {
-      double* J = (double*)smem_v + threadIdx.x;
+      double* J = (double*)jac + threadIdx.x;
       double* b = J + NV * NV * BS;
-#pragma unroll 1
-      for (int j = 0; j < NV; j++) {
-        double Pe[NV];
-#pragma unroll
-        for (int a = 0; a < NV; a++) Pe[a] = P[a];
-        // select component j without dynamic register indexing
-        double pj = 0.0;
-#pragma unroll
-        for (int a = 0; a < NV; a++) if (a == j) pj = P[a];
-        const double pe = fd_step(pj, p.eps64);
-#pragma unroll
-        for (int a = 0; a < NV; a++) if (a == j) Pe[a] = pe;
-        double re[NV];
-        zone_residual<double>(Pe, kk, p, re);
-        const double ih = 1.0 / (pe - pj);
-#pragma unroll
-        for (int i = 0; i < NV; i++) J[(i * NV + j) * BS] = (re[i] - r[i]) * ih;
-      }
+      fd_jacobian<double, BS>(z, r, k64, c64, p.eps64, J);
       o.evals64 += NV;
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
       ok = lu_solve_smem<double, BS>(J, b, dP);
       o.lu64++;
     } else {
-      float* J = (float*)smem_v + threadIdx.x;
+      const RC<float> c32 = make_rc<float>(p);
+      const KSm<float, BS> k32{kf};
+      float* J = (float*)jac + threadIdx.x;
       float* b = J + NV * NV * BS;
       float Pf[NV], rf[NV];
 #pragma unroll
       for (int a = 0; a < NV; a++) Pf[a] = (float)P[a];
-      zone_residual<float>(Pf, kf, p, rf);
-#pragma unroll 1
-      for (int j = 0; j < NV; j++) {
-        float Pe[NV];
-#pragma unroll
-        for (int a = 0; a < NV; a++) Pe[a] = Pf[a];
-        float pj = 0.0f;
-#pragma unroll
-        for (int a = 0; a < NV; a++) if (a == j) pj = Pf[a];
-        const float pe = fd_step(pj, p.eps32);
-#pragma unroll
-        for (int a = 0; a < NV; a++) if (a == j) Pe[a] = pe;
-        float re[NV];
-        zone_residual<float>(Pe, kf, p, re);
-        const float ih = 1.0f / (pe - pj);
-#pragma unroll
-        for (int i = 0; i < NV; i++) J[(i * NV + j) * BS] = (re[i] - rf[i]) * ih;
-      }
+      Z<float> zf;
+      z_load(zf, Pf, c32);
+      r_all(zf, k32, rf);
+      fd_jacobian<float, BS>(zf, rf, k32, c32, p.eps32, J);
       o.evals32 += NV + 1;
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = (float)(-r[i]);
@@ -195,13 +369,15 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
     if (!ok) { o.status |= ST_SINGULAR; break; }
     // quadratic backtracking line search on f = |r|^2
     double lam = 1.0, Pt[NV], rt[NV], ft = 0.0;
+    Z<double> zt;
     for (int t = 0;; t++) {
 #pragma unroll
-      for (int a = 0; a < NV; a++) Pt[a] = P[a] + lam * dP[a];
-      zone_residual<double>(Pt, kk, p, rt);
+      for (int a = 0; a < NV; a++) Pt[a] = fma(lam, dP[a], P[a]);
+      z_load(zt, Pt, c64);
+      r_all(zt, k64, rt);
       o.evals64++;
       ft = sum_sq10(rt);
-      const bool fin = isfinite(ft);
+      const bool fin = finite_bits(ft);
       const double lim = 1.0 - 1e-4 * lam;
       if (fin && ft < f * lim * lim) break;
       if (t >= p.lsmax) { o.status |= ST_LSSTALL; break; }
@@ -209,11 +385,13 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
     }
 #pragma unroll
     for (int a = 0; a < NV; a++) { P[a] = Pt[a]; r[a] = rt[a]; }
+    z = zt;
     f = ft;
     k++;
   }
   o.iters = k;
-  o.res = max_abs10(r);
+  unsigned long long mb = max_abits10(r);
+  o.res = __longlong_as_double((long long)mb);
   if (!(P[0] > 0.0) || !(P[1] > 0.0)) o.status |= ST_INADMISSIBLE;
   return o;
 }
@@ -238,26 +416,44 @@ __device__ __forceinline__ void accumulate(Counters* c, const ZoneResult& o, boo
   }
   if (active) {
     atomicAdd(&c->hist[o.iters < 31 ? o.iters : 31], 1ull);
-    if (isfinite(o.res)) atomicMax(&c->maxres_bits, (unsigned long long)__double_as_longlong(o.res));
+    if (finite_bits(o.res)) atomicMax(&c->maxres_bits, (unsigned long long)__double_as_longlong(o.res));
   }
 }
+
+// Shared memory per thread: zone constants (NK doubles, plus NK floats for
+// MIXED), the Jacobian and the right-hand side (110 elements of the Jacobian
+// precision).
+template <bool MIXED, int BS> struct NewtonSmem {
+  static constexpr size_t kd = sizeof(double) * NK * BS;
+  static constexpr size_t kf = MIXED ? sizeof(float) * NK * BS : 0;
+  static constexpr size_t jac = (MIXED ? sizeof(float) : sizeof(double)) * (NV * NV + NV) * BS;
+  static constexpr size_t bytes = kd + kf + jac;
+};
 
 template <bool MIXED, int BS>
 __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Params p, const double* __restrict__ K,
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt) {
-  extern __shared__ double smem[];
+  using S = NewtonSmem<MIXED, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* kd = (double*)smem_raw + threadIdx.x;
+  float* kf = (float*)(smem_raw + S::kd) + threadIdx.x;
+  void* jac = smem_raw + S::kd + S::kf;
   const long long N = p.N;
   const long long z = (long long)blockIdx.x * BS + threadIdx.x;
   const bool active = z < N;
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0.0};
   if (active) {
-    double kk[NK], Pz[NV];
 #pragma unroll
-    for (int a = 0; a < NK; a++) kk[a] = __ldg(K + a * N + z);
+    for (int a = 0; a < NK; a++) {
+      const double x = __ldg(K + a * N + z);
+      kd[a * BS] = x;
+      if (MIXED) kf[a * BS] = (float)x;
+    }
+    double Pz[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-    o = newton_zone<MIXED, BS>(p, kk, Pz, smem);
+    o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -272,39 +468,55 @@ __global__ void residual_once(const __grid_constant__ Params p, const double* __
   const long long N = p.N;
   const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= N) return;
-  double kk[NK], Pz[NV], r[NV];
-#pragma unroll
-  for (int a = 0; a < NK; a++) kk[a] = __ldg(K + a * N + z);
+  const KGl kg{K + z, N};
+  const RC<double> c = make_rc<double>(p);
+  double Pz[NV], r[NV];
 #pragma unroll
   for (int a = 0; a < NV; a++) Pz[a] = Pk[a * N + z];
-  zone_residual<double>(Pz, kk, p, r);
+  Z<double> zz;
+  z_load(zz, Pz, c);
+  r_all(zz, kg, r);
 #pragma unroll
   for (int a = 0; a < NV; a++) {
     // the row scale is kU * dt_s; divide it out for the raw residual
-    R[a * N + z] = scaled ? r[a] : r[a] / (kk[K_U + a] * dts);
+    R[a * N + z] = scaled ? r[a] : r[a] / (kg(K_U + a) * dts);
   }
+}
+
+// Reciprocal self-check: max |nr_rcp(x) - 1/x| / |1/x| over x = m * 2^e for
+// seeded mantissas m in [1, 2) and exponents e in [-300, 300], both signs.
+__global__ void rcp_check(int n, unsigned long long seed, double* worst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  unsigned long long s = seed + 0x9e3779b97f4a7c15ull * (unsigned long long)(t + 1);
+  s ^= s >> 33; s *= 0xff51afd7ed558ccdull; s ^= s >> 33;
+  const double m = 1.0 + (double)(s >> 11) * (1.0 / 9007199254740992.0);
+  const int e = (int)((s >> 3) % 601) - 300;
+  const double x = ((s & 1) ? -1.0 : 1.0) * ldexp(m, e);
+  const double a = nr_rcp(x), b = 1.0 / x;
+  const double rel = fabs(a - b) / fabs(b);
+  atomicMax((unsigned long long*)worst, (unsigned long long)__double_as_longlong(rel));
 }
 
 template <bool MIXED, int BS>
 static cudaError_t launch_newton_t(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                                    Counters* cnt, cudaStream_t st) {
-  const size_t elem = MIXED ? sizeof(float) : sizeof(double);
-  const size_t bytes = elem * (NV * NV + NV) * BS;
+  using S = NewtonSmem<MIXED, BS>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+                                         (int)S::bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const long long nb = (p.N + BS - 1) / BS;
-  newton_dense<MIXED, BS><<<(unsigned)nb, BS, bytes, st>>>(p, K, P, iters, status, cnt);
+  newton_dense<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                           Counters* cnt, cudaStream_t st) {
-  if (mixed) return launch_newton_t<true, 128>(p, K, P, iters, status, cnt, st);
+  if (mixed) return launch_newton_t<true, 64>(p, K, P, iters, status, cnt, st);
   return launch_newton_t<false, 64>(p, K, P, iters, status, cnt, st);
 }
 
@@ -313,6 +525,11 @@ cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, 
   const int bs = 128;
   const long long nb = (p.N + bs - 1) / bs;
   residual_once<<<(unsigned)nb, bs, 0, st>>>(p, K, Pk, scaled, dts, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cudaStream_t st) {
+  rcp_check<<<(n + 255) / 256, 256, 0, st>>>(n, seed, worst);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ _lib = None
 EXPORTS = (
     "grim_init", "grim_step", "grim_step_host", "grim_stage", "grim_residual", "grim_get_stats",
     "grim_reset_stats", "grim_last_error", "grim_strerror", "grim_destroy", "grim_peak_flops",
-    "grim_profile", "grim_kernel_times", "grim_step_static",
+    "grim_profile", "grim_kernel_times", "grim_step_static", "grim_math_selftest",
 )
 STATIC_MAX_ZONES = 65536
 KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual")
@@ -89,6 +89,7 @@ def load():
     lib.grim_step_static.argtypes = [ctypes.POINTER(GrimGrid), ctypes.POINTER(GrimMetric),
                                      ctypes.POINTER(GrimPhysics), ctypes.POINTER(GrimSolver), vp, vp, vp, dp]
     lib.grim_profile.argtypes = [vp, i]
+    lib.grim_math_selftest.argtypes = [i, ctypes.POINTER(dp)]
     lib.grim_kernel_times.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_ulonglong)]
     _lib = lib
     return lib
@@ -212,3 +213,13 @@ def peak_flops():
     if rc != 0:
         raise RuntimeError(f"grim_peak_flops failed: {lib.grim_strerror(rc).decode()}")
     return a.value, b.value
+
+
+def math_selftest(n: int = 1 << 20) -> float:
+    """Largest relative difference of the kernels' float64 reciprocal from IEEE division."""
+    lib = load()
+    out = ctypes.c_double()
+    rc = lib.grim_math_selftest(n, ctypes.byref(out))
+    if rc != 0:
+        raise RuntimeError(f"grim_math_selftest failed: {lib.grim_strerror(rc).decode()}")
+    return out.value

@@ -152,3 +152,10 @@ def test_full_size_sampled_parity(dev, orc):
         got = out.cpu().numpy().reshape(10, -1)[:, zs]
         assert rel_field_err(got, ref).max() < 1e-9
         g.close()
+
+
+def test_reciprocal_matches_ieee_division(dev):
+    """The Newton-Raphson reciprocal used for FD divisors and LU pivots stays
+    within one rounding of IEEE division over 2^-300..2^300."""
+    from paper_1702_01106_b300.grim import math_selftest
+    assert math_selftest(1 << 20) <= 2.0 ** -52
