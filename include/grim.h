@@ -134,10 +134,12 @@ int grim_residual(grim_ctx* ctx, const double* P_n, const double* P_E, double dt
                   int scaled, double* R_out);
 
 /* Kernel classes reported by grim_kernel_times. */
-#define GRIM_K_EXPLICIT 0  /* reconstruction, fluxes, flux-CT, stage constants */
+#define GRIM_K_EXPLICIT 0  /* fused tile kernel: reconstruction, fluxes, flux-CT, constants */
 #define GRIM_K_NEWTON64 1  /* Newton, float64 Jacobian */
 #define GRIM_K_NEWTON32 2  /* Newton, float32 Jacobian */
 #define GRIM_K_RESIDUAL 3  /* single residual evaluation */
+#define GRIM_K_FACES 4     /* face fluxes: reconstruction, LLF (one thread per face) */
+#define GRIM_K_ZONECONST 5 /* flux-CT, divergence, slopes, stage constants */
 #define GRIM_K_COUNT 8
 
 /* Enable (1) or disable (0) per-kernel timing: CUDA events are recorded on

@@ -15,6 +15,10 @@ cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P
 cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, int scaled, double dts, double* R,
                             cudaStream_t st);
 cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cudaStream_t st);
+long long face_scratch_doubles(int n1, int n2);
+cudaError_t launch_faces(const Params& p, const double* PE, double* faces, cudaStream_t st);
+cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
+                              double* K, double* P0, double* faces, cudaStream_t st);
 }  // namespace grim
 
 using grim::Params;
@@ -24,6 +28,7 @@ struct grim_ctx {
   int precision;
   cudaStream_t stream;
   double* K = nullptr;        // NK x N stage constants
+  double* faces = nullptr;    // face fluxes of one stage
   double* Ph = nullptr;       // half-step state
   uint8_t* iters = nullptr;   // per-zone Newton updates of the last stage
   uint8_t* status = nullptr;  // per-zone status bits of the last stage
@@ -100,6 +105,7 @@ const char* grim_last_error(grim_ctx* ctx) { return ctx ? ctx->err : "no context
 void grim_destroy(grim_ctx* ctx) {
   if (!ctx) return;
   cudaFree(ctx->K);
+  cudaFree(ctx->faces);
   cudaFree(ctx->Ph);
   cudaFree(ctx->iters);
   cudaFree(ctx->status);
@@ -148,6 +154,7 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   cudaError_t e;
   if ((e = cudaMalloc(&ctx->K, sizeof(double) * grim::NK * N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->Ph, sizeof(double) * grim::NV * N)) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->faces, sizeof(double) * grim::face_scratch_doubles(p.n1, p.n2))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->iters, N)) != cudaSuccess || (e = cudaMalloc(&ctx->status, N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->cnt, sizeof(grim::Counters))) != cudaSuccess) {
     grim_destroy(ctx);
@@ -161,12 +168,25 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   return GRIM_OK;
 }
 
+// The explicit part of a stage: face fluxes, then flux-CT and the constants.
+static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
+                        double* Pout) {
+  {
+    KernelMark m(ctx, GRIM_K_FACES);
+    GRIM_CUDA(grim::launch_faces(ctx->p, PE, ctx->faces, ctx->stream), "face kernel");
+  }
+  {
+    KernelMark m(ctx, GRIM_K_ZONECONST);
+    GRIM_CUDA(grim::launch_zone_const(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->faces, ctx->stream),
+              "zone-constant kernel");
+  }
+  return GRIM_OK;
+}
+
 static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
                      double* Pout, uint8_t* iters, uint8_t* status) {
-  {
-    KernelMark m(ctx, GRIM_K_EXPLICIT);
-    GRIM_CUDA(grim::launch_explicit(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->stream), "explicit kernel");
-  }
+  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout);
+  if (rc) return rc;
   {
     KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64);
     GRIM_CUDA(grim::launch_newton(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
@@ -212,11 +232,8 @@ int grim_residual(grim_ctx* ctx, const double* P_n, const double* P_E, double dt
                   double* R_out) {
   if (!ctx || !P_n || !P_E || !P_k || !R_out || !(dts > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_residual: bad argument");
   // the explicit kernel also writes an initial guess; send it to the half-step scratch
-  {
-    KernelMark m(ctx, GRIM_K_EXPLICIT);
-    GRIM_CUDA(grim::launch_explicit(ctx->p, P_n, P_E, nullptr, dts, ctx->K, ctx->Ph, ctx->stream),
-              "explicit kernel");
-  }
+  int rc = run_explicit(ctx, P_n, P_E, dts, nullptr, ctx->Ph);
+  if (rc) return rc;
   {
     KernelMark m(ctx, GRIM_K_RESIDUAL);
     GRIM_CUDA(grim::launch_residual(ctx->p, ctx->K, P_k, scaled, dts, R_out, ctx->stream), "residual kernel");

@@ -1,0 +1,411 @@
+// Explicit part of one stage (Section 2.3), 2-D, as two kernels that compute
+// every face exactly once:
+//
+//  face_flux_2d   one thread per face: reconstruction of P^E (generalized
+//                 minmod / WENO5, Section 2.4.1) on both sides, conserved
+//                 variables, fluxes and the wave-speed bound of Section 4.1 on
+//                 each side, the LLF combination (Section 2.4.2).  Faces of
+//                 direction X1 cover i = 0..n1, j = -1..n2 and faces of X2 cover
+//                 i = -1..n1, j = 0..n2: the transverse ring feeds flux-CT.
+//  zone_const_2d  one thread per zone: flux-CT corner values and the B fluxes
+//                 (Section 4.2), the flux divergence, the slope-limited
+//                 derivatives of Theta and u_mu at P^E, the relaxation targets'
+//                 explicit parts (Eqs. q0def, dP0def with Eqs. q, dP), and the
+//                 NK residual constants; also the Newton initial guess.
+//
+// Boundary rules are applied at load time (no ghost arrays).  The face fluxes
+// go through HBM (20 doubles per zone): the kernels are bound by the float64
+// pipe, not by memory, so computing each face once matters more than keeping
+// faces on chip.
+#include "grim_zone.cuh"
+
+namespace grim {
+
+__device__ __forceinline__ int map_idx(int i, int n, int lo, int hi, bool& flip) {
+  if (i >= 0 && i < n) return i;
+  const int bc = (i < 0) ? lo : hi;
+  if (bc == BC_PERIODIC) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  if (bc == BC_OUTFLOW) return i < 0 ? 0 : n - 1;
+  int m = i % (2 * n);
+  if (m < 0) m += 2 * n;
+  if (m >= n) {
+    flip = !flip;
+    return 2 * n - 1 - m;
+  }
+  return m;
+}
+
+// Zone (i, j) of a state with the boundary rules: its flat index and whether
+// the X1 / X2 components (u^1, B^1 / u^2, B^2) flip sign.
+__device__ __forceinline__ long long zone_at(const Params& p, int i, int j, bool& f1, bool& f2) {
+  f1 = f2 = false;
+  const int gi = map_idx(i, p.n1, p.bc[0][0], p.bc[0][1], f1);
+  const int gj = map_idx(j, p.n2, p.bc[1][0], p.bc[1][1], f2);
+  return (long long)gj * p.n1 + gi;
+}
+__device__ __forceinline__ double load_comp(const double* P, long long N, long long z, int v, bool f1, bool f2) {
+  double x = __ldg(P + v * N + z);
+  if ((f1 && (v == 2 || v == 5)) || (f2 && (v == 3 || v == 6))) x = -x;
+  return x;
+}
+
+// Generalized minmod slope (Section 2.4.1) of vm, v0, vp: sign-agreement and
+// magnitude tests run on the integer bit patterns.
+__device__ __forceinline__ double gm_slope(double theta, double vm, double v0, double vp) {
+  const double a = v0 - vm, c = vp - v0;
+  const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long bc = (unsigned long long)__double_as_longlong(c);
+  const unsigned long long ma = ba & 0x7fffffffffffffffull, mc = bc & 0x7fffffffffffffffull;
+  if (ma == 0 || mc == 0 || ((ba ^ bc) >> 63)) return 0.0;  // differences of opposite sign or zero
+  const double m1 = theta * __longlong_as_double((long long)(ma < mc ? ma : mc));
+  const double m2 = 0.5 * fabs(a + c);
+  const double m = abits(m1) < abits(m2) ? m1 : m2;
+  return (ba >> 63) ? -m : m;
+}
+
+// WENO5 of Jiang & Shu (1996): value at the right face of v2 from v0..v4.
+__device__ __forceinline__ double weno5v(double v0, double v1, double v2, double v3, double v4) {
+  const double eps = 1e-6;
+  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
+  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
+  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
+  const double d0 = v0 - 2.0 * v1 + v2, e0 = v0 - 4.0 * v1 + 3.0 * v2;
+  const double d1 = v1 - 2.0 * v2 + v3, e1 = v1 - v3;
+  const double d2 = v2 - 2.0 * v3 + v4, e2 = 3.0 * v2 - 4.0 * v3 + v4;
+  const double b0 = (13.0 / 12.0) * d0 * d0 + 0.25 * e0 * e0;
+  const double b1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;
+  const double b2 = (13.0 / 12.0) * d2 * d2 + 0.25 * e2 * e2;
+  const double a0 = 0.1 / ((eps + b0) * (eps + b0));
+  const double a1 = 0.6 / ((eps + b1) * (eps + b1));
+  const double a2 = 0.3 / ((eps + b2) * (eps + b2));
+  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+}
+
+// Conserved variables U and flux F^j (j = 1, 2, 3) of a face state (Eqs.
+// divN_explicit, divT_explicit, induction_eqn and the q~, dP~ equations), and
+// the largest |grid-frame speed| in direction j of waves moving at +-v_max in
+// the fluid frame (Section 4.1, Minkowski space): the roots c of
+// (u^j - c u^t)^2 (1 - v^2) = v^2 (1 - c^2).  kappa = cs~^2/c_s^2, a constant
+// of the closure chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R (Eq. modcs).
+template <int j>
+__device__ __forceinline__ double side_flux(const Z<double>& z, double gam, double kappa, double U[NV],
+                                            double F[NV]) {
+  const double q = z.qt * z.qs, dp = z.dpt * z.ds;
+  const double third = dp * (1.0 / 3.0);
+  const double wt = z.w0 + z.bsq + third;
+  const double A = wt * z.ut;
+  const double qb = q * z.bht, dpb = dp * z.bht, qut = q * z.ut;
+  const double pt = z.pg + 0.5 * z.bsq + third;
+  U[0] = z.rho * z.ut;
+  U[1] = -A * z.ut + z.bt * z.bt - 2.0 * qb * z.ut + dpb * z.bht + pt;
+#pragma unroll
+  for (int i = 0; i < 3; i++) U[2 + i] = A * z.v[i] - z.bt * z.bc[i] + qb * z.v[i] + qut * z.bh[i] - dpb * z.bh[i];
+  U[5] = z.B[0]; U[6] = z.B[1]; U[7] = z.B[2];
+  U[8] = z.qt * z.ut;
+  U[9] = z.dpt * z.ut;
+  // row j of T^mu_nu: (w + dP/3) u^j u_nu - b^j b_nu + q (bhat^j u_nu + u^j bhat_nu)
+  // - dP bhat^j bhat_nu + (p_t + dP/3) delta^j_nu
+  const double uj = z.v[j - 1], bj = z.bc[j - 1], bhj = z.bh[j - 1];
+  const double Aj = wt * uj, qbj = q * bhj, quj = q * uj, dpbj = dp * bhj;
+  F[0] = z.rho * uj;
+  F[1] = -Aj * z.ut + bj * z.bt - qbj * z.ut - quj * z.bht + dpbj * z.bht;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    double t = Aj * z.v[i] - bj * z.bc[i] + qbj * z.v[i] + quj * z.bh[i] - dpbj * z.bh[i];
+    if (i == j - 1) t += pt;
+    F[2 + i] = t;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; i++) F[5 + i] = z.bc[i] * uj - bj * z.v[i];
+  F[8] = z.qt * uj;
+  F[9] = z.dpt * uj;
+  // speeds
+  const double den = z.rho + gam * z.u;
+  const double vA2 = z.bsq * nr_rcp(den + z.bsq);
+  const double cs2t = kappa * gam * z.pg * z.iden;
+  const double v2 = cs2t + vA2 - cs2t * vA2;
+  const double om = 1.0 - v2;
+  const double Aq = om * z.ut * z.ut + v2;
+  const double Bq = -2.0 * om * z.ut * uj;
+  const double Cq = om * uj * uj - v2;
+  const double disc = fmax(Bq * Bq - 4.0 * Aq * Cq, 0.0);
+  return (fabs(Bq) + sqrt(disc)) * (0.5 * nr_rcp(Aq));
+}
+
+struct ExpArgs {
+  const double* Pn;
+  const double* PE;
+  const double* guess;
+  double dts;
+  double kappa;
+  double* K;
+  double* P0;
+  double* F1;  // [10][(n2+2)][(n1+1)]
+  double* F2;  // [10][(n2+1)][(n1+2)]
+};
+
+template <int D, bool WENO>
+__device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a, int i, int j, double* out,
+                                              long long plane) {
+  constexpr int di = (D == 0), dj = (D == 1);
+  const long long N = p.N;
+  // zones along the face normal at offsets -3..2 from the zone right of the face
+  constexpr int o0 = WENO ? -3 : -2, o1 = WENO ? 2 : 1;
+  long long zz[6];
+  bool fa[6], fb[6];
+#pragma unroll
+  for (int t = o0; t <= o1; t++) zz[t + 3] = zone_at(p, i + t * di, j + t * dj, fa[t + 3], fb[t + 3]);
+  double L[NV], R[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    double s[6];
+#pragma unroll
+    for (int t = o0; t <= o1; t++) s[t + 3] = load_comp(a.PE, N, zz[t + 3], v, fa[t + 3], fb[t + 3]);
+    if (WENO) {
+      L[v] = weno5v(s[0], s[1], s[2], s[3], s[4]);
+      R[v] = weno5v(s[5], s[4], s[3], s[2], s[1]);
+    } else {
+      L[v] = fma(0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
+      R[v] = fma(-0.5, gm_slope(p.theta, s[2], s[3], s[4]), s[3]);
+    }
+  }
+  const RC<double> c = make_rc<double>(p);
+  Z<double> zl, zr;
+  z_load(zl, L, c);
+  z_load(zr, R, c);
+  double UL[NV], FL[NV], UR[NV], FR[NV];
+  const double cl = side_flux<D + 1>(zl, p.gamma, a.kappa, UL, FL);
+  const double cr = side_flux<D + 1>(zr, p.gamma, a.kappa, UR, FR);
+  const double cm = fmax(cl, cr);
+#pragma unroll
+  for (int v = 0; v < NV; v++) out[v * plane] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+}
+
+__global__ void __launch_bounds__(128) face_flux_2d(const __grid_constant__ Params p,
+                                                   const __grid_constant__ ExpArgs a) {
+  const long long nf1 = (long long)(p.n1 + 1) * (p.n2 + 2);
+  const long long nf2 = (long long)(p.n1 + 2) * (p.n2 + 1);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf1 + nf2) return;
+  const bool weno = p.recon == RECON_WENO5;
+  if (f < nf1) {
+    const int i = (int)(f % (p.n1 + 1)), j = (int)(f / (p.n1 + 1)) - 1;
+    double* out = a.F1 + (long long)(j + 1) * (p.n1 + 1) + i;
+    if (weno) face_flux_dir<0, true>(p, a, i, j, out, nf1);
+    else face_flux_dir<0, false>(p, a, i, j, out, nf1);
+  } else {
+    const long long g = f - nf1;
+    const int i = (int)(g % (p.n1 + 2)) - 1, j = (int)(g / (p.n1 + 2));
+    double* out = a.F2 + (long long)j * (p.n1 + 2) + (i + 1);
+    if (weno) face_flux_dir<1, true>(p, a, i, j, out, nf2);
+    else face_flux_dir<1, false>(p, a, i, j, out, nf2);
+  }
+}
+
+// Theta and u_mu of the state at zone (i, j) of P^E (for the limited slopes).
+__device__ __forceinline__ void derived_at(const Params& p, const double* PE, int i, int j, double& th, double u[4]) {
+  bool f1, f2;
+  const long long z = zone_at(p, i, j, f1, f2);
+  const long long N = p.N;
+  const double rho = __ldg(PE + z), uu = __ldg(PE + N + z);
+  const double v1 = load_comp(PE, N, z, 2, f1, f2), v2 = load_comp(PE, N, z, 3, f1, f2);
+  const double v3 = __ldg(PE + 4 * N + z);
+  th = (p.gamma - 1.0) * uu * nr_rcp(rho);
+  u[0] = -sqrt(1.0 + v1 * v1 + v2 * v2 + v3 * v3);
+  u[1] = v1; u[2] = v2; u[3] = v3;
+}
+
+__global__ void __launch_bounds__(128) zone_const_2d(const __grid_constant__ Params p,
+                                                    const __grid_constant__ ExpArgs a) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const int i = (int)(z % p.n1), j = (int)(z / p.n1);
+  const long long w1 = p.n1 + 1, w2 = p.n1 + 2;
+  const long long nf1 = w1 * (p.n2 + 2), nf2 = w2 * (p.n2 + 1);
+  const double idx1 = p.idx[0], idx2 = p.idx[1];
+  // flux divergence; flux-CT replaces F^1[B^1], F^2[B^2] by 0 and the
+  // transverse B fluxes by averages of the corner values
+  // E(i', j') = (F^1[B^2](i',j') + F^1[B^2](i',j'-1) - F^2[B^1](i',j') - F^2[B^1](i'-1,j'))/4.
+  double divF[NV];
+  const long long f1lo = (long long)(j + 1) * w1 + i, f2lo = (long long)j * w2 + (i + 1);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const double* F1 = a.F1 + v * nf1;
+    const double* F2 = a.F2 + v * nf2;
+    divF[v] = (__ldg(F1 + f1lo + 1) - __ldg(F1 + f1lo)) * idx1 + (__ldg(F2 + f2lo + w2) - __ldg(F2 + f2lo)) * idx2;
+  }
+  {
+    const double* F1b2 = a.F1 + 6 * nf1;
+    const double* F2b1 = a.F2 + 5 * nf2;
+    double E[2][2];
+#pragma unroll
+    for (int dj = 0; dj < 2; dj++)
+#pragma unroll
+      for (int di = 0; di < 2; di++) {
+        const int ii = i + di, jj = j + dj;
+        E[dj][di] = 0.25 * (__ldg(F1b2 + (long long)(jj + 1) * w1 + ii) + __ldg(F1b2 + (long long)jj * w1 + ii) -
+                            __ldg(F2b1 + (long long)jj * w2 + ii + 1) - __ldg(F2b1 + (long long)jj * w2 + ii));
+      }
+    divF[6] = (0.5 * (E[0][1] + E[1][1]) - 0.5 * (E[0][0] + E[1][0])) * idx1;
+    divF[5] = (-0.5 * (E[1][0] + E[1][1]) + 0.5 * (E[0][0] + E[0][1])) * idx2;
+  }
+  // states at P^E and P_n
+  double PEz[NV], Pnz[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    PEz[v] = __ldg(a.PE + v * N + z);
+    Pnz[v] = __ldg(a.Pn + v * N + z);
+  }
+  const RC<double> c = make_rc<double>(p);
+  Z<double> ze, zn;
+  z_load(ze, PEz, c);
+  z_load(zn, Pnz, c);
+  // U(P_n)
+  double Un[NV];
+  {
+    const double dp = zn.dpt * zn.ds, q = zn.qt * zn.qs;
+    const double third = dp * (1.0 / 3.0);
+    const double A = (zn.w0 + zn.bsq + third) * zn.ut;
+    const double qb = q * zn.bht, dpb = dp * zn.bht, qut = q * zn.ut;
+    Un[0] = zn.rho * zn.ut;
+    Un[1] = -A * zn.ut + zn.bt * zn.bt - 2.0 * qb * zn.ut + dpb * zn.bht + zn.pg + 0.5 * zn.bsq + third;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      Un[2 + k] = A * zn.v[k] - zn.bt * zn.bc[k] + qb * zn.v[k] + qut * zn.bh[k] - dpb * zn.bh[k];
+    Un[5] = Pnz[5]; Un[6] = Pnz[6]; Un[7] = Pnz[7];
+    Un[8] = zn.qt * zn.ut;
+    Un[9] = zn.dpt * zn.ut;
+  }
+  // limited slopes at P^E of Theta and u_mu; the spatial part of nabla_mu u^mu
+  double dTh[2], du[2][4], divu_sp = 0.0;
+  {
+    double th0 = ze.theta, u0[4] = {-ze.ut, ze.v[0], ze.v[1], ze.v[2]};
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      double thm, thp, um[4], up[4];
+      derived_at(p, a.PE, i - (d == 0), j - (d == 1), thm, um);
+      derived_at(p, a.PE, i + (d == 0), j + (d == 1), thp, up);
+      const double ih = (d == 0) ? idx1 : idx2;
+      dTh[d] = gm_slope(p.theta, thm, th0, thp) * ih;
+#pragma unroll
+      for (int m = 0; m < 4; m++) du[d][m] = gm_slope(p.theta, um[m], u0[m], up[m]) * ih;
+      divu_sp += du[d][1 + d];
+    }
+  }
+  const double tau = p.tauR, dts = a.dts, idts = 1.0 / dts;
+  double* Kz = a.K + z;
+  double kU[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    // row scale s_v = dt_s/(|U_v(P_n)| + |U_0(P_n)|); kU = s_v/dt_s
+    kU[v] = nr_rcp(fabs(Un[v]) + fabs(Un[0]));
+    Kz[(K_U + v) * N] = kU[v];
+    Kz[(K_C + v) * N] = kU[v] * (dts * divF[v] - Un[v]);
+  }
+  const double bhu[4] = {ze.bht, ze.bh[0], ze.bh[1], ze.bh[2]};
+  const double ucovn[4] = {-zn.ut, zn.v[0], zn.v[1], zn.v[2]};
+  const double hoq = p.ho ? 0.5 * ze.qt : 0.0;
+  const double hod = p.ho ? 0.5 * ze.dpt : 0.0;
+  const double cs2E = p.gamma * ze.pg * ze.iden;
+  // heat flux row: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
+  double Aq = 0.0, Bq = 0.0, Cq[4] = {0.0, 0.0, 0.0, 0.0};
+  if (p.cond) {
+    const double chi = p.phi * cs2E * tau;
+    const double pre = -sqrt(tau * ze.rho * chi) * nr_rcp(ze.theta);  // -rho chi (tau/(chi rho Theta^2))^(1/2)
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; m++) acc += bhu[m] * (ze.v[0] * du[0][m] + ze.v[1] * du[1][m]);
+    Aq = pre * (bhu[1] * dTh[0] + bhu[2] * dTh[1] + ze.theta * acc);
+    Bq = pre * bhu[0];
+#pragma unroll
+    for (int m = 0; m < 4; m++) Cq[m] = pre * ze.theta * bhu[m] * ze.ut;
+  }
+  {
+    const double s8 = kU[8] * dts, it = 1.0 / tau;
+    double cst = -Un[8] * idts + divF[8] + 0.5 * zn.qt * it - Aq * it + Bq * zn.theta * idts * it;
+#pragma unroll
+    for (int m = 0; m < 4; m++) cst += Cq[m] * ucovn[m] * idts * it;
+    cst -= hoq * (divu_sp - zn.ut * idts);
+    Kz[(K_C + 8) * N] = s8 * cst;
+    Kz[(K_Q + 0) * N] = 0.5 * s8 * it;
+    Kz[(K_Q + 1) * N] = -s8 * Bq * idts * it;
+#pragma unroll
+    for (int m = 0; m < 4; m++) Kz[(K_Q + 2 + m) * N] = -s8 * Cq[m] * idts * it;
+    Kz[(K_Q + 6) * N] = -s8 * hoq * idts;
+  }
+  // anisotropy row: dP~_0 = Ad + Dd^nu (u_nu - u_nu,n)/dt_s + Ed (u^t - u^t_n)/dt_s
+  double Ad = 0.0, Dd[4] = {0.0, 0.0, 0.0, 0.0}, Ed = 0.0;
+  if (p.visc) {
+    const double nu = p.psi * cs2E * tau;
+    const double pre = 3.0 * sqrt(tau * ze.rho * nu * nr_rcp(ze.theta));  // 3 rho nu (tau/(nu rho Theta))^(1/2)
+    double sp = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; m++) sp += bhu[m] * (bhu[1] * du[0][m] + bhu[2] * du[1][m]);
+    Ad = pre * (sp - divu_sp * (1.0 / 3.0));
+#pragma unroll
+    for (int m = 0; m < 4; m++) Dd[m] = pre * bhu[0] * bhu[m];
+    Ed = -pre * (1.0 / 3.0);
+  }
+  {
+    const double s9 = kU[9] * dts, it = 1.0 / tau;
+    double cst = -Un[9] * idts + divF[9] + 0.5 * zn.dpt * it - Ad * it + Ed * zn.ut * idts * it;
+#pragma unroll
+    for (int m = 0; m < 4; m++) cst += Dd[m] * ucovn[m] * idts * it;
+    cst -= hod * (divu_sp - zn.ut * idts);
+    Kz[(K_C + 9) * N] = s9 * cst;
+    Kz[(K_D + 0) * N] = 0.5 * s9 * it;
+#pragma unroll
+    for (int m = 0; m < 4; m++) Kz[(K_D + 1 + m) * N] = -s9 * Dd[m] * idts * it;
+    Kz[(K_D + 5) * N] = -s9 * (Ed * idts * it + hod * idts);
+  }
+  // initial guess: P_n (or the given guess) with B from the explicit flux-CT update
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    double x = a.guess ? __ldg(a.guess + v * N + z) : Pnz[v];
+    if (v >= 5 && v <= 7) x = Pnz[v] - dts * divF[v];
+    a.P0[v * N + z] = x;
+  }
+}
+
+// Face arrays needed for an n1 x n2 grid, in doubles.
+long long face_scratch_doubles(int n1, int n2) {
+  return (long long)NV * ((long long)(n1 + 1) * (n2 + 2) + (long long)(n1 + 2) * (n2 + 1));
+}
+
+// cs~^2 / c_s^2 under the closure chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R
+// (Eq. modcs with v_q^2 = (gamma-1) chi/tau_R, v_dP^2 = 4 nu/(3 tau_R)).
+static double closure_kappa(const Params& p) {
+  const double a = p.cond ? (p.gamma - 1.0) * p.phi : 0.0;
+  const double b = p.visc ? 4.0 * p.psi / 3.0 : 0.0;
+  return 0.5 * (1.0 + a + sqrt(1.0 + a * a)) + b;
+}
+
+void explicit_args(const Params& p, const double* Pn, const double* PE, const double* guess, double dts, double* K,
+                   double* P0, double* faces, ExpArgs& a) {
+  a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.kappa = closure_kappa(p);
+  a.K = K; a.P0 = P0;
+  a.F1 = faces;
+  a.F2 = faces + (long long)NV * (p.n1 + 1) * (p.n2 + 2);
+}
+
+cudaError_t launch_faces(const Params& p, const double* PE, double* faces, cudaStream_t st) {
+  ExpArgs a;
+  explicit_args(p, nullptr, PE, nullptr, 1.0, nullptr, nullptr, faces, a);
+  const long long nf = (long long)(p.n1 + 1) * (p.n2 + 2) + (long long)(p.n1 + 2) * (p.n2 + 1);
+  face_flux_2d<<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(p, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
+                              double* K, double* P0, double* faces, cudaStream_t st) {
+  ExpArgs a;
+  explicit_args(p, Pn, PE, guess, dts, K, P0, faces, a);
+  zone_const_2d<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, a);
+  return cudaGetLastError();
+}
+
+}  // namespace grim

@@ -26,107 +26,9 @@
 //   MIXED -- the Jacobian (its residual evaluations) and the LU in float;
 //            the residual of the iterate, the update, the line search and the
 //            convergence test in double (inexact Newton).
-#include "grim_dev.cuh"
+#include "grim_zone.cuh"
 
 namespace grim {
-
-// ---------------------------------------------------------------- math helpers
-// Reciprocal by the Newton-Raphson iteration r <- r + r (1 - x r), started
-// from the hardware approximation and applied twice (quadratic convergence
-// takes its ~2^-20 relative error below 2^-53).  Checked against IEEE division
-// by grim_math_selftest.
-__device__ __forceinline__ double nr_rcp(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-__device__ __forceinline__ float nr_rcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double sqr_root(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqr_root(float x) { return sqrtf(x); }
-// |x| as an unsigned integer: ordered like |x| for every non-NaN value.
-__device__ __forceinline__ unsigned long long abits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-}
-__device__ __forceinline__ unsigned int abits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
-__device__ __forceinline__ bool finite_bits(double x) {
-  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-}
-
-// ---------------------------------------------------------------- residual
-// Constants of the residual in the working precision.
-template <typename T> struct RC {
-  T gam, gm1, sphig, spsig;  // gamma, gamma - 1, sqrt(phi gamma), sqrt(psi gamma)
-  int cond, visc;
-};
-template <typename T> __device__ __forceinline__ RC<T> make_rc(const Params& p) {
-  RC<T> c;
-  c.gam = T(p.gamma);
-  c.gm1 = T(p.gamma - 1.0);
-  c.sphig = T(sqrt(p.phi * p.gamma));
-  c.spsig = T(sqrt(p.psi * p.gamma));
-  c.cond = p.cond;
-  c.visc = p.visc;
-  return c;
-}
-
-// Intermediates of the residual at one state, grouped by dependence.
-template <typename T> struct Z {
-  T rho, u, pg, theta, qs, ds, w0;   // thermodynamic group (rho, u)
-  T v[3], ut;                        // kinematic group (u^i): u^t = sqrt(1 + u.u)
-  T iut;
-  T B[3], bt, bc[3], bsq, bht, bh[3];  // magnetic group (B^i, u^i)
-  T qt, dpt;
-};
-
-// P_g = (gamma-1)u, Theta = P_g/rho, and the factors that turn q~, dP~ into
-// q = q~ Theta (phi c_s^2 rho)^(1/2) and dP = dP~ (psi c_s^2 P_g)^(1/2)
-// (Eqs. q, dP with chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R, and
-// c_s^2 = gamma P_g/(rho + gamma u)); w0 = rho + u + P_g.
-template <typename T> __device__ __forceinline__ void z_thermo(Z<T>& z, const RC<T>& c) {
-  const T pg = c.gm1 * z.u;
-  const T ra = rsq(z.rho);               // rho^(-1/2)
-  const T rb = rsq(z.rho + c.gam * z.u); // (rho + gamma u)^(-1/2)
-  z.pg = pg;
-  z.theta = pg * ra * ra;
-  z.qs = c.cond ? c.sphig * z.theta * sqr_root(pg) * (z.rho * ra) * rb : T(0);
-  z.ds = c.visc ? c.spsig * pg * rb : T(0);
-  z.w0 = z.rho + z.u + pg;
-}
-template <typename T> __device__ __forceinline__ void z_kin(Z<T>& z) {
-  const T s = T(1) + z.v[0] * z.v[0] + z.v[1] * z.v[1] + z.v[2] * z.v[2];
-  z.iut = rsq(s);
-  z.ut = s * z.iut;
-}
-// b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t, b^2, bhat = b/|b| (Section 4).
-template <typename T> __device__ __forceinline__ void z_mag(Z<T>& z) {
-  z.bt = z.B[0] * z.v[0] + z.B[1] * z.v[1] + z.B[2] * z.v[2];
-#pragma unroll
-  for (int i = 0; i < 3; i++) z.bc[i] = (z.B[i] + z.bt * z.v[i]) * z.iut;
-  z.bsq = z.bc[0] * z.bc[0] + z.bc[1] * z.bc[1] + z.bc[2] * z.bc[2] - z.bt * z.bt;
-  if (z.bsq > T(0)) {
-    const T ib = rsq(z.bsq);
-    z.bht = z.bt * ib;
-#pragma unroll
-    for (int i = 0; i < 3; i++) z.bh[i] = z.bc[i] * ib;
-  } else {
-    z.bht = T(0);
-    z.bh[0] = z.bh[1] = z.bh[2] = T(0);
-  }
-}
-template <typename T> __device__ __forceinline__ void z_load(Z<T>& z, const T* P, const RC<T>& c) {
-  z.rho = P[0]; z.u = P[1];
-  z.v[0] = P[2]; z.v[1] = P[3]; z.v[2] = P[4];
-  z.B[0] = P[5]; z.B[1] = P[6]; z.B[2] = P[7];
-  z.qt = P[8]; z.dpt = P[9];
-  z_thermo(z, c);
-  z_kin(z);
-  z_mag(z);
-}
 
 // Zone-constant accessors: shared memory at stride BS, or global at stride N.
 template <typename T, int BS> struct KSm {

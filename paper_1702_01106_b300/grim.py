@@ -25,7 +25,7 @@ EXPORTS = (
     "grim_profile", "grim_kernel_times", "grim_step_static", "grim_math_selftest",
 )
 STATIC_MAX_ZONES = 65536
-KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual")
+KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual", "faces", "zone_const")
 
 
 class GrimGrid(ctypes.Structure):

@@ -159,3 +159,17 @@ def test_reciprocal_matches_ieee_division(dev):
     within one rounding of IEEE division over 2^-300..2^300."""
     from paper_1702_01106_b300.grim import math_selftest
     assert math_selftest(1 << 20) <= 2.0 ** -52
+
+
+@pytest.mark.parametrize("bc", [((1, 1), (2, 2), (0, 0)), ((2, 1), (0, 0), (0, 0)), ((0, 0), (1, 2), (0, 0))])
+def test_stage_parity_non_periodic_boundaries(dev, orc, bc):
+    """Outflow (copy) and reflecting boundaries applied by the tile/face loaders."""
+    prob, Pn = _ragged_turbulent(20, 18, tol=1e-14)
+    prob = prob.with_(bc=bc)
+    dts = 0.25 / 32
+    g = _g(prob)
+    out = torch.empty_like(_t(Pn, dev))
+    g.stage(_t(Pn, dev), _t(Pn, dev), dts, out)
+    ref, _, rst, _ = orc.stage(prob, Pn, Pn, dts)
+    assert rst.max() == 0
+    assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12

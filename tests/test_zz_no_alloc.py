@@ -26,7 +26,7 @@ def dev():
 @pytest.mark.parametrize("precision", [0, 1])
 def test_static_step_matches_context_step_twice(dev, precision):
     from paper_1702_01106_b300.grim import Grim, step_static
-    prob = inputs.turbulent_box_problem(32, tol=1e-12).with_(n=(72, 40, 1))
+    prob = inputs.turbulent_box_problem(32, tol=1e-14).with_(n=(72, 40, 1))
     P = torch.from_numpy(inputs.turbulent_box_state(prob)).to(dev)
     dt = 0.5 / 72
     g = Grim(prob, precision=precision)
