@@ -215,7 +215,7 @@ def time_device(g, a, b, dt, steps, warmup, world, torch):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -260,38 +260,60 @@ def main():
     fp64_value = world * N / (ms_d * 1e-3)
 
     # Roofline of the dominant kernel of the headline (mixed) path: FP64 pipe bound.
+    # Algorithmic flops per launch (tests/golden/flop_counts.txt per unit):
+    #   faces:      2 LLF face fluxes per zone (the flux-CT ring of boundary
+    #               faces is overhead, not counted)
+    #   zone_const: the per-zone explicit remainder
+    #   newton:     residual evaluations, LU solves and update bookkeeping,
+    #               split by precision from the kernel's own counters
     steps = args.steps
+
     def newton_flops(st):
         f64 = st["evals64"] * fl["residual"] + st["lu64"] * fl["lu_solve"]
         f64 += st["iters"] * (fl["newton_update_bookkeeping"] if st["lu64"] else 60)
-        f32 = st["evals32"] * fl["residual"] + st["lu32"] * fl["lu_solve"] + (st["lu32"] and st["iters"] * 220)
+        f32 = st["evals32"] * fl["residual"] + st["lu32"] * fl["lu_solve"] + (st["iters"] * 220 if st["lu32"] else 0)
         return f64, f32
-    exp_flops_launch = N * (2 * fl["face_flux"] + fl["zone_explicit_remainder_2d"])
-    kern = {}
-    for cls, (tot, n) in kt_m.items():
-        kern[cls] = tot / n
+
+    def class_flops(cls, st, launches):
+        if cls == "faces":
+            return 2 * N * fl["face_flux"], 0
+        if cls == "zone_const":
+            return N * fl["zone_explicit_remainder_2d"], 0
+        if cls == "explicit":
+            return N * (2 * fl["face_flux"] + fl["zone_explicit_remainder_2d"]), 0
+        f64, f32 = newton_flops(st)
+        return f64 / launches, f32 / launches
+
+    def rooflines(kt, st):
+        out = {}
+        for cls, (tot, n) in kt.items():
+            f64, f32 = class_flops(cls, st, n)
+            t = tot / n * 1e-3
+            out[cls] = {"ms_per_launch": tot / n, "share": None, "fp64_tflops": f64 / t / 1e12,
+                        "fp64_frac": f64 / t / 1e12 / p64, "fp32_tflops": f32 / t / 1e12}
+        total = sum(v[0] for v in kt.values())
+        for cls, (tot, n) in kt.items():
+            out[cls]["share"] = tot / total
+        return out
+
+    roof_m = rooflines(kt_m, st_m)
+    roof_d = rooflines(kt_d, st_d)
+    kern = {k: v["ms_per_launch"] for k, v in roof_m.items()}
     dom = max(kt_m.items(), key=lambda kv: kv[1][0])[0]
-    f64_m, f32_m = newton_flops(st_m)
-    if dom == "explicit":
-        ach = exp_flops_launch / (kern["explicit"] * 1e-3) / 1e12
-        dom_name = "explicit_stage_2d"
-    else:
-        launches = kt_m[dom][1]
-        ach = (f64_m / launches) / (kern[dom] * 1e-3) / 1e12
-        dom_name = "newton_dense<mixed>"
+    names = {"faces": "face_flux_2d", "zone_const": "zone_const_2d", "newton32": "newton_dense<mixed>",
+             "newton64": "newton_dense<fp64>", "explicit": "explicit_stage_2d"}
+    ach = roof_m[dom]["fp64_tflops"]
     roof = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s", "frac": ach / p64,
-            "traffic": None, "kernel": dom_name,
+            "traffic": None, "kernel": names.get(dom, dom),
             "peak_source": "FP64 FMA-chain microbenchmark on this GPU (grim_peak_flops), of measured",
-            "flops_convention": "oracle flop counter: +,-,*,/,sqrt = 1, FMA = 2 (tests/golden/flop_counts.txt)"}
-    # FP64 path: its Newton kernel against the FP64 peak too
+            "flops_convention": "oracle flop counter: +,-,*,/,sqrt = 1, FMA = 2 (tests/golden/flop_counts.txt)",
+            "per_kernel": roof_m}
     f64_d, _ = newton_flops(st_d)
-    n64 = kt_d["newton64"]
-    roof_fp64 = {"kernel": "newton_dense<fp64>", "achieved": (f64_d / n64[1]) / (n64[0] / n64[1] * 1e-3) / 1e12,
-                 "peak": p64, "unit": "TFLOP/s"}
-    roof_fp64["frac"] = roof_fp64["achieved"] / p64
-    whole_step = {"fp64": (st_d["evals64"] * fl["residual"] + st_d["lu64"] * fl["lu_solve"]
-                           + st_d["iters"] * fl["newton_update_bookkeeping"]) / steps + 2 * exp_flops_launch}
-    roof_fp64["whole_step_frac"] = whole_step["fp64"] / (ms_d * 1e-3) / 1e12 / p64
+    exp_flops_launch = N * (2 * fl["face_flux"] + fl["zone_explicit_remainder_2d"])
+    whole_fp64 = (f64_d / steps + 2 * exp_flops_launch) / (ms_d * 1e-3) / 1e12
+    roof_fp64 = {"kernel": "newton_dense<fp64>", "achieved": roof_d["newton64"]["fp64_tflops"], "peak": p64,
+                 "unit": "TFLOP/s", "frac": roof_d["newton64"]["fp64_frac"], "whole_step_frac": whole_fp64 / p64,
+                 "per_kernel": roof_d}
 
     # End to end through the C ABI with host buffers (pinned), copies inside the timed region.
     g_m.profile(False)

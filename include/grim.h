@@ -76,11 +76,16 @@ typedef struct {
  * r_a = dt_s R_a / (|U_a(P_n)| + |U_0(P_n)|).  eps_fd: the finite-difference
  * parameter epsilon of Section 3.1 (float64 Jacobian), eps_fd32 the same for
  * the float32 Jacobian of GRIM_MIXED.  k_max: Newton updates per stage;
- * ls_max: backtracks per line search. */
+ * ls_max: backtracks per line search.  fd32_central: 0 builds the float32
+ * Jacobian with the one-sided differences of Section 3.1, 1 with centred
+ * differences (r(P + h e_j) - r(P - h e_j))/(2h) on the same step h, which
+ * float32 rounding favours (an inexact-Newton choice; the float64 Jacobian
+ * always uses the paper's one-sided form). */
 typedef struct {
   int precision; /* GRIM_FP64 or GRIM_MIXED */
   double tol, eps_fd, eps_fd32;
   int k_max, ls_max;
+  int fd32_central;
 } grim_solver;
 
 /* Counters accumulated over calls since the last grim_reset_stats. */

@@ -18,7 +18,8 @@ cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cuda
 long long face_scratch_doubles(int n1, int n2);
 cudaError_t launch_faces(const Params& p, const double* PE, double* faces, cudaStream_t st);
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                              double* K, double* P0, double* faces, cudaStream_t st);
+                              double* K, double* P0, double* faces, double* cache, int mode, cudaStream_t st);
+long long pn_cache_doubles(long long N);
 }  // namespace grim
 
 using grim::Params;
@@ -29,6 +30,7 @@ struct grim_ctx {
   cudaStream_t stream;
   double* K = nullptr;        // NK x N stage constants
   double* faces = nullptr;    // face fluxes of one stage
+  double* pncache = nullptr;  // P_n quantities shared by the two stages of a step
   double* Ph = nullptr;       // half-step state
   uint8_t* iters = nullptr;   // per-zone Newton updates of the last stage
   uint8_t* status = nullptr;  // per-zone status bits of the last stage
@@ -106,6 +108,7 @@ void grim_destroy(grim_ctx* ctx) {
   if (!ctx) return;
   cudaFree(ctx->K);
   cudaFree(ctx->faces);
+  cudaFree(ctx->pncache);
   cudaFree(ctx->Ph);
   cudaFree(ctx->iters);
   cudaFree(ctx->status);
@@ -146,7 +149,7 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   p.gamma = phys->gamma; p.phi = phys->phi; p.psi = phys->psi; p.tauR = phys->tau_R; p.theta = phys->theta;
   p.cond = phys->conduction; p.visc = phys->viscosity; p.ho = phys->higher_order; p.recon = phys->recon;
   p.tol = solver->tol; p.eps64 = solver->eps_fd; p.eps32 = (float)solver->eps_fd32;
-  p.kmax = solver->k_max; p.lsmax = solver->ls_max;
+  p.kmax = solver->k_max; p.lsmax = solver->ls_max; p.fd32c = solver->fd32_central != 0;
   p.N = (long long)grid->n1 * grid->n2 * grid->n3;
   ctx->precision = solver->precision;
   ctx->stream = (cudaStream_t)stream;
@@ -155,6 +158,7 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   if ((e = cudaMalloc(&ctx->K, sizeof(double) * grim::NK * N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->Ph, sizeof(double) * grim::NV * N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->faces, sizeof(double) * grim::face_scratch_doubles(p.n1, p.n2))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->pncache, sizeof(double) * grim::pn_cache_doubles(p.N))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->iters, N)) != cudaSuccess || (e = cudaMalloc(&ctx->status, N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->cnt, sizeof(grim::Counters))) != cudaSuccess) {
     grim_destroy(ctx);
@@ -170,22 +174,23 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
 
 // The explicit part of a stage: face fluxes, then flux-CT and the constants.
 static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
-                        double* Pout) {
+                        double* Pout, int mode) {
   {
     KernelMark m(ctx, GRIM_K_FACES);
     GRIM_CUDA(grim::launch_faces(ctx->p, PE, ctx->faces, ctx->stream), "face kernel");
   }
   {
     KernelMark m(ctx, GRIM_K_ZONECONST);
-    GRIM_CUDA(grim::launch_zone_const(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->faces, ctx->stream),
+    GRIM_CUDA(grim::launch_zone_const(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->faces, ctx->pncache, mode,
+                                      ctx->stream),
               "zone-constant kernel");
   }
   return GRIM_OK;
 }
 
 static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
-                     double* Pout, uint8_t* iters, uint8_t* status) {
-  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout);
+                     double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
+  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode);
   if (rc) return rc;
   {
     KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64);
@@ -206,10 +211,11 @@ int grim_stage(grim_ctx* ctx, const double* P_n, const double* P_E, double dts, 
 
 int grim_step(grim_ctx* ctx, const double* P_in, double* P_out, double dt) {
   if (!ctx || !P_in || !P_out || !(dt > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_step: bad argument");
-  int rc = run_stage(ctx, P_in, P_in, 0.5 * dt, nullptr, ctx->Ph, nullptr, nullptr);
+  // The half step (P^E = P_n) caches the P_n quantities the full step reuses.
+  int rc = run_stage(ctx, P_in, P_in, 0.5 * dt, nullptr, ctx->Ph, nullptr, nullptr, 1);
   if (rc) return rc;
   // The full stage reads P_n only at each zone itself, so P_out may alias P_in.
-  return run_stage(ctx, P_in, ctx->Ph, dt, nullptr, P_out, nullptr, nullptr);
+  return run_stage(ctx, P_in, ctx->Ph, dt, nullptr, P_out, nullptr, nullptr, 2);
 }
 
 int grim_step_host(grim_ctx* ctx, const double* P_in_host, double* P_out_host, double dt) {
@@ -232,7 +238,7 @@ int grim_residual(grim_ctx* ctx, const double* P_n, const double* P_E, double dt
                   double* R_out) {
   if (!ctx || !P_n || !P_E || !P_k || !R_out || !(dts > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_residual: bad argument");
   // the explicit kernel also writes an initial guess; send it to the half-step scratch
-  int rc = run_explicit(ctx, P_n, P_E, dts, nullptr, ctx->Ph);
+  int rc = run_explicit(ctx, P_n, P_E, dts, nullptr, ctx->Ph, 0);
   if (rc) return rc;
   {
     KernelMark m(ctx, GRIM_K_RESIDUAL);

@@ -40,6 +40,7 @@ struct Params {
   double tol, eps64;
   float eps32;
   int kmax, lsmax;
+  int fd32c;  // centred differences for the float32 Jacobian
   long long N;
 };
 

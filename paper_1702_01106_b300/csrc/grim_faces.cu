@@ -145,7 +145,14 @@ struct ExpArgs {
   double* P0;
   double* F1;  // [10][(n2+2)][(n1+1)]
   double* F2;  // [10][(n2+1)][(n1+2)]
+  // P_n cache shared by the two stages of a step: U(P_n) [10], Theta_n, u^t_n.
+  // mode 0: general stage (no cache); 1: half step (P^E = P_n; writes the
+  // cache); 2: full step (reads the cache and the row weights K_U the half
+  // step wrote, which depend on P_n only).
+  double* cache;
+  int mode;
 };
+constexpr int NCACHE = NV + 2;
 
 template <int D, bool WENO>
 __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a, int i, int j, double* out,
@@ -258,15 +265,22 @@ __global__ void __launch_bounds__(128) zone_const_2d(const __grid_constant__ Par
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     PEz[v] = __ldg(a.PE + v * N + z);
-    Pnz[v] = __ldg(a.Pn + v * N + z);
+    Pnz[v] = (a.mode == 1) ? PEz[v] : __ldg(a.Pn + v * N + z);
   }
   const RC<double> c = make_rc<double>(p);
-  Z<double> ze, zn;
+  Z<double> ze;
   z_load(ze, PEz, c);
-  z_load(zn, Pnz, c);
-  // U(P_n)
-  double Un[NV];
-  {
+  // P_n quantities: U(P_n), Theta_n, u^t_n (from the cache in the full step)
+  double Un[NV], th_n, ut_n;
+  if (a.mode == 2) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) Un[v] = __ldg(a.cache + v * N + z);
+    th_n = __ldg(a.cache + NV * N + z);
+    ut_n = __ldg(a.cache + (NV + 1) * N + z);
+  } else {
+    Z<double> zn;
+    if (a.mode == 1) zn = ze;
+    else z_load(zn, Pnz, c);
     const double dp = zn.dpt * zn.ds, q = zn.qt * zn.qs;
     const double third = dp * (1.0 / 3.0);
     const double A = (zn.w0 + zn.bsq + third) * zn.ut;
@@ -279,7 +293,17 @@ __global__ void __launch_bounds__(128) zone_const_2d(const __grid_constant__ Par
     Un[5] = Pnz[5]; Un[6] = Pnz[6]; Un[7] = Pnz[7];
     Un[8] = zn.qt * zn.ut;
     Un[9] = zn.dpt * zn.ut;
+    th_n = zn.theta;
+    ut_n = zn.ut;
+    if (a.mode == 1) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) a.cache[v * N + z] = Un[v];
+      a.cache[NV * N + z] = th_n;
+      a.cache[(NV + 1) * N + z] = ut_n;
+    }
   }
+  const double qt_n = Pnz[8], dpt_n = Pnz[9];
+
   // limited slopes at P^E of Theta and u_mu; the spatial part of nabla_mu u^mu
   double dTh[2], du[2][4], divu_sp = 0.0;
   {
@@ -301,13 +325,17 @@ __global__ void __launch_bounds__(128) zone_const_2d(const __grid_constant__ Par
   double kU[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    // row scale s_v = dt_s/(|U_v(P_n)| + |U_0(P_n)|); kU = s_v/dt_s
-    kU[v] = nr_rcp(fabs(Un[v]) + fabs(Un[0]));
-    Kz[(K_U + v) * N] = kU[v];
+    // row scale s_v = dt_s/(|U_v(P_n)| + |U_0(P_n)|); kU = s_v/dt_s depends on P_n only
+    if (a.mode == 2) {
+      kU[v] = Kz[(K_U + v) * N];
+    } else {
+      kU[v] = nr_rcp(fabs(Un[v]) + fabs(Un[0]));
+      Kz[(K_U + v) * N] = kU[v];
+    }
     Kz[(K_C + v) * N] = kU[v] * (dts * divF[v] - Un[v]);
   }
   const double bhu[4] = {ze.bht, ze.bh[0], ze.bh[1], ze.bh[2]};
-  const double ucovn[4] = {-zn.ut, zn.v[0], zn.v[1], zn.v[2]};
+  const double ucovn[4] = {-ut_n, Pnz[2], Pnz[3], Pnz[4]};
   const double hoq = p.ho ? 0.5 * ze.qt : 0.0;
   const double hod = p.ho ? 0.5 * ze.dpt : 0.0;
   const double cs2E = p.gamma * ze.pg * ze.iden;
@@ -326,10 +354,10 @@ __global__ void __launch_bounds__(128) zone_const_2d(const __grid_constant__ Par
   }
   {
     const double s8 = kU[8] * dts, it = 1.0 / tau;
-    double cst = -Un[8] * idts + divF[8] + 0.5 * zn.qt * it - Aq * it + Bq * zn.theta * idts * it;
+    double cst = -Un[8] * idts + divF[8] + 0.5 * qt_n * it - Aq * it + Bq * th_n * idts * it;
 #pragma unroll
     for (int m = 0; m < 4; m++) cst += Cq[m] * ucovn[m] * idts * it;
-    cst -= hoq * (divu_sp - zn.ut * idts);
+    cst -= hoq * (divu_sp - ut_n * idts);
     Kz[(K_C + 8) * N] = s8 * cst;
     Kz[(K_Q + 0) * N] = 0.5 * s8 * it;
     Kz[(K_Q + 1) * N] = -s8 * Bq * idts * it;
@@ -352,10 +380,10 @@ __global__ void __launch_bounds__(128) zone_const_2d(const __grid_constant__ Par
   }
   {
     const double s9 = kU[9] * dts, it = 1.0 / tau;
-    double cst = -Un[9] * idts + divF[9] + 0.5 * zn.dpt * it - Ad * it + Ed * zn.ut * idts * it;
+    double cst = -Un[9] * idts + divF[9] + 0.5 * dpt_n * it - Ad * it + Ed * ut_n * idts * it;
 #pragma unroll
     for (int m = 0; m < 4; m++) cst += Dd[m] * ucovn[m] * idts * it;
-    cst -= hod * (divu_sp - zn.ut * idts);
+    cst -= hod * (divu_sp - ut_n * idts);
     Kz[(K_C + 9) * N] = s9 * cst;
     Kz[(K_D + 0) * N] = 0.5 * s9 * it;
 #pragma unroll
@@ -387,6 +415,7 @@ static double closure_kappa(const Params& p) {
 void explicit_args(const Params& p, const double* Pn, const double* PE, const double* guess, double dts, double* K,
                    double* P0, double* faces, ExpArgs& a) {
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.kappa = closure_kappa(p);
+  a.cache = nullptr; a.mode = 0;
   a.K = K; a.P0 = P0;
   a.F1 = faces;
   a.F2 = faces + (long long)NV * (p.n1 + 1) * (p.n2 + 2);
@@ -400,10 +429,16 @@ cudaError_t launch_faces(const Params& p, const double* PE, double* faces, cudaS
   return cudaGetLastError();
 }
 
+long long pn_cache_doubles(long long N) { return (long long)NCACHE * N; }
+
+// mode: 0 general stage, 1 half step (P_E == P_n; fills cache), 2 full step
+// of the same step (reads cache and K_U).
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                              double* K, double* P0, double* faces, cudaStream_t st) {
+                              double* K, double* P0, double* faces, double* cache, int mode, cudaStream_t st) {
   ExpArgs a;
   explicit_args(p, Pn, PE, guess, dts, K, P0, faces, a);
+  a.cache = cache;
+  a.mode = cache ? mode : 0;
   zone_const_2d<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, a);
   return cudaGetLastError();
 }

@@ -95,30 +95,19 @@ template <typename T> __device__ __forceinline__ T fd_step(T x, T eps) {
   return (fabs(x) < T(5) * eps) ? x + eps : (T(1) + eps) * x;
 }
 
-// Column C of the FD Jacobian, J_iC = (r_i(P_eps) - r_i(P)) / (P_eps,C - P_C),
-// written to shared memory (element (i, C) at Jc[(i*10 + C)*BS]).  Rows whose
-// residual cannot depend on component C are exact zeros.
-template <int C, typename T, int BS, class KA>
-__device__ __forceinline__ void fd_column(const Z<T>& z0, const T r[NV], const KA& k, const RC<T>& c, T eps,
-                                          T* Jc) {
+// Residual rows of the state z after its component C changed to x (groups
+// that depend on C recomputed); rows that cannot depend on C keep r.
+template <int C, typename T, class KA>
+__device__ __forceinline__ void perturbed_rows(const Z<T>& z0, T x, const T r[NV], const KA& k, const RC<T>& c,
+                                               T re[NV]) {
   Z<T> z = z0;
-  T pj;
-  if constexpr (C == 0) pj = z.rho;
-  else if constexpr (C == 1) pj = z.u;
-  else if constexpr (C <= 4) pj = z.v[C - 2];
-  else if constexpr (C <= 7) pj = z.B[C - 5];
-  else if constexpr (C == 8) pj = z.qt;
-  else pj = z.dpt;
-  const T pe = fd_step(pj, eps);
-  const T ih = nr_rcp(pe - pj);
-  if constexpr (C == 0) { z.rho = pe; z_thermo(z, c); }
-  else if constexpr (C == 1) { z.u = pe; z_thermo(z, c); }
-  else if constexpr (C <= 4) { z.v[C - 2] = pe; z_kin(z); z_mag(z); }
-  else if constexpr (C <= 7) { z.B[C - 5] = pe; z_mag(z); }
-  else if constexpr (C == 8) z.qt = pe;
-  else z.dpt = pe;
+  if constexpr (C == 0) { z.rho = x; z_thermo(z, c); }
+  else if constexpr (C == 1) { z.u = x; z_thermo(z, c); }
+  else if constexpr (C <= 4) { z.v[C - 2] = x; z_kin(z); z_mag(z); }
+  else if constexpr (C <= 7) { z.B[C - 5] = x; z_mag(z); }
+  else if constexpr (C == 8) z.qt = x;
+  else z.dpt = x;
   constexpr bool kin = (C >= 2 && C <= 4);
-  T re[NV];
 #pragma unroll
   for (int i = 0; i < NV; i++) re[i] = r[i];
   if constexpr (C == 0 || kin) re[0] = r_mass(z, k);
@@ -126,27 +115,63 @@ __device__ __forceinline__ void fd_column(const Z<T>& z0, const T r[NV], const K
   if constexpr (C >= 5 && C <= 7) re[C] = r_field(z, k, C - 5);
   if constexpr (C <= 4 || C == 8) re[8] = r_heat(z, k);
   if constexpr (kin || C == 9) re[9] = r_aniso(z, k);
+}
+
+// Whether residual row i can depend on component C (the other entries of the
+// FD Jacobian are exact zeros).
+template <int C> __device__ __forceinline__ constexpr bool row_depends(int i) {
+  constexpr bool kin = (C >= 2 && C <= 4);
+  return (i >= 1 && i <= 4) || (i == 0 && (C == 0 || kin)) || (i == C && C >= 5 && C <= 7) ||
+         (i == 8 && (C <= 4 || C == 8)) || (i == 9 && (kin || C == 9));
+}
+
+template <int C, typename T> __device__ __forceinline__ T component(const Z<T>& z) {
+  if constexpr (C == 0) return z.rho;
+  else if constexpr (C == 1) return z.u;
+  else if constexpr (C <= 4) return z.v[C - 2];
+  else if constexpr (C <= 7) return z.B[C - 5];
+  else if constexpr (C == 8) return z.qt;
+  else return z.dpt;
+}
+
+// Column C of the FD Jacobian, written to shared memory (element (i, C) at
+// Jc[(i*10 + C)*BS]).  One-sided (Section 3.1):
+// J_iC = (r_i(P_eps) - r_i(P)) / (P_eps,C - P_C).  Centred (float32 option):
+// J_iC = (r_i(P + h e_C) - r_i(P - h e_C)) / (2h) with h = P_eps,C - P_C.
+template <int C, bool CENTRAL, typename T, int BS, class KA>
+__device__ __forceinline__ void fd_column(const Z<T>& z, const T r[NV], const KA& k, const RC<T>& c, T eps,
+                                          T* Jc) {
+  const T pj = component<C>(z);
+  const T pe = fd_step(pj, eps);
+  const T h = pe - pj;
+  T rp[NV];
+  perturbed_rows<C>(z, pe, r, k, c, rp);
+  if constexpr (!CENTRAL) {
+    const T ih = nr_rcp(h);
 #pragma unroll
-  for (int i = 0; i < NV; i++) {
-    const bool dep = (i >= 1 && i <= 4) || (i == 0 && (C == 0 || kin)) || (i == C && C >= 5 && C <= 7) ||
-                     (i == 8 && (C <= 4 || C == 8)) || (i == 9 && (kin || C == 9));
-    Jc[(i * NV + C) * BS] = dep ? (re[i] - r[i]) * ih : T(0);
+    for (int i = 0; i < NV; i++) Jc[(i * NV + C) * BS] = row_depends<C>(i) ? (rp[i] - r[i]) * ih : T(0);
+  } else {
+    T rm[NV];
+    perturbed_rows<C>(z, pj - h, r, k, c, rm);
+    const T ih = T(0.5) * nr_rcp(h);
+#pragma unroll
+    for (int i = 0; i < NV; i++) Jc[(i * NV + C) * BS] = row_depends<C>(i) ? (rp[i] - rm[i]) * ih : T(0);
   }
 }
 
-template <typename T, int BS, class KA>
+template <typename T, bool CENTRAL, int BS, class KA>
 __device__ __forceinline__ void fd_jacobian(const Z<T>& z, const T r[NV], const KA& k, const RC<T>& c, T eps,
                                             T* J) {
-  fd_column<0, T, BS>(z, r, k, c, eps, J);
-  fd_column<1, T, BS>(z, r, k, c, eps, J);
-  fd_column<2, T, BS>(z, r, k, c, eps, J);
-  fd_column<3, T, BS>(z, r, k, c, eps, J);
-  fd_column<4, T, BS>(z, r, k, c, eps, J);
-  fd_column<5, T, BS>(z, r, k, c, eps, J);
-  fd_column<6, T, BS>(z, r, k, c, eps, J);
-  fd_column<7, T, BS>(z, r, k, c, eps, J);
-  fd_column<8, T, BS>(z, r, k, c, eps, J);
-  fd_column<9, T, BS>(z, r, k, c, eps, J);
+  fd_column<0, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<1, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<2, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<3, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<4, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<5, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<6, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<7, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<8, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  fd_column<9, CENTRAL, T, BS>(z, r, k, c, eps, J);
 }
 
 // Partial-pivot LU solve J x = b with J, b in shared memory at stride BS
@@ -241,7 +266,7 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
     if (!MIXED) {
       double* J = (double*)jac + threadIdx.x;
       double* b = J + NV * NV * BS;
-      fd_jacobian<double, BS>(z, r, k64, c64, p.eps64, J);
+      fd_jacobian<double, false, BS>(z, r, k64, c64, p.eps64, J);
       o.evals64 += NV;
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
@@ -258,8 +283,13 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       Z<float> zf;
       z_load(zf, Pf, c32);
       r_all(zf, k32, rf);
-      fd_jacobian<float, BS>(zf, rf, k32, c32, p.eps32, J);
-      o.evals32 += NV + 1;
+      if (p.fd32c) {
+        fd_jacobian<float, true, BS>(zf, rf, k32, c32, p.eps32, J);
+        o.evals32 += 2 * NV + 1;
+      } else {
+        fd_jacobian<float, false, BS>(zf, rf, k32, c32, p.eps32, J);
+        o.evals32 += NV + 1;
+      }
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = (float)(-r[i]);
       float df[NV];

@@ -81,7 +81,7 @@ int make_params(const grim_grid* grid, const grim_metric* metric, const grim_phy
   p.gamma = phys->gamma; p.phi = phys->phi; p.psi = phys->psi; p.tauR = phys->tau_R; p.theta = phys->theta;
   p.cond = phys->conduction; p.visc = phys->viscosity; p.ho = phys->higher_order; p.recon = phys->recon;
   p.tol = solver->tol; p.eps64 = solver->eps_fd; p.eps32 = (float)solver->eps_fd32;
-  p.kmax = solver->k_max; p.lsmax = solver->ls_max;
+  p.kmax = solver->k_max; p.lsmax = solver->ls_max; p.fd32c = solver->fd32_central != 0;
   p.N = (long long)grid->n1 * grid->n2 * grid->n3;
   return GRIM_OK;
 }

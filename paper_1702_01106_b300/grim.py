@@ -46,7 +46,8 @@ class GrimPhysics(ctypes.Structure):
 
 class GrimSolver(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("eps_fd", ctypes.c_double),
-                ("eps_fd32", ctypes.c_double), ("k_max", ctypes.c_int), ("ls_max", ctypes.c_int)]
+                ("eps_fd32", ctypes.c_double), ("k_max", ctypes.c_int), ("ls_max", ctypes.c_int),
+                ("fd32_central", ctypes.c_int)]
 
 
 class GrimStats(ctypes.Structure):
@@ -112,24 +113,28 @@ def _f64(t):
     return _ptr(t)
 
 
-def _config(prob, precision, eps_fd32):
+EPS_FD32 = 2.0 ** -7      # float32 Jacobian step (measured optimum with centred differences)
+FD32_CENTRAL = 1
+
+
+def _config(prob, precision, eps_fd32, fd32_central=FD32_CENTRAL):
     g = GrimGrid(prob.dim, prob.n[0], prob.n[1], prob.n[2],
                  (ctypes.c_double * 3)(*prob.x_start), (ctypes.c_double * 3)(*prob.x_end),
                  ((ctypes.c_int * 2) * 3)(*[(ctypes.c_int * 2)(*b) for b in prob.bc]))
     m = GrimMetric(prob.metric, prob.spin, prob.h_mks)
     ph = GrimPhysics(prob.gamma, prob.tau_R, prob.phi, prob.psi, int(prob.conduction), int(prob.viscosity),
                      int(prob.higher_order), prob.recon, prob.theta)
-    sv = GrimSolver(precision, prob.tol, prob.eps_fd, eps_fd32, prob.k_max, prob.ls_max)
+    sv = GrimSolver(precision, prob.tol, prob.eps_fd, eps_fd32, prob.k_max, prob.ls_max, int(fd32_central))
     return g, m, ph, sv
 
 
 def step_static(prob, P_in, P_out, dt: float, precision: int = GRIM_FP64, stream=None,
-                eps_fd32: float = 2.0 ** -12) -> int:
+                eps_fd32: float = EPS_FD32, fd32_central: int = FD32_CENTRAL) -> int:
     """grim_step_static: one step with the library's static scratch (no device
     allocation), for callers that cannot call cudaMalloc.  Returns the C code."""
     import torch
     lib = load()
-    g, m, ph, sv = _config(prob, precision, eps_fd32)
+    g, m, ph, sv = _config(prob, precision, eps_fd32, fd32_central)
     if stream is None:
         stream = torch.cuda.current_stream()
     return lib.grim_step_static(ctypes.byref(g), ctypes.byref(m), ctypes.byref(ph), ctypes.byref(sv),
@@ -139,11 +144,12 @@ def step_static(prob, P_in, P_out, dt: float, precision: int = GRIM_FP64, stream
 class Grim:
     """One context of the library (grim_init ... grim_destroy)."""
 
-    def __init__(self, prob, precision: int = GRIM_FP64, stream=None, eps_fd32: float = 2.0 ** -12):
+    def __init__(self, prob, precision: int = GRIM_FP64, stream=None, eps_fd32: float = EPS_FD32,
+                 fd32_central: int = FD32_CENTRAL):
         import torch
         self.lib = load()
         self.prob = prob
-        g, m, ph, sv = _config(prob, precision, eps_fd32)
+        g, m, ph, sv = _config(prob, precision, eps_fd32, fd32_central)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
