@@ -100,6 +100,7 @@ typedef struct {
   unsigned long long hist[32];  /* zone solves by number of Newton updates (31 = 31 or more) */
   double max_res;               /* largest final max_a |r_a| over zone solves */
   unsigned long long launches;  /* kernels launched by the library */
+  unsigned long long fallbacks; /* zone solves whose learned start lost to P_n (grim_set_guess) */
 } grim_stats;
 
 typedef struct grim_ctx grim_ctx;
@@ -145,6 +146,7 @@ int grim_residual(grim_ctx* ctx, const double* P_n, const double* P_E, double dt
 #define GRIM_K_RESIDUAL 3  /* single residual evaluation */
 #define GRIM_K_FACES 4     /* face fluxes: reconstruction, LLF (one thread per face) */
 #define GRIM_K_ZONECONST 5 /* flux-CT, divergence, slopes, stage constants */
+#define GRIM_K_MLP 6       /* learned initial guess (MLP inference) */
 #define GRIM_K_COUNT 8
 
 /* Enable (1) or disable (0) per-kernel timing: CUDA events are recorded on
@@ -199,6 +201,61 @@ int grim_step_static(const grim_grid* grid, const grim_metric* metric, const gri
  * FMA) to *fp64_tflops and *fp32_tflops.  Allocates and frees a small
  * device buffer; synchronises the device. */
 int grim_peak_flops(double* fp64_tflops, double* fp32_tflops);
+
+/* ---- Learned initial guess.  The paper starts each Newton solve from P_n
+ * (§3); these calls add a small MLP that predicts the stage change of the
+ * primitives, with P_n kept as the fallback.  Network 30 -> 128 -> 128 ->
+ * 128 -> head (SiLU), bfloat16 weights, float32 accumulation, on the tensor
+ * cores.  Features per zone (float32 [32]): x_a = -r_a(P_n), the scaled
+ * residual of the stage at its start (a = 0..9: for the conserved rows the
+ * explicit increment U* - U(P_n) in the residual's row scaling, for q~ and
+ * dP~ the explicit part of their relaxation equations), the ten g_{mu nu},
+ * P_n, two zeros.  The head's 80 outputs hold a 7x10 matrix M(x) (row-major)
+ * and an offset c(x); the standardised prediction of the seven predicted
+ * fields is y = M x_U + c, x_U the ten standardised increment features, so
+ * that the network learns a state-dependent inverse Jacobian.  Targets
+ * (float32 [16]): P_conv - P_n for rho, u, u^i, q~, dP~ at indices 0-4, 8, 9
+ * (the magnetic field is the explicit flux-CT update, not predicted), zeros
+ * elsewhere.  X and Y arrays are device, zone-major ([M][32], [M][16]). */
+typedef struct grim_mlp grim_mlp;
+
+/* Create an MLP with Kaiming-uniform weights from `seed`, zero biases, and an
+ * identity standardisation.  Allocates device memory; synchronises. */
+int grim_mlp_create(unsigned long long seed, grim_mlp** out);
+void grim_mlp_destroy(grim_mlp* mlp);
+/* Number of float32 parameters: W1[128][32], b1, W2[128][128], b2,
+ * W3[128][128], b3, W4[80][128], b4[80], in that order (row-major). */
+int grim_mlp_param_count(void);
+/* Copy parameters (host float32 [param_count]) and the standardisation
+ * (host float32 [96]: x_mean[32], x_std[32], y_mean[16], y_std[16]); either
+ * pointer may be NULL.  set resets the Adam state.  Synchronous. */
+int grim_mlp_get_params(grim_mlp* mlp, float* params, float* norm);
+int grim_mlp_set_params(grim_mlp* mlp, const float* params, const float* norm);
+/* Fit the standardisation to M training rows (per-column mean and standard
+ * deviation; a constant feature column keeps unit deviation, a constant
+ * target column gets deviation 0 and is predicted as its mean).
+ * Synchronous. */
+int grim_mlp_fit_norm(grim_mlp* mlp, const float* X, const float* Y, long long M);
+/* `steps` Adam steps (lr; betas 0.9, 0.999; eps 1e-8) on minibatches of
+ * `batch` rows (a multiple of 64) of the M training rows, visited in a fixed
+ * permutation that starts at `seed` mod M; loss = mean squared error of the
+ * standardised targets over the seven predicted fields.  *mean_loss: the
+ * mean of the minibatch losses.  Synchronous. */
+int grim_mlp_train(grim_mlp* mlp, const float* X, const float* Y, long long M, int batch, int steps, double lr,
+                   unsigned long long seed, double* mean_loss);
+/* Gradient of the loss over all M rows (M a multiple of 64, one batch) with
+ * respect to the parameters, to host float32 [param_count]; *loss its value. */
+int grim_mlp_gradient(grim_mlp* mlp, const float* X, const float* Y, long long M, float* grad, double* loss);
+/* Features (and, when P_conv and Y are non-NULL, targets) of every zone of
+ * the stage whose explicit kernels ran last on ctx (grim_stage,
+ * grim_residual or the full step of grim_step), with start-of-step state P_n
+ * and converged state P_conv. */
+int grim_mlp_sample(grim_ctx* ctx, const double* P_n, const double* P_conv, float* X, float* Y);
+/* Start every later Newton solve of ctx from the MLP's prediction (NULL:
+ * from P_n).  The learned start is kept when its max |r_a| <= accept; else
+ * the plain start P_n is evaluated too and the smaller |r|^2 wins (counted
+ * in grim_stats.fallbacks).  The MLP must outlive its use by ctx. */
+int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept);
 
 /* Self-check of the float64 reciprocal the kernels use for finite-difference
  * divisors and LU pivots (a Newton-Raphson refinement of the hardware

@@ -20,6 +20,12 @@ cudaError_t launch_faces(const Params& p, const double* PE, double* faces, cudaS
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
                               double* K, double* P0, double* faces, double* cache, int mode, cudaStream_t st);
 long long pn_cache_doubles(long long N);
+cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
+                             Counters* cnt, const double* Pfb, double accept, cudaStream_t st);
+cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
+                                float* Y, cudaStream_t st);
+cudaError_t launch_mlp_guess(const Params& p, const double* K, const double* Pn, const double* Un, const grim_mlp* m,
+                             double* P0, cudaStream_t st);
 }  // namespace grim
 
 using grim::Params;
@@ -38,6 +44,8 @@ struct grim_ctx {
   double* dev_in = nullptr;   // device copies for grim_step_host
   double* dev_out = nullptr;
   unsigned long long launches = 0;
+  grim_mlp* mlp = nullptr;    // learned initial guess (grim_set_guess)
+  double accept = 0.0;
   // per-kernel timing: (class, start, stop) event triples
   bool profile = false;
   struct Mark { int cls; cudaEvent_t a, b; };
@@ -192,10 +200,17 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
                      double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
   int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode);
   if (rc) return rc;
+  const bool learned = ctx->mlp && !guess;
+  if (learned) {
+    KernelMark m(ctx, GRIM_K_MLP);
+    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->K, Pn, mode ? ctx->pncache : nullptr, ctx->mlp, Pout, ctx->stream),
+              "mlp kernel");
+  }
   {
     KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64);
-    GRIM_CUDA(grim::launch_newton(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
-                                  status ? status : ctx->status, ctx->cnt, ctx->stream),
+    GRIM_CUDA(grim::launch_newton_fb(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
+                                     status ? status : ctx->status, ctx->cnt, learned ? Pn : nullptr, ctx->accept,
+                                     ctx->stream),
               "newton kernel");
   }
   return GRIM_OK;
@@ -261,6 +276,23 @@ int grim_get_stats(grim_ctx* ctx, grim_stats* out) {
   std::memcpy(&mr, &bits, sizeof(mr));
   out->max_res = mr;
   out->launches = ctx->launches;
+  out->fallbacks = c.fallbacks;
+  return GRIM_OK;
+}
+
+int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept) {
+  if (!ctx || !(accept >= 0.0)) return GRIM_EINVAL;
+  ctx->mlp = mlp;
+  ctx->accept = accept;
+  return GRIM_OK;
+}
+
+int grim_mlp_sample(grim_ctx* ctx, const double* P_n, const double* P_conv, float* X, float* Y) {
+  if (!ctx || !P_n || !X || (Y && !P_conv)) return GRIM_EINVAL;
+  {
+    KernelMark m(ctx, GRIM_K_MLP);
+    GRIM_CUDA(grim::launch_mlp_features(ctx->p, ctx->K, P_n, P_conv, X, Y, ctx->stream), "feature kernel");
+  }
   return GRIM_OK;
 }
 

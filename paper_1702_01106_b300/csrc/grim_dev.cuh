@@ -61,6 +61,7 @@ struct Counters {
   unsigned long long zones;     // zones solved
   unsigned long long hist[32];  // Newton updates per zone
   unsigned long long maxres_bits;  // max over zones of max_a |r_a|, as ordered bits
+  unsigned long long fallbacks;    // zones whose learned start lost to the plain start
 };
 
 // ----------------------------------------------------------------------------

@@ -243,9 +243,13 @@ struct ZoneResult {
 
 // Newton on one zone, starting from P (updated in place).  kd: the zone's
 // float64 constants in shared memory (stride BS); kf: their float copies.
+// Pfb (non-NULL with a learned start): the plain start P_n, whose magnetic
+// components are those of P; if the learned start's max|r| exceeds
+// accept_bits the plain start is evaluated too and the smaller |r|^2 wins.
 template <bool MIXED, int BS>
 __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double* kd, const float* kf, double P[NV],
-                                                  void* jac) {
+                                                  void* jac, const double* Pfb, long long fb_stride,
+                                                  unsigned long long accept_bits, bool& fellback) {
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0.0};
   const RC<double> c64 = make_rc<double>(p);
   const KSm<double, BS> k64{kd};
@@ -256,6 +260,24 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
   r_all(z, k64, r);
   o.evals64++;
   double f = sum_sq10(r);
+  fellback = false;
+  if (Pfb && !(max_abits10(r) <= accept_bits)) {
+    double Pp[NV], rp[NV];
+#pragma unroll
+    for (int a = 0; a < NV; a++) Pp[a] = (a >= 5 && a <= 7) ? P[a] : Pfb[a * fb_stride];
+    Z<double> zp;
+    z_load(zp, Pp, c64);
+    r_all(zp, k64, rp);
+    o.evals64++;
+    const double fp = sum_sq10(rp);
+    if (!(f <= fp)) {
+      fellback = true;
+#pragma unroll
+      for (int a = 0; a < NV; a++) { P[a] = Pp[a]; r[a] = rp[a]; }
+      z = zp;
+      f = fp;
+    }
+  }
   int k = 0;
   for (;;) {
     if (!finite_bits(f)) { o.status |= ST_NONFINITE; break; }
@@ -334,7 +356,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   return v;
 }
 
-__device__ __forceinline__ void accumulate(Counters* c, const ZoneResult& o, bool active) {
+__device__ __forceinline__ void accumulate(Counters* c, const ZoneResult& o, bool active, bool fellback) {
   const int lane = threadIdx.x & 31;
   unsigned long long e64 = active ? o.evals64 : 0, e32 = active ? o.evals32 : 0;
   unsigned long long l64 = active ? o.lu64 : 0, l32 = active ? o.lu32 : 0;
@@ -346,6 +368,8 @@ __device__ __forceinline__ void accumulate(Counters* c, const ZoneResult& o, boo
     atomicAdd(&c->lu64, l64); atomicAdd(&c->lu32, l32);
     atomicAdd(&c->iters, it); atomicAdd(&c->failed, fl); atomicAdd(&c->zones, zn);
   }
+  const unsigned fb = __ballot_sync(0xffffffffu, active && fellback);
+  if (lane == 0 && fb) atomicAdd(&c->fallbacks, (unsigned long long)__popc(fb));
   if (active) {
     atomicAdd(&c->hist[o.iters < 31 ? o.iters : 31], 1ull);
     if (finite_bits(o.res)) atomicMax(&c->maxres_bits, (unsigned long long)__double_as_longlong(o.res));
@@ -365,7 +389,8 @@ template <bool MIXED, int BS> struct NewtonSmem {
 template <bool MIXED, int BS>
 __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Params p, const double* __restrict__ K,
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
-                                                   uint8_t* __restrict__ status, Counters* __restrict__ cnt) {
+                                                   uint8_t* __restrict__ status, Counters* __restrict__ cnt,
+                                                   const double* __restrict__ Pfb, double accept) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -375,6 +400,7 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
   const long long z = (long long)blockIdx.x * BS + threadIdx.x;
   const bool active = z < N;
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0.0};
+  bool fellback = false;
   if (active) {
 #pragma unroll
     for (int a = 0; a < NK; a++) {
@@ -385,13 +411,13 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
     double Pz[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-    o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac);
+    o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, Pfb ? Pfb + z : nullptr, N, abits(accept), fellback);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
     status[z] = (uint8_t)o.status;
   }
-  accumulate(cnt, o, active);
+  accumulate(cnt, o, active, fellback);
 }
 
 // Evaluate the scaled (or raw) residual at Pk once per zone.
@@ -432,7 +458,7 @@ __global__ void rcp_check(int n, unsigned long long seed, double* worst) {
 
 template <bool MIXED, int BS>
 static cudaError_t launch_newton_t(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
-                                   Counters* cnt, cudaStream_t st) {
+                                   Counters* cnt, const double* Pfb, double accept, cudaStream_t st) {
   using S = NewtonSmem<MIXED, BS>;
   static bool configured = false;
   if (!configured) {
@@ -442,14 +468,19 @@ static cudaError_t launch_newton_t(const Params& p, const double* K, double* P, 
     configured = true;
   }
   const long long nb = (p.N + BS - 1) / BS;
-  newton_dense<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt);
+  newton_dense<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept);
   return cudaGetLastError();
+}
+
+cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
+                             Counters* cnt, const double* Pfb, double accept, cudaStream_t st) {
+  if (mixed) return launch_newton_t<true, 64>(p, K, P, iters, status, cnt, Pfb, accept, st);
+  return launch_newton_t<false, 64>(p, K, P, iters, status, cnt, Pfb, accept, st);
 }
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                           Counters* cnt, cudaStream_t st) {
-  if (mixed) return launch_newton_t<true, 64>(p, K, P, iters, status, cnt, st);
-  return launch_newton_t<false, 64>(p, K, P, iters, status, cnt, st);
+  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, st);
 }
 
 cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, int scaled, double dts, double* R,

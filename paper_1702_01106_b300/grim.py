@@ -23,9 +23,11 @@ EXPORTS = (
     "grim_init", "grim_step", "grim_step_host", "grim_stage", "grim_residual", "grim_get_stats",
     "grim_reset_stats", "grim_last_error", "grim_strerror", "grim_destroy", "grim_peak_flops",
     "grim_profile", "grim_kernel_times", "grim_step_static", "grim_math_selftest",
+    "grim_mlp_create", "grim_mlp_destroy", "grim_mlp_param_count", "grim_mlp_get_params", "grim_mlp_set_params",
+    "grim_mlp_fit_norm", "grim_mlp_train", "grim_mlp_gradient", "grim_mlp_sample", "grim_set_guess",
 )
 STATIC_MAX_ZONES = 65536
-KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual", "faces", "zone_const")
+KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual", "faces", "zone_const", "mlp")
 
 
 class GrimGrid(ctypes.Structure):
@@ -54,7 +56,7 @@ class GrimStats(ctypes.Structure):
     _fields_ = [("zones", ctypes.c_ulonglong), ("failed", ctypes.c_ulonglong), ("iters", ctypes.c_ulonglong),
                 ("evals64", ctypes.c_ulonglong), ("evals32", ctypes.c_ulonglong), ("lu64", ctypes.c_ulonglong),
                 ("lu32", ctypes.c_ulonglong), ("hist", ctypes.c_ulonglong * 32), ("max_res", ctypes.c_double),
-                ("launches", ctypes.c_ulonglong)]
+                ("launches", ctypes.c_ulonglong), ("fallbacks", ctypes.c_ulonglong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
@@ -91,6 +93,17 @@ def load():
                                      ctypes.POINTER(GrimPhysics), ctypes.POINTER(GrimSolver), vp, vp, vp, dp]
     lib.grim_profile.argtypes = [vp, i]
     lib.grim_math_selftest.argtypes = [i, ctypes.POINTER(dp)]
+    ll, ull, fp = ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)
+    lib.grim_mlp_create.argtypes = [ull, ctypes.POINTER(vp)]
+    lib.grim_mlp_destroy.argtypes = [vp]
+    lib.grim_mlp_destroy.restype = None
+    lib.grim_mlp_get_params.argtypes = [vp, vp, vp]
+    lib.grim_mlp_set_params.argtypes = [vp, vp, vp]
+    lib.grim_mlp_fit_norm.argtypes = [vp, vp, vp, ll]
+    lib.grim_mlp_train.argtypes = [vp, vp, vp, ll, i, i, dp, ull, ctypes.POINTER(dp)]
+    lib.grim_mlp_gradient.argtypes = [vp, vp, vp, ll, vp, ctypes.POINTER(dp)]
+    lib.grim_mlp_sample.argtypes = [vp, vp, vp, vp, vp]
+    lib.grim_set_guess.argtypes = [vp, vp, dp]
     lib.grim_kernel_times.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_ulonglong)]
     _lib = lib
     return lib
@@ -196,6 +209,16 @@ class Grim:
         self._check(self.lib.grim_kernel_times(self.h, ms, n), "grim_kernel_times")
         return {KERNEL_CLASSES[k]: (ms[k], n[k]) for k in range(len(KERNEL_CLASSES)) if n[k]}
 
+    def set_guess(self, mlp, accept: float = 1e-7):
+        """Start Newton from the MLP's prediction (None: from P_n)."""
+        self._check(self.lib.grim_set_guess(self.h, mlp.h if mlp is not None else None, accept), "grim_set_guess")
+        self._mlp = mlp
+
+    def mlp_sample(self, P_n, P_conv, X, Y=None):
+        """Features (and targets) of the last explicit stage into float32 X [N, 32], Y [N, 16]."""
+        self._check(self.lib.grim_mlp_sample(self.h, _f64(P_n), _f64(P_conv) if P_conv is not None else None,
+                                             _ptr(X), _ptr(Y)), "grim_mlp_sample")
+
     def reset_stats(self):
         self._check(self.lib.grim_reset_stats(self.h), "grim_reset_stats")
 
@@ -229,3 +252,62 @@ def math_selftest(n: int = 1 << 20) -> float:
     if rc != 0:
         raise RuntimeError(f"grim_math_selftest failed: {lib.grim_strerror(rc).decode()}")
     return out.value
+
+
+class MLP:
+    """Learned initial guess (grim_mlp_*): training and parameters on the device."""
+
+    def __init__(self, seed: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.grim_mlp_create(seed, ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"grim_mlp_create failed: {self.lib.grim_strerror(rc).decode()}")
+        self.h = h
+        self.nparam = int(self.lib.grim_mlp_param_count())
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} failed: {self.lib.grim_strerror(rc).decode()}")
+
+    def get_params(self):
+        p = np.empty(self.nparam, dtype=np.float32)
+        n = np.empty(96, dtype=np.float32)
+        self._check(self.lib.grim_mlp_get_params(self.h, p.ctypes.data_as(ctypes.c_void_p),
+                                                 n.ctypes.data_as(ctypes.c_void_p)), "grim_mlp_get_params")
+        return p, n
+
+    def set_params(self, params=None, norm=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        n = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        self._check(self.lib.grim_mlp_set_params(self.h, p.ctypes.data_as(ctypes.c_void_p) if p is not None else None,
+                                                 n.ctypes.data_as(ctypes.c_void_p) if n is not None else None),
+                    "grim_mlp_set_params")
+
+    def fit_norm(self, X, Y):
+        self._check(self.lib.grim_mlp_fit_norm(self.h, _ptr(X), _ptr(Y), X.shape[0]), "grim_mlp_fit_norm")
+
+    def train(self, X, Y, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0) -> float:
+        loss = ctypes.c_double()
+        self._check(self.lib.grim_mlp_train(self.h, _ptr(X), _ptr(Y), X.shape[0], batch, steps, lr, seed,
+                                            ctypes.byref(loss)), "grim_mlp_train")
+        return loss.value
+
+    def gradient(self, X, Y):
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.grim_mlp_gradient(self.h, _ptr(X), _ptr(Y), X.shape[0],
+                                               g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss)),
+                    "grim_mlp_gradient")
+        return g, loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grim_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,46 @@
+"""Training driver for the learned initial guess (host orchestration only).
+
+Collects (features, targets) from converged stages of the library's own
+float64 solver, fits the standardisation and runs the device Adam steps with
+a step-decayed learning rate.  Every step of data generation and training
+runs in libgrim's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from .grim import MLP, Grim, GRIM_FP64
+
+
+def collect(prob, P, dt: float, steps: int, device, tol: float = 1e-12):
+    """Features [M, 32] and targets [M, 16] (float32, device) of both stages of
+    `steps` float64 steps from the state P (numpy [10, n3, n2, n1]), solved
+    to `tol`; M = 2 * steps * zones.  Returns (X, Y, final state)."""
+    g = Grim(prob.with_(tol=tol), precision=GRIM_FP64)
+    a = torch.from_numpy(P).to(device)
+    half = torch.empty_like(a)
+    full = torch.empty_like(a)
+    N = prob.zones
+    X = torch.empty((2 * steps * N, 32), dtype=torch.float32, device=device)
+    Y = torch.empty((2 * steps * N, 16), dtype=torch.float32, device=device)
+    k = 0
+    for _ in range(steps):
+        for PE, dts, out in ((a, 0.5 * dt, half), (half, dt, full)):
+            g.stage(a, PE, dts, out)
+            g.mlp_sample(a, out, X[k * N:(k + 1) * N], Y[k * N:(k + 1) * N])
+            k += 1
+        a, full = full, a
+    g.close()
+    return X, Y, a
+
+
+def train(X, Y, steps: int = 6000, batch: int = 4096, lr: float = 3e-3, halvings: int = 3, seed: int = 1):
+    """A freshly initialised MLP trained with Adam; the learning rate halves
+    `halvings` times at equal intervals.  Returns (mlp, losses per interval)."""
+    m = MLP(seed=seed)
+    m.fit_norm(X, Y)
+    parts = halvings + 1
+    losses = []
+    for k in range(parts):
+        losses.append(m.train(X, Y, steps=steps // parts, batch=batch, lr=lr * 0.5 ** k, seed=seed * 1000 + k))
+    return m, losses
