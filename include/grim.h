@@ -202,6 +202,43 @@ int grim_step_static(const grim_grid* grid, const grim_metric* metric, const gri
  * device buffer; synchronises the device. */
 int grim_peak_flops(double* fp64_tflops, double* fp32_tflops);
 
+/* ---- Launch shapes, compaction, graphs. */
+/* Launch shape of a context.  newton_bs: threads per block of the Newton
+ * kernels (32, 64 or 128).  newton_kcut: after this many Newton updates a
+ * zone that has not converged leaves the in-order kernel for a queue that a
+ * persistent kernel works through densely, so that a few slow zones do not
+ * hold whole warps (>= k_max: no queue).  faces_bs, zone_bs: threads per
+ * block of the face-flux and zone-constant kernels (64, 128 or 256). */
+typedef struct {
+  int newton_bs, newton_kcut, faces_bs, zone_bs;
+} grim_tuning;
+
+int grim_get_tuning(grim_ctx* ctx, grim_tuning* out);
+/* GRIM_EINVAL for a value outside the sets above (newton_kcut >= 1). */
+int grim_set_tuning(grim_ctx* ctx, const grim_tuning* tuning);
+
+/* Choose the launch shape by timing grim_step from the device state P with
+ * step dt (P is not modified): each field of grim_tuning in turn over its
+ * allowed values, the others held, keeping the fastest (CUDA events, median
+ * of 3 steps after one warm-up step).  With cache_path non-NULL, a line of
+ * that text file (one JSON object per line, keyed by device name, grid,
+ * precision, reconstruction, closures and whether a learned guess is set)
+ * is used instead when present, and the result is written there otherwise.
+ * Sets the context's tuning, writes it to *out and the step time to
+ * *step_ms (either may be NULL); resets the statistics.  Allocates and
+ * frees one scratch state; synchronises the stream.  Errors: GRIM_EINVAL,
+ * GRIM_ECUDA, GRIM_ENOMEM; an unreadable or unwritable cache file is
+ * ignored. */
+int grim_autotune(grim_ctx* ctx, const double* P, double dt, const char* cache_path, grim_tuning* out,
+                  double* step_ms);
+
+/* enable != 0: grim_step (and grim_step_host) replays a CUDA graph of the
+ * step's launches, captured on the second call with the same (P_in, P_out,
+ * dt, tuning, learned guess); up to four graphs are kept per context.  The
+ * first call after enabling runs eagerly.  Ignored while profiling
+ * (grim_profile). */
+int grim_use_graphs(grim_ctx* ctx, int enable);
+
 /* ---- Learned initial guess.  The paper starts each Newton solve from P_n
  * (§3); these calls add a small MLP that predicts the stage change of the
  * primitives, with P_n kept as the fallback.  Network 30 -> 128 -> 128 ->

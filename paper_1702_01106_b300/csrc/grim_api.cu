@@ -1,7 +1,9 @@
 // C ABI of the grim library (declarations and documentation: include/grim.h).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <string>
 #include <vector>
 
 #include "grim_dev.cuh"
@@ -16,12 +18,14 @@ cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, 
                             cudaStream_t st);
 cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cudaStream_t st);
 long long face_scratch_doubles(int n1, int n2);
-cudaError_t launch_faces(const Params& p, const double* PE, double* faces, cudaStream_t st);
+cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, cudaStream_t st);
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                              double* K, double* P0, double* faces, double* cache, int mode, cudaStream_t st);
+                              double* K, double* P0, double* faces, double* cache, int mode, int bs,
+                              cudaStream_t st);
 long long pn_cache_doubles(long long N);
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
-                             Counters* cnt, const double* Pfb, double accept, cudaStream_t st);
+                             Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
+                             int* qcount, cudaStream_t st);
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const double* K, const double* Pn, const double* Un, const grim_mlp* m,
@@ -33,7 +37,21 @@ using grim::Params;
 struct grim_ctx {
   Params p;
   int precision;
-  cudaStream_t stream;
+  cudaStream_t stream;        // the caller's stream
+  cudaStream_t cur;           // where launches go: stream, or cap while capturing
+  cudaStream_t cap = nullptr; // private stream for graph capture
+  grim_tuning tune{64, 2, 128, 128};
+  int* queue = nullptr;       // zones left for the queue kernel
+  int* qcount = nullptr;      // their number
+  bool graphs = false, warmed = false;
+  grim_tuning warm_tune{};    // launch shape and guess of the last eager step: every
+  bool warm_mlp = false;      // kernel a capture records has been configured
+  struct Graph {
+    const double* in; double* out; double dt; grim_mlp* mlp; double accept; grim_tuning tune;
+    cudaGraphExec_t exec; unsigned long long kernels, last;
+  };
+  std::vector<Graph> gcache;
+  unsigned long long gclock = 0;
   double* K = nullptr;        // NK x N stage constants
   double* faces = nullptr;    // face fluxes of one stage
   double* pncache = nullptr;  // P_n quantities shared by the two stages of a step
@@ -68,14 +86,14 @@ struct KernelMark {
   grim_ctx* c;
   int cls;
   cudaEvent_t a = nullptr;
-  KernelMark(grim_ctx* ctx, int k) : c(ctx), cls(k) {
-    c->launches++;
-    if (c->profile) { a = c->event(); cudaEventRecord(a, c->stream); }
+  KernelMark(grim_ctx* ctx, int k, int n = 1) : c(ctx), cls(k) {
+    c->launches += n;
+    if (c->profile) { a = c->event(); cudaEventRecord(a, c->cur); }
   }
   ~KernelMark() {
     if (c->profile) {
       cudaEvent_t b = c->event();
-      cudaEventRecord(b, c->stream);
+      cudaEventRecord(b, c->cur);
       c->marks.push_back({cls, a, b});
     }
   }
@@ -123,6 +141,10 @@ void grim_destroy(grim_ctx* ctx) {
   cudaFree(ctx->cnt);
   cudaFree(ctx->dev_in);
   cudaFree(ctx->dev_out);
+  cudaFree(ctx->queue);
+  cudaFree(ctx->qcount);
+  for (auto& g : ctx->gcache) cudaGraphExecDestroy(g.exec);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
   for (auto& m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
@@ -161,6 +183,7 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   p.N = (long long)grid->n1 * grid->n2 * grid->n3;
   ctx->precision = solver->precision;
   ctx->stream = (cudaStream_t)stream;
+  ctx->cur = ctx->stream;
   const size_t N = (size_t)p.N;
   cudaError_t e;
   if ((e = cudaMalloc(&ctx->K, sizeof(double) * grim::NK * N)) != cudaSuccess ||
@@ -168,7 +191,10 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
       (e = cudaMalloc(&ctx->faces, sizeof(double) * grim::face_scratch_doubles(p.n1, p.n2))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->pncache, sizeof(double) * grim::pn_cache_doubles(p.N))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->iters, N)) != cudaSuccess || (e = cudaMalloc(&ctx->status, N)) != cudaSuccess ||
-      (e = cudaMalloc(&ctx->cnt, sizeof(grim::Counters))) != cudaSuccess) {
+      (e = cudaMalloc(&ctx->cnt, sizeof(grim::Counters))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->queue, sizeof(int) * N)) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->qcount, sizeof(int))) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking)) != cudaSuccess) {
     grim_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
   }
@@ -185,12 +211,12 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
                         double* Pout, int mode) {
   {
     KernelMark m(ctx, GRIM_K_FACES);
-    GRIM_CUDA(grim::launch_faces(ctx->p, PE, ctx->faces, ctx->stream), "face kernel");
+    GRIM_CUDA(grim::launch_faces(ctx->p, PE, ctx->faces, ctx->tune.faces_bs, ctx->cur), "face kernel");
   }
   {
     KernelMark m(ctx, GRIM_K_ZONECONST);
     GRIM_CUDA(grim::launch_zone_const(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->faces, ctx->pncache, mode,
-                                      ctx->stream),
+                                      ctx->tune.zone_bs, ctx->cur),
               "zone-constant kernel");
   }
   return GRIM_OK;
@@ -203,14 +229,15 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
   const bool learned = ctx->mlp && !guess;
   if (learned) {
     KernelMark m(ctx, GRIM_K_MLP);
-    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->K, Pn, mode ? ctx->pncache : nullptr, ctx->mlp, Pout, ctx->stream),
+    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->K, Pn, mode ? ctx->pncache : nullptr, ctx->mlp, Pout, ctx->cur),
               "mlp kernel");
   }
   {
-    KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64);
+    const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
+    KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64, cfg.kcut < ctx->p.kmax ? 2 : 1);
     GRIM_CUDA(grim::launch_newton_fb(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
                                      status ? status : ctx->status, ctx->cnt, learned ? Pn : nullptr, ctx->accept,
-                                     ctx->stream),
+                                     cfg, ctx->queue, ctx->qcount, ctx->cur),
               "newton kernel");
   }
   return GRIM_OK;
@@ -224,13 +251,207 @@ int grim_stage(grim_ctx* ctx, const double* P_n, const double* P_E, double dts, 
   return run_stage(ctx, P_n, P_E, dts, guess, P_out, iters, status);
 }
 
-int grim_step(grim_ctx* ctx, const double* P_in, double* P_out, double dt) {
-  if (!ctx || !P_in || !P_out || !(dt > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_step: bad argument");
+static int step_launches(grim_ctx* ctx, const double* P_in, double* P_out, double dt) {
   // The half step (P^E = P_n) caches the P_n quantities the full step reuses.
   int rc = run_stage(ctx, P_in, P_in, 0.5 * dt, nullptr, ctx->Ph, nullptr, nullptr, 1);
   if (rc) return rc;
   // The full stage reads P_n only at each zone itself, so P_out may alias P_in.
   return run_stage(ctx, P_in, ctx->Ph, dt, nullptr, P_out, nullptr, nullptr, 2);
+}
+
+static bool same_tuning(const grim_tuning& a, const grim_tuning& b) {
+  return a.newton_bs == b.newton_bs && a.newton_kcut == b.newton_kcut && a.faces_bs == b.faces_bs &&
+         a.zone_bs == b.zone_bs;
+}
+
+// Capture the step's launches on the private stream into an executable graph.
+static int capture_step(grim_ctx* ctx, const double* P_in, double* P_out, double dt, grim_ctx::Graph& g) {
+  GRIM_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  const unsigned long long before = ctx->launches;
+  ctx->cur = ctx->cap;
+  const int rc = step_launches(ctx, P_in, P_out, dt);
+  ctx->cur = ctx->stream;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap, &graph);
+  g.kernels = ctx->launches - before;
+  ctx->launches = before;
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (e != cudaSuccess) return fail(ctx, GRIM_ECUDA, "end capture", e);
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return fail(ctx, GRIM_ECUDA, "graph instantiate", ei);
+  g.in = P_in; g.out = P_out; g.dt = dt; g.mlp = ctx->mlp; g.accept = ctx->accept; g.tune = ctx->tune;
+  return GRIM_OK;
+}
+
+int grim_step(grim_ctx* ctx, const double* P_in, double* P_out, double dt) {
+  if (!ctx || !P_in || !P_out || !(dt > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_step: bad argument");
+  if (!ctx->graphs || ctx->profile || !ctx->warmed || !same_tuning(ctx->warm_tune, ctx->tune) ||
+      ctx->warm_mlp != (ctx->mlp != nullptr)) {
+    const int rc = step_launches(ctx, P_in, P_out, dt);
+    if (!rc) { ctx->warmed = true; ctx->warm_tune = ctx->tune; ctx->warm_mlp = ctx->mlp != nullptr; }
+    return rc;
+  }
+  grim_ctx::Graph* hit = nullptr;
+  for (auto& g : ctx->gcache)
+    if (g.in == P_in && g.out == P_out && g.dt == dt && g.mlp == ctx->mlp && g.accept == ctx->accept &&
+        same_tuning(g.tune, ctx->tune))
+      hit = &g;
+  if (!hit) {
+    grim_ctx::Graph g{};
+    const int rc = capture_step(ctx, P_in, P_out, dt, g);
+    if (rc) return rc;
+    if (ctx->gcache.size() >= 4) {  // drop the least recently used
+      auto lru = std::min_element(ctx->gcache.begin(), ctx->gcache.end(),
+                                  [](const grim_ctx::Graph& a, const grim_ctx::Graph& b) { return a.last < b.last; });
+      cudaGraphExecDestroy(lru->exec);
+      ctx->gcache.erase(lru);
+    }
+    ctx->gcache.push_back(g);
+    hit = &ctx->gcache.back();
+  }
+  hit->last = ++ctx->gclock;
+  GRIM_CUDA(cudaGraphLaunch(hit->exec, ctx->stream), "graph launch");
+  ctx->launches += hit->kernels;
+  return GRIM_OK;
+}
+
+int grim_use_graphs(grim_ctx* ctx, int enable) {
+  if (!ctx) return GRIM_EINVAL;
+  ctx->graphs = enable != 0;
+  return GRIM_OK;
+}
+
+static bool valid_tuning(const grim_tuning& t) {
+  auto in = [](int v, std::initializer_list<int> s) { return std::find(s.begin(), s.end(), v) != s.end(); };
+  return in(t.newton_bs, {32, 64, 128}) && t.newton_kcut >= 1 && in(t.faces_bs, {64, 128, 256}) &&
+         in(t.zone_bs, {64, 128, 256});
+}
+
+int grim_get_tuning(grim_ctx* ctx, grim_tuning* out) {
+  if (!ctx || !out) return GRIM_EINVAL;
+  *out = ctx->tune;
+  return GRIM_OK;
+}
+
+int grim_set_tuning(grim_ctx* ctx, const grim_tuning* t) {
+  if (!ctx || !t || !valid_tuning(*t)) return fail(ctx, GRIM_EINVAL, "grim_set_tuning: value outside the allowed set");
+  ctx->tune = *t;
+  return GRIM_OK;
+}
+
+// Key of a tuning-cache line: what the launch shapes depend on.
+static std::string tuning_key(grim_ctx* ctx) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  cudaGetDevice(&dev);
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) prop.name[0] = 0;
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|%dx%dx%d|prec%d|recon%d|cond%d|visc%d|ho%d|mlp%d|kmax%d", prop.name, ctx->p.n1,
+           ctx->p.n2, ctx->p.n3, ctx->precision, ctx->p.recon, ctx->p.cond, ctx->p.visc, ctx->p.ho,
+           ctx->mlp ? 1 : 0, ctx->p.kmax);
+  for (char* c = buf; *c; c++)
+    if (*c == '"' || *c == '\\') *c = '_';
+  return buf;
+}
+
+static bool read_cached_tuning(const char* path, const std::string& key, grim_tuning& t, double& ms) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  const std::string tag = "\"key\": \"" + key + "\"";
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    if (!std::strstr(line, tag.c_str())) continue;
+    const char* q = std::strstr(line, "\"newton_bs\":");
+    grim_tuning c;
+    double m = 0.0;
+    if (q && std::sscanf(q, "\"newton_bs\": %d, \"newton_kcut\": %d, \"faces_bs\": %d, \"zone_bs\": %d, \"step_ms\": %lf",
+                         &c.newton_bs, &c.newton_kcut, &c.faces_bs, &c.zone_bs, &m) == 5 &&
+        valid_tuning(c)) {
+      t = c; ms = m; found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+static void write_cached_tuning(const char* path, const std::string& key, const grim_tuning& t, double ms) {
+  std::vector<std::string> keep;
+  const std::string tag = "\"key\": \"" + key + "\"";
+  if (FILE* f = std::fopen(path, "r")) {
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f))
+      if (!std::strstr(line, tag.c_str()) && line[0] == '{') keep.push_back(line);
+    std::fclose(f);
+  }
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (auto& l : keep) std::fputs(l.c_str(), f);
+  std::fprintf(f, "{%s, \"newton_bs\": %d, \"newton_kcut\": %d, \"faces_bs\": %d, \"zone_bs\": %d, \"step_ms\": %.6f}\n",
+               tag.c_str(), t.newton_bs, t.newton_kcut, t.faces_bs, t.zone_bs, ms);
+  std::fclose(f);
+}
+
+// Median of 3 timed steps after one warm-up step, eagerly launched.
+static int time_steps(grim_ctx* ctx, const double* P, double* out, double dt, double& ms) {
+  cudaEvent_t a = ctx->event(), b = ctx->event();
+  float t[3];
+  int rc = step_launches(ctx, P, out, dt);
+  for (int i = 0; i < 3 && !rc; i++) {
+    cudaEventRecord(a, ctx->stream);
+    rc = step_launches(ctx, P, out, dt);
+    cudaEventRecord(b, ctx->stream);
+    if (!rc && cudaEventSynchronize(b) != cudaSuccess) rc = fail(ctx, GRIM_ECUDA, "autotune timing");
+    if (!rc) cudaEventElapsedTime(&t[i], a, b);
+  }
+  ctx->pool.push_back(a);
+  ctx->pool.push_back(b);
+  if (rc) return rc;
+  std::sort(t, t + 3);
+  ms = t[1];
+  return GRIM_OK;
+}
+
+int grim_autotune(grim_ctx* ctx, const double* P, double dt, const char* cache_path, grim_tuning* out,
+                  double* step_ms) {
+  if (!ctx || !P || !(dt > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_autotune: bad argument");
+  const std::string key = tuning_key(ctx);
+  grim_tuning best = ctx->tune;
+  double best_ms = 0.0;
+  if (!(cache_path && read_cached_tuning(cache_path, key, best, best_ms))) {
+    double* out_state = nullptr;
+    cudaError_t e = cudaMalloc(&out_state, sizeof(double) * grim::NV * (size_t)ctx->p.N);
+    if (e != cudaSuccess) return fail(ctx, GRIM_ENOMEM, "grim_autotune: scratch state", e);
+    const bool prof = ctx->profile;
+    ctx->profile = false;
+    int rc = time_steps(ctx, P, out_state, dt, best_ms);
+    const int kmax = ctx->p.kmax;
+    const std::vector<int> sets[4] = {{32, 64, 128}, {1, 2, 3, kmax > 3 ? kmax : 4}, {64, 128, 256}, {64, 128, 256}};
+    for (int f = 0; f < 4 && !rc; f++) {
+      for (int v : sets[f]) {
+        grim_tuning c = best;
+        int* field = f == 0 ? &c.newton_bs : f == 1 ? &c.newton_kcut : f == 2 ? &c.faces_bs : &c.zone_bs;
+        if (*field == v) continue;
+        *field = v;
+        ctx->tune = c;
+        double ms = 0.0;
+        rc = time_steps(ctx, P, out_state, dt, ms);
+        if (rc) break;
+        if (ms < best_ms) { best_ms = ms; best = c; }
+      }
+    }
+    ctx->profile = prof;
+    cudaFree(out_state);
+    if (rc) { ctx->tune = best; return rc; }
+    if (cache_path) write_cached_tuning(cache_path, key, best, best_ms);
+  }
+  ctx->tune = best;
+  if (out) *out = best;
+  if (step_ms) *step_ms = best_ms;
+  GRIM_CUDA(cudaMemsetAsync(ctx->cnt, 0, sizeof(grim::Counters), ctx->stream), "stats reset");
+  GRIM_CUDA(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  return GRIM_OK;
 }
 
 int grim_step_host(grim_ctx* ctx, const double* P_in_host, double* P_out_host, double dt) {

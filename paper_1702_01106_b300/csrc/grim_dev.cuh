@@ -44,6 +44,14 @@ struct Params {
   long long N;
 };
 
+// Launch shape of the Newton solves: threads per block (32, 64 or 128) and
+// the update count after which unconverged zones move to the queue kernel
+// (>= k_max: no queue).
+struct NewtonCfg {
+  int bs;
+  int kcut;
+};
+
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };
 enum { RECON_MC = 0, RECON_WENO5 = 1 };
 

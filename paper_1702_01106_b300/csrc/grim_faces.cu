@@ -191,8 +191,9 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   for (int v = 0; v < NV; v++) out[v * plane] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
 }
 
-__global__ void __launch_bounds__(128) face_flux_2d(const __grid_constant__ Params p,
-                                                   const __grid_constant__ ExpArgs a) {
+template <int BS>
+__global__ void __launch_bounds__(BS) face_flux_2d(const __grid_constant__ Params p,
+                                                  const __grid_constant__ ExpArgs a) {
   const long long nf1 = (long long)(p.n1 + 1) * (p.n2 + 2);
   const long long nf2 = (long long)(p.n1 + 2) * (p.n2 + 1);
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,8 +226,9 @@ __device__ __forceinline__ void derived_at(const Params& p, const double* PE, in
   u[1] = v1; u[2] = v2; u[3] = v3;
 }
 
-__global__ void __launch_bounds__(128) zone_const_2d(const __grid_constant__ Params p,
-                                                    const __grid_constant__ ExpArgs a) {
+template <int BS>
+__global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Params p,
+                                                   const __grid_constant__ ExpArgs a) {
   const long long N = p.N;
   const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= N) return;
@@ -421,11 +423,18 @@ void explicit_args(const Params& p, const double* Pn, const double* PE, const do
   a.F2 = faces + (long long)NV * (p.n1 + 1) * (p.n2 + 2);
 }
 
-cudaError_t launch_faces(const Params& p, const double* PE, double* faces, cudaStream_t st) {
+// bs: threads per block, 64, 128 or 256.
+cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, cudaStream_t st) {
   ExpArgs a;
   explicit_args(p, nullptr, PE, nullptr, 1.0, nullptr, nullptr, faces, a);
   const long long nf = (long long)(p.n1 + 1) * (p.n2 + 2) + (long long)(p.n1 + 2) * (p.n2 + 1);
-  face_flux_2d<<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(p, a);
+  const unsigned nb = (unsigned)((nf + bs - 1) / bs);
+  switch (bs) {
+    case 64: face_flux_2d<64><<<nb, 64, 0, st>>>(p, a); break;
+    case 128: face_flux_2d<128><<<nb, 128, 0, st>>>(p, a); break;
+    case 256: face_flux_2d<256><<<nb, 256, 0, st>>>(p, a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -434,12 +443,19 @@ long long pn_cache_doubles(long long N) { return (long long)NCACHE * N; }
 // mode: 0 general stage, 1 half step (P_E == P_n; fills cache), 2 full step
 // of the same step (reads cache and K_U).
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                              double* K, double* P0, double* faces, double* cache, int mode, cudaStream_t st) {
+                              double* K, double* P0, double* faces, double* cache, int mode, int bs,
+                              cudaStream_t st) {
   ExpArgs a;
   explicit_args(p, Pn, PE, guess, dts, K, P0, faces, a);
   a.cache = cache;
   a.mode = cache ? mode : 0;
-  zone_const_2d<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, a);
+  const unsigned nb = (unsigned)((p.N + bs - 1) / bs);
+  switch (bs) {
+    case 64: zone_const_2d<64><<<nb, 64, 0, st>>>(p, a); break;
+    case 128: zone_const_2d<128><<<nb, 128, 0, st>>>(p, a); break;
+    case 256: zone_const_2d<256><<<nb, 256, 0, st>>>(p, a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

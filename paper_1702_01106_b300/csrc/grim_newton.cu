@@ -238,19 +238,24 @@ __device__ __forceinline__ double sum_sq10(const double* r) {
 
 struct ZoneResult {
   int iters, status, evals64, evals32, lu64, lu32;
+  int done;       // Newton updates made by this call (iters counts from the zone's first)
+  bool pending;   // stopped at kstop, unconverged: the zone continues in the queue kernel
   double res;
 };
 
-// Newton on one zone, starting from P (updated in place).  kd: the zone's
-// float64 constants in shared memory (stride BS); kf: their float copies.
-// Pfb (non-NULL with a learned start): the plain start P_n, whose magnetic
-// components are those of P; if the learned start's max|r| exceeds
-// accept_bits the plain start is evaluated too and the smaller |r|^2 wins.
+// Newton on one zone, starting from P (updated in place) after k0 updates
+// made by an earlier call; stops unconverged (o.pending) once the zone has
+// made kstop updates, kstop < k_max.  kd: the zone's float64 constants in
+// shared memory (stride BS); kf: their float copies.  Pfb (non-NULL with a
+// learned start): the plain start P_n, whose magnetic components are those
+// of P; if the learned start's max|r| exceeds accept_bits the plain start is
+// evaluated too and the smaller |r|^2 wins.
 template <bool MIXED, int BS>
 __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double* kd, const float* kf, double P[NV],
                                                   void* jac, const double* Pfb, long long fb_stride,
-                                                  unsigned long long accept_bits, bool& fellback) {
-  ZoneResult o = {0, 0, 0, 0, 0, 0, 0.0};
+                                                  unsigned long long accept_bits, bool& fellback, int k0,
+                                                  int kstop) {
+  ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
   const RC<double> c64 = make_rc<double>(p);
   const KSm<double, BS> k64{kd};
   const unsigned long long tol_bits = abits(p.tol);
@@ -278,11 +283,12 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       f = fp;
     }
   }
-  int k = 0;
+  int k = k0;
   for (;;) {
     if (!finite_bits(f)) { o.status |= ST_NONFINITE; break; }
     if (max_abits10(r) <= tol_bits) break;
     if (k >= p.kmax) { o.status |= ST_MAXIT; break; }
+    if (k >= kstop) { o.pending = true; break; }
     double dP[NV];
     bool ok;
     if (!MIXED) {
@@ -344,6 +350,7 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
     k++;
   }
   o.iters = k;
+  o.done = k - k0;
   unsigned long long mb = max_abits10(r);
   o.res = __longlong_as_double((long long)mb);
   if (!(P[0] > 0.0) || !(P[1] > 0.0)) o.status |= ST_INADMISSIBLE;
@@ -356,24 +363,42 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   return v;
 }
 
+// Add one warp's zones to the counters.  Work counts (evaluations, LU
+// solves, updates, fallbacks) are added by every call; a zone's totals
+// (zones, failures, the update histogram, the residual maximum) only by the
+// call that finishes it.
 __device__ __forceinline__ void accumulate(Counters* c, const ZoneResult& o, bool active, bool fellback) {
   const int lane = threadIdx.x & 31;
+  const bool fin = active && !o.pending;
   unsigned long long e64 = active ? o.evals64 : 0, e32 = active ? o.evals32 : 0;
   unsigned long long l64 = active ? o.lu64 : 0, l32 = active ? o.lu32 : 0;
-  unsigned long long it = active ? o.iters : 0, fl = (active && o.status) ? 1 : 0, zn = active ? 1 : 0;
+  unsigned long long it = active ? o.done : 0, fl = (fin && o.status) ? 1 : 0, zn = fin ? 1 : 0;
+  const unsigned any = __ballot_sync(0xffffffffu, active);
   e64 = warp_sum(e64); e32 = warp_sum(e32); l64 = warp_sum(l64); l32 = warp_sum(l32);
   it = warp_sum(it); fl = warp_sum(fl); zn = warp_sum(zn);
-  if (lane == 0 && zn) {
+  if (lane == 0 && any) {
     atomicAdd(&c->evals64, e64); atomicAdd(&c->evals32, e32);
     atomicAdd(&c->lu64, l64); atomicAdd(&c->lu32, l32);
-    atomicAdd(&c->iters, it); atomicAdd(&c->failed, fl); atomicAdd(&c->zones, zn);
+    atomicAdd(&c->iters, it);
+    if (zn) { atomicAdd(&c->failed, fl); atomicAdd(&c->zones, zn); }
   }
   const unsigned fb = __ballot_sync(0xffffffffu, active && fellback);
   if (lane == 0 && fb) atomicAdd(&c->fallbacks, (unsigned long long)__popc(fb));
-  if (active) {
+  if (fin) {
     atomicAdd(&c->hist[o.iters < 31 ? o.iters : 31], 1ull);
     if (finite_bits(o.res)) atomicMax(&c->maxres_bits, (unsigned long long)__double_as_longlong(o.res));
   }
+}
+
+// Append the warp's pending zones to the queue (one atomic per warp).
+__device__ __forceinline__ void enqueue(int* queue, int* qcount, bool pending, long long z) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, pending);
+  if (!m) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(qcount, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pending) queue[base + __popc(m & ((1u << lane) - 1u))] = (int)z;
 }
 
 // Shared memory per thread: zone constants (NK doubles, plus NK floats for
@@ -386,11 +411,15 @@ template <bool MIXED, int BS> struct NewtonSmem {
   static constexpr size_t bytes = kd + kf + jac;
 };
 
+// One thread per zone, zones in order; each zone runs to convergence or to
+// kstop updates, after which it is appended to the queue (kstop >= k_max:
+// no queue).
 template <bool MIXED, int BS>
 __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Params p, const double* __restrict__ K,
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
-                                                   const double* __restrict__ Pfb, double accept) {
+                                                   const double* __restrict__ Pfb, double accept, int kstop,
+                                                   int* __restrict__ queue, int* __restrict__ qcount) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -399,7 +428,7 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
   const long long N = p.N;
   const long long z = (long long)blockIdx.x * BS + threadIdx.x;
   const bool active = z < N;
-  ZoneResult o = {0, 0, 0, 0, 0, 0, 0.0};
+  ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
   bool fellback = false;
   if (active) {
 #pragma unroll
@@ -411,13 +440,56 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
     double Pz[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-    o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, Pfb ? Pfb + z : nullptr, N, abits(accept), fellback);
+    o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, Pfb ? Pfb + z : nullptr, N, abits(accept), fellback, 0,
+                               kstop < p.kmax ? kstop : p.kmax);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
     status[z] = (uint8_t)o.status;
   }
+  if (queue) enqueue(queue, qcount, active && o.pending, z);
   accumulate(cnt, o, active, fellback);
+}
+
+// The zones queued by newton_dense, packed densely into warps: a persistent
+// grid strides over the queue and continues each zone from its state and
+// update count to convergence or k_max.
+template <bool MIXED, int BS>
+__global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Params p, const double* __restrict__ K,
+                                                   double* __restrict__ P, uint8_t* __restrict__ iters,
+                                                   uint8_t* __restrict__ status, Counters* __restrict__ cnt,
+                                                   const int* __restrict__ queue, const int* __restrict__ qcount) {
+  using S = NewtonSmem<MIXED, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* kd = (double*)smem_raw + threadIdx.x;
+  float* kf = (float*)(smem_raw + S::kd) + threadIdx.x;
+  void* jac = smem_raw + S::kd + S::kf;
+  const long long N = p.N;
+  const int count = *qcount;
+  for (int base = blockIdx.x * BS; base < count; base += gridDim.x * BS) {
+    const int q = base + (int)threadIdx.x;
+    const bool active = q < count;
+    ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
+    bool fellback = false;
+    if (active) {
+      const long long z = queue[q];
+#pragma unroll
+      for (int a = 0; a < NK; a++) {
+        const double x = __ldg(K + a * N + z);
+        kd[a * BS] = x;
+        if (MIXED) kf[a * BS] = (float)x;
+      }
+      double Pz[NV];
+#pragma unroll
+      for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
+      o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, nullptr, N, 0ull, fellback, iters[z], p.kmax);
+#pragma unroll
+      for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
+      iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
+      status[z] = (uint8_t)o.status;
+    }
+    accumulate(cnt, o, active, fellback);
+  }
 }
 
 // Evaluate the scaled (or raw) residual at Pk once per zone.
@@ -456,31 +528,71 @@ __global__ void rcp_check(int n, unsigned long long seed, double* worst) {
   atomicMax((unsigned long long*)worst, (unsigned long long)__double_as_longlong(rel));
 }
 
-template <bool MIXED, int BS>
-static cudaError_t launch_newton_t(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
-                                   Counters* cnt, const double* Pfb, double accept, cudaStream_t st) {
+template <bool MIXED, int BS> struct NewtonKernels {
   using S = NewtonSmem<MIXED, BS>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
+  static cudaError_t configure(int& qgrid) {
+    static bool done = false;
+    static int grid = 0;
+    if (!done) {
+      cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)S::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(newton_queue<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+      int dev = 0, sms = 0, per_sm = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue<MIXED, BS>, BS, S::bytes);
+      if (e != cudaSuccess) return e;
+      grid = sms * (per_sm > 0 ? per_sm : 1);
+      done = true;
+    }
+    qgrid = grid;
+    return cudaSuccess;
   }
-  const long long nb = (p.N + BS - 1) / BS;
-  newton_dense<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept);
-  return cudaGetLastError();
+  static cudaError_t launch(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
+                            Counters* cnt, const double* Pfb, double accept, int kcut, int* queue, int* qcount,
+                            cudaStream_t st) {
+    int qgrid = 0;
+    cudaError_t e = configure(qgrid);
+    if (e != cudaSuccess) return e;
+    const bool compact = queue && qcount && kcut < p.kmax;
+    if (compact && (e = cudaMemsetAsync(qcount, 0, sizeof(int), st)) != cudaSuccess) return e;
+    const long long nb = (p.N + BS - 1) / BS;
+    newton_dense<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
+                                                                 compact ? kcut : p.kmax, compact ? queue : nullptr,
+                                                                 qcount);
+    if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
+    newton_queue<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue, qcount);
+    return cudaGetLastError();
+  }
+};
+
+template <bool MIXED>
+static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
+                                   Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
+                                   int* qcount, cudaStream_t st) {
+  switch (cfg.bs) {
+    case 32: return NewtonKernels<MIXED, 32>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, st);
+    case 64: return NewtonKernels<MIXED, 64>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, st);
+    case 128: return NewtonKernels<MIXED, 128>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
+// Newton solves of one stage: the in-order kernel, then (cfg.kcut < k_max)
+// the queue kernel over the zones still unconverged after kcut updates.
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
-                             Counters* cnt, const double* Pfb, double accept, cudaStream_t st) {
-  if (mixed) return launch_newton_t<true, 64>(p, K, P, iters, status, cnt, Pfb, accept, st);
-  return launch_newton_t<false, 64>(p, K, P, iters, status, cnt, Pfb, accept, st);
+                             Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
+                             int* qcount, cudaStream_t st) {
+  if (mixed) return launch_newton_bs<true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, st);
+  return launch_newton_bs<false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, st);
 }
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                           Counters* cnt, cudaStream_t st) {
-  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, st);
+  const NewtonCfg cfg{64, 1 << 30};
+  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, st);
 }
 
 cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, int scaled, double dts, double* R,

@@ -25,6 +25,7 @@ EXPORTS = (
     "grim_profile", "grim_kernel_times", "grim_step_static", "grim_math_selftest",
     "grim_mlp_create", "grim_mlp_destroy", "grim_mlp_param_count", "grim_mlp_get_params", "grim_mlp_set_params",
     "grim_mlp_fit_norm", "grim_mlp_train", "grim_mlp_gradient", "grim_mlp_sample", "grim_set_guess",
+    "grim_get_tuning", "grim_set_tuning", "grim_autotune", "grim_use_graphs",
 )
 STATIC_MAX_ZONES = 65536
 KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual", "faces", "zone_const", "mlp")
@@ -50,6 +51,14 @@ class GrimSolver(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("eps_fd", ctypes.c_double),
                 ("eps_fd32", ctypes.c_double), ("k_max", ctypes.c_int), ("ls_max", ctypes.c_int),
                 ("fd32_central", ctypes.c_int)]
+
+
+class GrimTuning(ctypes.Structure):
+    _fields_ = [("newton_bs", ctypes.c_int), ("newton_kcut", ctypes.c_int), ("faces_bs", ctypes.c_int),
+                ("zone_bs", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class GrimStats(ctypes.Structure):
@@ -105,6 +114,10 @@ def load():
     lib.grim_mlp_sample.argtypes = [vp, vp, vp, vp, vp]
     lib.grim_set_guess.argtypes = [vp, vp, dp]
     lib.grim_kernel_times.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.grim_get_tuning.argtypes = [vp, ctypes.POINTER(GrimTuning)]
+    lib.grim_set_tuning.argtypes = [vp, ctypes.POINTER(GrimTuning)]
+    lib.grim_autotune.argtypes = [vp, vp, dp, ctypes.c_char_p, ctypes.POINTER(GrimTuning), ctypes.POINTER(dp)]
+    lib.grim_use_graphs.argtypes = [vp, i]
     _lib = lib
     return lib
 
@@ -221,6 +234,27 @@ class Grim:
 
     def reset_stats(self):
         self._check(self.lib.grim_reset_stats(self.h), "grim_reset_stats")
+
+    def tuning(self) -> dict:
+        t = GrimTuning()
+        self._check(self.lib.grim_get_tuning(self.h, ctypes.byref(t)), "grim_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        """Change fields of the launch shape (newton_bs, newton_kcut, faces_bs, zone_bs)."""
+        t = GrimTuning(**{**self.tuning(), **kw})
+        self._check(self.lib.grim_set_tuning(self.h, ctypes.byref(t)), "grim_set_tuning")
+
+    def autotune(self, P, dt: float, cache_path=None):
+        """grim_autotune: (tuning dict, step ms)."""
+        t, ms = GrimTuning(), ctypes.c_double()
+        path = cache_path.encode() if cache_path else None
+        self._check(self.lib.grim_autotune(self.h, _f64(P), dt, path, ctypes.byref(t), ctypes.byref(ms)),
+                    "grim_autotune")
+        return t.as_dict(), ms.value
+
+    def use_graphs(self, enable: bool = True):
+        self._check(self.lib.grim_use_graphs(self.h, int(enable)), "grim_use_graphs")
 
     def close(self):
         if getattr(self, "h", None):
