@@ -215,6 +215,53 @@ def time_device(g, a, b, dt, steps, warmup, world, torch):
     return ms, stats, g.kernel_times(), a
 
 
+def bench_batched(dev, mlp, torch, world, steps=3):
+    """64 independent linear-mode boxes of sides drawn from {128, 256, 512,
+    1024} (seeded), stepped together through grim_batch_step (one graph
+    launch per step after capture): zone-updates/s per arm."""
+    from paper_1702_01106_b300 import inputs
+    from paper_1702_01106_b300.grim import Batch, GRIM_FP64, GRIM_MIXED
+    boxes = inputs.batched_boxes()
+    probs = [b[0] for b in boxes]
+    dts = [b[2] for b in boxes]
+    zones = sum(p.zones for p in probs)
+    host = [torch.from_numpy(b[1]) for b in boxes]
+    out = {"boxes": len(boxes), "zones": zones, "sides": [p.n[0] for p in probs], "steps": steps,
+           "timing": "2 untimed steps (eager, graph capture), then CUDA events around the timed steps"}
+    for name, prec, learned in (("fp64", GRIM_FP64, False), ("mixed", GRIM_MIXED, False),
+                                ("mixed_learned", GRIM_MIXED, True)):
+        bt = Batch(probs, precision=prec)
+        if learned:
+            bt.set_guess(mlp, accept=1e-3)
+        A = [h.to(dev) for h in host]
+        B = [torch.empty_like(a) for a in A]
+        for _ in range(2):
+            bt.step(A, B, dts)
+            A, B = B, A
+        torch.cuda.synchronize()
+        bt.reset_stats()
+        l0 = bt.stats()["launches"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            bt.step(A, B, dts)
+            A, B = B, A
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+        s = bt.stats()
+        out[name] = {"value": world * zones / (ms * 1e-3), "ms_per_step": ms,
+                     "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]), "failed": s["failed"],
+                     "max_res": s["max_res"], "kernels_per_step": (s["launches"] - l0) / steps}
+        bt.close()
+        del A, B
+        torch.cuda.empty_cache()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed_learned"]["ms_per_step"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,6 +269,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true", help="skip the 64-box batched measurement")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -368,6 +416,8 @@ def main():
     e2e = {"value": world * N / e2e_s, "unit": "zone-updates/s", "h2d_bytes_per_step": int(P.nbytes),
            "d2h_bytes_per_step": int(P.nbytes)}
 
+    batched = None if args.skip_batched else bench_batched(dev, mlp, torch, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample, _ = cpu_baseline(prob, P, dt)
@@ -403,6 +453,7 @@ def main():
             "roofline": roof, "roofline_fp64_newton": roof_fp64,
             "peaks": {"fp64_tflops": p64, "fp32_tflops": p32, "hbm_gbs": peaks.get("hbm_gbs"),
                       "hbm_source": peak_kind},
+            "batched_64_boxes": batched,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_timed,
             "clocks": clocks,
         }

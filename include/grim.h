@@ -239,6 +239,33 @@ int grim_autotune(grim_ctx* ctx, const double* P, double dt, const char* cache_p
  * (grim_profile). */
 int grim_use_graphs(grim_ctx* ctx, int enable);
 
+/* ---- Batched boxes.  nbox independent grids (any sizes; one metric,
+ * physics and solver) stepped together: each box has its own context; a
+ * batched step forks the caller's stream onto up to 16 side streams, gives
+ * box i the side stream i mod 16, and joins them back, so that small boxes
+ * run concurrently.  From the second call on (graphs enabled, the default)
+ * the whole batched step is one CUDA graph launch, captured per distinct
+ * (P_in[], P_out[], dt[]) (two graphs kept: ping-pong buffers).  Results
+ * equal grim_step on each box. */
+typedef struct grim_batch grim_batch;
+
+/* Create nbox contexts (grids[0..nbox-1]); errors as grim_init. */
+int grim_batch_init(int nbox, const grim_grid* grids, const grim_metric* metric, const grim_physics* phys,
+                    const grim_solver* solver, void* stream, grim_batch** out);
+void grim_batch_destroy(grim_batch* batch);
+/* The context of box i (for grim_set_guess, grim_set_tuning, grim_stage...);
+ * owned by the batch. */
+int grim_batch_context(grim_batch* batch, int i, grim_ctx** out);
+/* One step of every box: P_in[i], P_out[i] device states of box i (P_out[i]
+ * may equal P_in[i]), dt[i] its step; host arrays of nbox entries. */
+int grim_batch_step(grim_batch* batch, const double* const* P_in, double* const* P_out, const double* dt);
+int grim_batch_use_graphs(grim_batch* batch, int enable);
+/* Counters summed over the boxes (max_res: the largest); launches counts the
+ * kernels of batched steps.  Synchronises the stream. */
+int grim_batch_get_stats(grim_batch* batch, grim_stats* out);
+int grim_batch_reset_stats(grim_batch* batch);
+const char* grim_batch_last_error(grim_batch* batch);
+
 /* ---- Learned initial guess.  The paper starts each Newton solve from P_n
  * (§3); these calls add a small MLP that predicts the stage change of the
  * primitives, with P_n kept as the fallback.  Network 30 -> 128 -> 128 ->

@@ -562,4 +562,190 @@ int grim_math_selftest(int n, double* max_rel_err) {
   return e == cudaSuccess ? GRIM_OK : GRIM_ECUDA;
 }
 
+// ---------------------------------------------------------------- batched boxes
+// Independent boxes of any sizes stepped together: one context per box, the
+// boxes' launch sequences spread round-robin over side streams forked from
+// the caller's stream (so small boxes run concurrently), the whole step
+// replayed as one CUDA graph once captured.
+struct grim_batch {
+  std::vector<grim_ctx*> box;
+  cudaStream_t stream = nullptr;           // the caller's stream
+  cudaStream_t cap = nullptr;              // capture origin
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;             // fork event + one join event per side stream
+  bool graphs = true, warmed = false;
+  struct Graph {
+    std::vector<const double*> in; std::vector<double*> out; std::vector<double> dt;
+    cudaGraphExec_t exec = nullptr; unsigned long long kernels = 0, last = 0;
+  };
+  std::vector<Graph> gcache;
+  unsigned long long clock = 0, launches = 0;
+  char err[256] = {0};
+};
+
+static int batch_fail(grim_batch* b, int code, const char* what, cudaError_t e = cudaSuccess) {
+  if (b) snprintf(b->err, sizeof(b->err), "%s%s%s", what, e != cudaSuccess ? ": " : "",
+                  e != cudaSuccess ? cudaGetErrorString(e) : "");
+  return code;
+}
+
+void grim_batch_destroy(grim_batch* b) {
+  if (!b) return;
+  for (auto c : b->box) grim_destroy(c);
+  for (auto& g : b->gcache) cudaGraphExecDestroy(g.exec);
+  for (auto s : b->side) cudaStreamDestroy(s);
+  for (auto e : b->ev) cudaEventDestroy(e);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+int grim_batch_init(int nbox, const grim_grid* grids, const grim_metric* metric, const grim_physics* phys,
+                    const grim_solver* solver, void* stream, grim_batch** out) {
+  if (!out) return GRIM_EINVAL;
+  *out = nullptr;
+  if (nbox < 1 || !grids) return GRIM_EINVAL;
+  grim_batch* b = new grim_batch();
+  b->stream = (cudaStream_t)stream;
+  for (int i = 0; i < nbox; i++) {
+    grim_ctx* c = nullptr;
+    const int rc = grim_init(&grids[i], metric, phys, solver, stream, &c);
+    if (rc) { grim_batch_destroy(b); return rc; }
+    b->box.push_back(c);
+  }
+  const int ns = nbox < 16 ? nbox : 16;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int i = 0; i < ns && e == cudaSuccess; i++) {
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->side.push_back(s);
+  }
+  for (int i = 0; i <= ns && e == cudaSuccess; i++) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev.push_back(ev);
+  }
+  if (e != cudaSuccess) { grim_batch_destroy(b); return GRIM_ECUDA; }
+  *out = b;
+  return GRIM_OK;
+}
+
+int grim_batch_context(grim_batch* b, int i, grim_ctx** out) {
+  if (!b || !out || i < 0 || i >= (int)b->box.size()) return GRIM_EINVAL;
+  *out = b->box[i];
+  return GRIM_OK;
+}
+
+int grim_batch_use_graphs(grim_batch* b, int enable) {
+  if (!b) return GRIM_EINVAL;
+  b->graphs = enable != 0;
+  return GRIM_OK;
+}
+
+// Fork from `origin` onto the side streams, launch every box, join back.
+static int batch_launches(grim_batch* b, cudaStream_t origin, const double* const* P_in, double* const* P_out,
+                          const double* dt, unsigned long long& kernels) {
+  const int ns = (int)b->side.size();
+  cudaError_t e = cudaEventRecord(b->ev[0], origin);
+  for (int s = 0; s < ns && e == cudaSuccess; s++) e = cudaStreamWaitEvent(b->side[s], b->ev[0], 0);
+  if (e != cudaSuccess) return batch_fail(b, GRIM_ECUDA, "batch fork", e);
+  int rc = GRIM_OK;
+  kernels = 0;
+  for (size_t i = 0; i < b->box.size() && !rc; i++) {
+    grim_ctx* c = b->box[i];
+    c->cur = b->side[i % ns];
+    const unsigned long long before = c->launches;
+    rc = step_launches(c, P_in[i], P_out[i], dt[i]);
+    kernels += c->launches - before;
+    c->cur = c->stream;
+    if (rc) batch_fail(b, rc, c->err);
+  }
+  for (int s = 0; s < ns; s++) {
+    cudaError_t e1 = cudaEventRecord(b->ev[1 + s], b->side[s]);
+    if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(origin, b->ev[1 + s], 0);
+    if (e1 != cudaSuccess && !rc) rc = batch_fail(b, GRIM_ECUDA, "batch join", e1);
+  }
+  return rc;
+}
+
+int grim_batch_step(grim_batch* b, const double* const* P_in, double* const* P_out, const double* dt) {
+  if (!b || !P_in || !P_out || !dt) return GRIM_EINVAL;
+  const size_t n = b->box.size();
+  for (size_t i = 0; i < n; i++)
+    if (!P_in[i] || !P_out[i] || !(dt[i] > 0.0)) return batch_fail(b, GRIM_EINVAL, "grim_batch_step: bad argument");
+  bool profiling = false;
+  for (auto c : b->box) profiling = profiling || c->profile;
+  if (!b->graphs || !b->warmed || profiling) {
+    unsigned long long k = 0;
+    const int rc = batch_launches(b, b->stream, P_in, P_out, dt, k);
+    b->launches += k;
+    if (!rc) b->warmed = true;
+    return rc;
+  }
+  grim_batch::Graph* hit = nullptr;
+  for (auto& g : b->gcache) {
+    bool same = true;
+    for (size_t i = 0; i < n && same; i++) same = g.in[i] == P_in[i] && g.out[i] == P_out[i] && g.dt[i] == dt[i];
+    if (same) hit = &g;
+  }
+  if (!hit) {
+    grim_batch::Graph g;
+    g.in.assign(P_in, P_in + n);
+    g.out.assign(P_out, P_out + n);
+    g.dt.assign(dt, dt + n);
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, GRIM_ECUDA, "begin capture", e);
+    const int rc = batch_launches(b, b->cap, P_in, P_out, dt, g.kernels);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return batch_fail(b, GRIM_ECUDA, "end capture", e);
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return batch_fail(b, GRIM_ECUDA, "graph instantiate", e);
+    if (b->gcache.size() >= 2) {
+      auto lru = std::min_element(b->gcache.begin(), b->gcache.end(),
+                                  [](const grim_batch::Graph& x, const grim_batch::Graph& y) { return x.last < y.last; });
+      cudaGraphExecDestroy(lru->exec);
+      b->gcache.erase(lru);
+    }
+    b->gcache.push_back(g);
+    hit = &b->gcache.back();
+  }
+  hit->last = ++b->clock;
+  cudaError_t e = cudaGraphLaunch(hit->exec, b->stream);
+  if (e != cudaSuccess) return batch_fail(b, GRIM_ECUDA, "graph launch", e);
+  b->launches += hit->kernels;
+  return GRIM_OK;
+}
+
+int grim_batch_get_stats(grim_batch* b, grim_stats* out) {
+  if (!b || !out) return GRIM_EINVAL;
+  grim_stats t;
+  std::memset(&t, 0, sizeof(t));
+  for (auto c : b->box) {
+    grim_stats s;
+    const int rc = grim_get_stats(c, &s);
+    if (rc) return rc;
+    t.zones += s.zones; t.failed += s.failed; t.iters += s.iters;
+    t.evals64 += s.evals64; t.evals32 += s.evals32; t.lu64 += s.lu64; t.lu32 += s.lu32;
+    for (int i = 0; i < 32; i++) t.hist[i] += s.hist[i];
+    t.max_res = std::max(t.max_res, s.max_res);
+    t.fallbacks += s.fallbacks;
+  }
+  t.launches = b->launches;
+  *out = t;
+  return GRIM_OK;
+}
+
+int grim_batch_reset_stats(grim_batch* b) {
+  if (!b) return GRIM_EINVAL;
+  for (auto c : b->box) {
+    const int rc = grim_reset_stats(c);
+    if (rc) return rc;
+  }
+  return GRIM_OK;
+}
+
+const char* grim_batch_last_error(grim_batch* b) { return b ? b->err : "no batch"; }
+
 }  // extern "C"

@@ -26,6 +26,8 @@ EXPORTS = (
     "grim_mlp_create", "grim_mlp_destroy", "grim_mlp_param_count", "grim_mlp_get_params", "grim_mlp_set_params",
     "grim_mlp_fit_norm", "grim_mlp_train", "grim_mlp_gradient", "grim_mlp_sample", "grim_set_guess",
     "grim_get_tuning", "grim_set_tuning", "grim_autotune", "grim_use_graphs",
+    "grim_batch_init", "grim_batch_destroy", "grim_batch_context", "grim_batch_step", "grim_batch_use_graphs",
+    "grim_batch_get_stats", "grim_batch_reset_stats", "grim_batch_last_error",
 )
 STATIC_MAX_ZONES = 65536
 KERNEL_CLASSES = ("explicit", "newton64", "newton32", "residual", "faces", "zone_const", "mlp")
@@ -118,6 +120,17 @@ def load():
     lib.grim_set_tuning.argtypes = [vp, ctypes.POINTER(GrimTuning)]
     lib.grim_autotune.argtypes = [vp, vp, dp, ctypes.c_char_p, ctypes.POINTER(GrimTuning), ctypes.POINTER(dp)]
     lib.grim_use_graphs.argtypes = [vp, i]
+    lib.grim_batch_init.argtypes = [i, ctypes.POINTER(GrimGrid), ctypes.POINTER(GrimMetric),
+                                    ctypes.POINTER(GrimPhysics), ctypes.POINTER(GrimSolver), vp, ctypes.POINTER(vp)]
+    lib.grim_batch_destroy.argtypes = [vp]
+    lib.grim_batch_destroy.restype = None
+    lib.grim_batch_context.argtypes = [vp, i, ctypes.POINTER(vp)]
+    lib.grim_batch_step.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(dp)]
+    lib.grim_batch_use_graphs.argtypes = [vp, i]
+    lib.grim_batch_get_stats.argtypes = [vp, ctypes.POINTER(GrimStats)]
+    lib.grim_batch_reset_stats.argtypes = [vp]
+    lib.grim_batch_last_error.argtypes = [vp]
+    lib.grim_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -259,6 +272,73 @@ class Grim:
     def close(self):
         if getattr(self, "h", None):
             self.lib.grim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent boxes stepped together (grim_batch_*): probs share
+    metric, physics and solver settings; grids may differ."""
+
+    def __init__(self, probs, precision: int = GRIM_FP64, stream=None, eps_fd32: float = EPS_FD32,
+                 fd32_central: int = FD32_CENTRAL):
+        import torch
+        self.lib = load()
+        cfgs = [_config(p, precision, eps_fd32, fd32_central) for p in probs]
+        grids = (GrimGrid * len(probs))(*[c[0] for c in cfgs])
+        _, m, ph, sv = cfgs[0]
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.n = len(probs)
+        h = ctypes.c_void_p()
+        rc = self.lib.grim_batch_init(self.n, grids, ctypes.byref(m), ctypes.byref(ph), ctypes.byref(sv),
+                                      ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"grim_batch_init failed: {self.lib.grim_strerror(rc).decode()}")
+        self.h = h
+        self._keep = []
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} failed ({self.lib.grim_strerror(rc).decode()}): "
+                               f"{self.lib.grim_batch_last_error(self.h).decode()}")
+
+    def step(self, P_in, P_out, dts):
+        vp = ctypes.c_void_p
+        pin = (vp * self.n)(*[_f64(t) for t in P_in])
+        pout = (vp * self.n)(*[_f64(t) for t in P_out])
+        d = (ctypes.c_double * self.n)(*dts)
+        self._check(self.lib.grim_batch_step(self.h, pin, pout, d), "grim_batch_step")
+
+    def use_graphs(self, enable: bool = True):
+        self._check(self.lib.grim_batch_use_graphs(self.h, int(enable)), "grim_batch_use_graphs")
+
+    def set_guess(self, mlp, accept: float = 1e-3):
+        for i in range(self.n):
+            c = ctypes.c_void_p()
+            self._check(self.lib.grim_batch_context(self.h, i, ctypes.byref(c)), "grim_batch_context")
+            rc = self.lib.grim_set_guess(c, mlp.h if mlp is not None else None, accept)
+            if rc != 0:
+                raise RuntimeError("grim_set_guess failed")
+        self._mlp = mlp
+
+    def stats(self) -> dict:
+        s = GrimStats()
+        self._check(self.lib.grim_batch_get_stats(self.h, ctypes.byref(s)), "grim_batch_get_stats")
+        return s.as_dict()
+
+    def reset_stats(self):
+        self._check(self.lib.grim_batch_reset_stats(self.h), "grim_batch_reset_stats")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grim_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
