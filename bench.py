@@ -29,6 +29,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "zone-updates/s at |R|<=1e-10 (mixed vs FP64 plain, 1 B300); % roofline"
 N_SIDE = 1024
+# bfloat16 MACs per zone of the learned-start network (32x128, 2 x 128x128,
+# 128x80), 2 flops each.
+MLP_FLOPS_PER_ZONE = 2 * (32 * 128 + 2 * 128 * 128 + 128 * 80)
+# DRAM bytes read + written per launch at 1024^2 from the ncu captures in
+# profiles/explicit_turbulent_box_1024.md and profiles/newton_turbulent_box_1024.md
+# (None once a kernel changes after its capture).
+NCU_TRAFFIC_BYTES = {"faces": 298.4e6, "zone_const": 642.0e6, "newton64": 428.4e6, "newton32": 427.6e6}
 TOL = 1e-10
 
 
@@ -187,6 +194,43 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def nvtx_push(torch, name):
+    """Mark the timed region (ncu --nvtx --nvtx-include "timed/" profiles only it)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop(torch):
+    try:
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+def profile_case(args, dev, torch):
+    """--case-only: the float64 and mixed steps of the turbulent box alone
+    (autotuned, warmed up, then `--steps` steps in the NVTX range "timed"),
+    for ncu captures of single kernels; prints one JSON line of timings."""
+    from paper_1702_01106_b300 import inputs
+    from paper_1702_01106_b300.grim import Grim, GRIM_FP64, GRIM_MIXED
+    prob = inputs.turbulent_box_problem(args.side, tol=TOL)
+    P = inputs.turbulent_box_state(prob)
+    dt = 0.5 / args.side
+    out = {"case": f"turbulent box {args.side}x{args.side}", "steps": args.steps}
+    for name, prec in (("fp64", GRIM_FP64), ("mixed", GRIM_MIXED)):
+        g = Grim(prob, precision=prec)
+        a = torch.from_numpy(P).to(dev)
+        b = torch.empty_like(a)
+        out[name + "_tuning"] = g.autotune(a, dt)[0]
+        ms, st, kt, _ = time_device(g, a, b, dt, args.steps, args.warmup, 1, torch)
+        out[name] = {"ms_per_step": ms, "kernel_ms": {k: v[0] / v[1] for k, v in kt.items()},
+                     "iters_per_zone_stage": st["iters"] / max(1, st["zones"]), "failed": st["failed"]}
+        g.close()
+    print(json.dumps(out))
+
+
 def time_device(g, a, b, dt, steps, warmup, world, torch):
     for _ in range(warmup):
         g.step(a, b, dt)
@@ -201,11 +245,13 @@ def time_device(g, a, b, dt, steps, warmup, world, torch):
     st = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    nvtx_push(torch, "timed")
     e0.record(st)
     for _ in range(steps):
         g.step(a, b, dt)
         a, b = b, a
     e1.record(st)
+    nvtx_pop(torch)
     torch.cuda.synchronize()
     barrier(world)
     g.profile(False)
@@ -270,6 +316,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batched", action="store_true", help="skip the 64-box batched measurement")
+    ap.add_argument("--case-only", action="store_true",
+                    help="only the float64 and mixed steps of a --side box (for ncu captures)")
+    ap.add_argument("--side", type=int, default=N_SIDE, help="box side for --case-only")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -283,6 +332,9 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.case_only:
+        profile_case(args, dev, torch)
+        return
     prob = inputs.turbulent_box_problem(N_SIDE, tol=TOL)
     P = inputs.turbulent_box_state(prob)
     dt = 0.5 / N_SIDE
@@ -365,6 +417,8 @@ def main():
             return N * fl["zone_explicit_remainder_2d"], 0
         if cls == "explicit":
             return N * (2 * fl["face_flux"] + fl["zone_explicit_remainder_2d"]), 0
+        if cls == "mlp":
+            return 0, 0
         f64, f32 = newton_flops(st)
         return f64 / launches, f32 / launches
 
@@ -375,6 +429,9 @@ def main():
             t = tot / n * 1e-3
             out[cls] = {"ms_per_launch": tot / n, "share": None, "fp64_tflops": f64 / t / 1e12,
                         "fp64_frac": f64 / t / 1e12 / p64, "fp32_tflops": f32 / t / 1e12}
+            if cls == "mlp":    # bfloat16 tensor-core MACs of the network, 2 flops each
+                bf = N * MLP_FLOPS_PER_ZONE / t / 1e12
+                out[cls].update({"bf16_tflops": bf, "bf16_frac": bf / peaks.get("bf16_tflops_sustained", 1400.0)})
         total = sum(v[0] for v in kt.values())
         for cls, (tot, n) in kt.items():
             out[cls]["share"] = tot / total
@@ -388,7 +445,7 @@ def main():
              "newton64": "newton_dense<fp64>", "explicit": "explicit_stage_2d"}
     ach = roof_m[dom]["fp64_tflops"]
     roof = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s", "frac": ach / p64,
-            "traffic": None, "kernel": names.get(dom, dom),
+            "traffic": NCU_TRAFFIC_BYTES.get(dom), "kernel": names.get(dom, dom),
             "peak_source": "FP64 FMA-chain microbenchmark on this GPU (grim_peak_flops), of measured",
             "flops_convention": "oracle flop counter: +,-,*,/,sqrt = 1, FMA = 2 (tests/golden/flop_counts.txt)",
             "per_kernel": roof_m}
