@@ -43,6 +43,7 @@ extern "C" {
 #define GRIM_BC_REFLECT 2
 
 #define GRIM_METRIC_MINKOWSKI 0
+#define GRIM_METRIC_MKS_KERR 1 /* Kerr (M = 1, spin a) in modified Kerr-Schild coordinates (Section 2.1) */
 
 #define GRIM_RECON_MC 0    /* generalized minmod, parameter theta (2 = MC, 1 = minmod) */
 #define GRIM_RECON_WENO5 1 /* Jiang & Shu WENO5 */
@@ -57,8 +58,11 @@ typedef struct {
   int bc[3][2]; /* GRIM_BC_* for the low and high side of each direction */
 } grim_grid;
 
+/* Metric.  GRIM_METRIC_MKS_KERR: X^1 = log r, theta = pi X^2 + ((1-h)/2)
+ * sin(2 pi X^2), phi = X^3 (Section 2.1), over the Kerr-Schild form of the
+ * Kerr metric with spin a; the relaxation time becomes tau_R r^{3/2}. */
 typedef struct {
-  int kind; /* GRIM_METRIC_MINKOWSKI */
+  int kind; /* GRIM_METRIC_* */
   double spin, h;
 } grim_metric;
 
@@ -70,6 +74,11 @@ typedef struct {
   int conduction, viscosity, higher_order;
   int recon;    /* GRIM_RECON_* */
   double theta; /* generalized minmod parameter, also used for source slopes */
+  int floors;   /* after every stage: a zone whose Newton iteration ended with a
+                   non-zero status reverts to its start (P_n, flux-CT field);
+                   then rho >= 1e-5 r^{-3/2}, u >= 1e-7 r^{-5/2} (r = 1 in
+                   Minkowski space), -b^2 <= dP <= b^2/2.  General-metric
+                   path only (3-D or Kerr grids). */
 } grim_physics;
 
 /* Nonlinear solver (Section 3).  Converged when max_a |r_a| <= tol with
@@ -108,8 +117,15 @@ typedef struct grim_ctx grim_ctx;
 /* Create a context: validates the configuration, allocates the library's
  * scratch for n1*n2*n3 zones on the current device, binds the CUDA stream
  * `stream` (a cudaStream_t; NULL = the legacy default stream).
- * Errors: GRIM_EINVAL (dim != 2, n3 != 1, sizes < 1, unsupported metric or
- * reconstruction), GRIM_ENOMEM, GRIM_ECUDA.  *out is NULL on failure. */
+ * dim 2 (n3 = 1) or 3.  Two-dimensional Minkowski grids run the specialised
+ * flat-space kernels; 3-D grids and the Kerr metric run the general-metric
+ * kernels, whose geometry tables (metric, inverse, sqrt(-g), lapse,
+ * connection and tau_R at zone centres and faces; axisymmetric, so n1 x n2
+ * only) are computed here once, on the stream.  The learned start
+ * (grim_set_guess) is for 2-D Minkowski grids only.
+ * Errors: GRIM_EINVAL (dim not 2 or 3, n3 != 1 in 2-D, sizes < 1, unsupported
+ * metric or reconstruction), GRIM_ENOMEM, GRIM_ECUDA.  *out is NULL on
+ * failure. */
 int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physics* phys,
               const grim_solver* solver, void* stream, grim_ctx** out);
 

@@ -156,6 +156,17 @@ template <class T> Dual<T> sqrt(Dual<T> a) {
   return Dual<T>(s, a.d / (2.0 * s));
 }
 
+template <class T> Dual<T> exp(Dual<T> a) {
+  T e = std::exp(a.v);
+  return Dual<T>(e, e * a.d);
+}
+template <class T> Dual<T> sin(Dual<T> a) { return Dual<T>(std::sin(a.v), std::cos(a.v) * a.d); }
+template <class T> Dual<T> cos(Dual<T> a) { return Dual<T>(std::cos(a.v), -std::sin(a.v) * a.d); }
+template <class T> Dual<T> fabs_d(Dual<T> a) { return a.v < 0 ? -a : a; }
+inline double fabs_d(double a) { return std::fabs(a); }
+using std::exp;
+using std::sin;
+using std::cos;
 inline double re(double a) { return a; }
 inline double re(const std::complex<double>& a) { return a.real(); }
 template <class T> double re(const Dual<T>& a) { return re(a.v); }
@@ -166,18 +177,19 @@ using cplx = std::complex<double>;
 // Integer and real parameter vectors, laid out as documented in oracle.py.
 enum {
   I_DIM, I_N1, I_N2, I_N3, I_BC1L, I_BC1H, I_BC2L, I_BC2H, I_BC3L, I_BC3H,
-  I_METRIC, I_RECON, I_COND, I_VISC, I_HO, I_KMAX, I_LSMAX, I_NTHREADS, I_COUNT
+  I_METRIC, I_RECON, I_COND, I_VISC, I_HO, I_KMAX, I_LSMAX, I_FLOORS, I_NTHREADS, I_COUNT
 };
 enum {
   D_X01, D_X02, D_X03, D_DX1, D_DX2, D_DX3, D_GAMMA, D_PHI, D_PSI, D_TAUR,
   D_THETA, D_TOL, D_EPS, D_A, D_H, D_COUNT
 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };
+enum { METRIC_MINKOWSKI = 0, METRIC_MKS_KERR = 1 };
 enum { RECON_MC = 0, RECON_WENO5 = 1 };
 enum { ST_MAXIT = 1, ST_LSSTALL = 2, ST_SINGULAR = 4, ST_NONFINITE = 8, ST_INADMISSIBLE = 16 };
 
 struct Params {
-  int dim, n[3], bc[3][2], metric, recon, cond, visc, ho, kmax, lsmax;
+  int dim, n[3], bc[3][2], metric, recon, cond, visc, ho, kmax, lsmax, floors;
   double x0[3], dx[3], gamma, phi, psi, tauR, theta, tol, eps, a, h;
   long long N;
 };
@@ -191,7 +203,7 @@ static Params read_params(const int* ip, const double* dp) {
   p.bc[2][0] = ip[I_BC3L]; p.bc[2][1] = ip[I_BC3H];
   p.metric = ip[I_METRIC]; p.recon = ip[I_RECON];
   p.cond = ip[I_COND]; p.visc = ip[I_VISC]; p.ho = ip[I_HO];
-  p.kmax = ip[I_KMAX]; p.lsmax = ip[I_LSMAX];
+  p.kmax = ip[I_KMAX]; p.lsmax = ip[I_LSMAX]; p.floors = ip[I_FLOORS];
   for (int d = 0; d < 3; d++) { p.x0[d] = dp[D_X01 + d]; p.dx[d] = dp[D_DX1 + d]; }
   p.gamma = dp[D_GAMMA]; p.phi = dp[D_PHI]; p.psi = dp[D_PSI]; p.tauR = dp[D_TAUR];
   p.theta = dp[D_THETA]; p.tol = dp[D_TOL]; p.eps = dp[D_EPS]; p.a = dp[D_A]; p.h = dp[D_H];
@@ -213,9 +225,119 @@ static void geom_minkowski(Geom& g, double tauR) {
   g.sqrtg = 1.0; g.alpha = 1.0; g.tauR = tauR;
 }
 
+// Modified Kerr-Schild coordinates (Section 2.1 with the Kerr-Schild form of
+// the Kerr metric, M = 1): r = exp(X^1), theta = pi X^2 + ((1-h)/2) sin(2 pi
+// X^2), phi = X^3.  g_{mu nu}(X) = L^a_mu L^b_nu g^KS_ab with L = diag(1,
+// dr/dX^1, dtheta/dX^2, 1).  Kerr-Schild (t, r, theta, phi), Sigma = r^2 +
+// a^2 cos^2 theta:
+//   g_tt = -(1 - 2r/Sigma), g_tr = 2r/Sigma, g_tphi = -2 a r sin^2/Sigma,
+//   g_rr = 1 + 2r/Sigma, g_rphi = -a sin^2 (1 + 2r/Sigma), g_thth = Sigma,
+//   g_phiphi = sin^2 (Sigma + a^2 sin^2 (1 + 2r/Sigma)).
+// T is double or a dual number (derivative along X^1 or X^2).
+template <class T> static void mks_theta(double h, T X2, T& th, T& dth) {
+  th = M_PI * X2 + 0.5 * (1.0 - h) * sin(2.0 * M_PI * X2);
+  dth = M_PI * (1.0 + (1.0 - h) * cos(2.0 * M_PI * X2));
+}
+template <class T> static void mks_gcov(double a, double h, T X1, T X2, T g[4][4]) {
+  T r = exp(X1);
+  T th, dth;
+  mks_theta(h, X2, th, dth);
+  T sn = sin(th), cs = cos(th);
+  T s2 = sn * sn;
+  T sig = r * r + a * a * cs * cs;
+  T f = 2.0 * r / sig;
+  T ks[4][4];
+  for (int m = 0; m < 4; m++)
+    for (int n = 0; n < 4; n++) ks[m][n] = T(0.0);
+  ks[0][0] = -(1.0 - f);
+  ks[0][1] = f;
+  ks[0][3] = -a * f * s2;
+  ks[1][1] = 1.0 + f;
+  ks[1][3] = -a * s2 * (1.0 + f);
+  ks[2][2] = sig;
+  ks[3][3] = s2 * (sig + a * a * s2 * (1.0 + f));
+  T L[4] = {T(1.0), r, dth, T(1.0)};
+  for (int m = 0; m < 4; m++)
+    for (int n = m; n < 4; n++) {
+      g[m][n] = ks[m][n] * L[m] * L[n];
+      g[n][m] = g[m][n];
+    }
+}
+
+// Inverse and determinant of a symmetric 4x4 by Gauss-Jordan elimination with
+// partial pivoting.
+static double invert4(const double A[4][4], double inv[4][4]) {
+  double M[4][8];
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 8; j++) M[i][j] = (j < 4) ? A[i][j] : (j - 4 == i ? 1.0 : 0.0);
+  double det = 1.0;
+  for (int c = 0; c < 4; c++) {
+    int pv = c;
+    for (int i = c + 1; i < 4; i++)
+      if (std::fabs(M[i][c]) > std::fabs(M[pv][c])) pv = i;
+    if (pv != c) {
+      for (int j = 0; j < 8; j++) std::swap(M[c][j], M[pv][j]);
+      det = -det;
+    }
+    const double d = M[c][c];
+    det *= d;
+    for (int j = 0; j < 8; j++) M[c][j] /= d;
+    for (int i = 0; i < 4; i++) {
+      if (i == c) continue;
+      const double f = M[i][c];
+      for (int j = 0; j < 8; j++) M[i][j] -= f * M[c][j];
+    }
+  }
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) inv[i][j] = M[i][j + 4];
+  return det;
+}
+
+// Geometry of MKS-Kerr at X (X^3 plays no role: the metric is axisymmetric
+// and stationary).  Gamma^l_{mu nu} = (1/2) g^{l k} (d_mu g_{k nu} + d_nu
+// g_{k mu} - d_k g_{mu nu}) with the derivatives along X^1 and X^2 from
+// forward dual numbers.  sqrt(-g) from the determinant.  tau_R = tau_R0
+// r^{3/2} (the relaxation time grows with the local dynamical time).
+static void geom_mks(const Params& p, const double X[3], Geom& G) {
+  std::memset(&G, 0, sizeof(G));
+  double g[4][4];
+  mks_gcov<double>(p.a, p.h, X[0], X[1], g);
+  std::memcpy(G.gcov, g, sizeof(g));
+  const double det = invert4(g, G.gcon);
+  G.sqrtg = std::sqrt(-det);
+  G.alpha = 1.0 / std::sqrt(-G.gcon[0][0]);
+  double dg[4][4][4];  // dg[k][m][n] = d_k g_{mn}
+  std::memset(dg, 0, sizeof(dg));
+  for (int d = 1; d <= 2; d++) {
+    Dual<double> x1(X[0], d == 1 ? 1.0 : 0.0), x2(X[1], d == 2 ? 1.0 : 0.0);
+    Dual<double> gd[4][4];
+    mks_gcov<Dual<double>>(p.a, p.h, x1, x2, gd);
+    for (int m = 0; m < 4; m++)
+      for (int n = 0; n < 4; n++) dg[d][m][n] = gd[m][n].d;
+  }
+  for (int l = 0; l < 4; l++)
+    for (int m = 0; m < 4; m++)
+      for (int n = 0; n < 4; n++) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; k++) acc += G.gcon[l][k] * (dg[m][k][n] + dg[n][k][m] - dg[k][m][n]);
+        G.Gam[l][m][n] = 0.5 * acc;
+      }
+  const double r = std::exp(X[0]);
+  G.tauR = p.tauR * r * std::sqrt(r);
+}
+
+// A face of MKS-Kerr on the polar axis (sin theta = 0 there, so sqrt(-g) and
+// every flux through it vanish).
+static bool polar_face(const Params& p, const double X[3], int d) {
+  if (p.metric != METRIC_MKS_KERR || d != 1) return false;
+  double th, dth;
+  mks_theta<double>(p.h, X[1], th, dth);
+  return std::fabs(std::sin(th)) < 1e-10;
+}
+
 static void geom_at(const Params& p, const double X[3], Geom& g) {
-  (void)X;
-  geom_minkowski(g, p.tauR);
+  if (p.metric == METRIC_MKS_KERR) geom_mks(p, X, g);
+  else geom_minkowski(g, p.tauR);
 }
 
 // ---------------------------------------------------------------- fluid state
@@ -486,6 +608,10 @@ static void face_flux(const Grid& G, const double* PE, int d, int i, int j, int 
   double X[3];
   G.center(i, j, k, X);
   X[d] -= 0.5 * p.dx[d];
+  if (polar_face(p, X, d)) {
+    for (int v = 0; v < 10; v++) Fout[v] = 0.0;
+    return;
+  }
   Geom g;
   geom_at(p, X, g);
   State<double> sl, sr;
@@ -810,6 +936,25 @@ static void zone_const(const Stage& S, const double* Pn, const double* PE, doubl
   }
 }
 
+// Post-stage limits for the accreting torus (the paper describes floors and an
+// anisotropy limiter without values; a zone whose Newton iteration ended
+// with a non-zero status first reverts to its start, see oracle_stage_masked): rho >= 1e-5 r^{-3/2}, u >= 1e-7
+// r^{-5/2} (r = 1 in Minkowski space), then the pressure anisotropy clamped
+// to the firehose and mirror thresholds, -b^2 <= dP <= b^2/2.
+static void apply_floors(const Params& p, const double X[3], const Geom& g, double P[10]) {
+  const double r = (p.metric == METRIC_MKS_KERR) ? std::exp(X[0]) : 1.0;
+  P[0] = std::max(P[0], 1e-5 / (r * std::sqrt(r)));
+  P[1] = std::max(P[1], 1e-7 / (r * r * std::sqrt(r)));
+  if (!p.visc) return;
+  State<double> s;
+  make_state(P, g, p, s);
+  const double f = std::sqrt(s.nu * s.rho * s.Theta / g.tauR);  // dP = f dP~
+  if (!(f > 0.0)) return;
+  const double lo = -s.bsq, hi = 0.5 * s.bsq;
+  if (s.dP > hi) P[9] = hi / f;
+  else if (s.dP < lo) P[9] = lo / f;
+}
+
 static void set_threads(int n) {
 #ifdef _OPENMP
   if (n > 0) omp_set_num_threads(n);
@@ -865,6 +1010,17 @@ int oracle_stage_masked(const int* ip, const double* dp, const double* Pn, const
         for (int c = 0; c < 3; c++)
           P[5 + c] = (z.Un[5 + c] - dts * z.divF[5 + c]) / z.g.sqrtg;
         NewtonOut o = newton(z, p, P);
+        if (p.floors) {
+          // a zone left without an admissible root keeps its start (P_n with
+          // the flux-CT field); then the floors
+          if (o.status) {
+            for (int v = 0; v < 10; v++) P[v] = Pn[v * p.N + zi];
+            for (int c = 0; c < 3; c++) P[5 + c] = (z.Un[5 + c] - dts * z.divF[5 + c]) / z.g.sqrtg;
+          }
+          double X[3];
+          S.G.center(i, j, k, X);
+          apply_floors(p, X, z.g, P);
+        }
         for (int v = 0; v < 10; v++) Pout[v * p.N + zi] = P[v];
         if (iters) iters[zi] = o.iters;
         if (status) status[zi] = o.status;
@@ -982,6 +1138,31 @@ int oracle_step(const int* ip, const double* dp, const double* Pn, double dt, do
   if (status)
     for (long long z = 0; z < p.N; z++) status[z] |= st1[z];
   if (evals) *evals = e1 + e2;
+  return 0;
+}
+
+// Geometry at the point X (for the tests): g_{mu nu}, g^{mu nu} (row-major
+// 4x4), sqrt(-g), alpha, Gamma^l_{mu nu} ([l][mu][nu]) and tau_R.
+int oracle_geometry(const int* ip, const double* dp, const double* X, double* gcov, double* gcon, double* sqrtg,
+                    double* alpha, double* Gam, double* tauR) {
+  Params p = read_params(ip, dp);
+  Geom g;
+  geom_at(p, X, g);
+  std::memcpy(gcov, g.gcov, sizeof(g.gcov));
+  std::memcpy(gcon, g.gcon, sizeof(g.gcon));
+  *sqrtg = g.sqrtg;
+  *alpha = g.alpha;
+  std::memcpy(Gam, g.Gam, sizeof(g.Gam));
+  *tauR = g.tauR;
+  return 0;
+}
+
+// Post-stage floors at the zone centre X (for the tests): P updated in place.
+int oracle_floors(const int* ip, const double* dp, const double* X, double* P) {
+  Params p = read_params(ip, dp);
+  Geom g;
+  geom_at(p, X, g);
+  apply_floors(p, X, g, P);
   return 0;
 }
 

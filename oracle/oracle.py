@@ -6,7 +6,7 @@ it; the product library never imports it.
 
 Parameter vectors passed to the C++ side:
   ip = [dim, n1, n2, n3, bc1lo, bc1hi, bc2lo, bc2hi, bc3lo, bc3hi, metric,
-        recon, conduction, viscosity, higher_order, k_max, ls_max, nthreads]
+        recon, conduction, viscosity, higher_order, k_max, ls_max, floors, nthreads]
   dp = [x0_1, x0_2, x0_3, dx1, dx2, dx3, gamma, phi, psi, tau_R, theta, tol,
         eps_fd, spin, h_mks]
 """
@@ -21,7 +21,7 @@ from . import build as _build
 
 _lib = None
 
-I_COUNT = 18
+I_COUNT = 19
 D_COUNT = 15
 ST_MAXIT, ST_LSSTALL, ST_SINGULAR, ST_NONFINITE, ST_INADMISSIBLE = 1, 2, 4, 8, 16
 
@@ -47,7 +47,7 @@ def params(prob, threads: int = 0):
                    prob.bc[0][0], prob.bc[0][1], prob.bc[1][0], prob.bc[1][1],
                    prob.bc[2][0], prob.bc[2][1], prob.metric, prob.recon,
                    int(prob.conduction), int(prob.viscosity), int(prob.higher_order),
-                   prob.k_max, prob.ls_max, threads], dtype=np.int32)
+                   prob.k_max, prob.ls_max, int(prob.floors), threads], dtype=np.int32)
     dx = prob.dx
     dp = np.array([prob.x_start[0], prob.x_start[1], prob.x_start[2], dx[0], dx[1], dx[2],
                    prob.gamma, prob.phi, prob.psi, prob.tau_R, prob.theta, prob.tol,
@@ -103,6 +103,27 @@ def fluxes(prob, PE, threads: int = 0):
     PE = _c(PE)
     out = np.empty((prob.dim, 10) + PE.shape[1:])
     lib().oracle_fluxes(_iptr(ip), _dptr(dp), _dptr(PE), _dptr(out))
+    return out
+
+
+def geometry(prob, X):
+    """Metric quantities at the point X (3 coordinates): dict with gcov, gcon
+    [4,4], sqrtg, alpha, Gam [4,4,4] ([l][mu][nu]) and tauR."""
+    ip, dp = params(prob)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    gcov = np.empty((4, 4)); gcon = np.empty((4, 4)); Gam = np.empty((4, 4, 4))
+    sg, al, tr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().oracle_geometry(_iptr(ip), _dptr(dp), _dptr(X), _dptr(gcov), _dptr(gcon), ctypes.byref(sg),
+                          ctypes.byref(al), _dptr(Gam), ctypes.byref(tr))
+    return {"gcov": gcov, "gcon": gcon, "sqrtg": sg.value, "alpha": al.value, "Gam": Gam, "tauR": tr.value}
+
+
+def floors(prob, X, P):
+    """The post-stage floors applied to one primitive vector at X (copy)."""
+    ip, dp = params(prob)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.array(P, dtype=np.float64, copy=True)
+    lib().oracle_floors(_iptr(ip), _dptr(dp), _dptr(X), _dptr(out))
     return out
 
 

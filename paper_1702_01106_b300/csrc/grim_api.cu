@@ -1,5 +1,6 @@
 // C ABI of the grim library (declarations and documentation: include/grim.h).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
@@ -30,6 +31,20 @@ cudaError_t launch_mlp_features(const Params& p, const double* K, const double* 
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const double* K, const double* Pn, const double* Un, const grim_mlp* m,
                              double* P0, cudaStream_t st);
+long long gr_geometry_doubles(const Params& p);
+long long gr_face_doubles(const Params& p);
+cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double h, const double x0[3],
+                               double* geo, cudaStream_t st);
+cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo, double* faces, cudaStream_t st);
+cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
+                                 const double* geo, double* faces, double* K, double* P0, cudaStream_t st);
+cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K, const double* Pn,
+                             const uint8_t* status, double* P, cudaStream_t st);
+cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
+                             uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
+                             int* qcount, cudaStream_t st);
+cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,
+                               double dts, double* R, cudaStream_t st);
 }  // namespace grim
 
 using grim::Params;
@@ -52,6 +67,8 @@ struct grim_ctx {
   };
   std::vector<Graph> gcache;
   unsigned long long gclock = 0;
+  bool gr = false;            // general-metric kernels (3-D or Kerr)
+  double* geo = nullptr;      // geometry tables of the general-metric path
   double* K = nullptr;        // NK x N stage constants
   double* faces = nullptr;    // face fluxes of one stage
   double* pncache = nullptr;  // P_n quantities shared by the two stages of a step
@@ -133,6 +150,7 @@ const char* grim_last_error(grim_ctx* ctx) { return ctx ? ctx->err : "no context
 void grim_destroy(grim_ctx* ctx) {
   if (!ctx) return;
   cudaFree(ctx->K);
+  cudaFree(ctx->geo);
   cudaFree(ctx->faces);
   cudaFree(ctx->pncache);
   cudaFree(ctx->Ph);
@@ -155,8 +173,10 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   if (!out) return GRIM_EINVAL;
   *out = nullptr;
   if (!grid || !metric || !phys || !solver) return GRIM_EINVAL;
-  if (grid->dim != 2 || grid->n3 != 1 || grid->n1 < 1 || grid->n2 < 1) return GRIM_EINVAL;
-  if (metric->kind != GRIM_METRIC_MINKOWSKI) return GRIM_EINVAL;
+  if (grid->dim < 2 || grid->dim > 3 || grid->n1 < 1 || grid->n2 < 1 || grid->n3 < 1) return GRIM_EINVAL;
+  if (grid->dim == 2 && grid->n3 != 1) return GRIM_EINVAL;
+  if (metric->kind != GRIM_METRIC_MINKOWSKI && metric->kind != GRIM_METRIC_MKS_KERR) return GRIM_EINVAL;
+  if (metric->kind == GRIM_METRIC_MKS_KERR && !(std::fabs(metric->spin) < 1.0)) return GRIM_EINVAL;
   if (phys->recon != GRIM_RECON_MC && phys->recon != GRIM_RECON_WENO5) return GRIM_EINVAL;
   if (solver->precision != GRIM_FP64 && solver->precision != GRIM_MIXED) return GRIM_EINVAL;
   if (!(phys->gamma > 1.0) || !(phys->tau_R > 0.0) || !(solver->tol > 0.0) || solver->k_max < 0 ||
@@ -180,15 +200,20 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   p.cond = phys->conduction; p.visc = phys->viscosity; p.ho = phys->higher_order; p.recon = phys->recon;
   p.tol = solver->tol; p.eps64 = solver->eps_fd; p.eps32 = (float)solver->eps_fd32;
   p.kmax = solver->k_max; p.lsmax = solver->ls_max; p.fd32c = solver->fd32_central != 0;
+  p.metric = metric->kind; p.floors = phys->floors;
   p.N = (long long)grid->n1 * grid->n2 * grid->n3;
   ctx->precision = solver->precision;
+  ctx->gr = grid->dim == 3 || metric->kind != GRIM_METRIC_MINKOWSKI;
   ctx->stream = (cudaStream_t)stream;
   ctx->cur = ctx->stream;
   const size_t N = (size_t)p.N;
   cudaError_t e;
   if ((e = cudaMalloc(&ctx->K, sizeof(double) * grim::NK * N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->Ph, sizeof(double) * grim::NV * N)) != cudaSuccess ||
-      (e = cudaMalloc(&ctx->faces, sizeof(double) * grim::face_scratch_doubles(p.n1, p.n2))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->faces, sizeof(double) * (ctx->gr ? grim::gr_face_doubles(p)
+                                                              : grim::face_scratch_doubles(p.n1, p.n2)))) !=
+          cudaSuccess ||
+      (ctx->gr && (e = cudaMalloc(&ctx->geo, sizeof(double) * grim::gr_geometry_doubles(p))) != cudaSuccess) ||
       (e = cudaMalloc(&ctx->pncache, sizeof(double) * grim::pn_cache_doubles(p.N))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->iters, N)) != cudaSuccess || (e = cudaMalloc(&ctx->status, N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->cnt, sizeof(grim::Counters))) != cudaSuccess ||
@@ -198,7 +223,9 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
     grim_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
   }
-  if ((e = cudaMemsetAsync(ctx->cnt, 0, sizeof(grim::Counters), ctx->stream)) != cudaSuccess) {
+  if ((e = cudaMemsetAsync(ctx->cnt, 0, sizeof(grim::Counters), ctx->stream)) != cudaSuccess ||
+      (ctx->gr && (e = grim::launch_gr_geometry(p, metric->kind, metric->spin, metric->h, grid->x_start, ctx->geo,
+                                                ctx->stream)) != cudaSuccess)) {
     grim_destroy(ctx);
     return GRIM_ECUDA;
   }
@@ -209,6 +236,16 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
 // The explicit part of a stage: face fluxes, then flux-CT and the constants.
 static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
                         double* Pout, int mode) {
+  if (ctx->gr) {
+    {
+      KernelMark m(ctx, GRIM_K_FACES, ctx->p.dim);
+      GRIM_CUDA(grim::launch_gr_faces(ctx->p, PE, ctx->geo, ctx->faces, ctx->cur), "face kernel");
+    }
+    KernelMark m(ctx, GRIM_K_ZONECONST);
+    GRIM_CUDA(grim::launch_gr_zone_const(ctx->p, Pn, PE, guess, dts, ctx->geo, ctx->faces, ctx->K, Pout, ctx->cur),
+              "zone-constant kernel");
+    return GRIM_OK;
+  }
   {
     KernelMark m(ctx, GRIM_K_FACES);
     GRIM_CUDA(grim::launch_faces(ctx->p, PE, ctx->faces, ctx->tune.faces_bs, ctx->cur), "face kernel");
@@ -226,11 +263,27 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
                      double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
   int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode);
   if (rc) return rc;
-  const bool learned = ctx->mlp && !guess;
+  const bool learned = ctx->mlp && !guess && !ctx->gr;
   if (learned) {
     KernelMark m(ctx, GRIM_K_MLP);
     GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->K, Pn, mode ? ctx->pncache : nullptr, ctx->mlp, Pout, ctx->cur),
               "mlp kernel");
+  }
+  if (ctx->gr) {
+    const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
+    {
+      KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64, cfg.kcut < ctx->p.kmax ? 2 : 1);
+      GRIM_CUDA(grim::launch_newton_gr(ctx->p, ctx->precision, ctx->K, ctx->geo, Pout, iters ? iters : ctx->iters,
+                                       status ? status : ctx->status, ctx->cnt, cfg, ctx->queue, ctx->qcount,
+                                       ctx->cur),
+                "newton kernel");
+    }
+    if (ctx->p.floors) {
+      KernelMark m(ctx, GRIM_K_ZONECONST);
+      GRIM_CUDA(grim::launch_gr_floors(ctx->p, ctx->geo, ctx->K, Pn, status ? status : ctx->status, Pout, ctx->cur),
+                "floor kernel");
+    }
+    return GRIM_OK;
   }
   {
     const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
@@ -478,7 +531,11 @@ int grim_residual(grim_ctx* ctx, const double* P_n, const double* P_E, double dt
   if (rc) return rc;
   {
     KernelMark m(ctx, GRIM_K_RESIDUAL);
-    GRIM_CUDA(grim::launch_residual(ctx->p, ctx->K, P_k, scaled, dts, R_out, ctx->stream), "residual kernel");
+    if (ctx->gr)
+      GRIM_CUDA(grim::launch_residual_gr(ctx->p, ctx->K, ctx->geo, P_k, scaled, dts, R_out, ctx->stream),
+                "residual kernel");
+    else
+      GRIM_CUDA(grim::launch_residual(ctx->p, ctx->K, P_k, scaled, dts, R_out, ctx->stream), "residual kernel");
   }
   return GRIM_OK;
 }
@@ -503,6 +560,7 @@ int grim_get_stats(grim_ctx* ctx, grim_stats* out) {
 
 int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept) {
   if (!ctx || !(accept >= 0.0)) return GRIM_EINVAL;
+  if (mlp && ctx->gr) return fail(ctx, GRIM_EINVAL, "grim_set_guess: the learned start is for 2-D Minkowski grids");
   ctx->mlp = mlp;
   ctx->accept = accept;
   return GRIM_OK;
@@ -510,6 +568,7 @@ int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept) {
 
 int grim_mlp_sample(grim_ctx* ctx, const double* P_n, const double* P_conv, float* X, float* Y) {
   if (!ctx || !P_n || !X || (Y && !P_conv)) return GRIM_EINVAL;
+  if (ctx->gr) return fail(ctx, GRIM_EINVAL, "grim_mlp_sample: the learned start is for 2-D Minkowski grids");
   {
     KernelMark m(ctx, GRIM_K_MLP);
     GRIM_CUDA(grim::launch_mlp_features(ctx->p, ctx->K, P_n, P_conv, X, Y, ctx->stream), "feature kernel");

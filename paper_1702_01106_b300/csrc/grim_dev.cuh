@@ -41,6 +41,7 @@ struct Params {
   float eps32;
   int kmax, lsmax;
   int fd32c;  // centred differences for the float32 Jacobian
+  int metric, floors;
   long long N;
 };
 

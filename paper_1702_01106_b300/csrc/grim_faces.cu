@@ -52,38 +52,6 @@ __device__ __forceinline__ double load_comp(const double* P, long long N, long l
   return x;
 }
 
-// Generalized minmod slope (Section 2.4.1) of vm, v0, vp: sign-agreement and
-// magnitude tests run on the integer bit patterns.
-__device__ __forceinline__ double gm_slope(double theta, double vm, double v0, double vp) {
-  const double a = v0 - vm, c = vp - v0;
-  const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
-  const unsigned long long bc = (unsigned long long)__double_as_longlong(c);
-  const unsigned long long ma = ba & 0x7fffffffffffffffull, mc = bc & 0x7fffffffffffffffull;
-  if (ma == 0 || mc == 0 || ((ba ^ bc) >> 63)) return 0.0;  // differences of opposite sign or zero
-  const double m1 = theta * __longlong_as_double((long long)(ma < mc ? ma : mc));
-  const double m2 = 0.5 * fabs(a + c);
-  const double m = abits(m1) < abits(m2) ? m1 : m2;
-  return (ba >> 63) ? -m : m;
-}
-
-// WENO5 of Jiang & Shu (1996): value at the right face of v2 from v0..v4.
-__device__ __forceinline__ double weno5v(double v0, double v1, double v2, double v3, double v4) {
-  const double eps = 1e-6;
-  const double q0 = (2.0 * v0 - 7.0 * v1 + 11.0 * v2) * (1.0 / 6.0);
-  const double q1 = (-v1 + 5.0 * v2 + 2.0 * v3) * (1.0 / 6.0);
-  const double q2 = (2.0 * v2 + 5.0 * v3 - v4) * (1.0 / 6.0);
-  const double d0 = v0 - 2.0 * v1 + v2, e0 = v0 - 4.0 * v1 + 3.0 * v2;
-  const double d1 = v1 - 2.0 * v2 + v3, e1 = v1 - v3;
-  const double d2 = v2 - 2.0 * v3 + v4, e2 = 3.0 * v2 - 4.0 * v3 + v4;
-  const double b0 = (13.0 / 12.0) * d0 * d0 + 0.25 * e0 * e0;
-  const double b1 = (13.0 / 12.0) * d1 * d1 + 0.25 * e1 * e1;
-  const double b2 = (13.0 / 12.0) * d2 * d2 + 0.25 * e2 * e2;
-  const double a0 = 0.1 / ((eps + b0) * (eps + b0));
-  const double a1 = 0.6 / ((eps + b1) * (eps + b1));
-  const double a2 = 0.3 / ((eps + b2) * (eps + b2));
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
-}
-
 // Conserved variables U and flux F^j (j = 1, 2, 3) of a face state (Eqs.
 // divN_explicit, divT_explicit, induction_eqn and the q~, dP~ equations), and
 // the largest |grid-frame speed| in direction j of waves moving at +-v_max in

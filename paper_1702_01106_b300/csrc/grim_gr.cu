@@ -1,0 +1,623 @@
+// The explicit part of a stage in a general metric and in 3-D (Sections 2.1,
+// 2.3, 2.4, 4.2): the geometry tables, the face fluxes along every active
+// direction, and per zone the flux-CT on every pair of directions, the flux
+// divergence, the geometric source, the limited slopes and the stage
+// constants of the residual.  Also the post-stage floors and a residual
+// evaluation.  Used for 3-D grids and for the modified Kerr-Schild metric;
+// 2-D Minkowski grids take the specialised kernels of grim_faces.cu.
+#include "grim_gr.cuh"
+
+namespace grim {
+
+// ---------------------------------------------------------------- geometry
+// Value and derivatives along X^1 and X^2 (forward mode).
+struct D2 {
+  double v, d1, d2;
+  __device__ D2(double x = 0.0, double a = 0.0, double b = 0.0) : v(x), d1(a), d2(b) {}
+};
+__device__ __forceinline__ D2 operator+(D2 a, D2 b) { return D2(a.v + b.v, a.d1 + b.d1, a.d2 + b.d2); }
+__device__ __forceinline__ D2 operator-(D2 a, D2 b) { return D2(a.v - b.v, a.d1 - b.d1, a.d2 - b.d2); }
+__device__ __forceinline__ D2 operator-(D2 a) { return D2(-a.v, -a.d1, -a.d2); }
+__device__ __forceinline__ D2 operator*(D2 a, D2 b) {
+  return D2(a.v * b.v, a.d1 * b.v + a.v * b.d1, a.d2 * b.v + a.v * b.d2);
+}
+__device__ __forceinline__ D2 operator*(double s, D2 a) { return D2(s * a.v, s * a.d1, s * a.d2); }
+__device__ __forceinline__ D2 operator/(D2 a, D2 b) {
+  const double q = a.v / b.v;
+  return D2(q, (a.d1 - q * b.d1) / b.v, (a.d2 - q * b.d2) / b.v);
+}
+__device__ __forceinline__ D2 dexp(D2 a) { const double e = exp(a.v); return D2(e, e * a.d1, e * a.d2); }
+__device__ __forceinline__ D2 dsin(D2 a) { const double c = cos(a.v); return D2(sin(a.v), c * a.d1, c * a.d2); }
+__device__ __forceinline__ D2 dcos(D2 a) { const double s = sin(a.v); return D2(cos(a.v), -s * a.d1, -s * a.d2); }
+
+// Modified Kerr-Schild metric at (X^1, X^2): r = exp(X^1), theta = pi X^2 +
+// ((1-h)/2) sin(2 pi X^2); g_{mu nu} = L^a_mu L^b_nu g^KS_ab with L =
+// diag(1, r, dtheta/dX^2, 1) and the Kerr-Schild form of the Kerr metric
+// (M = 1, Sigma = r^2 + a^2 cos^2 theta, f = 2r/Sigma): g_tt = -(1 - f),
+// g_tr = f, g_tphi = -a f sin^2, g_rr = 1 + f, g_rphi = -a (1 + f) sin^2,
+// g_thth = Sigma, g_phiphi = sin^2 (Sigma + a^2 (1 + f) sin^2).
+__device__ void mks_metric(double a, double h, double X1, double X2, D2 g[10]) {
+  const D2 x1(X1, 1.0, 0.0), x2(X2, 0.0, 1.0);
+  const double tp = 2.0 * M_PI;
+  const D2 r = dexp(x1);
+  const D2 th = M_PI * x2 + (0.5 * (1.0 - h)) * dsin(tp * x2);
+  const D2 dth = M_PI * (D2(1.0) + (1.0 - h) * dcos(tp * x2));
+  const D2 sn = dsin(th), cs = dcos(th);
+  const D2 s2 = sn * sn;
+  const D2 sig = r * r + (a * a) * (cs * cs);
+  const D2 f = 2.0 * r / sig;
+  const D2 one(1.0);
+  for (int q = 0; q < 10; q++) g[q] = D2(0.0);
+  g[sym(0, 0)] = f - one;
+  g[sym(0, 1)] = f * r;
+  g[sym(0, 3)] = -a * (f * s2);
+  g[sym(1, 1)] = (one + f) * r * r;
+  g[sym(1, 3)] = -a * ((one + f) * s2 * r);
+  g[sym(2, 2)] = sig * dth * dth;
+  g[sym(3, 3)] = s2 * (sig + (a * a) * ((one + f) * s2));
+}
+
+// Inverse of a symmetric 4x4 (Gauss-Jordan, partial pivoting) and its
+// determinant.
+__device__ double inv4(const double g[10], double gi[10]) {
+  double M[4][8];
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) { M[i][j] = g[sym(i, j)]; M[i][4 + j] = (i == j) ? 1.0 : 0.0; }
+  double det = 1.0;
+  for (int c = 0; c < 4; c++) {
+    int pv = c;
+    for (int i = c + 1; i < 4; i++)
+      if (fabs(M[i][c]) > fabs(M[pv][c])) pv = i;
+    if (pv != c) {
+      for (int j = 0; j < 8; j++) { const double t = M[c][j]; M[c][j] = M[pv][j]; M[pv][j] = t; }
+      det = -det;
+    }
+    const double d = M[c][c];
+    det *= d;
+    const double id = 1.0 / d;
+    for (int j = 0; j < 8; j++) M[c][j] *= id;
+    for (int i = 0; i < 4; i++) {
+      if (i == c) continue;
+      const double m = M[i][c];
+      for (int j = 0; j < 8; j++) M[i][j] -= m * M[c][j];
+    }
+  }
+  for (int i = 0; i < 4; i++)
+    for (int j = i; j < 4; j++) gi[sym(i, j)] = 0.5 * (M[i][4 + j] + M[j][4 + i]);
+  return det;
+}
+
+struct GeoArgs {
+  int metric;
+  double a, h;
+  double x0[3], dx[3];
+  double tau0;
+  int n1, n2;
+  double* gc;   // centres, NGC planes
+  double* gf1;  // X1 faces, NGF planes
+  double* gf2;  // X2 faces, NGF planes
+};
+
+// One geometry point at (X1, X2); kind 0: zone centre (all planes), 1: face.
+__device__ void geometry_point(const GeoArgs& A, double X1, double X2, bool polar_check, double* out,
+                               long long stride, bool centre) {
+  double g[10], gi[10], Gam[40], sqrtg, alpha, tau, r;
+  if (A.metric == 0) {
+    for (int q = 0; q < 10; q++) g[q] = gi[q] = 0.0;
+    g[sym(0, 0)] = gi[sym(0, 0)] = -1.0;
+    for (int i = 1; i < 4; i++) g[sym(i, i)] = gi[sym(i, i)] = 1.0;
+    for (int q = 0; q < 40; q++) Gam[q] = 0.0;
+    sqrtg = 1.0; alpha = 1.0; r = 1.0; tau = A.tau0;
+  } else {
+    D2 gd[10];
+    mks_metric(A.a, A.h, X1, X2, gd);
+    for (int q = 0; q < 10; q++) g[q] = gd[q].v;
+    const double det = inv4(g, gi);
+    sqrtg = sqrt(-det);
+    alpha = 1.0 / sqrt(-gi[sym(0, 0)]);
+    r = exp(X1);
+    tau = A.tau0 * r * sqrt(r);
+    // Gamma^l_{mn} = (1/2) g^{lk} (d_m g_{kn} + d_n g_{km} - d_k g_{mn}); d_0 = d_3 = 0
+    auto dg = [&](int k, int m, int n) -> double {
+      return k == 1 ? gd[sym(m, n)].d1 : (k == 2 ? gd[sym(m, n)].d2 : 0.0);
+    };
+    for (int l = 0; l < 4; l++)
+      for (int m = 0; m < 4; m++)
+        for (int n = m; n < 4; n++) {
+          double s = 0.0;
+          for (int k = 0; k < 4; k++) s += gi[sym(l, k)] * (dg(m, k, n) + dg(n, k, m) - dg(k, m, n));
+          Gam[10 * l + sym(m, n)] = 0.5 * s;
+        }
+    if (polar_check) {
+      const double th = M_PI * X2 + 0.5 * (1.0 - A.h) * sin(2.0 * M_PI * X2);
+      if (fabs(sin(th)) < 1e-10) sqrtg = 0.0;  // polar face: no flux through it
+    }
+  }
+  for (int q = 0; q < 10; q++) { out[(G_COV + q) * stride] = g[q]; out[(G_CON + q) * stride] = gi[q]; }
+  out[G_SQRTG * stride] = sqrtg;
+  out[G_ALPHA * stride] = alpha;
+  if (centre) {
+    out[G_TAUR * stride] = tau;
+    out[G_R * stride] = r;
+    for (int q = 0; q < 40; q++) out[(G_GAM + q) * stride] = Gam[q];
+  }
+}
+
+__global__ void geometry_tables(const GeoArgs A) {
+  const long long nc = (long long)(A.n1 + 2) * (A.n2 + 2);
+  const long long nf1 = (long long)(A.n1 + 1) * (A.n2 + 2);
+  const long long nf2 = (long long)(A.n1 + 2) * (A.n2 + 1);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nc) {
+    const int i = (int)(t % (A.n1 + 2)) - 1, j = (int)(t / (A.n1 + 2)) - 1;
+    geometry_point(A, A.x0[0] + (i + 0.5) * A.dx[0], A.x0[1] + (j + 0.5) * A.dx[1], false, A.gc + t, nc, true);
+  } else if (t < nc + nf1) {
+    const long long u = t - nc;
+    const int i = (int)(u % (A.n1 + 1)), j = (int)(u / (A.n1 + 1)) - 1;
+    geometry_point(A, A.x0[0] + i * A.dx[0], A.x0[1] + (j + 0.5) * A.dx[1], false, A.gf1 + u, nf1, false);
+  } else if (t < nc + nf1 + nf2) {
+    const long long u = t - nc - nf1;
+    const int i = (int)(u % (A.n1 + 2)) - 1, j = (int)(u / (A.n1 + 2));
+    geometry_point(A, A.x0[0] + (i + 0.5) * A.dx[0], A.x0[1] + j * A.dx[1], true, A.gf2 + u, nf2, false);
+  }
+}
+
+// ---------------------------------------------------------------- grid access
+struct GrArgs {
+  const double* Pn;
+  const double* PE;
+  const double* guess;
+  double dts, kappa;
+  double* K;
+  double* P0;
+  double* F[3];
+  const double* gc;
+  const double* gf[2];
+};
+
+// Extents and offsets of the face array of direction D: along D the faces
+// 0..n_D; across it one ring of ghost faces in every active direction.
+struct FaceBox {
+  int e[3], o[3];
+  long long size;
+  __device__ __host__ long long at(int i, int j, int k) const {
+    return ((long long)(k + o[2]) * e[1] + (j + o[1])) * e[0] + (i + o[0]);
+  }
+};
+__host__ __device__ inline FaceBox face_box(const Params& p, int D) {
+  FaceBox b;
+  const int n[3] = {p.n1, p.n2, p.n3};
+  for (int d = 0; d < 3; d++) {
+    const bool act = d < p.dim;
+    b.e[d] = (d == D) ? n[d] + 1 : (act ? n[d] + 2 : 1);
+    b.o[d] = (d == D) ? 0 : (act ? 1 : 0);
+  }
+  b.size = (long long)b.e[0] * b.e[1] * b.e[2];
+  return b;
+}
+
+// Map one index by the boundary rule of direction d (periodic, outflow copy,
+// or reflection with period 2n and a sign flip of the d-components of u~ and
+// B); inactive directions map to 0.
+__device__ __forceinline__ int gr_map(const Params& p, int d, int i, bool& flip) {
+  const int n = d == 0 ? p.n1 : d == 1 ? p.n2 : p.n3;
+  if (d >= p.dim) return 0;
+  if (i >= 0 && i < n) return i;
+  const int bc = p.bc[d][i < 0 ? 0 : 1];
+  if (bc == BC_PERIODIC) return ((i % n) + n) % n;
+  if (bc == BC_OUTFLOW) return i < 0 ? 0 : n - 1;
+  const int m = ((i % (2 * n)) + 2 * n) % (2 * n);
+  if (m >= n) { flip = !flip; return 2 * n - 1 - m; }
+  return m;
+}
+__device__ __forceinline__ long long gr_zone(const Params& p, int i, int j, int k, bool f[3]) {
+  f[0] = f[1] = f[2] = false;
+  const int a = gr_map(p, 0, i, f[0]), b = gr_map(p, 1, j, f[1]), c = gr_map(p, 2, k, f[2]);
+  return ((long long)c * p.n2 + b) * p.n1 + a;
+}
+__device__ __forceinline__ void gr_prim(const Params& p, const double* P, int i, int j, int k, double out[NV]) {
+  bool f[3];
+  const long long z = gr_zone(p, i, j, k, f);
+#pragma unroll
+  for (int v = 0; v < NV; v++) out[v] = __ldg(P + v * p.N + z);
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+    if (f[d]) { out[2 + d] = -out[2 + d]; out[5 + d] = -out[5 + d]; }
+}
+
+// Table accessor at a 2-D index with a plane stride.
+struct GT {
+  const double* p;
+  long long s;
+  __device__ __forceinline__ double operator()(int a) const { return __ldg(p + a * s); }
+};
+__device__ __forceinline__ GT centre_geo(const Params& p, const double* gc, int i, int j) {
+  const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+  if (p.dim < 2) j = 0;
+  return GT{gc + (long long)(j + 1) * (p.n1 + 2) + (i + 1), nc};
+}
+
+// cs~^2 / c_s^2 of the closure (Eq. modcs with v_q^2 = (gamma-1) chi/tau_R,
+// v_dP^2 = 4 nu/(3 tau_R), chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R).
+static double gr_kappa(const Params& p) {
+  const double a = p.cond ? (p.gamma - 1.0) * p.phi : 0.0;
+  const double b = p.visc ? 4.0 * p.psi / 3.0 : 0.0;
+  return 0.5 * (1.0 + a + sqrt(1.0 + a * a)) + b;
+}
+
+// ---------------------------------------------------------------- faces
+// LLF flux (Section 2.4.2) on the face at the low side of zone (i,j,k) in
+// direction D, from MC or WENO5 face states of P^E.
+template <int D>
+__global__ void __launch_bounds__(128) face_flux_gr(const __grid_constant__ Params p,
+                                                    const __grid_constant__ GrArgs a) {
+  const FaceBox fb = face_box(p, D);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= fb.size) return;
+  const int i = (int)(f % fb.e[0]) - fb.o[0];
+  const int j = (int)((f / fb.e[0]) % fb.e[1]) - fb.o[1];
+  const int k = (int)(f / ((long long)fb.e[0] * fb.e[1])) - fb.o[2];
+  double* out = a.F[D] + f;
+  // face geometry
+  GT g;
+  if (D == 0) g = GT{a.gf[0] + (long long)((p.dim >= 2 ? j : 0) + 1) * (p.n1 + 1) + i,
+                     (long long)(p.n1 + 1) * (p.n2 + 2)};
+  else if (D == 1) g = GT{a.gf[1] + (long long)j * (p.n1 + 2) + (i + 1), (long long)(p.n1 + 2) * (p.n2 + 1)};
+  else g = centre_geo(p, a.gc, i, j);
+  const double sg = g(G_SQRTG);
+  if (sg == 0.0) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) out[v * fb.size] = 0.0;
+    return;
+  }
+  const bool weno = p.recon == RECON_WENO5;
+  double L[NV], R[NV];
+  {
+    double s[6][NV];
+    const int o0 = weno ? -3 : -2, o1 = weno ? 2 : 1;
+    for (int t = o0; t <= o1; t++)
+      gr_prim(p, a.PE, i + (D == 0) * t, j + (D == 1) * t, k + (D == 2) * t, s[t + 3]);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      if (weno) {
+        L[v] = weno5v(s[0][v], s[1][v], s[2][v], s[3][v], s[4][v]);
+        R[v] = weno5v(s[5][v], s[4][v], s[3][v], s[2][v], s[1][v]);
+      } else {
+        L[v] = fma(0.5, gm_slope(p.theta, s[1][v], s[2][v], s[3][v]), s[2][v]);
+        R[v] = fma(-0.5, gm_slope(p.theta, s[2][v], s[3][v], s[4][v]), s[3][v]);
+      }
+    }
+  }
+  Met<double> m;
+  met_load(m, g);
+  const RC<double> c = make_rc<double>(p);
+  ZG<double> zl, zr;
+  zg_load(zl, L, m, c);
+  zg_load(zr, R, m, c);
+  double UL[NV], UR[NV], FL[NV], FR[NV];
+  zg_conserved(zl, UL);
+  zg_conserved(zr, UR);
+  zg_flux(zl, D + 1, FL);
+  zg_flux(zr, D + 1, FR);
+  const double gtt = g(G_CON + sym(0, 0)), gtj = g(G_CON + sym(0, D + 1)), gjj = g(G_CON + sym(D + 1, D + 1));
+  const double cm = fmax(zg_cmax(zl, gtt, gtj, gjj, D + 1, p.gamma, a.kappa),
+                         zg_cmax(zr, gtt, gtj, gjj, D + 1, p.gamma, a.kappa));
+#pragma unroll
+  for (int v = 0; v < NV; v++) out[v * fb.size] = sg * (0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]));
+}
+
+// ---------------------------------------------------------------- zone constants
+// Theta, u_mu and sqrt(-g) u^d of the P^E state of zone (i,j,k) (ghosts by the
+// boundary rules, geometry of the ghost centre itself).
+__device__ void gr_derived(const Params& p, const GrArgs& a, int i, int j, int k, const RC<double>& c, double& th,
+                           double ucov[4], double sgu[3]) {
+  double P[NV];
+  gr_prim(p, a.PE, i, j, k, P);
+  const GT g = centre_geo(p, a.gc, i, j);
+  Met<double> m;
+  met_load(m, g);
+  ZG<double> z;
+  zg_load(z, P, m, c);
+  th = z.theta;
+  const double sg = g(G_SQRTG);
+#pragma unroll
+  for (int q = 0; q < 4; q++) ucov[q] = z.ucov[q];
+#pragma unroll
+  for (int d = 0; d < 3; d++) sgu[d] = sg * z.ucon[d + 1];
+}
+
+__global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Params p,
+                                                     const __grid_constant__ GrArgs a) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const int i = (int)(z % p.n1), j = (int)((z / p.n1) % p.n2), k = (int)(z / ((long long)p.n1 * p.n2));
+  const int ijk[3] = {i, j, k};
+  // --- flux divergence with flux-CT on every pair of active directions
+  FaceBox fb[3];
+  for (int d = 0; d < 3; d++) fb[d] = face_box(p, d);
+  double divF[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) divF[v] = 0.0;
+  for (int d = 0; d < p.dim; d++) {
+    const long long lo = fb[d].at(i, j, k);
+    const long long hi = fb[d].at(i + (d == 0), j + (d == 1), k + (d == 2));
+    const double* F = a.F[d];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      // F^d[B^d] = 0; F^d[B^c] for an active c comes from the corner averages
+      // below; for an inactive c (B^3 in 2-D) it is the face flux itself
+      if (v >= 5 && v <= 7 && (v - 5 == d || v - 5 < p.dim)) continue;
+      divF[v] += (__ldg(F + v * fb[d].size + hi) - __ldg(F + v * fb[d].size + lo)) * p.idx[d];
+    }
+  }
+  for (int A = 0; A < p.dim; A++)
+    for (int B = A + 1; B < p.dim; B++) {
+      // E_AB at the four (A,B) edges of the zone: E(sa, sb) at zone ijk + sa e_A + sb e_B,
+      // E(q) = (F^A[B^B](q) + F^A[B^B](q - e_B) - F^B[B^A](q) - F^B[B^A](q - e_A)) / 4
+      double E[2][2];
+      const double* FA = a.F[A] + (5 + B) * fb[A].size;
+      const double* FB = a.F[B] + (5 + A) * fb[B].size;
+      for (int sa = 0; sa < 2; sa++)
+        for (int sb = 0; sb < 2; sb++) {
+          int q[3] = {ijk[0], ijk[1], ijk[2]};
+          q[A] += sa;
+          q[B] += sb;
+          int qb[3] = {q[0], q[1], q[2]}; qb[B] -= 1;
+          int qa[3] = {q[0], q[1], q[2]}; qa[A] -= 1;
+          E[sa][sb] = 0.25 * (__ldg(FA + fb[A].at(q[0], q[1], q[2])) + __ldg(FA + fb[A].at(qb[0], qb[1], qb[2])) -
+                              __ldg(FB + fb[B].at(q[0], q[1], q[2])) - __ldg(FB + fb[B].at(qa[0], qa[1], qa[2])));
+        }
+      // F^A[B^B] = (E(q) + E(q + e_B))/2 on A faces; F^B[B^A] = -(E(q) + E(q + e_A))/2 on B faces
+      divF[5 + B] += (0.5 * (E[1][0] + E[1][1]) - 0.5 * (E[0][0] + E[0][1])) * p.idx[A];
+      divF[5 + A] += (-0.5 * (E[0][1] + E[1][1]) + 0.5 * (E[0][0] + E[1][0])) * p.idx[B];
+    }
+  // --- states at P^E and P_n, geometry of the zone
+  const RC<double> c = make_rc<double>(p);
+  const GT g = centre_geo(p, a.gc, i, j);
+  Met<double> m;
+  met_load(m, g);
+  const double sg = g(G_SQRTG), tau = g(G_TAUR);
+  double PEz[NV], Pnz[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) { PEz[v] = __ldg(a.PE + v * N + z); Pnz[v] = __ldg(a.Pn + v * N + z); }
+  ZG<double> ze, zn;
+  zg_load(ze, PEz, m, c);
+  zg_load(zn, Pnz, m, c);
+  double Un[NV];
+  zg_conserved(zn, Un);
+#pragma unroll
+  for (int v = 0; v < NV; v++) Un[v] *= sg;
+  // --- geometric source at P^E: sqrt(-g) T^k_l Gamma^l_{nu k} (rows 1..4)
+  double Sg[4] = {0.0, 0.0, 0.0, 0.0};
+  {
+    double T[4][4];
+    for (int r = 0; r < 4; r++) zg_stress_row(ze, r, T[r]);
+    for (int n = 0; n < 4; n++) {
+      double s = 0.0;
+      for (int kk = 0; kk < 4; kk++)
+        for (int l = 0; l < 4; l++) s += T[kk][l] * g(G_GAM + 10 * l + sym(n, kk));
+      Sg[n] = sg * s;
+    }
+  }
+  // --- limited slopes at P^E of Theta, u_mu and sqrt(-g) u^d
+  double dTh[3] = {0.0, 0.0, 0.0}, du[3][4], divu_sp = 0.0;
+  for (int d = 0; d < 3; d++)
+    for (int q = 0; q < 4; q++) du[d][q] = 0.0;
+  {
+    double th0, u0[4], s0[3];
+    gr_derived(p, a, i, j, k, c, th0, u0, s0);
+    for (int d = 0; d < p.dim; d++) {
+      double thm, thp, um[4], up[4], sm[3], sp[3];
+      gr_derived(p, a, i - (d == 0), j - (d == 1), k - (d == 2), c, thm, um, sm);
+      gr_derived(p, a, i + (d == 0), j + (d == 1), k + (d == 2), c, thp, up, sp);
+      dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
+      for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
+      divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
+    }
+    divu_sp /= sg;
+  }
+  // --- stage constants (row scale folded in; sqrt(-g) folded into kU)
+  const double dts = a.dts, idts = 1.0 / dts, it = 1.0 / tau;
+  double* Kz = a.K + z;
+  double sr[NV];  // 1/(|U_v(P_n)| + |U_0(P_n)|)
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    sr[v] = 1.0 / (fabs(Un[v]) + fabs(Un[0]));
+    Kz[(K_U + v) * N] = sr[v] * sg;
+    const double S = (v >= 1 && v <= 4) ? Sg[v - 1] : 0.0;
+    Kz[(K_C + v) * N] = sr[v] * (dts * (divF[v] - S) - Un[v]);
+  }
+  const double cs2E = p.gamma * ze.pg / (ze.rho + p.gamma * ze.u);
+  const double* bh = ze.bhcon;
+  // sum over nu, l of Gamma^l_{nu mu} u^nu u_l at P^E, for each mu
+  double Gu[4];
+  for (int mu = 0; mu < 4; mu++) {
+    double s = 0.0;
+    for (int l = 0; l < 4; l++)
+      for (int nu = 0; nu < 4; nu++) s += g(G_GAM + 10 * l + sym(nu, mu)) * ze.ucon[nu] * ze.ucov[l];
+    Gu[mu] = s;
+  }
+  const double hoq = p.ho ? 0.5 * ze.qt : 0.0, hod = p.ho ? 0.5 * ze.dpt : 0.0;
+  // heat flux: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
+  double Aq = 0.0, Bq = 0.0, Cq[4] = {0.0, 0.0, 0.0, 0.0};
+  if (p.cond) {
+    const double chi = p.phi * cs2E * tau;
+    const double pre = -sqrt(tau * ze.rho * chi) / ze.theta;
+    double acc = 0.0;
+    for (int mu = 0; mu < 4; mu++) {
+      double a_sp = -Gu[mu];
+      for (int d = 0; d < 3; d++) a_sp += ze.ucon[d + 1] * du[d][mu];
+      acc += bh[mu] * a_sp;
+    }
+    Aq = pre * (bh[1] * dTh[0] + bh[2] * dTh[1] + bh[3] * dTh[2] + ze.theta * acc);
+    Bq = pre * bh[0];
+    for (int mu = 0; mu < 4; mu++) Cq[mu] = pre * ze.theta * bh[mu] * ze.ucon[0];
+  }
+  {
+    const double s8 = sr[8] * dts;
+    double cst = -Un[8] * idts + divF[8];
+    double src = 0.5 * zn.qt * it - Aq * it + Bq * zn.theta * idts * it;
+    for (int mu = 0; mu < 4; mu++) src += Cq[mu] * zn.ucov[mu] * idts * it;
+    src -= hoq * (divu_sp - zn.ucon[0] * idts);
+    cst += sg * src;
+    Kz[(K_C + 8) * N] = s8 * cst;
+    Kz[(K_Q + 0) * N] = sg * 0.5 * s8 * it;
+    Kz[(K_Q + 1) * N] = -sg * s8 * Bq * idts * it;
+    for (int mu = 0; mu < 4; mu++) Kz[(K_Q + 2 + mu) * N] = -sg * s8 * Cq[mu] * idts * it;
+    Kz[(K_Q + 6) * N] = -sg * s8 * hoq * idts;
+  }
+  // anisotropy: dP~_0 = Ad + Dd^nu (u_nu - u_nu,n)/dt_s + Ed (u^t - u^t_n)/dt_s
+  double Ad = 0.0, Dd[4] = {0.0, 0.0, 0.0, 0.0}, Ed = 0.0;
+  if (p.visc) {
+    const double nu = p.psi * cs2E * tau;
+    const double pre = 3.0 * sqrt(tau * ze.rho * nu / ze.theta);
+    double sp = 0.0;
+    for (int mu = 0; mu < 4; mu++)
+      for (int nn = 0; nn < 4; nn++) {
+        double nab = 0.0;
+        if (mu >= 1) nab = du[mu - 1][nn];
+        for (int l = 0; l < 4; l++) nab -= g(G_GAM + 10 * l + sym(mu, nn)) * ze.ucov[l];
+        sp += bh[mu] * bh[nn] * nab;
+      }
+    Ad = pre * (sp - divu_sp * (1.0 / 3.0));
+    for (int nn = 0; nn < 4; nn++) Dd[nn] = pre * bh[0] * bh[nn];
+    Ed = -pre * (1.0 / 3.0);
+  }
+  {
+    const double s9 = sr[9] * dts;
+    double cst = -Un[9] * idts + divF[9];
+    double src = 0.5 * zn.dpt * it - Ad * it + Ed * zn.ucon[0] * idts * it;
+    for (int nn = 0; nn < 4; nn++) src += Dd[nn] * zn.ucov[nn] * idts * it;
+    src -= hod * (divu_sp - zn.ucon[0] * idts);
+    cst += sg * src;
+    Kz[(K_C + 9) * N] = s9 * cst;
+    Kz[(K_D + 0) * N] = sg * 0.5 * s9 * it;
+    for (int nn = 0; nn < 4; nn++) Kz[(K_D + 1 + nn) * N] = -sg * s9 * Dd[nn] * idts * it;
+    Kz[(K_D + 5) * N] = -sg * s9 * (Ed * idts * it + hod * idts);
+  }
+  // --- initial guess: P_n (or the given guess), B from the flux-CT update
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    double x = a.guess ? __ldg(a.guess + v * N + z) : Pnz[v];
+    if (v >= 5 && v <= 7) x = (Un[v] - dts * divF[v]) / sg;
+    a.P0[v * N + z] = x;
+  }
+}
+
+// ---------------------------------------------------------------- floors
+// After the Newton solves of a stage: a zone whose iteration ended with a
+// non-zero status (no admissible root found) reverts to its start, P_n with
+// the flux-CT field B = -kC/kU of its field rows; then rho >= 1e-5 r^{-3/2},
+// u >= 1e-7 r^{-5/2} (r = 1 in Minkowski space), and -b^2 <= dP <= b^2/2 on
+// the physical anisotropy dP = dP~ (psi c_s^2 P_g)^(1/2).
+__global__ void floors_gr(const __grid_constant__ Params p, const double* __restrict__ gc,
+                          const double* __restrict__ K, const double* __restrict__ Pn,
+                          const uint8_t* __restrict__ status, double* __restrict__ P) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const int i = (int)(z % p.n1), j = (int)((z / p.n1) % p.n2);
+  const GT g = centre_geo(p, gc, i, j);
+  const double r = g(G_R);
+  double Pz[NV];
+  const bool failed = status[z] != 0;
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    if (failed) Pz[v] = (v >= 5 && v <= 7) ? -__ldg(K + (K_C + v) * N + z) / __ldg(K + (K_U + v) * N + z)
+                                           : __ldg(Pn + v * N + z);
+    else Pz[v] = P[v * N + z];
+  }
+  Pz[0] = fmax(Pz[0], 1e-5 / (r * sqrt(r)));
+  Pz[1] = fmax(Pz[1], 1e-7 / (r * r * sqrt(r)));
+  if (p.visc) {
+    Met<double> m;
+    met_load(m, g);
+    const RC<double> c = make_rc<double>(p);
+    ZG<double> zz;
+    zg_load(zz, Pz, m, c);
+    const double f = zz.ds;
+    if (f > 0.0) {
+      const double dP = Pz[9] * f, hi = 0.5 * zz.bsq, lo = -zz.bsq;
+      if (dP > hi) Pz[9] = hi / f;
+      else if (dP < lo) Pz[9] = lo / f;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; v++) P[v * N + z] = Pz[v];
+}
+
+// ---------------------------------------------------------------- host side
+long long gr_geometry_doubles(const Params& p) {
+  return (long long)NGC * (p.n1 + 2) * (p.n2 + 2) + (long long)NGF * (p.n1 + 1) * (p.n2 + 2) +
+         (long long)NGF * (p.n1 + 2) * (p.n2 + 1);
+}
+long long gr_face_doubles(const Params& p) {
+  long long s = 0;
+  for (int d = 0; d < p.dim; d++) s += (long long)NV * face_box(p, d).size;
+  return s;
+}
+
+static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a) {
+  a.gc = geo;
+  a.gf[0] = geo + (long long)NGC * (p.n1 + 2) * (p.n2 + 2);
+  a.gf[1] = a.gf[0] + (long long)NGF * (p.n1 + 1) * (p.n2 + 2);
+  double* f = faces;
+  for (int d = 0; d < 3; d++) {
+    a.F[d] = f;
+    if (d < p.dim) f += (long long)NV * face_box(p, d).size;
+  }
+  a.kappa = gr_kappa(p);
+}
+
+cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double h, const double x0[3],
+                               double* geo, cudaStream_t st) {
+  GeoArgs A;
+  A.metric = metric;
+  A.a = spin;
+  A.h = h;
+  for (int d = 0; d < 3; d++) { A.x0[d] = x0[d]; A.dx[d] = p.dx[d]; }
+  A.tau0 = p.tauR;
+  A.n1 = p.n1;
+  A.n2 = p.dim >= 2 ? p.n2 : 1;
+  A.gc = geo;
+  A.gf1 = geo + (long long)NGC * (A.n1 + 2) * (A.n2 + 2);
+  A.gf2 = A.gf1 + (long long)NGF * (A.n1 + 1) * (A.n2 + 2);
+  const long long n = (long long)(A.n1 + 2) * (A.n2 + 2) + (long long)(A.n1 + 1) * (A.n2 + 2) +
+                      (long long)(A.n1 + 2) * (A.n2 + 1);
+  geometry_tables<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo, double* faces, cudaStream_t st) {
+  GrArgs a{};
+  gr_args(p, geo, faces, a);
+  a.PE = PE;
+  for (int d = 0; d < p.dim; d++) {
+    const long long n = face_box(p, d).size;
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    if (d == 0) face_flux_gr<0><<<nb, 128, 0, st>>>(p, a);
+    else if (d == 1) face_flux_gr<1><<<nb, 128, 0, st>>>(p, a);
+    else face_flux_gr<2><<<nb, 128, 0, st>>>(p, a);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
+                                 const double* geo, double* faces, double* K, double* P0, cudaStream_t st) {
+  GrArgs a{};
+  gr_args(p, geo, faces, a);
+  a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.K = K; a.P0 = P0;
+  zone_const_gr<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K, const double* Pn,
+                             const uint8_t* status, double* P, cudaStream_t st) {
+  floors_gr<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, geo, K, Pn, status, P);
+  return cudaGetLastError();
+}
+
+}  // namespace grim

@@ -609,3 +609,366 @@ cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cuda
 }
 
 }  // namespace grim
+
+// ============================================================================
+// General metric (3-D grids and modified Kerr-Schild): the same Newton
+// iteration on the residual in a general metric.  The zone's metric (g_{mu
+// nu}, alpha, g^{ti}) comes from the centre table and sits in shared memory
+// beside the zone constants.  The FD Jacobian recomputes the whole state per
+// column (no structural specialisation), with the same step rule.
+#include "grim_gr.cuh"
+
+namespace grim {
+
+constexpr int NMET = 14;  // g_{mu nu} (10), alpha, g^{ti} (3)
+
+template <typename T, int BS> __device__ __forceinline__ Met<T> met_smem(const double* md) {
+  Met<T> m;
+#pragma unroll
+  for (int a = 0; a < 10; a++) m.gcov[a] = T(md[a * BS]);
+  m.alpha = T(md[10 * BS]);
+#pragma unroll
+  for (int i = 0; i < 3; i++) m.gti[i] = T(md[(11 + i) * BS]);
+  return m;
+}
+
+// Scaled residual of the stage in a general metric: r_a = kU_a U~_a(P) + kC_a
+// with U~ = U/sqrt(-g), plus the implicit relaxation terms of the q~ and dP~
+// rows in Theta, u_mu and u^t.
+template <typename T, class KA> __device__ __forceinline__ void r_all_gr(const ZG<T>& z, const KA& k, T r[NV]) {
+  T U[NV];
+  zg_conserved(z, U);
+#pragma unroll
+  for (int a = 0; a < NV; a++) r[a] = k(K_U + a) * U[a] + k(K_C + a);
+  T h = k(K_Q + 0) * z.qt + k(K_Q + 1) * z.theta + k(K_Q + 6) * z.ucon[0];
+  T d = k(K_D + 0) * z.dpt + k(K_D + 5) * z.ucon[0];
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+    h += k(K_Q + 2 + m) * z.ucov[m];
+    d += k(K_D + 1 + m) * z.ucov[m];
+  }
+  r[8] += h;
+  r[9] += d;
+}
+
+// Column steps: the FP64 Jacobian uses the step rule of Section 3.1
+// (fd_step).  The float32 Jacobian (SCALED) takes h_j = eps (|P_j| + s_j)
+// with the natural scale of each component: s = 0 for rho and u (their step
+// is relative; the torus atmosphere holds rho ~ 1e-7, u ~ 1e-10, where an
+// absolute float32 step would jump by orders of magnitude), 1/sqrt(g_jj)
+// for the velocity u~^j (unit proper speed), sqrt(rho) for B^i, q~ and dP~
+// (field-like: they enter the stress as squares over rho).
+template <typename T, bool CENTRAL, bool SCALED, int BS, class KA>
+__device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], const KA& k, const Met<T>& m,
+                                               const RC<T>& c, T eps, T* J) {
+  T sfield = T(0);
+  if (SCALED) sfield = sqr_root(fabs(P[0]));
+#pragma unroll 1
+  for (int col = 0; col < NV; col++) {
+    T Pe[NV];
+#pragma unroll
+    for (int a = 0; a < NV; a++) Pe[a] = P[a];
+    const T pj = P[col];
+    T pe;
+    if (SCALED) {
+      T s = sfield;
+      if (col <= 1) s = T(0);
+      else if (col <= 4) s = rsq(m.gcov[sym(col - 1, col - 1)]);
+      pe = pj + eps * (fabs(pj) + s);
+    } else {
+      pe = fd_step(pj, eps);
+    }
+    const T hstep = pe - pj;
+    Pe[col] = pe;
+    ZG<T> z;
+    zg_load(z, Pe, m, c);
+    T rp[NV];
+    r_all_gr(z, k, rp);
+    if (!CENTRAL) {
+      const T ih = nr_rcp(hstep);
+#pragma unroll
+      for (int i = 0; i < NV; i++) J[(i * NV + col) * BS] = (rp[i] - r[i]) * ih;
+    } else {
+      Pe[col] = pj - hstep;
+      zg_load(z, Pe, m, c);
+      T rm[NV];
+      r_all_gr(z, k, rm);
+      const T ih = T(0.5) * nr_rcp(hstep);
+#pragma unroll
+      for (int i = 0; i < NV; i++) J[(i * NV + col) * BS] = (rp[i] - rm[i]) * ih;
+    }
+  }
+}
+
+template <bool MIXED, int BS>
+__device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const float* kf, const double* md,
+                                     double P[NV], void* jac, int k0, int kstop) {
+  ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
+  const RC<double> c64 = make_rc<double>(p);
+  const KSm<double, BS> k64{kd};
+  const Met<double> m64 = met_smem<double, BS>(md);
+  const unsigned long long tol_bits = abits(p.tol);
+  ZG<double> z;
+  zg_load(z, P, m64, c64);
+  double r[NV];
+  r_all_gr(z, k64, r);
+  o.evals64++;
+  double f = sum_sq10(r);
+  int k = k0;
+  for (;;) {
+    if (!finite_bits(f)) { o.status |= ST_NONFINITE; break; }
+    if (max_abits10(r) <= tol_bits) break;
+    if (k >= p.kmax) { o.status |= ST_MAXIT; break; }
+    if (k >= kstop) { o.pending = true; break; }
+    double dP[NV];
+    bool ok;
+    if (!MIXED) {
+      double* J = (double*)jac + threadIdx.x;
+      double* b = J + NV * NV * BS;
+      fd_jacobian_gr<double, false, false, BS>(P, r, k64, m64, c64, p.eps64, J);
+      o.evals64 += NV;
+#pragma unroll
+      for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
+      ok = lu_solve_smem<double, BS>(J, b, dP);
+      o.lu64++;
+    } else {
+      const RC<float> c32 = make_rc<float>(p);
+      const KSm<float, BS> k32{kf};
+      const Met<float> m32 = met_smem<float, BS>(md);
+      float* J = (float*)jac + threadIdx.x;
+      float* b = J + NV * NV * BS;
+      float Pf[NV], rf[NV];
+#pragma unroll
+      for (int a = 0; a < NV; a++) Pf[a] = (float)P[a];
+      ZG<float> zf;
+      zg_load(zf, Pf, m32, c32);
+      r_all_gr(zf, k32, rf);
+      if (p.fd32c) {
+        fd_jacobian_gr<float, true, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J);
+        o.evals32 += 2 * NV + 1;
+      } else {
+        fd_jacobian_gr<float, false, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J);
+        o.evals32 += NV + 1;
+      }
+#pragma unroll
+      for (int i = 0; i < NV; i++) b[i * BS] = (float)(-r[i]);
+      float df[NV];
+      ok = lu_solve_smem<float, BS>(J, b, df);
+#pragma unroll
+      for (int i = 0; i < NV; i++) dP[i] = (double)df[i];
+      o.lu32++;
+    }
+    if (!ok) { o.status |= ST_SINGULAR; break; }
+    double lam = 1.0, Pt[NV], rt[NV], ft = 0.0;
+    for (int t = 0;; t++) {
+#pragma unroll
+      for (int a = 0; a < NV; a++) Pt[a] = fma(lam, dP[a], P[a]);
+      zg_load(z, Pt, m64, c64);
+      r_all_gr(z, k64, rt);
+      o.evals64++;
+      ft = sum_sq10(rt);
+      const bool fin = finite_bits(ft);
+      const double lim = 1.0 - 1e-4 * lam;
+      if (fin && ft < f * lim * lim) break;
+      if (t >= p.lsmax) { o.status |= ST_LSSTALL; break; }
+      lam = fin ? f * lam * lam / (ft + (2.0 * lam - 1.0) * f) : 0.5 * lam;
+    }
+#pragma unroll
+    for (int a = 0; a < NV; a++) { P[a] = Pt[a]; r[a] = rt[a]; }
+    f = ft;
+    k++;
+  }
+  o.iters = k;
+  o.done = k - k0;
+  o.res = __longlong_as_double((long long)max_abits10(r));
+  if (!(P[0] > 0.0) || !(P[1] > 0.0)) o.status |= ST_INADMISSIBLE;
+  return o;
+}
+
+template <bool MIXED, int BS> struct NewtonSmemGr {
+  static constexpr size_t kd = sizeof(double) * NK * BS;
+  static constexpr size_t md = sizeof(double) * NMET * BS;
+  static constexpr size_t kf = MIXED ? sizeof(float) * NK * BS : 0;
+  static constexpr size_t jac = (MIXED ? sizeof(float) : sizeof(double)) * (NV * NV + NV) * BS;
+  static constexpr size_t bytes = kd + md + kf + jac;
+};
+
+// Zone z's constants and metric into shared memory (this thread's column).
+template <bool MIXED, int BS>
+__device__ __forceinline__ void load_zone_gr(const Params& p, const double* K, const double* gc, long long z,
+                                             double* kd, float* kf, double* md) {
+  const long long N = p.N;
+#pragma unroll
+  for (int a = 0; a < NK; a++) {
+    const double x = __ldg(K + a * N + z);
+    kd[a * BS] = x;
+    if (MIXED) kf[a * BS] = (float)x;
+  }
+  const int i = (int)(z % p.n1), j = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
+  const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+  const double* g = gc + (long long)(j + 1) * (p.n1 + 2) + (i + 1);
+#pragma unroll
+  for (int a = 0; a < 10; a++) md[a * BS] = __ldg(g + (G_COV + a) * nc);
+  md[10 * BS] = __ldg(g + G_ALPHA * nc);
+#pragma unroll
+  for (int q = 0; q < 3; q++) md[(11 + q) * BS] = __ldg(g + (G_CON + sym(0, q + 1)) * nc);
+}
+
+template <bool MIXED, int BS>
+__global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Params p, const double* __restrict__ K,
+                                                      const double* __restrict__ gc, double* __restrict__ P,
+                                                      uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
+                                                      Counters* __restrict__ cnt, int kstop, int* __restrict__ queue,
+                                                      int* __restrict__ qcount) {
+  using S = NewtonSmemGr<MIXED, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* kd = (double*)smem_raw + threadIdx.x;
+  double* md = (double*)(smem_raw + S::kd) + threadIdx.x;
+  float* kf = (float*)(smem_raw + S::kd + S::md) + threadIdx.x;
+  void* jac = smem_raw + S::kd + S::md + S::kf;
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * BS + threadIdx.x;
+  const bool active = z < N;
+  ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
+  if (active) {
+    load_zone_gr<MIXED, BS>(p, K, gc, z, kd, kf, md);
+    double Pz[NV];
+#pragma unroll
+    for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
+    o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax);
+#pragma unroll
+    for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
+    iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
+    status[z] = (uint8_t)o.status;
+  }
+  if (queue) enqueue(queue, qcount, active && o.pending, z);
+  accumulate(cnt, o, active, false);
+}
+
+template <bool MIXED, int BS>
+__global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Params p, const double* __restrict__ K,
+                                                      const double* __restrict__ gc, double* __restrict__ P,
+                                                      uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
+                                                      Counters* __restrict__ cnt, const int* __restrict__ queue,
+                                                      const int* __restrict__ qcount) {
+  using S = NewtonSmemGr<MIXED, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* kd = (double*)smem_raw + threadIdx.x;
+  double* md = (double*)(smem_raw + S::kd) + threadIdx.x;
+  float* kf = (float*)(smem_raw + S::kd + S::md) + threadIdx.x;
+  void* jac = smem_raw + S::kd + S::md + S::kf;
+  const long long N = p.N;
+  const int count = *qcount;
+  for (int base = blockIdx.x * BS; base < count; base += gridDim.x * BS) {
+    const int q = base + (int)threadIdx.x;
+    const bool active = q < count;
+    ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
+    if (active) {
+      const long long z = queue[q];
+      load_zone_gr<MIXED, BS>(p, K, gc, z, kd, kf, md);
+      double Pz[NV];
+#pragma unroll
+      for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
+      o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, iters[z], p.kmax);
+#pragma unroll
+      for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
+      iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
+      status[z] = (uint8_t)o.status;
+    }
+    accumulate(cnt, o, active, false);
+  }
+}
+
+// Scaled (or raw) residual at Pk, general metric.
+__global__ void residual_once_gr(const __grid_constant__ Params p, const double* __restrict__ K,
+                                 const double* __restrict__ gc, const double* __restrict__ Pk, int scaled,
+                                 double dts, double* __restrict__ R) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const KGl kg{K + z, N};
+  const RC<double> c = make_rc<double>(p);
+  const int i = (int)(z % p.n1), j = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
+  const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+  const double* g = gc + (long long)(j + 1) * (p.n1 + 2) + (i + 1);
+  Met<double> m;
+#pragma unroll
+  for (int a = 0; a < 10; a++) m.gcov[a] = __ldg(g + (G_COV + a) * nc);
+  m.alpha = __ldg(g + G_ALPHA * nc);
+#pragma unroll
+  for (int q = 0; q < 3; q++) m.gti[q] = __ldg(g + (G_CON + sym(0, q + 1)) * nc);
+  const double sg = __ldg(g + G_SQRTG * nc);
+  double Pz[NV], r[NV];
+#pragma unroll
+  for (int a = 0; a < NV; a++) Pz[a] = Pk[a * N + z];
+  ZG<double> zz;
+  zg_load(zz, Pz, m, c);
+  r_all_gr(zz, kg, r);
+#pragma unroll
+  for (int a = 0; a < NV; a++) {
+    // the row weight is sqrt(-g) s_a / dt_s; divide out s_a / dt_s for the raw residual
+    R[a * N + z] = scaled ? r[a] : r[a] * sg / (kg(K_U + a) * dts);
+  }
+}
+
+template <bool MIXED, int BS> struct NewtonKernelsGr {
+  using S = NewtonSmemGr<MIXED, BS>;
+  static cudaError_t configure(int& qgrid) {
+    static bool done = false;
+    static int grid = 0;
+    if (!done) {
+      cudaError_t e = cudaFuncSetAttribute(newton_dense_gr<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)S::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(newton_queue_gr<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)S::bytes);
+      int dev = 0, sms = 0, per_sm = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue_gr<MIXED, BS>, BS, S::bytes);
+      if (e != cudaSuccess) return e;
+      grid = sms * (per_sm > 0 ? per_sm : 1);
+      done = true;
+    }
+    qgrid = grid;
+    return cudaSuccess;
+  }
+  static cudaError_t launch(const Params& p, const double* K, const double* gc, double* P, uint8_t* iters,
+                            uint8_t* status, Counters* cnt, int kcut, int* queue, int* qcount, cudaStream_t st) {
+    int qgrid = 0;
+    cudaError_t e = configure(qgrid);
+    if (e != cudaSuccess) return e;
+    const bool compact = queue && qcount && kcut < p.kmax;
+    if (compact && (e = cudaMemsetAsync(qcount, 0, sizeof(int), st)) != cudaSuccess) return e;
+    const long long nb = (p.N + BS - 1) / BS;
+    newton_dense_gr<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
+                                                                    compact ? kcut : p.kmax,
+                                                                    compact ? queue : nullptr, qcount);
+    if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
+    newton_queue_gr<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt, queue,
+                                                                      qcount);
+    return cudaGetLastError();
+  }
+};
+
+// Newton solves of one stage in a general metric (block size 32 or 64).
+cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
+                             uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
+                             int* qcount, cudaStream_t st) {
+  const bool b32 = cfg.bs == 32;
+  if (mixed) {
+    if (b32) return NewtonKernelsGr<true, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
+    return NewtonKernelsGr<true, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
+  }
+  if (b32) return NewtonKernelsGr<false, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
+  return NewtonKernelsGr<false, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
+}
+
+cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,
+                               double dts, double* R, cudaStream_t st) {
+  residual_once_gr<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, K, gc, Pk, scaled, dts, R);
+  return cudaGetLastError();
+}
+
+}  // namespace grim

@@ -23,6 +23,7 @@ FIELDS = ("rho", "u", "u1", "u2", "u3", "B1", "B2", "B3", "qt", "dPt")
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT = 0, 1, 2
 RECON_MC, RECON_WENO5 = 0, 1
 METRIC_MINKOWSKI = 0
+METRIC_MKS_KERR = 1
 
 
 @dataclass
@@ -50,6 +51,7 @@ class Problem:
     ls_max: int = 10
     spin: float = 0.0
     h_mks: float = 0.3
+    floors: bool = False        # post-stage density/energy floors and anisotropy clamp
 
     @property
     def dx(self):
@@ -189,3 +191,190 @@ def batched_boxes(seed_size: int = 6, seed_angle: int = 7, count: int = 64,
         P[6] = P[6] - 0.3 + bmag * math.sin(ang)
         out.append((prob, P, 0.5 / side))
     return out
+
+
+# ---------------------------------------------------------------- Kerr torus
+# Initial data only: a Fishbone-Moncrief torus around a Kerr black hole in
+# the modified Kerr-Schild coordinates of Section 2.1 (r = exp(X^1), theta =
+# pi X^2 + ((1-h)/2) sin(2 pi X^2), phi = X^3).  The closed forms below are
+# those of the Kerr metric in Boyer-Lindquist and Kerr-Schild form; they
+# build the starting state and the step size and are not used by the method.
+
+def torus_problem(n1: int = 192, n2: int = 192, n3: int = 128, spin: float = 0.9375, h: float = 0.3,
+                  r_out: float = 40.0, **kw) -> Problem:
+    """Config: 3-D MKS-Kerr, a = 0.9375, h = 0.3, r in [0.98 r_+, 40],
+    theta in [0, pi], phi in [0, 2 pi]; gamma = 13/9, phi = psi = 0.5,
+    tau_R = r^{3/2}; X1 outflow, X2 reflecting (polar axis), X3 periodic;
+    floors on.  n3 = 1 gives the axisymmetric 2-D version."""
+    r_hor = 1.0 + math.sqrt(1.0 - spin * spin)
+    dim = 3 if n3 > 1 else 2
+    base = dict(dim=dim, n=(n1, n2, n3), x_start=(math.log(0.98 * r_hor), 0.0, 0.0),
+                x_end=(math.log(r_out), 1.0, 2.0 * math.pi),
+                bc=((BC_OUTFLOW, BC_OUTFLOW), (BC_REFLECT, BC_REFLECT), (BC_PERIODIC, BC_PERIODIC)),
+                metric=METRIC_MKS_KERR, spin=spin, h_mks=h, gamma=13.0 / 9.0, phi=0.5, psi=0.5, tau_R=1.0,
+                floors=True)
+    base.update(kw)
+    return Problem(**base)
+
+
+def _mks_point(prob: Problem, X1, X2):
+    r = np.exp(X1)
+    th = math.pi * X2 + 0.5 * (1.0 - prob.h_mks) * np.sin(2.0 * math.pi * X2)
+    dth = math.pi * (1.0 + (1.0 - prob.h_mks) * np.cos(2.0 * math.pi * X2))
+    return r, th, dth
+
+
+def _fm_potential(a: float, l: float, r, th):
+    """W = -ln|u_phi| + l u_t/u_phi for the Fishbone-Moncrief flow with
+    u^t u_phi = l (Boyer-Lindquist); ln h = W - W(inner edge).  Also returns
+    u^t and u^phi (Boyer-Lindquist).  From the normalisation g^{ab} u_a u_b =
+    -1 with u_t = (l/u_phi - g^{t phi} u_phi)/g^{tt}: D u_phi^4 - g^{tt}
+    u_phi^2 - l^2 = 0, D = (g^{t phi})^2 - g^{tt} g^{phi phi}."""
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * np.cos(th) ** 2
+    dlt = r * r - 2.0 * r + a * a
+    A = (r * r + a * a) ** 2 - a * a * dlt * s2
+    gtt = -A / (sig * dlt)
+    gtp = -2.0 * a * r / (sig * dlt)
+    gpp = (dlt - a * a * s2) / (sig * dlt * s2)
+    D = gtp * gtp - gtt * gpp
+    y = (gtt + np.sqrt(gtt * gtt + 4.0 * D * l * l)) / (2.0 * D)
+    uphi_cov = np.sqrt(y)
+    ut_cov = (l / uphi_cov - gtp * uphi_cov) / gtt
+    W = -np.log(uphi_cov) + l * ut_cov / uphi_cov
+    ut = gtt * ut_cov + gtp * uphi_cov
+    uphi = gtp * ut_cov + gpp * uphi_cov
+    return W, ut, uphi
+
+
+def _fm_l(a: float, r_max: float) -> float:
+    """u^t u_phi of the circular equatorial geodesic at the pressure maximum
+    (where the pressure gradient vanishes): Omega = 1/(r^{3/2} + a)."""
+    r = r_max
+    om = 1.0 / (r ** 1.5 + a)
+    gtt, gtp, gpp = -(1.0 - 2.0 / r), -2.0 * a / r, r * r + a * a + 2.0 * a * a / r
+    ut = 1.0 / math.sqrt(-(gtt + 2.0 * gtp * om + gpp * om * om))
+    return ut * ut * (gtp + gpp * om)
+
+
+def _torus_thermo(prob: Problem, X1, X2, r_in: float, r_max: float):
+    """(rho, u, u^t, u^phi, inside) of the torus at the points (X1, X2)."""
+    a, gam = prob.spin, prob.gamma
+    l = _fm_l(a, r_max)
+    r, th, _ = _mks_point(prob, X1, X2)
+    W_in, _, _ = _fm_potential(a, l, np.array(r_in), np.array(0.5 * math.pi))
+    W_pk, _, _ = _fm_potential(a, l, np.array(r_max), np.array(0.5 * math.pi))
+    h_pk = math.exp(float(W_pk - W_in))
+    K = (h_pk - 1.0) * (gam - 1.0) / gam       # rho = 1 at the pressure maximum
+    with np.errstate(invalid="ignore", divide="ignore"):
+        W, ut, uphi = _fm_potential(a, l, r, th)
+        lnh = W - W_in
+    inside = (r >= r_in) & np.isfinite(lnh) & (lnh > 0.0)
+    hh = np.where(inside, np.exp(np.where(inside, lnh, 0.0)), 1.0)
+    rho = np.where(inside, ((hh - 1.0) * (gam - 1.0) / (K * gam)) ** (1.0 / (gam - 1.0)), 0.0)
+    u = K * rho ** gam / (gam - 1.0)
+    return rho, u, np.where(inside, ut, 1.0), np.where(inside, uphi, 0.0), inside
+
+
+def _ks_mks_gcov(prob: Problem, X1, X2):
+    """Covariant MKS metric components (t, 1, 2, 3), closed form."""
+    a = prob.spin
+    r, th, dth = _mks_point(prob, X1, X2)
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * np.cos(th) ** 2
+    f = 2.0 * r / sig
+    g = np.zeros((4, 4) + np.shape(r))
+    g[0, 0] = -(1.0 - f)
+    g[0, 1] = g[1, 0] = f * r
+    g[0, 3] = g[3, 0] = -a * f * s2
+    g[1, 1] = (1.0 + f) * r * r
+    g[1, 3] = g[3, 1] = -a * s2 * (1.0 + f) * r
+    g[2, 2] = sig * dth * dth
+    g[3, 3] = s2 * (sig + a * a * s2 * (1.0 + f))
+    return g
+
+
+def torus_state(prob: Problem, seed: int = 4, r_in: float = 6.0, r_max: float = 12.0, beta: float = 100.0,
+                noise: float = 0.04) -> np.ndarray:
+    """Fishbone-Moncrief torus (inner edge r_in, pressure maximum r_max,
+    rho_max = 1, p = K rho^gamma) in an atmosphere at the floors
+    (rho = 1e-5 r^{-3/2}, u = 1e-7 r^{-5/2}, at rest for the normal observer);
+    one poloidal loop A_phi = max(rho/rho_max - 0.2, 0) at the zone corners,
+    B scaled so that max P_g / max (b^2/2) = beta; u *= 1 + noise (xi - 1/2),
+    xi ~ U[0,1) (Philox seed) inside the torus; q~ = dP~ = 0.  The primitive
+    velocity is the normal-observer velocity u~^i = u^i - u^t g^{ti}/g^{tt}:
+    the torus moves along phi only (u^r = u^theta = 0 in Boyer-Lindquist and
+    Kerr-Schild), so u~^1 = 2 u^t / (Sigma + 2 r) and u~^3 = u^phi."""
+    n1, n2, n3 = prob.n
+    x1, x2, _ = zone_centers(prob)
+    X1, X2 = x1[0], x2[0]                  # axisymmetric: [n2, n1]
+    a, gam = prob.spin, prob.gamma
+    rho, u, ut, uphi, inside = _torus_thermo(prob, X1, X2, r_in, r_max)
+    r, th, dth = _mks_point(prob, X1, X2)
+    sig = r * r + a * a * np.cos(th) ** 2
+    P = np.zeros((NVAR, n3, n2, n1))
+    rho_fl, u_fl = 1e-5 * r ** -1.5, 1e-7 * r ** -2.5
+    P[0] = np.maximum(np.where(inside, rho, 0.0), rho_fl)
+    P[1] = np.maximum(np.where(inside, u, 0.0), u_fl)
+    P[2] = np.where(inside, 2.0 * ut / (sig + 2.0 * r), 0.0)
+    P[4] = np.where(inside, uphi, 0.0)
+    # vector potential at the corners (i - 1/2, j - 1/2)
+    dx1, dx2 = prob.dx[0], prob.dx[1]
+    c1 = prob.x_start[0] + np.arange(n1 + 1) * dx1
+    c2 = prob.x_start[1] + np.arange(n2 + 1) * dx2
+    C2, C1 = np.meshgrid(c2, c1, indexing="ij")
+    rho_c, _, _, _, _ = _torus_thermo(prob, C1, C2, r_in, r_max)
+    Aphi = np.maximum(rho_c - 0.2, 0.0)
+    sqrtg = sig * np.abs(np.sin(th)) * r * dth
+    B1 = ((Aphi[1:, :-1] + Aphi[1:, 1:]) - (Aphi[:-1, :-1] + Aphi[:-1, 1:])) / (2.0 * dx2 * sqrtg)
+    B2 = -((Aphi[:-1, 1:] + Aphi[1:, 1:]) - (Aphi[:-1, :-1] + Aphi[1:, :-1])) / (2.0 * dx1 * sqrtg)
+    # b^2 for the normalisation: u^mu from the normal-observer velocity
+    g = _ks_mks_gcov(prob, X1, X2)
+    vt = np.stack([P[2, 0], P[3, 0], P[4, 0]])
+    qsq = sum(g[i + 1, j + 1] * vt[i] * vt[j] for i in range(3) for j in range(3))
+    lor = np.sqrt(1.0 + qsq)
+    f = 2.0 * r / sig
+    alpha = 1.0 / np.sqrt(1.0 + f)                      # Kerr-Schild lapse (g^tt = -(1 + 2r/Sigma))
+    ucon = np.zeros((4,) + r.shape)
+    ucon[0] = lor / alpha
+    gti = [f / r, 0.0, 0.0]                             # g^{t1} = g^{tr}/r, g^{t2} = g^{t3} = 0
+    for i in range(3):
+        ucon[i + 1] = vt[i] - lor * alpha * gti[i]
+    ucov = np.einsum("mn...,n...->m...", g, ucon)
+    Bv = np.stack([B1, B2, np.zeros_like(B1)])
+    bt = sum(Bv[i] * ucov[i + 1] for i in range(3))
+    bcon = np.zeros_like(ucon)
+    bcon[0] = bt
+    for i in range(3):
+        bcon[i + 1] = (Bv[i] + bt * ucon[i + 1]) / ucon[0]
+    bsq = np.einsum("m...,mn...,n...->...", bcon, g, bcon)
+    pg_max = ((gam - 1.0) * np.where(inside, u, 0.0)).max()
+    pb_max = (0.5 * bsq).max()
+    scale = math.sqrt(pg_max / (beta * pb_max)) if pb_max > 0 else 0.0
+    P[5] = scale * B1
+    P[6] = scale * B2
+    rng = np.random.Generator(np.random.Philox(seed))
+    xi = rng.random((n3, n2, n1))
+    P[1] = np.where(inside, P[1] * (1.0 + noise * (xi - 0.5)), P[1])
+    return P
+
+
+def torus_dt(prob: Problem, cfl: float = 0.5) -> float:
+    """Fixed step: cfl x the smallest over zones and directions of dX^d over
+    the largest coordinate light speed along X^d (roots c of g^{tt} c^2 -
+    2 g^{td} c + g^{dd} = 0, Kerr-Schild inverse metric in MKS form)."""
+    a = prob.spin
+    x1, x2, _ = zone_centers(prob)
+    r, th, dth = _mks_point(prob, x1[0], x2[0])
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * np.cos(th) ** 2
+    dlt = r * r - 2.0 * r + a * a
+    gtt = -(1.0 + 2.0 * r / sig)
+    gtd = [2.0 * r / sig / r, np.zeros_like(r), np.zeros_like(r)]
+    gdd = [dlt / sig / (r * r), 1.0 / (sig * dth * dth), 1.0 / (sig * s2)]
+    dt = np.inf
+    for d in range(prob.dim):
+        disc = np.sqrt(gtd[d] ** 2 - gtt * gdd[d])
+        cmax = np.maximum(np.abs((gtd[d] + disc) / gtt), np.abs((gtd[d] - disc) / gtt))
+        dt = min(dt, float((prob.dx[d] / cmax).min()))
+    return cfl * dt
