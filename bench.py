@@ -308,6 +308,50 @@ def bench_batched(dev, mlp, torch, world, steps=3):
     return out
 
 
+def bench_kerr(dev, torch, world, steps=3, warmup=2):
+    """3-D Fishbone-Moncrief torus around a Kerr black hole (a = 0.9375,
+    modified Kerr-Schild, 192 x 192 x 128, floors on), dt fixed at CFL 0.5 of
+    the light-speed bound: zone-updates/s of the float64 and mixed arms."""
+    from paper_1702_01106_b300 import inputs
+    from paper_1702_01106_b300.grim import Grim, GRIM_FP64, GRIM_MIXED
+    prob = inputs.torus_problem(192, 192, 128)
+    P = torch.from_numpy(inputs.torus_state(prob))
+    dt = inputs.torus_dt(prob)
+    out = {"workload": "3-D Kerr torus a=0.9375 MKS 192x192x128, FM r_in=6 r_max=12, beta=100, floors, tol 1e-10",
+           "zones": prob.zones, "dt": dt, "steps": steps}
+    for name, prec in (("fp64", GRIM_FP64), ("mixed", GRIM_MIXED)):
+        g = Grim(prob, precision=prec)
+        a = P.to(dev)
+        b = torch.empty_like(a)
+        for _ in range(warmup):
+            g.step(a, b, dt)
+            a, b = b, a
+        torch.cuda.synchronize()
+        g.reset_stats()
+        g.kernel_times()
+        g.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            g.step(a, b, dt)
+            a, b = b, a
+        e1.record()
+        torch.cuda.synchronize()
+        g.profile(False)
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+        s = g.stats()
+        kt = g.kernel_times()
+        out[name] = {"value": world * prob.zones / (ms * 1e-3), "ms_per_step": ms,
+                     "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]), "failed": s["failed"],
+                     "max_res": s["max_res"], "kernel_ms_per_stage": {k: v[0] / v[1] for k, v in kt.items()}}
+        g.close()
+        del a, b
+        torch.cuda.empty_cache()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +360,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batched", action="store_true", help="skip the 64-box batched measurement")
+    ap.add_argument("--skip-kerr", action="store_true", help="skip the 3-D Kerr torus measurement")
     ap.add_argument("--case-only", action="store_true",
                     help="only the float64 and mixed steps of a --side box (for ncu captures)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="box side for --case-only")
@@ -474,6 +519,7 @@ def main():
            "d2h_bytes_per_step": int(P.nbytes)}
 
     batched = None if args.skip_batched else bench_batched(dev, mlp, torch, world)
+    kerr = None if args.skip_kerr else bench_kerr(dev, torch, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -511,6 +557,7 @@ def main():
             "peaks": {"fp64_tflops": p64, "fp32_tflops": p32, "hbm_gbs": peaks.get("hbm_gbs"),
                       "hbm_source": peak_kind},
             "batched_64_boxes": batched,
+            "kerr_torus_3d": kerr,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_timed,
             "clocks": clocks,
         }

@@ -247,7 +247,65 @@ static double gr_kappa(const Params& p) {
 
 // ---------------------------------------------------------------- faces
 // LLF flux (Section 2.4.2) on the face at the low side of zone (i,j,k) in
-// direction D, from MC or WENO5 face states of P^E.
+// direction D, from MC or WENO5 face states of P^E.  The stencil's zone
+// indices and reflection flips are resolved once; the fields are then loaded
+// and reconstructed one at a time.
+template <int D, bool WENO>
+__device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int i, int j, int k, const GT& g,
+                                          double* out, long long plane) {
+  constexpr int o0 = WENO ? -3 : -2, o1 = WENO ? 2 : 1, NS = o1 - o0 + 1;
+  long long zz[NS];
+  int fl[NS];  // reflection flips of the stencil zone, bit d for direction d
+#pragma unroll
+  for (int t = 0; t < NS; t++) {
+    bool f[3];
+    zz[t] = gr_zone(p, i + (D == 0) * (t + o0), j + (D == 1) * (t + o0), k + (D == 2) * (t + o0), f);
+    fl[t] = (f[0] ? 1 : 0) | (f[1] ? 2 : 0) | (f[2] ? 4 : 0);
+  }
+  const long long N = p.N;
+  double L[NV], R[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    // u~^d and B^d change sign in a zone mirrored across a boundary of direction d
+    const int bit = (v >= 2 && v <= 4) ? 1 << (v - 2) : (v >= 5 && v <= 7) ? 1 << (v - 5) : 0;
+    double s[NS];
+#pragma unroll
+    for (int t = 0; t < NS; t++) {
+      const double x = __ldg(a.PE + v * N + zz[t]);
+      s[t] = (fl[t] & bit) ? -x : x;
+    }
+    if (WENO) {
+      L[v] = weno5v(s[0], s[1], s[2], s[3], s[4]);
+      R[v] = weno5v(s[5], s[4], s[3], s[2], s[1]);
+    } else {
+      L[v] = fma(0.5, gm_slope(p.theta, s[0], s[1], s[2]), s[1]);
+      R[v] = fma(-0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
+    }
+  }
+  Met<double> m;
+  met_load(m, g);
+  const RC<double> c = make_rc<double>(p);
+  double FL[NV], FR[NV], UL[NV], UR[NV], cl, cr;
+  const double gtt = g(G_CON + sym(0, 0)), gtj = g(G_CON + sym(0, D + 1)), gjj = g(G_CON + sym(D + 1, D + 1));
+  {
+    ZG<double> z;
+    zg_load(z, L, m, c);
+    zg_conserved(z, UL);
+    zg_flux(z, D + 1, FL);
+    cl = zg_cmax(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa);
+  }
+  {
+    ZG<double> z;
+    zg_load(z, R, m, c);
+    zg_conserved(z, UR);
+    zg_flux(z, D + 1, FR);
+    cr = zg_cmax(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa);
+  }
+  const double cm = fmax(cl, cr), sg = g(G_SQRTG);
+#pragma unroll
+  for (int v = 0; v < NV; v++) out[v * plane] = sg * (0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]));
+}
+
 template <int D>
 __global__ void __launch_bounds__(128) face_flux_gr(const __grid_constant__ Params p,
                                                     const __grid_constant__ GrArgs a) {
@@ -264,46 +322,13 @@ __global__ void __launch_bounds__(128) face_flux_gr(const __grid_constant__ Para
                      (long long)(p.n1 + 1) * (p.n2 + 2)};
   else if (D == 1) g = GT{a.gf[1] + (long long)j * (p.n1 + 2) + (i + 1), (long long)(p.n1 + 2) * (p.n2 + 1)};
   else g = centre_geo(p, a.gc, i, j);
-  const double sg = g(G_SQRTG);
-  if (sg == 0.0) {
+  if (g(G_SQRTG) == 0.0) {
 #pragma unroll
     for (int v = 0; v < NV; v++) out[v * fb.size] = 0.0;
     return;
   }
-  const bool weno = p.recon == RECON_WENO5;
-  double L[NV], R[NV];
-  {
-    double s[6][NV];
-    const int o0 = weno ? -3 : -2, o1 = weno ? 2 : 1;
-    for (int t = o0; t <= o1; t++)
-      gr_prim(p, a.PE, i + (D == 0) * t, j + (D == 1) * t, k + (D == 2) * t, s[t + 3]);
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-      if (weno) {
-        L[v] = weno5v(s[0][v], s[1][v], s[2][v], s[3][v], s[4][v]);
-        R[v] = weno5v(s[5][v], s[4][v], s[3][v], s[2][v], s[1][v]);
-      } else {
-        L[v] = fma(0.5, gm_slope(p.theta, s[1][v], s[2][v], s[3][v]), s[2][v]);
-        R[v] = fma(-0.5, gm_slope(p.theta, s[2][v], s[3][v], s[4][v]), s[3][v]);
-      }
-    }
-  }
-  Met<double> m;
-  met_load(m, g);
-  const RC<double> c = make_rc<double>(p);
-  ZG<double> zl, zr;
-  zg_load(zl, L, m, c);
-  zg_load(zr, R, m, c);
-  double UL[NV], UR[NV], FL[NV], FR[NV];
-  zg_conserved(zl, UL);
-  zg_conserved(zr, UR);
-  zg_flux(zl, D + 1, FL);
-  zg_flux(zr, D + 1, FR);
-  const double gtt = g(G_CON + sym(0, 0)), gtj = g(G_CON + sym(0, D + 1)), gjj = g(G_CON + sym(D + 1, D + 1));
-  const double cm = fmax(zg_cmax(zl, gtt, gtj, gjj, D + 1, p.gamma, a.kappa),
-                         zg_cmax(zr, gtt, gtj, gjj, D + 1, p.gamma, a.kappa));
-#pragma unroll
-  for (int v = 0; v < NV; v++) out[v * fb.size] = sg * (0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]));
+  if (p.recon == RECON_WENO5) face_body<D, true>(p, a, i, j, k, g, out, fb.size);
+  else face_body<D, false>(p, a, i, j, k, g, out, fb.size);
 }
 
 // ---------------------------------------------------------------- zone constants
@@ -335,11 +360,14 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
   const int ijk[3] = {i, j, k};
   // --- flux divergence with flux-CT on every pair of active directions
   FaceBox fb[3];
+#pragma unroll
   for (int d = 0; d < 3; d++) fb[d] = face_box(p, d);
   double divF[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) divF[v] = 0.0;
-  for (int d = 0; d < p.dim; d++) {
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    if (d >= p.dim) continue;
     const long long lo = fb[d].at(i, j, k);
     const long long hi = fb[d].at(i + (d == 0), j + (d == 1), k + (d == 2));
     const double* F = a.F[d];
@@ -351,14 +379,19 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
       divF[v] += (__ldg(F + v * fb[d].size + hi) - __ldg(F + v * fb[d].size + lo)) * p.idx[d];
     }
   }
-  for (int A = 0; A < p.dim; A++)
-    for (int B = A + 1; B < p.dim; B++) {
+#pragma unroll
+  for (int A = 0; A < 3; A++)
+#pragma unroll
+    for (int B = A + 1; B < 3; B++) {
+      if (B >= p.dim) continue;
       // E_AB at the four (A,B) edges of the zone: E(sa, sb) at zone ijk + sa e_A + sb e_B,
       // E(q) = (F^A[B^B](q) + F^A[B^B](q - e_B) - F^B[B^A](q) - F^B[B^A](q - e_A)) / 4
       double E[2][2];
       const double* FA = a.F[A] + (5 + B) * fb[A].size;
       const double* FB = a.F[B] + (5 + A) * fb[B].size;
+#pragma unroll
       for (int sa = 0; sa < 2; sa++)
+#pragma unroll
         for (int sb = 0; sb < 2; sb++) {
           int q[3] = {ijk[0], ijk[1], ijk[2]};
           q[A] += sa;
@@ -392,26 +425,35 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
   double Sg[4] = {0.0, 0.0, 0.0, 0.0};
   {
     double T[4][4];
+#pragma unroll
     for (int r = 0; r < 4; r++) zg_stress_row(ze, r, T[r]);
+#pragma unroll
     for (int n = 0; n < 4; n++) {
       double s = 0.0;
+#pragma unroll
       for (int kk = 0; kk < 4; kk++)
+#pragma unroll
         for (int l = 0; l < 4; l++) s += T[kk][l] * g(G_GAM + 10 * l + sym(n, kk));
       Sg[n] = sg * s;
     }
   }
   // --- limited slopes at P^E of Theta, u_mu and sqrt(-g) u^d
   double dTh[3] = {0.0, 0.0, 0.0}, du[3][4], divu_sp = 0.0;
+#pragma unroll
   for (int d = 0; d < 3; d++)
+#pragma unroll
     for (int q = 0; q < 4; q++) du[d][q] = 0.0;
   {
     double th0, u0[4], s0[3];
     gr_derived(p, a, i, j, k, c, th0, u0, s0);
-    for (int d = 0; d < p.dim; d++) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      if (d >= p.dim) continue;
       double thm, thp, um[4], up[4], sm[3], sp[3];
       gr_derived(p, a, i - (d == 0), j - (d == 1), k - (d == 2), c, thm, um, sm);
       gr_derived(p, a, i + (d == 0), j + (d == 1), k + (d == 2), c, thp, up, sp);
       dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
+#pragma unroll
       for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
       divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
     }
@@ -432,8 +474,10 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
   const double* bh = ze.bhcon;
   // sum over nu, l of Gamma^l_{nu mu} u^nu u_l at P^E, for each mu
   double Gu[4];
+  #pragma unroll
   for (int mu = 0; mu < 4; mu++) {
     double s = 0.0;
+    #pragma unroll
     for (int l = 0; l < 4; l++)
       for (int nu = 0; nu < 4; nu++) s += g(G_GAM + 10 * l + sym(nu, mu)) * ze.ucon[nu] * ze.ucov[l];
     Gu[mu] = s;
@@ -445,25 +489,30 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
     const double chi = p.phi * cs2E * tau;
     const double pre = -sqrt(tau * ze.rho * chi) / ze.theta;
     double acc = 0.0;
+    #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
       double a_sp = -Gu[mu];
+      #pragma unroll
       for (int d = 0; d < 3; d++) a_sp += ze.ucon[d + 1] * du[d][mu];
       acc += bh[mu] * a_sp;
     }
     Aq = pre * (bh[1] * dTh[0] + bh[2] * dTh[1] + bh[3] * dTh[2] + ze.theta * acc);
     Bq = pre * bh[0];
+    #pragma unroll
     for (int mu = 0; mu < 4; mu++) Cq[mu] = pre * ze.theta * bh[mu] * ze.ucon[0];
   }
   {
     const double s8 = sr[8] * dts;
     double cst = -Un[8] * idts + divF[8];
     double src = 0.5 * zn.qt * it - Aq * it + Bq * zn.theta * idts * it;
+    #pragma unroll
     for (int mu = 0; mu < 4; mu++) src += Cq[mu] * zn.ucov[mu] * idts * it;
     src -= hoq * (divu_sp - zn.ucon[0] * idts);
     cst += sg * src;
     Kz[(K_C + 8) * N] = s8 * cst;
     Kz[(K_Q + 0) * N] = sg * 0.5 * s8 * it;
     Kz[(K_Q + 1) * N] = -sg * s8 * Bq * idts * it;
+    #pragma unroll
     for (int mu = 0; mu < 4; mu++) Kz[(K_Q + 2 + mu) * N] = -sg * s8 * Cq[mu] * idts * it;
     Kz[(K_Q + 6) * N] = -sg * s8 * hoq * idts;
   }
@@ -473,14 +522,18 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
     const double nu = p.psi * cs2E * tau;
     const double pre = 3.0 * sqrt(tau * ze.rho * nu / ze.theta);
     double sp = 0.0;
+    #pragma unroll
     for (int mu = 0; mu < 4; mu++)
+      #pragma unroll
       for (int nn = 0; nn < 4; nn++) {
         double nab = 0.0;
         if (mu >= 1) nab = du[mu - 1][nn];
+        #pragma unroll
         for (int l = 0; l < 4; l++) nab -= g(G_GAM + 10 * l + sym(mu, nn)) * ze.ucov[l];
         sp += bh[mu] * bh[nn] * nab;
       }
     Ad = pre * (sp - divu_sp * (1.0 / 3.0));
+    #pragma unroll
     for (int nn = 0; nn < 4; nn++) Dd[nn] = pre * bh[0] * bh[nn];
     Ed = -pre * (1.0 / 3.0);
   }
@@ -488,11 +541,13 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
     const double s9 = sr[9] * dts;
     double cst = -Un[9] * idts + divF[9];
     double src = 0.5 * zn.dpt * it - Ad * it + Ed * zn.ucon[0] * idts * it;
+    #pragma unroll
     for (int nn = 0; nn < 4; nn++) src += Dd[nn] * zn.ucov[nn] * idts * it;
     src -= hod * (divu_sp - zn.ucon[0] * idts);
     cst += sg * src;
     Kz[(K_C + 9) * N] = s9 * cst;
     Kz[(K_D + 0) * N] = sg * 0.5 * s9 * it;
+    #pragma unroll
     for (int nn = 0; nn < 4; nn++) Kz[(K_D + 1 + nn) * N] = -sg * s9 * Dd[nn] * idts * it;
     Kz[(K_D + 5) * N] = -sg * s9 * (Ed * idts * it + hod * idts);
   }
