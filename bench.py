@@ -450,9 +450,11 @@ def main():
     steps = args.steps
 
     def newton_flops(st):
-        f64 = st["evals64"] * fl["residual"] + st["lu64"] * fl["lu_solve"]
-        f64 += st["iters"] * (fl["newton_update_bookkeeping"] if st["lu64"] else 60)
-        f32 = st["evals32"] * fl["residual"] + st["lu32"] * fl["lu_solve"] + (st["iters"] * 220 if st["lu32"] else 0)
+        # the kernels solve the 7x7 non-magnetic block (7 Jacobian columns)
+        f64 = st["evals64"] * fl["residual"] + st["lu64"] * fl["lu_solve_7x7"]
+        f64 += st["iters"] * (fl["newton_update_bookkeeping_7x7"] if st["lu64"] else 60)
+        f32 = st["evals32"] * fl["residual"] + st["lu32"] * fl["lu_solve_7x7"]
+        f32 += st["iters"] * 154 if st["lu32"] else 0
         return f64, f32
 
     def class_flops(cls, st, launches):

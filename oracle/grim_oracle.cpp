@@ -780,30 +780,31 @@ static void residual(const ZoneConst& z, const Params& p, const T* P, T* r) {
 
 // Partial-pivot LU solve of J x = b (10x10, row-major J, overwritten).
 // Returns false on an exactly zero pivot.  Pivot: largest |a_ik|, lowest row on ties.
-template <class T> static bool lu_solve(T J[10][10], T b[10], T x[10]) {
-  for (int k = 0; k < 10; k++) {
+template <int N, class T> static bool lu_solve_n(T J[N][N], T b[N], T x[N]) {
+  for (int k = 0; k < N; k++) {
     int piv = k;
     double best = std::fabs(re(J[k][k]));
-    for (int i = k + 1; i < 10; i++)
+    for (int i = k + 1; i < N; i++)
       if (std::fabs(re(J[i][k])) > best) { best = std::fabs(re(J[i][k])); piv = i; }
     if (best == 0.0) return false;
     if (piv != k) {
-      for (int c = 0; c < 10; c++) std::swap(J[k][c], J[piv][c]);
+      for (int c = 0; c < N; c++) std::swap(J[k][c], J[piv][c]);
       std::swap(b[k], b[piv]);
     }
-    for (int i = k + 1; i < 10; i++) {
+    for (int i = k + 1; i < N; i++) {
       T l = J[i][k] / J[k][k];
-      for (int c = k + 1; c < 10; c++) J[i][c] = J[i][c] - l * J[k][c];
+      for (int c = k + 1; c < N; c++) J[i][c] = J[i][c] - l * J[k][c];
       b[i] = b[i] - l * b[k];
     }
   }
-  for (int i = 9; i >= 0; i--) {
+  for (int i = N - 1; i >= 0; i--) {
     T acc = b[i];
-    for (int c = i + 1; c < 10; c++) acc = acc - J[i][c] * x[c];
+    for (int c = i + 1; c < N; c++) acc = acc - J[i][c] * x[c];
     x[i] = acc / J[i][i];
   }
   return true;
 }
+template <class T> static bool lu_solve(T J[10][10], T b[10], T x[10]) { return lu_solve_n<10>(J, b, x); }
 
 static double maxabs(const double* r) {
   double m = 0;
@@ -1441,7 +1442,17 @@ int oracle_flop_counts(const int* ip, const double* dp, const double* zc, const 
   // differences, 100 residual differences and 100 divisions, 10 step
   // updates (2 each), the two norms (20 each).
   out4[2] = 10 + 10 + 100 + 100 + 20 + 40;
-  out4[3] = -1;  // explicit part: not counted here
+  // the 7x7 block of the non-magnetic components (rows and columns of rho,
+  // u, u^i, q~, dP~): the solve of the paper's EMHD form (Section 8.2)
+  static const int nb[7] = {0, 1, 2, 3, 4, 8, 9};
+  Cnt J7[7][7], b7[7], x7[7];
+  for (int i = 0; i < 7; i++) {
+    b7[i] = Cnt(1.0 + i, true);
+    for (int j = 0; j < 7; j++) J7[i][j] = Cnt(Jd[nb[i]][nb[j]], true);
+  }
+  g_flops = 0;
+  lu_solve_n<7>(J7, b7, x7);
+  out4[3] = g_flops;
   return 0;
 }
 

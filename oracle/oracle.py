@@ -179,7 +179,8 @@ def lu_solve(J, b):
 
 
 def flop_counts(prob, zc, P):
-    """(residual, LU solve, Newton bookkeeping, explicit) algorithmic flops."""
+    """(residual, 10x10 LU solve, Newton bookkeeping, 7x7 LU solve of the
+    non-magnetic block) algorithmic flops."""
     ip, dp = params(prob)
     out = np.zeros(4, dtype=np.int64)
     lib().oracle_flop_counts(_iptr(ip), _dptr(dp), _dptr(_c(zc)), _dptr(_c(P)),

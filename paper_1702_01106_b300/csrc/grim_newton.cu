@@ -159,6 +159,11 @@ __device__ __forceinline__ void fd_column(const Z<T>& z, const T r[NV], const KA
   }
 }
 
+// The Jacobian columns of rho, u, u^i, q~, dP~.  The B columns are not
+// formed: the B rows are linear in B alone (r_B = kU_B B + kC_B) and the
+// start already holds their root, the flux-CT field, so the Newton update of
+// B is zero to round-off and the system reduces to the 7x7 block of the
+// other components (the paper's EMHD solve, Section 8.2).
 template <typename T, bool CENTRAL, int BS, class KA>
 __device__ __forceinline__ void fd_jacobian(const Z<T>& z, const T r[NV], const KA& k, const RC<T>& c, T eps,
                                             T* J) {
@@ -167,11 +172,66 @@ __device__ __forceinline__ void fd_jacobian(const Z<T>& z, const T r[NV], const 
   fd_column<2, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<3, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<4, CENTRAL, T, BS>(z, r, k, c, eps, J);
-  fd_column<5, CENTRAL, T, BS>(z, r, k, c, eps, J);
-  fd_column<6, CENTRAL, T, BS>(z, r, k, c, eps, J);
-  fd_column<7, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<8, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<9, CENTRAL, T, BS>(z, r, k, c, eps, J);
+}
+
+// Index of the m-th non-magnetic component (rho, u, u^1..3, q~, dP~).
+__host__ __device__ constexpr int nb7(int m) { return m < 5 ? m : m + 3; }
+
+// Partial-pivot LU solve of the 7x7 non-magnetic block of J (rows and columns
+// nb7(0..6) of the 10x10 layout in shared memory, stride BS); x[5..7] = 0.
+// Pivot: largest |a_ik|, lowest row on ties.  Returns false on a zero pivot.
+template <typename T, int BS>
+__device__ __forceinline__ bool lu_solve7_smem(T* J, T* b, T x[NV]) {
+  T inv[7];
+#pragma unroll
+  for (int k = 0; k < 7; k++) {
+    const int kk = nb7(k);
+    int piv = k;
+    auto best = abits(J[(kk * NV + kk) * BS]);
+#pragma unroll
+    for (int i = k + 1; i < 7; i++) {
+      const auto a = abits(J[(nb7(i) * NV + kk) * BS]);
+      if (a > best) { best = a; piv = i; }
+    }
+    if (best == 0) return false;
+    if (piv != k) {
+      const int pp = nb7(piv);
+#pragma unroll
+      for (int c = k; c < 7; c++) {
+        const int cc = nb7(c);
+        const T t = J[(kk * NV + cc) * BS];
+        J[(kk * NV + cc) * BS] = J[(pp * NV + cc) * BS];
+        J[(pp * NV + cc) * BS] = t;
+      }
+      const T t = b[kk * BS];
+      b[kk * BS] = b[pp * BS];
+      b[pp * BS] = t;
+    }
+    inv[k] = nr_rcp(J[(kk * NV + kk) * BS]);
+    const T bk = b[kk * BS];
+#pragma unroll
+    for (int i = k + 1; i < 7; i++) {
+      const int ii = nb7(i);
+      const T a = J[(ii * NV + kk) * BS];
+      if (abits(a) == 0) continue;  // zero multiplier: row i is unchanged
+      const T l = a * inv[k];
+#pragma unroll
+      for (int c = k + 1; c < 7; c++) J[(ii * NV + nb7(c)) * BS] -= l * J[(kk * NV + nb7(c)) * BS];
+      b[ii * BS] -= l * bk;
+    }
+  }
+  x[5] = x[6] = x[7] = T(0);
+#pragma unroll
+  for (int i = 6; i >= 0; i--) {
+    const int ii = nb7(i);
+    T acc = b[ii * BS];
+#pragma unroll
+    for (int c = i + 1; c < 7; c++) acc -= J[(ii * NV + nb7(c)) * BS] * x[nb7(c)];
+    x[ii] = acc * inv[i];
+  }
+  return true;
 }
 
 // Partial-pivot LU solve J x = b with J, b in shared memory at stride BS
@@ -295,10 +355,10 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       double* J = (double*)jac + threadIdx.x;
       double* b = J + NV * NV * BS;
       fd_jacobian<double, false, BS>(z, r, k64, c64, p.eps64, J);
-      o.evals64 += NV;
+      o.evals64 += 7;
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
-      ok = lu_solve_smem<double, BS>(J, b, dP);
+      ok = lu_solve7_smem<double, BS>(J, b, dP);
       o.lu64++;
     } else {
       const RC<float> c32 = make_rc<float>(p);
@@ -313,15 +373,15 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       r_all(zf, k32, rf);
       if (p.fd32c) {
         fd_jacobian<float, true, BS>(zf, rf, k32, c32, p.eps32, J);
-        o.evals32 += 2 * NV + 1;
+        o.evals32 += 2 * 7 + 1;
       } else {
         fd_jacobian<float, false, BS>(zf, rf, k32, c32, p.eps32, J);
-        o.evals32 += NV + 1;
+        o.evals32 += 7 + 1;
       }
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = (float)(-r[i]);
       float df[NV];
-      ok = lu_solve_smem<float, BS>(J, b, df);
+      ok = lu_solve7_smem<float, BS>(J, b, df);
 #pragma unroll
       for (int i = 0; i < NV; i++) dP[i] = (double)df[i];
       o.lu32++;
@@ -664,7 +724,8 @@ __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], con
   T sfield = T(0);
   if (SCALED) sfield = sqr_root(fabs(P[0]));
 #pragma unroll 1
-  for (int col = 0; col < NV; col++) {
+  for (int mc = 0; mc < 7; mc++) {  // the non-magnetic columns (7x7 solve, see fd_jacobian)
+    const int col = nb7(mc);
     T Pe[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pe[a] = P[a];
@@ -726,10 +787,10 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       double* J = (double*)jac + threadIdx.x;
       double* b = J + NV * NV * BS;
       fd_jacobian_gr<double, false, false, BS>(P, r, k64, m64, c64, p.eps64, J);
-      o.evals64 += NV;
+      o.evals64 += 7;
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
-      ok = lu_solve_smem<double, BS>(J, b, dP);
+      ok = lu_solve7_smem<double, BS>(J, b, dP);
       o.lu64++;
     } else {
       const RC<float> c32 = make_rc<float>(p);
@@ -745,15 +806,15 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       r_all_gr(zf, k32, rf);
       if (p.fd32c) {
         fd_jacobian_gr<float, true, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J);
-        o.evals32 += 2 * NV + 1;
+        o.evals32 += 2 * 7 + 1;
       } else {
         fd_jacobian_gr<float, false, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J);
-        o.evals32 += NV + 1;
+        o.evals32 += 7 + 1;
       }
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = (float)(-r[i]);
       float df[NV];
-      ok = lu_solve_smem<float, BS>(J, b, df);
+      ok = lu_solve7_smem<float, BS>(J, b, df);
 #pragma unroll
       for (int i = 0; i < NV; i++) dP[i] = (double)df[i];
       o.lu32++;

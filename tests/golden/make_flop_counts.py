@@ -26,12 +26,17 @@ def counts():
     Pn = P[:, 1000].copy()
     Pn[8:10] = 1e-3 * rng.standard_normal(2)       # a zone with heat flux and anisotropy
     zc = zone_vector(oracle, prob, Pn, Pn, 0.25 / 1024, divu=0.01)
-    res, lu, book, _ = oracle.flop_counts(prob, zc, Pn * 1.001)
+    res, lu, book, lu7 = oracle.flop_counts(prob, zc, Pn * 1.001)
     line = np.stack([P[:, 1000 + t] for t in range(-4, 4)])
     line[:, 8:10] = 1e-3
     face, zone = oracle.explicit_flops(prob, line, Pn)
+    # bookkeeping with the 7 non-magnetic Jacobian columns: 7 perturbations,
+    # 7 divisor differences, 70 residual differences and 70 divisions, the
+    # 10 step updates (2 each) and the two norms (20 each)
+    book7 = 7 + 7 + 70 + 70 + 20 + 40
     return {"residual": int(res), "lu_solve": int(lu), "newton_update_bookkeeping": int(book),
-            "face_flux": int(face), "zone_explicit_remainder_2d": int(zone)}
+            "face_flux": int(face), "zone_explicit_remainder_2d": int(zone), "lu_solve_7x7": int(lu7),
+            "newton_update_bookkeeping_7x7": book7}
 
 
 def main():
