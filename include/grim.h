@@ -48,6 +48,9 @@ extern "C" {
 #define GRIM_RECON_MC 0    /* generalized minmod, parameter theta (2 = MC, 1 = minmod) */
 #define GRIM_RECON_WENO5 1 /* Jiang & Shu WENO5 */
 
+#define GRIM_FLUX_LLF 0    /* local Lax-Friedrichs (Section 2.4.2) */
+#define GRIM_FLUX_HLLE 1   /* HLLE with the bounds c_R = max(c, 0), c_L = max(-c, 0) (Section 2.4.2) */
+
 #define GRIM_FP64 0        /* Jacobian, LU, residual all in float64 */
 #define GRIM_MIXED 1       /* Jacobian and LU in float32; residual, update and test in float64 */
 
@@ -79,6 +82,7 @@ typedef struct {
                    then rho >= 1e-5 r^{-3/2}, u >= 1e-7 r^{-5/2} (r = 1 in
                    Minkowski space), -b^2 <= dP <= b^2/2.  General-metric
                    path only (3-D or Kerr grids). */
+  int riemann;  /* GRIM_FLUX_LLF or GRIM_FLUX_HLLE (grim_step_static: LLF only) */
 } grim_physics;
 
 /* Nonlinear solver (Section 3).  Converged when max_a |r_a| <= tol with

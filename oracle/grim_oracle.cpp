@@ -177,7 +177,7 @@ using cplx = std::complex<double>;
 // Integer and real parameter vectors, laid out as documented in oracle.py.
 enum {
   I_DIM, I_N1, I_N2, I_N3, I_BC1L, I_BC1H, I_BC2L, I_BC2H, I_BC3L, I_BC3H,
-  I_METRIC, I_RECON, I_COND, I_VISC, I_HO, I_KMAX, I_LSMAX, I_FLOORS, I_NTHREADS, I_COUNT
+  I_METRIC, I_RECON, I_COND, I_VISC, I_HO, I_KMAX, I_LSMAX, I_FLOORS, I_RIEMANN, I_NTHREADS, I_COUNT
 };
 enum {
   D_X01, D_X02, D_X03, D_DX1, D_DX2, D_DX3, D_GAMMA, D_PHI, D_PSI, D_TAUR,
@@ -189,7 +189,7 @@ enum { RECON_MC = 0, RECON_WENO5 = 1 };
 enum { ST_MAXIT = 1, ST_LSSTALL = 2, ST_SINGULAR = 4, ST_NONFINITE = 8, ST_INADMISSIBLE = 16 };
 
 struct Params {
-  int dim, n[3], bc[3][2], metric, recon, cond, visc, ho, kmax, lsmax, floors;
+  int dim, n[3], bc[3][2], metric, recon, cond, visc, ho, kmax, lsmax, floors, riemann;
   double x0[3], dx[3], gamma, phi, psi, tauR, theta, tol, eps, a, h;
   long long N;
 };
@@ -203,7 +203,7 @@ static Params read_params(const int* ip, const double* dp) {
   p.bc[2][0] = ip[I_BC3L]; p.bc[2][1] = ip[I_BC3H];
   p.metric = ip[I_METRIC]; p.recon = ip[I_RECON];
   p.cond = ip[I_COND]; p.visc = ip[I_VISC]; p.ho = ip[I_HO];
-  p.kmax = ip[I_KMAX]; p.lsmax = ip[I_LSMAX]; p.floors = ip[I_FLOORS];
+  p.kmax = ip[I_KMAX]; p.lsmax = ip[I_LSMAX]; p.floors = ip[I_FLOORS]; p.riemann = ip[I_RIEMANN];
   for (int d = 0; d < 3; d++) { p.x0[d] = dp[D_X01 + d]; p.dx[d] = dp[D_DX1 + d]; }
   p.gamma = dp[D_GAMMA]; p.phi = dp[D_PHI]; p.psi = dp[D_PSI]; p.tauR = dp[D_TAUR];
   p.theta = dp[D_THETA]; p.tol = dp[D_TOL]; p.eps = dp[D_EPS]; p.a = dp[D_A]; p.h = dp[D_H];
@@ -587,7 +587,7 @@ struct Stage {
 };
 
 // LLF flux at the face on the low side of zone (i,j,k) in direction d
-// (Section 2.4.2): F = (F^+ + F^-)/2 - c_max/2 (U^+ - U^-).
+// (Section 2.4.2): F = (F^+ + F^-)/2 - c_max/2 (U^+ - U^-); or HLLE.
 static void face_flux(const Grid& G, const double* PE, int d, int i, int j, int k, double Fout[10]) {
   const Params& p = G.p;
   double L[10], R[10];
@@ -625,6 +625,14 @@ static void face_flux(const Grid& G, const double* PE, int d, int i, int j, int 
   double cminL, cmaxL, cminR, cmaxR;
   wave_speeds(sl, g, p, d + 1, cminL, cmaxL);
   wave_speeds(sr, g, p, d + 1, cminR, cmaxR);
+  if (p.riemann == 1) {
+    // HLLE (Section 2.4.2): right- and left-going bounds cR = max(c, 0),
+    // cL = max(-c, 0) over both sides; L is the left state P^-, R the right P^+
+    const double cR = std::max(std::max(cmaxL, cmaxR), 0.0);
+    const double cL = std::max(-std::min(cminL, cminR), 0.0);
+    for (int v = 0; v < 10; v++) Fout[v] = (cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) / (cL + cR);
+    return;
+  }
   double cm = std::max(std::max(std::fabs(cminL), std::fabs(cmaxL)), std::max(std::fabs(cminR), std::fabs(cmaxR)));
   for (int v = 0; v < 10; v++) Fout[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
 }

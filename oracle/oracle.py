@@ -6,7 +6,8 @@ it; the product library never imports it.
 
 Parameter vectors passed to the C++ side:
   ip = [dim, n1, n2, n3, bc1lo, bc1hi, bc2lo, bc2hi, bc3lo, bc3hi, metric,
-        recon, conduction, viscosity, higher_order, k_max, ls_max, floors, nthreads]
+        recon, conduction, viscosity, higher_order, k_max, ls_max, floors, riemann,
+        nthreads]
   dp = [x0_1, x0_2, x0_3, dx1, dx2, dx3, gamma, phi, psi, tau_R, theta, tol,
         eps_fd, spin, h_mks]
 """
@@ -21,7 +22,7 @@ from . import build as _build
 
 _lib = None
 
-I_COUNT = 19
+I_COUNT = 20
 D_COUNT = 15
 ST_MAXIT, ST_LSSTALL, ST_SINGULAR, ST_NONFINITE, ST_INADMISSIBLE = 1, 2, 4, 8, 16
 
@@ -47,7 +48,7 @@ def params(prob, threads: int = 0):
                    prob.bc[0][0], prob.bc[0][1], prob.bc[1][0], prob.bc[1][1],
                    prob.bc[2][0], prob.bc[2][1], prob.metric, prob.recon,
                    int(prob.conduction), int(prob.viscosity), int(prob.higher_order),
-                   prob.k_max, prob.ls_max, int(prob.floors), threads], dtype=np.int32)
+                   prob.k_max, prob.ls_max, int(prob.floors), prob.riemann, threads], dtype=np.int32)
     dx = prob.dx
     dp = np.array([prob.x_start[0], prob.x_start[1], prob.x_start[2], dx[0], dx[1], dx[2],
                    prob.gamma, prob.phi, prob.psi, prob.tau_R, prob.theta, prob.tol,

@@ -178,6 +178,7 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   if (metric->kind != GRIM_METRIC_MINKOWSKI && metric->kind != GRIM_METRIC_MKS_KERR) return GRIM_EINVAL;
   if (metric->kind == GRIM_METRIC_MKS_KERR && !(std::fabs(metric->spin) < 1.0)) return GRIM_EINVAL;
   if (phys->recon != GRIM_RECON_MC && phys->recon != GRIM_RECON_WENO5) return GRIM_EINVAL;
+  if (phys->riemann != GRIM_FLUX_LLF && phys->riemann != GRIM_FLUX_HLLE) return GRIM_EINVAL;
   if (solver->precision != GRIM_FP64 && solver->precision != GRIM_MIXED) return GRIM_EINVAL;
   if (!(phys->gamma > 1.0) || !(phys->tau_R > 0.0) || !(solver->tol > 0.0) || solver->k_max < 0 ||
       solver->k_max > 250 || solver->ls_max < 0)
@@ -200,7 +201,7 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   p.cond = phys->conduction; p.visc = phys->viscosity; p.ho = phys->higher_order; p.recon = phys->recon;
   p.tol = solver->tol; p.eps64 = solver->eps_fd; p.eps32 = (float)solver->eps_fd32;
   p.kmax = solver->k_max; p.lsmax = solver->ls_max; p.fd32c = solver->fd32_central != 0;
-  p.metric = metric->kind; p.floors = phys->floors;
+  p.metric = metric->kind; p.floors = phys->floors; p.riemann = phys->riemann;
   p.N = (long long)grid->n1 * grid->n2 * grid->n3;
   ctx->precision = solver->precision;
   ctx->gr = grid->dim == 3 || metric->kind != GRIM_METRIC_MINKOWSKI;

@@ -42,6 +42,7 @@ struct Params {
   int kmax, lsmax;
   int fd32c;  // centred differences for the float32 Jacobian
   int metric, floors;
+  int riemann;  // 0 LLF, 1 HLLE
   long long N;
 };
 

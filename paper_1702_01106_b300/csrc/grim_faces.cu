@@ -54,13 +54,13 @@ __device__ __forceinline__ double load_comp(const double* P, long long N, long l
 
 // Conserved variables U and flux F^j (j = 1, 2, 3) of a face state (Eqs.
 // divN_explicit, divT_explicit, induction_eqn and the q~, dP~ equations), and
-// the largest |grid-frame speed| in direction j of waves moving at +-v_max in
-// the fluid frame (Section 4.1, Minkowski space): the roots c of
+// the grid-frame speeds in direction j of waves moving at +-v_max in the
+// fluid frame (Section 4.1, Minkowski space): the roots cmin <= cmax of
 // (u^j - c u^t)^2 (1 - v^2) = v^2 (1 - c^2).  kappa = cs~^2/c_s^2, a constant
 // of the closure chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R (Eq. modcs).
 template <int j>
-__device__ __forceinline__ double side_flux(const Z<double>& z, double gam, double kappa, double U[NV],
-                                            double F[NV]) {
+__device__ __forceinline__ void side_flux(const Z<double>& z, double gam, double kappa, double U[NV], double F[NV],
+                                          double& cmin, double& cmax) {
   const double q = z.qt * z.qs, dp = z.dpt * z.ds;
   const double third = dp * (1.0 / 3.0);
   const double wt = z.w0 + z.bsq + third;
@@ -100,7 +100,28 @@ __device__ __forceinline__ double side_flux(const Z<double>& z, double gam, doub
   const double Bq = -2.0 * om * z.ut * uj;
   const double Cq = om * uj * uj - v2;
   const double disc = fmax(Bq * Bq - 4.0 * Aq * Cq, 0.0);
-  return (fabs(Bq) + sqrt(disc)) * (0.5 * nr_rcp(Aq));
+  const double sq = sqrt(disc), h = 0.5 * nr_rcp(Aq);  // Aq > 0
+  cmax = (sq - Bq) * h;
+  cmin = -((sq + Bq) * h);
+}
+
+// LLF (F^- + F^+)/2 - c_max (U^+ - U^-)/2 with c_max the largest |c| of both
+// sides, or HLLE (c_R F^- + c_L F^+ - c_R c_L (U^+ - U^-))/(c_L + c_R) with
+// c_R = max(c, 0), c_L = max(-c, 0) over both sides (Section 2.4.2);
+// L: the left state P^-, R: the right state P^+.
+__device__ __forceinline__ void riemann_flux(int kind, const double FL[NV], const double FR[NV], const double UL[NV],
+                                             const double UR[NV], double cminL, double cmaxL, double cminR,
+                                             double cmaxR, double* out, long long plane) {
+  if (kind == 1) {
+    const double cR = fmax(fmax(cmaxL, cmaxR), 0.0), cL = fmax(-fmin(cminL, cminR), 0.0);
+    const double iw = 1.0 / (cL + cR);
+#pragma unroll
+    for (int v = 0; v < NV; v++) out[v * plane] = (cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) * iw;
+  } else {
+    const double cm = fmax(fmax(cmaxL, -cminL), fmax(cmaxR, -cminR));
+#pragma unroll
+    for (int v = 0; v < NV; v++) out[v * plane] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+  }
 }
 
 struct ExpArgs {
@@ -152,11 +173,10 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   z_load(zl, L, c);
   z_load(zr, R, c);
   double UL[NV], FL[NV], UR[NV], FR[NV];
-  const double cl = side_flux<D + 1>(zl, p.gamma, a.kappa, UL, FL);
-  const double cr = side_flux<D + 1>(zr, p.gamma, a.kappa, UR, FR);
-  const double cm = fmax(cl, cr);
-#pragma unroll
-  for (int v = 0; v < NV; v++) out[v * plane] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+  double cminL, cmaxL, cminR, cmaxR;
+  side_flux<D + 1>(zl, p.gamma, a.kappa, UL, FL, cminL, cmaxL);
+  side_flux<D + 1>(zr, p.gamma, a.kappa, UR, FR, cminR, cmaxR);
+  riemann_flux(p.riemann, FL, FR, UL, UR, cminL, cmaxL, cminR, cmaxR, out, plane);
 }
 
 template <int BS>

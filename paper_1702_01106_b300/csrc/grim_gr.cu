@@ -285,25 +285,36 @@ __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int 
   Met<double> m;
   met_load(m, g);
   const RC<double> c = make_rc<double>(p);
-  double FL[NV], FR[NV], UL[NV], UR[NV], cl, cr;
+  double FL[NV], FR[NV], UL[NV], UR[NV], cminL, cmaxL, cminR, cmaxR;
   const double gtt = g(G_CON + sym(0, 0)), gtj = g(G_CON + sym(0, D + 1)), gjj = g(G_CON + sym(D + 1, D + 1));
   {
     ZG<double> z;
     zg_load(z, L, m, c);
     zg_conserved(z, UL);
     zg_flux(z, D + 1, FL);
-    cl = zg_cmax(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa);
+    zg_speeds(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa, cminL, cmaxL);
   }
   {
     ZG<double> z;
     zg_load(z, R, m, c);
     zg_conserved(z, UR);
     zg_flux(z, D + 1, FR);
-    cr = zg_cmax(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa);
+    zg_speeds(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa, cminR, cmaxR);
   }
-  const double cm = fmax(cl, cr), sg = g(G_SQRTG);
+  const double sg = g(G_SQRTG);
+  double Fv[NV];
+  if (p.riemann == 1) {  // HLLE (Section 2.4.2)
+    const double cR = fmax(fmax(cmaxL, cmaxR), 0.0), cL = fmax(-fmin(cminL, cminR), 0.0);
+    const double iw = 1.0 / (cL + cR);
 #pragma unroll
-  for (int v = 0; v < NV; v++) out[v * plane] = sg * (0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]));
+    for (int v = 0; v < NV; v++) Fv[v] = (cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) * iw;
+  } else {               // LLF
+    const double cm = fmax(fmax(cmaxL, -cminL), fmax(cmaxR, -cminR));
+#pragma unroll
+    for (int v = 0; v < NV; v++) Fv[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; v++) out[v * plane] = sg * Fv[v];
 }
 
 template <int D>

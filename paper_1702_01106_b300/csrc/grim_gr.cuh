@@ -148,9 +148,9 @@ template <typename T> __device__ __forceinline__ void zg_flux(const ZG<T>& z, in
 // cs~^2 vA^2, Section 4.1): roots c of (k.u)^2 = v^2 (k.k + (k.u)^2),
 // k_mu = (-c, e_j), i.e. A c^2 + B c + C = 0 with A = (1-v^2)(u^t)^2 - v^2
 // g^tt, B = -2((1-v^2) u^t u^j - v^2 g^tj), C = (1-v^2)(u^j)^2 - v^2 g^jj.
-// kappa = cs~^2 / cs^2 (a constant of the closure).  Returns max |c|.
-__device__ __forceinline__ double zg_cmax(const ZG<double>& z, double gtt, double gtj, double gjj, int j,
-                                          double gam, double kappa) {
+// kappa = cs~^2 / cs^2 (a constant of the closure).  cmin <= cmax.
+__device__ __forceinline__ void zg_speeds(const ZG<double>& z, double gtt, double gtj, double gjj, int j,
+                                          double gam, double kappa, double& cmin, double& cmax) {
   const double iden = 1.0 / (z.rho + gam * z.u + z.bsq);
   const double cs2 = gam * z.pg / (z.rho + gam * z.u);
   const double cs2t = kappa * cs2;
@@ -166,7 +166,8 @@ __device__ __forceinline__ double zg_cmax(const ZG<double>& z, double gtt, doubl
   const double sq = sqrt(disc);
   const double i2a = 0.5 / A;
   const double c1 = (-B + sq) * i2a, c2 = (-B - sq) * i2a;
-  return fmax(fabs(c1), fabs(c2));
+  cmin = fmin(c1, c2);
+  cmax = fmax(c1, c2);
 }
 
 }  // namespace grim

@@ -62,6 +62,7 @@ int make_params(const grim_grid* grid, const grim_metric* metric, const grim_phy
   if (grid->dim != 2 || grid->n3 != 1 || grid->n1 < 1 || grid->n2 < 1) return GRIM_EINVAL;
   if (metric->kind != GRIM_METRIC_MINKOWSKI) return GRIM_EINVAL;
   if (phys->recon != GRIM_RECON_MC && phys->recon != GRIM_RECON_WENO5) return GRIM_EINVAL;
+  if (phys->riemann != GRIM_FLUX_LLF) return GRIM_EINVAL;  // the tile kernel has the LLF flux only
   if (solver->precision != GRIM_FP64 && solver->precision != GRIM_MIXED) return GRIM_EINVAL;
   if (!(phys->gamma > 1.0) || !(phys->tau_R > 0.0) || !(solver->tol > 0.0) || solver->k_max < 0 ||
       solver->k_max > 250 || solver->ls_max < 0)

@@ -47,7 +47,7 @@ class GrimPhysics(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("tau_R", ctypes.c_double), ("phi", ctypes.c_double),
                 ("psi", ctypes.c_double), ("conduction", ctypes.c_int), ("viscosity", ctypes.c_int),
                 ("higher_order", ctypes.c_int), ("recon", ctypes.c_int), ("theta", ctypes.c_double),
-                ("floors", ctypes.c_int)]
+                ("floors", ctypes.c_int), ("riemann", ctypes.c_int)]
 
 
 class GrimSolver(ctypes.Structure):
@@ -163,7 +163,7 @@ def _config(prob, precision, eps_fd32, fd32_central=FD32_CENTRAL):
                  ((ctypes.c_int * 2) * 3)(*[(ctypes.c_int * 2)(*b) for b in prob.bc]))
     m = GrimMetric(prob.metric, prob.spin, prob.h_mks)
     ph = GrimPhysics(prob.gamma, prob.tau_R, prob.phi, prob.psi, int(prob.conduction), int(prob.viscosity),
-                     int(prob.higher_order), prob.recon, prob.theta, int(prob.floors))
+                     int(prob.higher_order), prob.recon, prob.theta, int(prob.floors), int(prob.riemann))
     sv = GrimSolver(precision, prob.tol, prob.eps_fd, eps_fd32, prob.k_max, prob.ls_max, int(fd32_central))
     return g, m, ph, sv
 

@@ -22,6 +22,7 @@ FIELDS = ("rho", "u", "u1", "u2", "u3", "B1", "B2", "B3", "qt", "dPt")
 
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT = 0, 1, 2
 RECON_MC, RECON_WENO5 = 0, 1
+FLUX_LLF, FLUX_HLLE = 0, 1
 METRIC_MINKOWSKI = 0
 METRIC_MKS_KERR = 1
 
@@ -52,6 +53,7 @@ class Problem:
     spin: float = 0.0
     h_mks: float = 0.3
     floors: bool = False        # post-stage density/energy floors and anisotropy clamp
+    riemann: int = FLUX_LLF     # approximate Riemann solver of the face fluxes
 
     @property
     def dx(self):

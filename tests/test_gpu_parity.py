@@ -173,3 +173,18 @@ def test_stage_parity_non_periodic_boundaries(dev, orc, bc):
     ref, _, rst, _ = orc.stage(prob, Pn, Pn, dts)
     assert rst.max() == 0
     assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("recon", [inputs.RECON_MC, inputs.RECON_WENO5])
+def test_stage_parity_hlle(dev, orc, recon):
+    """The HLLE flux (Section 2.4.2) on the flat path: one stage within 1e-12
+    of the oracle."""
+    prob, Pn = _ragged_turbulent(recon=recon, riemann=inputs.FLUX_HLLE)
+    dts = 0.25 / 32
+    g = _g(prob)
+    out = torch.empty_like(_t(Pn, dev))
+    g.stage(_t(Pn, dev), _t(Pn, dev), dts, out)
+    ref, _, rst, _ = orc.stage(prob, Pn, Pn, dts)
+    assert rst.max() == 0
+    assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
+    g.close()
