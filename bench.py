@@ -32,6 +32,7 @@ N_SIDE = 1024
 # bfloat16 MACs per zone of the learned-start network (32x128, 2 x 128x128,
 # 128x80), 2 flops each.
 MLP_FLOPS_PER_ZONE = 2 * (32 * 128 + 2 * 128 * 128 + 128 * 80)
+MLP_TRAIN_STEPS = 24000   # Adam steps of the learned start (untimed, about 20 s)
 # DRAM bytes read + written per launch at 1024^2 from the ncu captures in
 # profiles/explicit_turbulent_box_1024.md and profiles/newton_turbulent_box_1024.md
 # (None once a kernel changes after its capture).
@@ -393,7 +394,7 @@ def main():
     from paper_1702_01106_b300 import guess
     t0 = time.perf_counter()
     Xtr, Ytr, _ = guess.collect(prob, P, dt, 8, dev)
-    mlp, losses = guess.train(Xtr, Ytr, steps=6000)
+    mlp, losses = guess.train(Xtr, Ytr, steps=MLP_TRAIN_STEPS)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     n_samples = int(Xtr.shape[0])
@@ -549,7 +550,7 @@ def main():
                               "failed": st_m["failed"], "max_res": st_m["max_res"],
                               "fallback_rate": st_m["fallbacks"] / max(1, st_m["zones"]),
                               "one_step_max_rel_diff_vs_fp64": learned_err,
-                              "training": {"samples": n_samples, "adam_steps": 6000, "batch": 4096,
+                              "training": {"samples": n_samples, "adam_steps": MLP_TRAIN_STEPS, "batch": 4096,
                                            "loss_per_quarter": losses, "seconds": train_s}},
             "tuning": tunings,
             "speedup_mixed_learned_vs_fp64": ms_d / ms_m,

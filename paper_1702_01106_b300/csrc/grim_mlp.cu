@@ -416,6 +416,7 @@ __global__ void mlp_colstats(const float* __restrict__ X, long long M, int ncol,
 // fragment loads conflict-free).  The result replaces the non-magnetic
 // components of the Newton initial guess: P0 = P_n + prediction.
 constexpr int IW1 = MLP_IN + 8, IWH = MLP_H + 8;
+constexpr int INF_WARPS = 12; // warps per block: one block per SM shares one copy of the weights
 struct InferSmem {
   __nv_bfloat16 w0[MLP_H][IW1];
   __nv_bfloat16 w1[MLP_H][IWH];
@@ -423,9 +424,9 @@ struct InferSmem {
   __nv_bfloat16 w3[MLP_HEAD][IWH];
   float b[3 * MLP_H + MLP_HEAD];
   float norm[2 * MLP_IN + 2 * MLP_Y];
-  __nv_bfloat16 x[4][16][IW1];   // per-warp input tile
-  float xh[4][16][MLP_XU];       // per-warp head features (float32)
-  float y[4][16][MLP_HEAD + 1];  // per-warp head output tile
+  __nv_bfloat16 x[INF_WARPS][16][IW1];   // per-warp input tile
+  float xh[INF_WARPS][16][MLP_XU];       // per-warp head features (float32)
+  float y[INF_WARPS][16][MLP_HEAD + 1];  // per-warp head output tile
 };
 
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
@@ -468,7 +469,7 @@ __device__ __forceinline__ void to_afrag(float acc[16][4], const float* b, unsig
   }
 }
 
-__global__ void __launch_bounds__(128) mlp_guess(const __grid_constant__ Params p, const double* __restrict__ K,
+__global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constant__ Params p, const double* __restrict__ K,
                                                 const double* __restrict__ Pn, const double* __restrict__ Un,
                                                 const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
                                                 const float* __restrict__ norm, double* __restrict__ P0) {
@@ -476,14 +477,15 @@ __global__ void __launch_bounds__(128) mlp_guess(const __grid_constant__ Params 
   InferSmem& S = *reinterpret_cast<InferSmem*>(smraw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // weights to shared memory
-  for (int i = tid; i < MLP_H * MLP_IN; i += 128) S.w0[i / MLP_IN][i % MLP_IN] = wb[mlp_woff(0) - 0 + i];
+  constexpr int NT = INF_WARPS * 32;
+  for (int i = tid; i < MLP_H * MLP_IN; i += NT) S.w0[i / MLP_IN][i % MLP_IN] = wb[mlp_woff(0) - 0 + i];
   const int o1 = MLP_H * MLP_IN, o2 = o1 + MLP_H * MLP_H, o3 = o2 + MLP_H * MLP_H;
-  for (int i = tid; i < MLP_H * MLP_H; i += 128) {
+  for (int i = tid; i < MLP_H * MLP_H; i += NT) {
     S.w1[i / MLP_H][i % MLP_H] = wb[o1 + i];
     S.w2[i / MLP_H][i % MLP_H] = wb[o2 + i];
   }
-  for (int i = tid; i < MLP_HEAD * MLP_H; i += 128) S.w3[i / MLP_H][i % MLP_H] = wb[o3 + i];
-  for (int i = tid; i < MLP_H; i += 128) {
+  for (int i = tid; i < MLP_HEAD * MLP_H; i += NT) S.w3[i / MLP_H][i % MLP_H] = wb[o3 + i];
+  for (int i = tid; i < MLP_H; i += NT) {
     S.b[i] = params[mlp_boff(0) + i];
     S.b[MLP_H + i] = params[mlp_boff(1) + i];
     S.b[2 * MLP_H + i] = params[mlp_boff(2) + i];
@@ -494,8 +496,9 @@ __global__ void __launch_bounds__(128) mlp_guess(const __grid_constant__ Params 
   const long long N = p.N;
   const RC<double> c = make_rc<double>(p);
   const float g[10] = {-1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f};
-  // persistent over tiles of 64 zones (16 per warp)
-  for (long long base = (long long)blockIdx.x * 64; base < N; base += (long long)gridDim.x * 64) {
+  // persistent over tiles of 16 zones per warp
+  for (long long base = (long long)blockIdx.x * (16 * INF_WARPS); base < N;
+       base += (long long)gridDim.x * (16 * INF_WARPS)) {
     // features: lanes 0..15 of each warp build one zone each
     const long long zw = base + warp * 16;
     if (lane < 16) {
@@ -851,10 +854,11 @@ cudaError_t launch_mlp_guess(const Params& p, const double* K, const double* Pn,
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  long long tiles = (p.N + 63) / 64;
-  long long grid = sms * 2;
+  long long tiles = (p.N + 16 * INF_WARPS - 1) / (16 * INF_WARPS);
+  long long grid = sms;  // persistent: one block (and one copy of the weights) per SM
   if (grid > tiles) grid = tiles;
-  mlp_guess<<<(unsigned)grid, 128, sizeof(InferSmem), st>>>(p, K, Pn, Un, m->wb, m->params, m->norm, P0);
+  mlp_guess<<<(unsigned)grid, INF_WARPS * 32, sizeof(InferSmem), st>>>(p, K, Pn, Un, m->wb, m->params, m->norm,
+                                                                       P0);
   return cudaGetLastError();
 }
 }  // namespace grim
