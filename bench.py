@@ -211,23 +211,32 @@ def nvtx_pop(torch):
 
 
 def profile_case(args, dev, torch):
-    """--case-only: the float64 and mixed steps of the turbulent box alone
+    """--case-only: the float64 and mixed steps of one workload alone
     (autotuned, warmed up, then `--steps` steps in the NVTX range "timed"),
-    for ncu captures of single kernels; prints one JSON line of timings."""
+    for ncu captures of single kernels; prints one JSON line of timings.
+    --case box: the turbulent box of side --side; --case torus: the Kerr
+    torus on a --side x --side x --side/3 grid."""
     from paper_1702_01106_b300 import inputs
     from paper_1702_01106_b300.grim import Grim, GRIM_FP64, GRIM_MIXED
-    prob = inputs.turbulent_box_problem(args.side, tol=TOL)
-    P = inputs.turbulent_box_state(prob)
-    dt = 0.5 / args.side
-    out = {"case": f"turbulent box {args.side}x{args.side}", "steps": args.steps}
-    for name, prec in (("fp64", GRIM_FP64), ("mixed", GRIM_MIXED)):
+    if args.case == "torus":
+        prob = inputs.torus_problem(args.side, args.side, max(1, args.side // 3))
+        P = inputs.torus_state(prob)
+        dt = inputs.torus_dt(prob)
+        name = f"Kerr torus {args.side}x{args.side}x{max(1, args.side // 3)}"
+    else:
+        prob = inputs.turbulent_box_problem(args.side, tol=TOL)
+        P = inputs.turbulent_box_state(prob)
+        dt = 0.5 / args.side
+        name = f"turbulent box {args.side}x{args.side}"
+    out = {"case": name, "steps": args.steps}
+    for nm, prec in (("fp64", GRIM_FP64), ("mixed", GRIM_MIXED)):
         g = Grim(prob, precision=prec)
         a = torch.from_numpy(P).to(dev)
         b = torch.empty_like(a)
-        out[name + "_tuning"] = g.autotune(a, dt)[0]
+        out[nm + "_tuning"] = g.autotune(a, dt)[0]
         ms, st, kt, _ = time_device(g, a, b, dt, args.steps, args.warmup, 1, torch)
-        out[name] = {"ms_per_step": ms, "kernel_ms": {k: v[0] / v[1] for k, v in kt.items()},
-                     "iters_per_zone_stage": st["iters"] / max(1, st["zones"]), "failed": st["failed"]}
+        out[nm] = {"ms_per_step": ms, "kernel_ms": {k: v[0] / v[1] for k, v in kt.items()},
+                   "iters_per_zone_stage": st["iters"] / max(1, st["zones"]), "failed": st["failed"]}
         g.close()
     print(json.dumps(out))
 
@@ -364,7 +373,8 @@ def main():
     ap.add_argument("--skip-kerr", action="store_true", help="skip the 3-D Kerr torus measurement")
     ap.add_argument("--case-only", action="store_true",
                     help="only the float64 and mixed steps of a --side box (for ncu captures)")
-    ap.add_argument("--side", type=int, default=N_SIDE, help="box side for --case-only")
+    ap.add_argument("--side", type=int, default=N_SIDE, help="grid side for --case-only")
+    ap.add_argument("--case", default="box", choices=["box", "torus"], help="workload of --case-only")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
