@@ -131,15 +131,27 @@ def cpu_baseline(prob, P, dt, target_s=12.0):
 
 
 def dist_setup(args):
+    """Rank, world size and local rank from the torchrun environment; one
+    process group for the barrier and the max-over-ranks timing (NCCL on GPU
+    ranks, gloo for the CPU reference arm or without CUDA).  No collective
+    touches the data path: every rank steps its own box (weak scaling)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+        gpu = torch.cuda.is_available() and args.impl != "reference"
+        if gpu:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if gpu else "gloo")
     return world, rank, local
+
+
+def aggregate_rate(units_per_rank, seconds, world):
+    """Whole-job throughput: every rank processed units_per_rank in the
+    (max-over-ranks) time."""
+    return world * units_per_rank / seconds
 
 
 def barrier(world):
@@ -153,7 +165,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    on_gpu = torch.cuda.is_available() and dist.get_backend() == "nccl"
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -307,7 +320,7 @@ def bench_batched(dev, mlp, torch, world, steps=3):
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
         s = bt.stats()
-        out[name] = {"value": world * zones / (ms * 1e-3), "ms_per_step": ms,
+        out[name] = {"value": aggregate_rate(zones, ms * 1e-3, world), "ms_per_step": ms,
                      "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]), "failed": s["failed"],
                      "max_res": s["max_res"], "kernels_per_step": (s["launches"] - l0) / steps}
         bt.close()
@@ -352,7 +365,7 @@ def bench_kerr(dev, torch, world, steps=3, warmup=2):
         ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
         s = g.stats()
         kt = g.kernel_times()
-        out[name] = {"value": world * prob.zones / (ms * 1e-3), "ms_per_step": ms,
+        out[name] = {"value": aggregate_rate(prob.zones, ms * 1e-3, world), "ms_per_step": ms,
                      "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]), "failed": s["failed"],
                      "max_res": s["max_res"], "kernel_ms_per_stage": {k: v[0] / v[1] for k, v in kt.items()}}
         g.close()
@@ -447,9 +460,9 @@ def main():
     for nm, (ms, st, _, _) in results.items():
         if st["failed"] or st["max_res"] > TOL:
             print(f"warning: {nm} path: {st['failed']} zone solves failed, max|r| {st['max_res']:.2e}", file=sys.stderr)
-    value = world * N / (ms_m * 1e-3)
-    fp64_value = world * N / (ms_d * 1e-3)
-    mixed_plain_value = world * N / (ms_mp * 1e-3)
+    value = aggregate_rate(N, ms_m * 1e-3, world)
+    fp64_value = aggregate_rate(N, ms_d * 1e-3, world)
+    mixed_plain_value = aggregate_rate(N, ms_mp * 1e-3, world)
 
     # Roofline of the dominant kernel of the headline (mixed) path: FP64 pipe bound.
     # Algorithmic flops per launch (tests/golden/flop_counts.txt per unit):
@@ -528,7 +541,7 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / steps, world)
-    e2e = {"value": world * N / e2e_s, "unit": "zone-updates/s", "h2d_bytes_per_step": int(P.nbytes),
+    e2e = {"value": aggregate_rate(N, e2e_s, world), "unit": "zone-updates/s", "h2d_bytes_per_step": int(P.nbytes),
            "d2h_bytes_per_step": int(P.nbytes)}
 
     batched = None if args.skip_batched else bench_batched(dev, mlp, torch, world)
