@@ -12,10 +12,12 @@ import torch
 from .grim import MLP, Grim, GRIM_FP64
 
 
-def collect(prob, P, dt: float, steps: int, device, tol: float = 1e-12):
+def collect(prob, P, dt: float, steps: int, device, tol: float = 1e-12, stride: int = 1):
     """Features [M, 32] and targets [M, 16] (float32, device) of both stages of
-    `steps` float64 steps from the state P (numpy [10, n3, n2, n1]), solved
-    to `tol`; M = 2 * steps * zones.  Returns (X, Y, final state)."""
+    every stride-th of steps * stride float64 steps from the state P (numpy
+    [10, n3, n2, n1]), solved to `tol`; M = 2 * steps * zones.  A stride > 1
+    spreads the samples over a longer stretch of the evolution.  Returns
+    (X, Y, final state)."""
     g = Grim(prob.with_(tol=tol), precision=GRIM_FP64)
     a = torch.from_numpy(P).to(device)
     half = torch.empty_like(a)
@@ -24,11 +26,13 @@ def collect(prob, P, dt: float, steps: int, device, tol: float = 1e-12):
     X = torch.empty((2 * steps * N, 32), dtype=torch.float32, device=device)
     Y = torch.empty((2 * steps * N, 16), dtype=torch.float32, device=device)
     k = 0
-    for _ in range(steps):
+    for s in range(steps * stride):
+        sample = s % stride == 0
         for PE, dts, out in ((a, 0.5 * dt, half), (half, dt, full)):
             g.stage(a, PE, dts, out)
-            g.mlp_sample(a, out, X[k * N:(k + 1) * N], Y[k * N:(k + 1) * N])
-            k += 1
+            if sample:
+                g.mlp_sample(a, out, X[k * N:(k + 1) * N], Y[k * N:(k + 1) * N])
+                k += 1
         a, full = full, a
     g.close()
     return X, Y, a
