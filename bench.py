@@ -37,7 +37,7 @@ MLP_SAMPLE_STRIDE = 6     # training stages from every 6th of the first 48 steps
 # DRAM bytes read + written per launch at 1024^2 from the ncu captures in
 # profiles/explicit_turbulent_box_1024.md and profiles/newton_turbulent_box_1024.md
 # (None while a kernel has changed since its capture).
-NCU_TRAFFIC_BYTES = {"faces": None, "zone_const": None, "newton64": None, "newton32": None}
+NCU_TRAFFIC_BYTES = {"faces": 296.5e6, "zone_const": 641.5e6, "newton64": 428.0e6, "newton32": None}
 TOL = 1e-10
 
 
