@@ -108,21 +108,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(prob, P, dt, target_s=12.0):
+def cpu_baseline(prob, P, dt, target_s=12.0, threads=0, max_side=512):
     """The oracle as it stands on the host cores, on a bounded sample of the
     same workload: a contiguous square block of zones of the 1024^2 box,
     stepped once (half step on the block plus a 4-zone margin, full step on
-    the block).  Returns (zone-updates/s, cores, sample description, seconds)."""
+    the block).  threads = 0: all cores.  Returns (zone-updates/s, cores,
+    sample description, seconds)."""
     import numpy as np
     from oracle import oracle
-    cores = oracle.max_threads()
-    side, elapsed = 32, 0.0
+    cores = threads if threads > 0 else oracle.max_threads()
+    side, elapsed = 16, 0.0
     while True:
         zs = np.array([(j * N_SIDE + i) for j in range(side) for i in range(side)], dtype=np.int64)
         t0 = time.perf_counter()
-        out, it, st, _ = oracle.step_sampled(prob, P, dt, zs)
+        out, it, st, _ = oracle.step_sampled(prob, P, dt, zs, threads=threads)
         elapsed = time.perf_counter() - t0
-        if elapsed >= target_s / 4 or side >= 512:
+        if elapsed >= target_s / 4 or side >= max_side:
             break
         side *= 2
     rate = side * side / elapsed
@@ -228,8 +229,9 @@ def profile_case(args, dev, torch):
     """--case-only: the float64 and mixed steps of one workload alone
     (autotuned, warmed up, then `--steps` steps in the NVTX range "timed"),
     for ncu captures of single kernels; prints one JSON line of timings.
-    --case box: the turbulent box of side --side; --case torus: the Kerr
-    torus on a --side x --side x --side/3 grid."""
+    --case box: the turbulent box of side --side; --case box-learned: its
+    mixed arm with a learned start; --case torus: the Kerr torus on a --side x
+    --side x --side/3 grid."""
     from paper_1702_01106_b300 import inputs
     from paper_1702_01106_b300.grim import Grim, GRIM_FP64, GRIM_MIXED
     if args.case == "torus":
@@ -243,8 +245,18 @@ def profile_case(args, dev, torch):
         dt = 0.5 / args.side
         name = f"turbulent box {args.side}x{args.side}"
     out = {"case": name, "steps": args.steps}
-    for nm, prec in (("fp64", GRIM_FP64), ("mixed", GRIM_MIXED)):
+    arms = [("fp64", GRIM_FP64), ("mixed", GRIM_MIXED)]
+    mlp = None
+    if args.case == "box-learned":
+        # the learned start's inference costs the same whatever the weights:
+        # an untrained network (its starts lose to P_n and fall back)
+        from paper_1702_01106_b300.grim import MLP
+        mlp = MLP(seed=1)
+        arms = [("learned", GRIM_MIXED)]
+    for nm, prec in arms:
         g = Grim(prob, precision=prec)
+        if mlp is not None:
+            g.set_guess(mlp, accept=1e-3)
         a = torch.from_numpy(P).to(dev)
         b = torch.empty_like(a)
         out[nm + "_tuning"] = g.autotune(a, dt)[0]
@@ -253,6 +265,17 @@ def profile_case(args, dev, torch):
                    "iters_per_zone_stage": st["iters"] / max(1, st["zones"]), "failed": st["failed"]}
         g.close()
     print(json.dumps(out))
+
+
+def iters_p99(hist):
+    """99th percentile of the per-zone Newton update counts (histogram)."""
+    tot = sum(hist)
+    acc = 0
+    for k, n in enumerate(hist):
+        acc += n
+        if acc >= 0.99 * tot:
+            return k
+    return len(hist) - 1
 
 
 def time_device(g, a, b, dt, steps, warmup, world, torch):
@@ -388,7 +411,8 @@ def main():
     ap.add_argument("--case-only", action="store_true",
                     help="only the float64 and mixed steps of a --side box (for ncu captures)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side for --case-only")
-    ap.add_argument("--case", default="box", choices=["box", "torus"], help="workload of --case-only")
+    ap.add_argument("--case", default="box", choices=["box", "box-learned", "torus"],
+                    help="workload of --case-only")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -549,10 +573,12 @@ def main():
     batched = None if args.skip_batched else bench_batched(dev, mlp, torch, world)
     kerr = None if args.skip_kerr else bench_kerr(dev, torch, world)
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample, _ = cpu_baseline(prob, P, dt)
         cpu = {"value": rate, "unit": "zone-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
+        rate1, _, sample1, _ = cpu_baseline(prob, P, dt, target_s=8.0, threads=1, max_side=128)
+        cpu1 = {"value": rate1, "unit": "zone-updates/s", "cores": 1, "kind": "oracle", "sample": sample1}
 
     launches_timed = int(st_m["launches_timed"])
     if rank == 0:
@@ -567,11 +593,14 @@ def main():
                        "l2": "no flush: per-step working set ~0.6 GB (states, stage constants) > 126 MB L2"},
             "fp64_plain": {"value": fp64_value, "ms_per_step": ms_d, "dtype": "f64",
                            "newton_iters_per_zone_stage": st_d["iters"] / max(1, st_d["zones"]),
+                           "newton_iters_p99": iters_p99(st_d["hist"]),
                            "failed": st_d["failed"], "max_res": st_d["max_res"]},
             "mixed_plain_start": {"value": mixed_plain_value, "ms_per_step": ms_mp,
                                   "newton_iters_per_zone_stage": st_mp["iters"] / max(1, st_mp["zones"]),
+                                  "newton_iters_p99": iters_p99(st_mp["hist"]),
                                   "failed": st_mp["failed"], "max_res": st_mp["max_res"]},
             "mixed_learned": {"newton_iters_per_zone_stage": st_m["iters"] / max(1, st_m["zones"]),
+                              "newton_iters_p99": iters_p99(st_m["hist"]),
                               "failed": st_m["failed"], "max_res": st_m["max_res"],
                               "fallback_rate": st_m["fallbacks"] / max(1, st_m["zones"]),
                               "one_step_max_rel_diff_vs_fp64": learned_err,
@@ -586,7 +615,7 @@ def main():
                       "hbm_source": peak_kind},
             "batched_64_boxes": batched,
             "kerr_torus_3d": kerr,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_timed,
+            "cpu_baseline": cpu, "cpu_baseline_1core": cpu1, "e2e": e2e, "gpu_launches": launches_timed,
             "clocks": clocks,
         }
         print(json.dumps(line))
