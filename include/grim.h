@@ -47,6 +47,7 @@ extern "C" {
 
 #define GRIM_RECON_MC 0    /* generalized minmod, parameter theta (2 = MC, 1 = minmod) */
 #define GRIM_RECON_WENO5 1 /* Jiang & Shu WENO5 */
+#define GRIM_RECON_PPM 2   /* Colella & Woodward PPM face values with limited slopes (theta) */
 
 #define GRIM_FLUX_LLF 0    /* local Lax-Friedrichs (Section 2.4.2) */
 #define GRIM_FLUX_HLLE 1   /* HLLE with the bounds c_R = max(c, 0), c_L = max(-c, 0) (Section 2.4.2) */
@@ -75,7 +76,7 @@ typedef struct {
 typedef struct {
   double gamma, tau_R, phi, psi;
   int conduction, viscosity, higher_order;
-  int recon;    /* GRIM_RECON_* */
+  int recon;    /* GRIM_RECON_* (grim_step_static: MC or WENO5) */
   double theta; /* generalized minmod parameter, also used for source slopes */
   int floors;   /* after every stage: a zone whose Newton iteration ended with a
                    non-zero status reverts to its start (P_n, flux-CT field);

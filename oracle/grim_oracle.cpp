@@ -185,7 +185,7 @@ enum {
 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };
 enum { METRIC_MINKOWSKI = 0, METRIC_MKS_KERR = 1 };
-enum { RECON_MC = 0, RECON_WENO5 = 1 };
+enum { RECON_MC = 0, RECON_WENO5 = 1, RECON_PPM = 2 };
 enum { ST_MAXIT = 1, ST_LSSTALL = 2, ST_SINGULAR = 4, ST_NONFINITE = 8, ST_INADMISSIBLE = 16 };
 
 struct Params {
@@ -560,7 +560,38 @@ template <class T> static T weno5_right(const T v[5]) {
 
 // Face states of the zone whose 7-point line (offsets -3..3) is s[]: the value
 // at its left face (lo) and right face (hi).
+// PPM (Colella & Woodward 1984) face values of the middle zone of v[0..4]:
+// interface values a_{i+-1/2} = (a_i + a_{i+-1})/2 -+ (da_{i+-1} - da_i)/6
+// from limited slopes da (generalized minmod, theta), then the monotonicity
+// constraints: at a local extremum both faces take the zone value; an
+// interpolating parabola that would overshoot has the far face moved to
+// 3 a_i - 2 a_near.
+template <class T> static void ppm_zone(double theta, const T v[5], T& lo, T& hi) {
+  T d1 = gminmod(theta, v[0], v[1], v[2]);
+  T d2 = gminmod(theta, v[1], v[2], v[3]);
+  T d3 = gminmod(theta, v[2], v[3], v[4]);
+  T aL = 0.5 * (v[1] + v[2]) - (d2 - d1) / 6.0;
+  T aR = 0.5 * (v[2] + v[3]) - (d3 - d2) / 6.0;
+  const T a = v[2];
+  if (!((aR - a) * (a - aL) > 0.0)) {
+    aL = a;
+    aR = a;
+  } else {
+    T D = aR - aL;
+    T m6 = 6.0 * (a - 0.5 * (aL + aR));
+    if (D * m6 > D * D) aL = 3.0 * a - 2.0 * aR;
+    else if (D * m6 < -(D * D)) aR = 3.0 * a - 2.0 * aL;
+  }
+  lo = aL;
+  hi = aR;
+}
+
 template <class T> static void recon_zone(const Params& p, const T s[7], T& lo, T& hi) {
+  if (p.recon == RECON_PPM) {
+    T v[5] = {s[1], s[2], s[3], s[4], s[5]};
+    ppm_zone(p.theta, v, lo, hi);
+    return;
+  }
   if (p.recon == RECON_WENO5) {
     T f[5] = {s[1], s[2], s[3], s[4], s[5]};
     T b[5] = {s[5], s[4], s[3], s[2], s[1]};

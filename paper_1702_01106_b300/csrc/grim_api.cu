@@ -177,7 +177,8 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
   if (grid->dim == 2 && grid->n3 != 1) return GRIM_EINVAL;
   if (metric->kind != GRIM_METRIC_MINKOWSKI && metric->kind != GRIM_METRIC_MKS_KERR) return GRIM_EINVAL;
   if (metric->kind == GRIM_METRIC_MKS_KERR && !(std::fabs(metric->spin) < 1.0)) return GRIM_EINVAL;
-  if (phys->recon != GRIM_RECON_MC && phys->recon != GRIM_RECON_WENO5) return GRIM_EINVAL;
+  if (phys->recon != GRIM_RECON_MC && phys->recon != GRIM_RECON_WENO5 && phys->recon != GRIM_RECON_PPM)
+    return GRIM_EINVAL;
   if (phys->riemann != GRIM_FLUX_LLF && phys->riemann != GRIM_FLUX_HLLE) return GRIM_EINVAL;
   if (solver->precision != GRIM_FP64 && solver->precision != GRIM_MIXED) return GRIM_EINVAL;
   if (!(phys->gamma > 1.0) || !(phys->tau_R > 0.0) || !(solver->tol > 0.0) || solver->k_max < 0 ||

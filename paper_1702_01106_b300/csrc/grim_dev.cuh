@@ -55,7 +55,7 @@ struct NewtonCfg {
 };
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };
-enum { RECON_MC = 0, RECON_WENO5 = 1 };
+enum { RECON_MC = 0, RECON_WENO5 = 1, RECON_PPM = 2 };
 
 // Status bits per zone.
 enum { ST_MAXIT = 1, ST_LSSTALL = 2, ST_SINGULAR = 4, ST_NONFINITE = 8, ST_INADMISSIBLE = 16 };

@@ -143,13 +143,14 @@ struct ExpArgs {
 };
 constexpr int NCACHE = NV + 2;
 
-template <int D, bool WENO>
+template <int D, int RECON>
 __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a, int i, int j, double* out,
                                               long long plane) {
   constexpr int di = (D == 0), dj = (D == 1);
   const long long N = p.N;
   // zones along the face normal at offsets -3..2 from the zone right of the face
-  constexpr int o0 = WENO ? -3 : -2, o1 = WENO ? 2 : 1;
+  constexpr bool WIDE = RECON != RECON_MC;
+  constexpr int o0 = WIDE ? -3 : -2, o1 = WIDE ? 2 : 1;
   long long zz[6];
   bool fa[6], fb[6];
 #pragma unroll
@@ -160,9 +161,15 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
     double s[6];
 #pragma unroll
     for (int t = o0; t <= o1; t++) s[t + 3] = load_comp(a.PE, N, zz[t + 3], v, fa[t + 3], fb[t + 3]);
-    if (WENO) {
+    if (RECON == RECON_WENO5) {
       L[v] = weno5v(s[0], s[1], s[2], s[3], s[4]);
       R[v] = weno5v(s[5], s[4], s[3], s[2], s[1]);
+    } else if (RECON == RECON_PPM) {
+      double lo, hi;
+      ppm_zone(p.theta, s[0], s[1], s[2], s[3], s[4], lo, hi);  // zone left of the face
+      L[v] = hi;
+      ppm_zone(p.theta, s[1], s[2], s[3], s[4], s[5], lo, hi);  // zone right of the face
+      R[v] = lo;
     } else {
       L[v] = fma(0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
       R[v] = fma(-0.5, gm_slope(p.theta, s[2], s[3], s[4]), s[3]);
@@ -186,18 +193,19 @@ __global__ void __launch_bounds__(BS) face_flux_2d(const __grid_constant__ Param
   const long long nf2 = (long long)(p.n1 + 2) * (p.n2 + 1);
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf1 + nf2) return;
-  const bool weno = p.recon == RECON_WENO5;
   if (f < nf1) {
     const int i = (int)(f % (p.n1 + 1)), j = (int)(f / (p.n1 + 1)) - 1;
     double* out = a.F1 + (long long)(j + 1) * (p.n1 + 1) + i;
-    if (weno) face_flux_dir<0, true>(p, a, i, j, out, nf1);
-    else face_flux_dir<0, false>(p, a, i, j, out, nf1);
+    if (p.recon == RECON_WENO5) face_flux_dir<0, RECON_WENO5>(p, a, i, j, out, nf1);
+    else if (p.recon == RECON_PPM) face_flux_dir<0, RECON_PPM>(p, a, i, j, out, nf1);
+    else face_flux_dir<0, RECON_MC>(p, a, i, j, out, nf1);
   } else {
     const long long g = f - nf1;
     const int i = (int)(g % (p.n1 + 2)) - 1, j = (int)(g / (p.n1 + 2));
     double* out = a.F2 + (long long)j * (p.n1 + 2) + (i + 1);
-    if (weno) face_flux_dir<1, true>(p, a, i, j, out, nf2);
-    else face_flux_dir<1, false>(p, a, i, j, out, nf2);
+    if (p.recon == RECON_WENO5) face_flux_dir<1, RECON_WENO5>(p, a, i, j, out, nf2);
+    else if (p.recon == RECON_PPM) face_flux_dir<1, RECON_PPM>(p, a, i, j, out, nf2);
+    else face_flux_dir<1, RECON_MC>(p, a, i, j, out, nf2);
   }
 }
 

@@ -250,10 +250,11 @@ static double gr_kappa(const Params& p) {
 // direction D, from MC or WENO5 face states of P^E.  The stencil's zone
 // indices and reflection flips are resolved once; the fields are then loaded
 // and reconstructed one at a time.
-template <int D, bool WENO>
+template <int D, int RECON>
 __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int i, int j, int k, const GT& g,
                                           double* out, long long plane) {
-  constexpr int o0 = WENO ? -3 : -2, o1 = WENO ? 2 : 1, NS = o1 - o0 + 1;
+  constexpr bool WIDE = RECON != RECON_MC;
+  constexpr int o0 = WIDE ? -3 : -2, o1 = WIDE ? 2 : 1, NS = o1 - o0 + 1;
   long long zz[NS];
   int fl[NS];  // reflection flips of the stencil zone, bit d for direction d
 #pragma unroll
@@ -274,9 +275,15 @@ __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int 
       const double x = __ldg(a.PE + v * N + zz[t]);
       s[t] = (fl[t] & bit) ? -x : x;
     }
-    if (WENO) {
+    if (RECON == RECON_WENO5) {
       L[v] = weno5v(s[0], s[1], s[2], s[3], s[4]);
       R[v] = weno5v(s[5], s[4], s[3], s[2], s[1]);
+    } else if (RECON == RECON_PPM) {
+      double lo, hi;
+      ppm_zone(p.theta, s[0], s[1], s[2], s[3], s[4], lo, hi);
+      L[v] = hi;
+      ppm_zone(p.theta, s[1], s[2], s[3], s[4], s[5], lo, hi);
+      R[v] = lo;
     } else {
       L[v] = fma(0.5, gm_slope(p.theta, s[0], s[1], s[2]), s[1]);
       R[v] = fma(-0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
@@ -338,8 +345,9 @@ __global__ void __launch_bounds__(128) face_flux_gr(const __grid_constant__ Para
     for (int v = 0; v < NV; v++) out[v * fb.size] = 0.0;
     return;
   }
-  if (p.recon == RECON_WENO5) face_body<D, true>(p, a, i, j, k, g, out, fb.size);
-  else face_body<D, false>(p, a, i, j, k, g, out, fb.size);
+  if (p.recon == RECON_WENO5) face_body<D, RECON_WENO5>(p, a, i, j, k, g, out, fb.size);
+  else if (p.recon == RECON_PPM) face_body<D, RECON_PPM>(p, a, i, j, k, g, out, fb.size);
+  else face_body<D, RECON_MC>(p, a, i, j, k, g, out, fb.size);
 }
 
 // ---------------------------------------------------------------- zone constants

@@ -66,6 +66,31 @@ __device__ __forceinline__ double weno5v(double v0, double v1, double v2, double
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
+// PPM (Colella & Woodward 1984) face values of the middle zone of v0..v4:
+// interface values from limited slopes, a_{i+-1/2} = (a_i + a_{i+-1})/2 -+
+// (da_{i+-1} - da_i)/6, then the monotonicity constraints (both faces take
+// the zone value at an extremum; an overshooting parabola has its far face
+// moved to 3 a_i - 2 a_near).
+__device__ __forceinline__ void ppm_zone(double theta, double v0, double v1, double v2, double v3, double v4,
+                                         double& lo, double& hi) {
+  const double d1 = gm_slope(theta, v0, v1, v2);
+  const double d2 = gm_slope(theta, v1, v2, v3);
+  const double d3 = gm_slope(theta, v2, v3, v4);
+  double aL = 0.5 * (v1 + v2) - (d2 - d1) * (1.0 / 6.0);
+  double aR = 0.5 * (v2 + v3) - (d3 - d2) * (1.0 / 6.0);
+  if (!((aR - v2) * (v2 - aL) > 0.0)) {
+    aL = v2;
+    aR = v2;
+  } else {
+    const double D = aR - aL;
+    const double m6 = 6.0 * (v2 - 0.5 * (aL + aR));
+    if (D * m6 > D * D) aL = 3.0 * v2 - 2.0 * aR;
+    else if (D * m6 < -(D * D)) aR = 3.0 * v2 - 2.0 * aL;
+  }
+  lo = aL;
+  hi = aR;
+}
+
 // ---------------------------------------------------------------- residual
 // Constants of the residual in the working precision.
 template <typename T> struct RC {

@@ -21,7 +21,7 @@ NVAR = 10
 FIELDS = ("rho", "u", "u1", "u2", "u3", "B1", "B2", "B3", "qt", "dPt")
 
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT = 0, 1, 2
-RECON_MC, RECON_WENO5 = 0, 1
+RECON_MC, RECON_WENO5, RECON_PPM = 0, 1, 2
 FLUX_LLF, FLUX_HLLE = 0, 1
 METRIC_MINKOWSKI = 0
 METRIC_MKS_KERR = 1

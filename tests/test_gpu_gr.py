@@ -164,12 +164,13 @@ def test_gr_kerr_conservation_of_mass(dev):
     g.close()
 
 
-def test_gr_step_hlle(dev, orc):
+@pytest.mark.parametrize("recon", [inputs.RECON_MC, inputs.RECON_PPM])
+def test_gr_step_hlle(dev, orc, recon):
     """HLLE on the general-metric path: one step of the 3-D box and one stage
-    of the axisymmetric torus within 1e-12 of the oracle."""
+    of the axisymmetric torus within 1e-12 of the oracle (MC and PPM)."""
     from paper_1702_01106_b300.grim import Grim
     prob, P = _box3d()
-    prob = prob.with_(riemann=inputs.FLUX_HLLE)
+    prob = prob.with_(riemann=inputs.FLUX_HLLE, recon=recon)
     g = Grim(prob)
     out = torch.empty_like(_t(P, dev))
     g.step(_t(P, dev), out, 0.5 / 12)
@@ -178,7 +179,7 @@ def test_gr_step_hlle(dev, orc):
     assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
     g.close()
     prob, Pn = _torus(20, 16, 1)
-    prob = prob.with_(riemann=inputs.FLUX_HLLE)
+    prob = prob.with_(riemann=inputs.FLUX_HLLE, recon=recon)
     dts = 0.5 * inputs.torus_dt(prob)
     g = Grim(prob)
     out = torch.empty_like(_t(Pn, dev))

@@ -55,7 +55,7 @@ def test_residual_parity(dev, orc):
             assert np.all(err < 1e-12 * mag), err / mag
 
 
-@pytest.mark.parametrize("recon", [inputs.RECON_MC, inputs.RECON_WENO5])
+@pytest.mark.parametrize("recon", [inputs.RECON_MC, inputs.RECON_WENO5, inputs.RECON_PPM])
 def test_stage_parity(dev, orc, recon):
     prob, Pn = _ragged_turbulent(recon=recon)
     dts = 0.25 / 32
@@ -175,7 +175,7 @@ def test_stage_parity_non_periodic_boundaries(dev, orc, bc):
     assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
 
 
-@pytest.mark.parametrize("recon", [inputs.RECON_MC, inputs.RECON_WENO5])
+@pytest.mark.parametrize("recon", [inputs.RECON_MC, inputs.RECON_WENO5, inputs.RECON_PPM])
 def test_stage_parity_hlle(dev, orc, recon):
     """The HLLE flux (Section 2.4.2) on the flat path: one stage within 1e-12
     of the oracle."""

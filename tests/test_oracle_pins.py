@@ -367,6 +367,30 @@ def test_weno5_reconstruction_order(orc):
     assert math.log2(errs[0] / errs[1]) > 4.5 and math.log2(errs[1] / errs[2]) > 4.5
 
 
+def test_ppm_reconstruction(orc):
+    """PPM: exact on linear data; flat at an extremum; the overshoot
+    constraint; third order on a smooth monotone profile (the limited
+    slopes cap it below the unlimited fourth order)."""
+    prob = inputs.linear_mode_problem(8, recon=inputs.RECON_PPM)
+    lo, hi = orc.recon(prob, 0.3 + 0.7 * np.arange(-3, 4))
+    assert lo == pytest.approx(-0.05, abs=1e-14) and hi == pytest.approx(0.65, abs=1e-14)
+    lo, hi = orc.recon(prob, np.array([0, 0, 0.2, 1.0, 0.5, 0, 0]))
+    assert lo == 1.0 and hi == 1.0
+    # a steep step next to a flat zone: the interpolant is monotone on the zone
+    lo, hi = orc.recon(prob, np.array([0, 0, 0.0, 0.1, 1.0, 1.0, 1.0]))
+    assert min(lo, hi) >= 0.0 - 1e-15 and max(lo, hi) <= 1.0 + 1e-15
+    assert (hi - 0.1) * (0.1 - lo) >= 0
+    errs = []
+    for n in (40, 80, 160):
+        h = 1.0 / n
+        x0 = 0.1
+        avg = lambda m: (np.cos(2 * np.pi * (x0 + (m - 0.5) * h)) - np.cos(2 * np.pi * (x0 + (m + 0.5) * h))) / (2 * np.pi * h)
+        line = np.array([avg(m) for m in range(-3, 4)])
+        lo, hi = orc.recon(prob, line)
+        errs.append(abs(hi - np.sin(2 * np.pi * (x0 + 0.5 * h))))
+    assert math.log2(errs[0] / errs[1]) > 2.5 and math.log2(errs[1] / errs[2]) > 2.5
+
+
 # ---------------------------------------------------------------- grid invariants
 def _corner_divb(P, dx):
     B1, B2 = P[5, 0], P[6, 0]
