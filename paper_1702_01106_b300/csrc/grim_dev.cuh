@@ -1,7 +1,8 @@
 // Device-side definitions shared by the grim CUDA kernels (sm_103a).
 //
 // The implicit zone step of Chandra, Foucart & Gammie (2017) for the
-// 10-field extended GRMHD system, Minkowski space.  Fields, in order:
+// 10-field extended GRMHD system (Minkowski space here; the general-metric
+// definitions are in grim_gr.cuh).  Fields, in order:
 // rho, u, u^1, u^2, u^3, B^1, B^2, B^3, q~, dP~ (q~, dP~ are the rescaled
 // heat flux and pressure anisotropy of Section 4, Eqs. q and dP).
 // State arrays are structure-of-arrays float64 [10][n3][n2][n1], X1 fastest.
@@ -85,7 +86,8 @@ __device__ __forceinline__ double grsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float grsqrt(float x) { return rsqrtf(x); }
 
 // ----------------------------------------------------------------------------
-// Point physics in Minkowski space.  Primitive velocity components are u^i;
+// Point physics in Minkowski space for the fused tile kernel of the
+// no-allocation step.  Primitive velocity components are u^i;
 // u^t = sqrt(1 + u^i u^i), u_t = -u^t, u_i = u^i.
 template <typename T> struct Pt {
   T rho, u, ut, uc[3];      // u^t and u^i

@@ -1,6 +1,7 @@
 // Point physics in a general metric (Section 4 with the geometry of Section
 // 2.1), for the 3-D and curved-space path.  The metric at a point comes from
-// precomputed tables (grim_geom.cu); everything here is per point.
+// precomputed tables (geometry_tables in grim_gr.cu); everything here is
+// per point.
 //
 // Primitive velocity: the normal-observer velocity u~^i, so that u^t =
 // gamma/alpha and u^i = u~^i - gamma alpha g^{ti} with gamma = (1 + g_ij u~^i
