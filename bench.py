@@ -613,6 +613,10 @@ def main():
             "roofline": roof, "roofline_fp64_newton": roof_fp64,
             "peaks": {"fp64_tflops": p64, "fp32_tflops": p32, "hbm_gbs": peaks.get("hbm_gbs"),
                       "hbm_source": peak_kind},
+            "paper_context": {"value": 138000.0, "unit": "zone-updates/s",
+                              "what": "grim's whole-step throughput per GPU, NVIDIA K20, FP64, 3-D 64^3 "
+                                      "zones per GPU (Section 6); another machine and workload: context "
+                                      "only"},
             "batched_64_boxes": batched,
             "kerr_torus_3d": kerr,
             "cpu_baseline": cpu, "cpu_baseline_1core": cpu1, "e2e": e2e, "gpu_launches": launches_timed,

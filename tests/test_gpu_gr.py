@@ -189,3 +189,50 @@ def test_gr_step_hlle(dev, orc, recon):
     assert np.array_equal(st.cpu().numpy() != 0, rst != 0)
     assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
     g.close()
+
+
+def test_gr_full_size_torus_sampled_parity(dev, orc):
+    """The 192 x 192 x 128 Kerr torus in the benchmark's configuration (tol
+    1e-10, float64 and mixed): zones sampled across the torus, its surface,
+    the atmosphere, the inner boundary and the axis agree with the oracle's
+    step of those zones (solved to 1e-14) within 1e-9; no zone fails."""
+    from paper_1702_01106_b300.grim import Grim
+    prob = inputs.torus_problem(192, 192, 128)
+    P = inputs.torus_state(prob)
+    dt = inputs.torus_dt(prob)
+    n1, n2, n3 = prob.n
+    rng = np.random.default_rng(17)
+    pick = [(0, 96, 0), (n1 - 1, 96, 5), (60, 0, 7), (60, n2 - 1, n3 - 1), (70, 96, 64), (45, 80, 3)]
+    pick += [tuple(int(x) for x in rng.integers(0, [n1, n2, n3])) for _ in range(18)]
+    zs = np.array([(k * n2 + j) * n1 + i for i, j, k in pick], dtype=np.int64)
+    ref, _, st, _ = orc.step_sampled(prob.with_(tol=1e-14), P, dt, zs)
+    for precision in (0, 1):
+        g = Grim(prob, precision=precision)
+        out = torch.empty_like(_t(P, dev))
+        g.step(_t(P, dev), out, dt)
+        s = g.stats()
+        assert s["failed"] == 0 and s["max_res"] <= prob.tol
+        got = out.cpu().numpy().reshape(10, -1)[:, zs]
+        assert rel_field_err(got, ref).max() < 1e-9
+        g.close()
+
+
+@pytest.mark.parametrize("shape", [(9, 7, 3), (5, 11, 2), (13, 1, 1)])
+def test_gr_odd_grids_minkowski(dev, orc, shape):
+    """Ragged 3-D grids (and a one-zone-wide 2-D one) on the general-metric
+    path: one float64 step within 1e-12 of the oracle."""
+    from paper_1702_01106_b300.grim import Grim
+    n = shape
+    dim = 3 if n[2] > 1 else 2
+    prob, P = _box3d(n=n)
+    prob = prob.with_(dim=dim)
+    if dim == 2:
+        prob = prob.with_(metric=inputs.METRIC_MINKOWSKI)
+        P = P[:, :1]
+    g = Grim(prob)
+    out = torch.empty_like(_t(P, dev))
+    g.step(_t(P, dev), out, 0.5 / 13)
+    ref, _, st, _ = orc.step(prob, P, 0.5 / 13)
+    assert st.max() == 0 and g.stats()["failed"] == 0
+    assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
+    g.close()
