@@ -339,7 +339,10 @@ int grim_mlp_sample(grim_ctx* ctx, const double* P_n, const double* P_conv, floa
 /* Start every later Newton solve of ctx from the MLP's prediction (NULL:
  * from P_n).  The learned start is kept when its max |r_a| <= accept; else
  * the plain start P_n is evaluated too and the smaller |r|^2 wins (counted
- * in grim_stats.fallbacks).  The MLP must outlive its use by ctx. */
+ * in grim_stats.fallbacks).  The MLP must outlive its use by ctx.  The first
+ * call with an MLP allocates a feature buffer (10 floats per zone), which the
+ * zone-constant kernel fills each stage.  GRIM_EINVAL on a 3-D or Kerr
+ * context; GRIM_ENOMEM. */
 int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept);
 
 /* Self-check of the float64 reciprocal the kernels use for finite-difference

@@ -21,7 +21,7 @@ cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cuda
 long long face_scratch_doubles(int n1, int n2);
 cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, cudaStream_t st);
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                              double* K, double* P0, double* faces, double* cache, int mode, int bs,
+                              double* K, double* P0, double* faces, double* cache, int mode, int bs, float* feat,
                               cudaStream_t st);
 long long pn_cache_doubles(long long N);
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
@@ -29,8 +29,8 @@ cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double
                              int* qcount, cudaStream_t st);
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
-cudaError_t launch_mlp_guess(const Params& p, const double* K, const double* Pn, const double* Un, const grim_mlp* m,
-                             double* P0, cudaStream_t st);
+cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
+                             cudaStream_t st);
 long long gr_geometry_doubles(const Params& p);
 long long gr_face_doubles(const Params& p);
 cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double h, const double x0[3],
@@ -80,6 +80,7 @@ struct grim_ctx {
   double* dev_out = nullptr;
   unsigned long long launches = 0;
   grim_mlp* mlp = nullptr;    // learned initial guess (grim_set_guess)
+  float* feat = nullptr;      // its increment features [10][N], written by the zone kernel
   double accept = 0.0;
   // per-kernel timing: (class, start, stop) event triples
   bool profile = false;
@@ -161,6 +162,7 @@ void grim_destroy(grim_ctx* ctx) {
   cudaFree(ctx->dev_out);
   cudaFree(ctx->queue);
   cudaFree(ctx->qcount);
+  cudaFree(ctx->feat);
   for (auto& g : ctx->gcache) cudaGraphExecDestroy(g.exec);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   for (auto& m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
@@ -237,7 +239,7 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
 
 // The explicit part of a stage: face fluxes, then flux-CT and the constants.
 static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
-                        double* Pout, int mode) {
+                        double* Pout, int mode, float* feat = nullptr) {
   if (ctx->gr) {
     {
       KernelMark m(ctx, GRIM_K_FACES, ctx->p.dim);
@@ -255,7 +257,7 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
   {
     KernelMark m(ctx, GRIM_K_ZONECONST);
     GRIM_CUDA(grim::launch_zone_const(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->faces, ctx->pncache, mode,
-                                      ctx->tune.zone_bs, ctx->cur),
+                                      ctx->tune.zone_bs, feat, ctx->cur),
               "zone-constant kernel");
   }
   return GRIM_OK;
@@ -263,13 +265,12 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
 
 static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
                      double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
-  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode);
-  if (rc) return rc;
   const bool learned = ctx->mlp && !guess && !ctx->gr;
+  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode, learned ? ctx->feat : nullptr);
+  if (rc) return rc;
   if (learned) {
     KernelMark m(ctx, GRIM_K_MLP);
-    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->K, Pn, mode ? ctx->pncache : nullptr, ctx->mlp, Pout, ctx->cur),
-              "mlp kernel");
+    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->cur), "mlp kernel");
   }
   if (ctx->gr) {
     const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
@@ -563,6 +564,10 @@ int grim_get_stats(grim_ctx* ctx, grim_stats* out) {
 int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept) {
   if (!ctx || !(accept >= 0.0)) return GRIM_EINVAL;
   if (mlp && ctx->gr) return fail(ctx, GRIM_EINVAL, "grim_set_guess: the learned start is for 2-D Minkowski grids");
+  if (mlp && !ctx->feat) {
+    const cudaError_t e = cudaMalloc(&ctx->feat, sizeof(float) * grim::NV * (size_t)ctx->p.N);
+    if (e != cudaSuccess) return fail(ctx, GRIM_ENOMEM, "grim_set_guess: feature buffer", e);
+  }
   ctx->mlp = mlp;
   ctx->accept = accept;
   return GRIM_OK;

@@ -140,6 +140,9 @@ struct ExpArgs {
   // step wrote, which depend on P_n only).
   double* cache;
   int mode;
+  // with a learned start: the ten increment features -r_a(P_n) of each zone
+  // (float32 [10][N]), from the constants computed here
+  float* feat;
 };
 constexpr int NCACHE = NV + 2;
 
@@ -321,6 +324,9 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
   const double tau = p.tauR, dts = a.dts, idts = 1.0 / dts;
   double* Kz = a.K + z;
   double kU[NV];
+  // the learned start's features x_a = -r_a(P_n) (the scaled residual of this
+  // stage at its start), written beside the constants when requested
+  float* feat = a.feat ? a.feat + z : nullptr;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     // row scale s_v = dt_s/(|U_v(P_n)| + |U_0(P_n)|); kU = s_v/dt_s depends on P_n only
@@ -330,7 +336,11 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
       kU[v] = nr_rcp(fabs(Un[v]) + fabs(Un[0]));
       Kz[(K_U + v) * N] = kU[v];
     }
-    Kz[(K_C + v) * N] = kU[v] * (dts * divF[v] - Un[v]);
+    if (v < 8) {
+      const double kc = kU[v] * (dts * divF[v] - Un[v]);
+      Kz[(K_C + v) * N] = kc;
+      if (feat) feat[v * N] = (float)(-(kU[v] * Un[v] + kc));
+    }
   }
   const double bhu[4] = {ze.bht, ze.bh[0], ze.bh[1], ze.bh[2]};
   const double ucovn[4] = {-ut_n, Pnz[2], Pnz[3], Pnz[4]};
@@ -356,12 +366,21 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
 #pragma unroll
     for (int m = 0; m < 4; m++) cst += Cq[m] * ucovn[m] * idts * it;
     cst -= hoq * (divu_sp - ut_n * idts);
-    Kz[(K_C + 8) * N] = s8 * cst;
-    Kz[(K_Q + 0) * N] = 0.5 * s8 * it;
-    Kz[(K_Q + 1) * N] = -s8 * Bq * idts * it;
+    double kQ[7];
+    const double kc = s8 * cst;
+    kQ[0] = 0.5 * s8 * it;
+    kQ[1] = -s8 * Bq * idts * it;
 #pragma unroll
-    for (int m = 0; m < 4; m++) Kz[(K_Q + 2 + m) * N] = -s8 * Cq[m] * idts * it;
-    Kz[(K_Q + 6) * N] = -s8 * hoq * idts;
+    for (int m = 0; m < 4; m++) kQ[2 + m] = -s8 * Cq[m] * idts * it;
+    kQ[6] = -s8 * hoq * idts;
+    Kz[(K_C + 8) * N] = kc;
+#pragma unroll
+    for (int q = 0; q < 7; q++) Kz[(K_Q + q) * N] = kQ[q];
+    if (feat) {
+      const double r8 = kU[8] * Un[8] + kc + kQ[0] * Pnz[8] + kQ[1] * th_n + kQ[6] * ut_n - kQ[2] * ut_n +
+                        kQ[3] * Pnz[2] + kQ[4] * Pnz[3] + kQ[5] * Pnz[4];
+      feat[8 * N] = (float)(-r8);
+    }
   }
   // anisotropy row: dP~_0 = Ad + Dd^nu (u_nu - u_nu,n)/dt_s + Ed (u^t - u^t_n)/dt_s
   double Ad = 0.0, Dd[4] = {0.0, 0.0, 0.0, 0.0}, Ed = 0.0;
@@ -382,11 +401,20 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
 #pragma unroll
     for (int m = 0; m < 4; m++) cst += Dd[m] * ucovn[m] * idts * it;
     cst -= hod * (divu_sp - ut_n * idts);
-    Kz[(K_C + 9) * N] = s9 * cst;
-    Kz[(K_D + 0) * N] = 0.5 * s9 * it;
+    double kD[6];
+    const double kc = s9 * cst;
+    kD[0] = 0.5 * s9 * it;
 #pragma unroll
-    for (int m = 0; m < 4; m++) Kz[(K_D + 1 + m) * N] = -s9 * Dd[m] * idts * it;
-    Kz[(K_D + 5) * N] = -s9 * (Ed * idts * it + hod * idts);
+    for (int m = 0; m < 4; m++) kD[1 + m] = -s9 * Dd[m] * idts * it;
+    kD[5] = -s9 * (Ed * idts * it + hod * idts);
+    Kz[(K_C + 9) * N] = kc;
+#pragma unroll
+    for (int q = 0; q < 6; q++) Kz[(K_D + q) * N] = kD[q];
+    if (feat) {
+      const double r9 = kU[9] * Un[9] + kc + kD[0] * Pnz[9] + kD[5] * ut_n - kD[1] * ut_n + kD[2] * Pnz[2] +
+                        kD[3] * Pnz[3] + kD[4] * Pnz[4];
+      feat[9 * N] = (float)(-r9);
+    }
   }
   // initial guess: P_n (or the given guess) with B from the explicit flux-CT update
 #pragma unroll
@@ -413,7 +441,7 @@ static double closure_kappa(const Params& p) {
 void explicit_args(const Params& p, const double* Pn, const double* PE, const double* guess, double dts, double* K,
                    double* P0, double* faces, ExpArgs& a) {
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.kappa = closure_kappa(p);
-  a.cache = nullptr; a.mode = 0;
+  a.cache = nullptr; a.mode = 0; a.feat = nullptr;
   a.K = K; a.P0 = P0;
   a.F1 = faces;
   a.F2 = faces + (long long)NV * (p.n1 + 1) * (p.n2 + 2);
@@ -439,12 +467,13 @@ long long pn_cache_doubles(long long N) { return (long long)NCACHE * N; }
 // mode: 0 general stage, 1 half step (P_E == P_n; fills cache), 2 full step
 // of the same step (reads cache and K_U).
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                              double* K, double* P0, double* faces, double* cache, int mode, int bs,
+                              double* K, double* P0, double* faces, double* cache, int mode, int bs, float* feat,
                               cudaStream_t st) {
   ExpArgs a;
   explicit_args(p, Pn, PE, guess, dts, K, P0, faces, a);
   a.cache = cache;
   a.mode = cache ? mode : 0;
+  a.feat = feat;
   const unsigned nb = (unsigned)((p.N + bs - 1) / bs);
   switch (bs) {
     case 64: zone_const_2d<64><<<nb, 64, 0, st>>>(p, a); break;

@@ -469,10 +469,12 @@ __device__ __forceinline__ void to_afrag(float acc[16][4], const float* b, unsig
   }
 }
 
-__global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constant__ Params p, const double* __restrict__ K,
-                                                const double* __restrict__ Pn, const double* __restrict__ Un,
-                                                const __nv_bfloat16* __restrict__ wb, const float* __restrict__ params,
-                                                const float* __restrict__ norm, double* __restrict__ P0) {
+__global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constant__ Params p,
+                                                             const float* __restrict__ feat,
+                                                             const double* __restrict__ Pn,
+                                                             const __nv_bfloat16* __restrict__ wb,
+                                                             const float* __restrict__ params,
+                                                             const float* __restrict__ norm, double* __restrict__ P0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smraw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -494,47 +496,29 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
   if (tid < 2 * MLP_IN + 2 * MLP_Y) S.norm[tid] = norm[tid];
   __syncthreads();
   const long long N = p.N;
-  const RC<double> c = make_rc<double>(p);
   const float g[10] = {-1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f};
   // persistent over tiles of 16 zones per warp
   for (long long base = (long long)blockIdx.x * (16 * INF_WARPS); base < N;
        base += (long long)gridDim.x * (16 * INF_WARPS)) {
-    // features: lanes 0..15 of each warp build one zone each
+    // features: lanes 0..15 of each warp build one zone each (the increment
+    // features come from the zone-constant kernel of this stage)
     const long long zw = base + warp * 16;
+    double Pkeep[MLP_NP];
     if (lane < 16) {
       const long long z = zw + lane;
       float xf[MLP_IN];
       if (z < N) {
-        double P[NV], U[NV], th_n, ut_n;
 #pragma unroll
-        for (int v = 0; v < NV; v++) P[v] = __ldg(Pn + v * N + z);
-        if (Un) {
-#pragma unroll
-          for (int v = 0; v < NV; v++) U[v] = __ldg(Un + v * N + z);
-          th_n = __ldg(Un + NV * N + z);
-          ut_n = __ldg(Un + (NV + 1) * N + z);
-        } else {
-          Z<double> zz;
-          z_load(zz, P, c);
-          const double q = zz.qt * zz.qs, dp = zz.dpt * zz.ds, third = dp * (1.0 / 3.0);
-          const double A = (zz.w0 + zz.bsq + third) * zz.ut;
-          const double qb = q * zz.bht, dpb = dp * zz.bht, qut = q * zz.ut;
-          U[0] = zz.rho * zz.ut;
-          U[1] = -A * zz.ut + zz.bt * zz.bt - 2.0 * qb * zz.ut + dpb * zz.bht + zz.pg + 0.5 * zz.bsq + third;
-#pragma unroll
-          for (int k = 0; k < 3; k++)
-            U[2 + k] = A * zz.v[k] - zz.bt * zz.bc[k] + qb * zz.v[k] + qut * zz.bh[k] - dpb * zz.bh[k];
-          U[5] = P[5]; U[6] = P[6]; U[7] = P[7];
-          U[8] = zz.qt * zz.ut;
-          U[9] = zz.dpt * zz.ut;
-          th_n = zz.theta;
-          ut_n = zz.ut;
-        }
-        increment_features(K, N, z, P, U, th_n, ut_n, xf);
+        for (int a = 0; a < NV; a++) xf[a] = __ldg(feat + a * N + z);
 #pragma unroll
         for (int a = 0; a < 10; a++) xf[NV + a] = g[a];
 #pragma unroll
-        for (int a = 0; a < NV; a++) xf[2 * NV + a] = (float)P[a];
+        for (int a = 0; a < NV; a++) {
+          const double x = __ldg(Pn + a * N + z);
+          xf[2 * NV + a] = (float)x;
+          if (a < 5) Pkeep[a] = x;
+          else if (a >= 8) Pkeep[a - 3] = x;
+        }
         xf[30] = xf[31] = 0.f;
       } else {
 #pragma unroll
@@ -596,7 +580,7 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
           for (int j = 0; j < MLP_XU; j++) yi = fmaf(yo[i * MLP_XU + j] + hb[i * MLP_XU + j], x[j], yi);
           const int f = mlp_field(i);
           const double d = (double)(yi * S.norm[2 * MLP_IN + MLP_Y + f] + S.norm[2 * MLP_IN + f]);
-          P0[f * N + z] = __ldg(Pn + f * N + z) + d;
+          P0[f * N + z] = Pkeep[i] + d;
         }
       }
     }
@@ -843,8 +827,8 @@ cudaError_t launch_mlp_features(const Params& p, const double* K, const double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_guess(const Params& p, const double* K, const double* Pn, const double* Un, const grim_mlp* m,
-                             double* P0, cudaStream_t st) {
+cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
+                             cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(mlp_guess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(InferSmem));
@@ -857,8 +841,7 @@ cudaError_t launch_mlp_guess(const Params& p, const double* K, const double* Pn,
   long long tiles = (p.N + 16 * INF_WARPS - 1) / (16 * INF_WARPS);
   long long grid = sms;  // persistent: one block (and one copy of the weights) per SM
   if (grid > tiles) grid = tiles;
-  mlp_guess<<<(unsigned)grid, INF_WARPS * 32, sizeof(InferSmem), st>>>(p, K, Pn, Un, m->wb, m->params, m->norm,
-                                                                       P0);
+  mlp_guess<<<(unsigned)grid, INF_WARPS * 32, sizeof(InferSmem), st>>>(p, feat, Pn, m->wb, m->params, m->norm, P0);
   return cudaGetLastError();
 }
 }  // namespace grim
