@@ -425,8 +425,8 @@ struct InferSmem {
   float b[3 * MLP_H + MLP_HEAD];
   float norm[2 * MLP_IN + 2 * MLP_Y];
   __nv_bfloat16 x[INF_WARPS][16][IW1];   // per-warp input tile
-  float xh[INF_WARPS][16][MLP_XU];       // per-warp head features (float32)
-  float y[INF_WARPS][16][MLP_HEAD + 1];  // per-warp head output tile
+  __align__(16) float xh[INF_WARPS][16][12];  // per-warp head features (float32; 10 used)
+  __align__(16) float y[INF_WARPS][16][84];   // per-warp head output tile, bias added (80 used)
 };
 
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
@@ -434,22 +434,34 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   return *reinterpret_cast<unsigned*>(&h);
 }
 
+// B fragments of n-tiles j and j+1 for one k16 step from the row-major
+// [n][k] weights in shared memory with one ldmatrix.x4: matrix q (lanes
+// 8q..8q+7 give its row addresses) covers n-tile j + q/2, k half q%2, and the
+// m8n8 distribution (row lane/4, columns 2(lane%4), +1) is the mma B layout.
+__device__ __forceinline__ void ldsm_b2(const __nv_bfloat16* W, int ldw, int j, int ks, int lane, unsigned b[4]) {
+  const int q = lane >> 3, r = lane & 7;
+  const __nv_bfloat16* row = W + ((j + (q >> 1)) * 8 + r) * ldw + ks * 16 + (q & 1) * 8;
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+               : "r"(addr));
+}
+
 template <int NOUT_TILES>
 __device__ __forceinline__ void layer_mma(float acc[][4], const unsigned (*afr)[4], int ksteps,
                                           const __nv_bfloat16* W, int ldw, int lane) {
-  const int ar = lane >> 2, ac = (lane & 3) * 2;
+  static_assert(NOUT_TILES % 2 == 0, "n-tiles are loaded in pairs");
 #pragma unroll
   for (int j = 0; j < NOUT_TILES; j++) {
     acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
   }
   for (int ks = 0; ks < ksteps; ks++) {
 #pragma unroll
-    for (int j = 0; j < NOUT_TILES; j++) {
-      const __nv_bfloat16* wr = W + (j * 8 + ar) * ldw + ks * 16 + ac;
-      unsigned bfr[2];
-      bfr[0] = *reinterpret_cast<const unsigned*>(wr);
-      bfr[1] = *reinterpret_cast<const unsigned*>(wr + 8);
-      mma_bf16(acc[j], afr[ks], bfr);
+    for (int j = 0; j < NOUT_TILES; j += 2) {
+      unsigned b[4];
+      ldsm_b2(W, ldw, j, ks, lane, b);
+      mma_bf16(acc[j], afr[ks], b);
+      mma_bf16(acc[j + 1], afr[ks], b + 2);
     }
   }
 }
@@ -558,11 +570,13 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
     {
       const int ar = lane >> 2, ac = (lane & 3) * 2;
 #pragma unroll
+      const float* hb = S.b + 3 * MLP_H;
       for (int j = 0; j < NT; j++) {
-        S.y[warp][ar][j * 8 + ac] = out[j][0];
-        S.y[warp][ar][j * 8 + ac + 1] = out[j][1];
-        S.y[warp][ar + 8][j * 8 + ac] = out[j][2];
-        S.y[warp][ar + 8][j * 8 + ac + 1] = out[j][3];
+        const float b0 = hb[j * 8 + ac], b1 = hb[j * 8 + ac + 1];
+        S.y[warp][ar][j * 8 + ac] = out[j][0] + b0;
+        S.y[warp][ar][j * 8 + ac + 1] = out[j][1] + b1;
+        S.y[warp][ar + 8][j * 8 + ac] = out[j][2] + b0;
+        S.y[warp][ar + 8][j * 8 + ac + 1] = out[j][3] + b1;
       }
     }
     __syncwarp();
@@ -570,14 +584,24 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
     if (lane < 16) {
       const long long z = zw + lane;
       if (z < N) {
-        const float* hb = S.b + 3 * MLP_H;
-        const float* yo = S.y[warp][lane];
-        const float* x = S.xh[warp][lane];
+        float yo[80], x[12];
+        const float4* yv = reinterpret_cast<const float4*>(S.y[warp][lane]);
+        const float4* xv = reinterpret_cast<const float4*>(S.xh[warp][lane]);
+#pragma unroll
+        for (int q = 0; q < 20; q++) {
+          const float4 t = yv[q];
+          yo[4 * q] = t.x; yo[4 * q + 1] = t.y; yo[4 * q + 2] = t.z; yo[4 * q + 3] = t.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+          const float4 t = xv[q];
+          x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+        }
 #pragma unroll
         for (int i = 0; i < MLP_NP; i++) {
-          float yi = yo[MLP_NP * MLP_XU + i] + hb[MLP_NP * MLP_XU + i];
+          float yi = yo[MLP_NP * MLP_XU + i];
 #pragma unroll
-          for (int j = 0; j < MLP_XU; j++) yi = fmaf(yo[i * MLP_XU + j] + hb[i * MLP_XU + j], x[j], yi);
+          for (int j = 0; j < MLP_XU; j++) yi = fmaf(yo[i * MLP_XU + j], x[j], yi);
           const int f = mlp_field(i);
           const double d = (double)(yi * S.norm[2 * MLP_IN + MLP_Y + f] + S.norm[2 * MLP_IN + f]);
           P0[f * N + z] = Pkeep[i] + d;
