@@ -19,10 +19,10 @@ cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, 
                             cudaStream_t st);
 cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cudaStream_t st);
 long long face_scratch_doubles(int n1, int n2);
-cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, cudaStream_t st);
+cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, int ffstates, cudaStream_t st);
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
                               double* K, double* P0, double* faces, double* cache, int mode, int bs, float* feat,
-                              cudaStream_t st);
+                              int ffslopes, cudaStream_t st);
 long long pn_cache_doubles(long long N);
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
@@ -252,12 +252,13 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
   }
   {
     KernelMark m(ctx, GRIM_K_FACES);
-    GRIM_CUDA(grim::launch_faces(ctx->p, PE, ctx->faces, ctx->tune.faces_bs, ctx->cur), "face kernel");
+    GRIM_CUDA(grim::launch_faces(ctx->p, PE, ctx->faces, ctx->tune.faces_bs, ctx->precision == GRIM_MIXED, ctx->cur),
+              "face kernel");
   }
   {
     KernelMark m(ctx, GRIM_K_ZONECONST);
     GRIM_CUDA(grim::launch_zone_const(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->faces, ctx->pncache, mode,
-                                      ctx->tune.zone_bs, feat, ctx->cur),
+                                      ctx->tune.zone_bs, feat, ctx->precision == GRIM_MIXED, ctx->cur),
               "zone-constant kernel");
   }
   return GRIM_OK;

@@ -17,7 +17,10 @@
 // go through HBM (20 doubles per zone): the kernels are bound by the float64
 // pipe, not by memory, so computing each face once matters more than keeping
 // faces on chip.
+#include <type_traits>
+
 #include "grim_zone.cuh"
+#include "grim_ff.cuh"
 
 namespace grim {
 
@@ -58,17 +61,17 @@ __device__ __forceinline__ double load_comp(const double* P, long long N, long l
 // fluid frame (Section 4.1, Minkowski space): the roots cmin <= cmax of
 // (u^j - c u^t)^2 (1 - v^2) = v^2 (1 - c^2).  kappa = cs~^2/c_s^2, a constant
 // of the closure chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R (Eq. modcs).
-template <int j>
-__device__ __forceinline__ void side_flux(const Z<double>& z, double gam, double kappa, double U[NV], double F[NV],
-                                          double& cmin, double& cmax) {
-  const double q = z.qt * z.qs, dp = z.dpt * z.ds;
-  const double third = dp * (1.0 / 3.0);
-  const double wt = z.w0 + z.bsq + third;
-  const double A = wt * z.ut;
-  const double qb = q * z.bht, dpb = dp * z.bht, qut = q * z.ut;
-  const double pt = z.pg + 0.5 * z.bsq + third;
+// gam: gamma; kg: kappa gamma (both in the working precision).
+template <int j, typename T>
+__device__ __forceinline__ void side_flux(const Z<T>& z, T gam, T kg, T U[NV], T F[NV], T& cmin, T& cmax) {
+  const T q = z.qt * z.qs, dp = z.dpt * z.ds;
+  const T third = dp * tconst<T>(1.0 / 3.0);
+  const T wt = z.w0 + z.bsq + third;
+  const T A = wt * z.ut;
+  const T qb = q * z.bht, dpb = dp * z.bht, qut = q * z.ut;
+  const T pt = z.pg + tconst<T>(0.5) * z.bsq + third;
   U[0] = z.rho * z.ut;
-  U[1] = -A * z.ut + z.bt * z.bt - 2.0 * qb * z.ut + dpb * z.bht + pt;
+  U[1] = -A * z.ut + z.bt * z.bt - tconst<T>(2.0) * qb * z.ut + dpb * z.bht + pt;
 #pragma unroll
   for (int i = 0; i < 3; i++) U[2 + i] = A * z.v[i] - z.bt * z.bc[i] + qb * z.v[i] + qut * z.bh[i] - dpb * z.bh[i];
   U[5] = z.B[0]; U[6] = z.B[1]; U[7] = z.B[2];
@@ -76,14 +79,14 @@ __device__ __forceinline__ void side_flux(const Z<double>& z, double gam, double
   U[9] = z.dpt * z.ut;
   // row j of T^mu_nu: (w + dP/3) u^j u_nu - b^j b_nu + q (bhat^j u_nu + u^j bhat_nu)
   // - dP bhat^j bhat_nu + (p_t + dP/3) delta^j_nu
-  const double uj = z.v[j - 1], bj = z.bc[j - 1], bhj = z.bh[j - 1];
-  const double Aj = wt * uj, qbj = q * bhj, quj = q * uj, dpbj = dp * bhj;
+  const T uj = z.v[j - 1], bj = z.bc[j - 1], bhj = z.bh[j - 1];
+  const T Aj = wt * uj, qbj = q * bhj, quj = q * uj, dpbj = dp * bhj;
   F[0] = z.rho * uj;
   F[1] = -Aj * z.ut + bj * z.bt - qbj * z.ut - quj * z.bht + dpbj * z.bht;
 #pragma unroll
   for (int i = 0; i < 3; i++) {
-    double t = Aj * z.v[i] - bj * z.bc[i] + qbj * z.v[i] + quj * z.bh[i] - dpbj * z.bh[i];
-    if (i == j - 1) t += pt;
+    T t = Aj * z.v[i] - bj * z.bc[i] + qbj * z.v[i] + quj * z.bh[i] - dpbj * z.bh[i];
+    if (i == j - 1) t = t + pt;
     F[2 + i] = t;
   }
 #pragma unroll
@@ -91,16 +94,16 @@ __device__ __forceinline__ void side_flux(const Z<double>& z, double gam, double
   F[8] = z.qt * uj;
   F[9] = z.dpt * uj;
   // speeds
-  const double den = z.rho + gam * z.u;
-  const double vA2 = z.bsq * nr_rcp(den + z.bsq);
-  const double cs2t = kappa * gam * z.pg * z.iden;
-  const double v2 = cs2t + vA2 - cs2t * vA2;
-  const double om = 1.0 - v2;
-  const double Aq = om * z.ut * z.ut + v2;
-  const double Bq = -2.0 * om * z.ut * uj;
-  const double Cq = om * uj * uj - v2;
-  const double disc = fmax(Bq * Bq - 4.0 * Aq * Cq, 0.0);
-  const double sq = sqrt(disc), h = 0.5 * nr_rcp(Aq);  // Aq > 0
+  const T den = z.rho + gam * z.u;
+  const T vA2 = z.bsq * nr_rcp(den + z.bsq);
+  const T cs2t = kg * z.pg * z.iden;
+  const T v2 = cs2t + vA2 - cs2t * vA2;
+  const T om = tconst<T>(1.0) - v2;
+  const T Aq = om * z.ut * z.ut + v2;
+  const T Bq = tconst<T>(-2.0) * om * z.ut * uj;
+  const T Cq = om * uj * uj - v2;
+  const T disc = fmax(Bq * Bq - tconst<T>(4.0) * Aq * Cq, tconst<T>(0.0));
+  const T sq = sqr_root(disc), h = tconst<T>(0.5) * nr_rcp(Aq);  // Aq > 0
   cmax = (sq - Bq) * h;
   cmin = -((sq + Bq) * h);
 }
@@ -108,19 +111,20 @@ __device__ __forceinline__ void side_flux(const Z<double>& z, double gam, double
 // LLF (F^- + F^+)/2 - c_max (U^+ - U^-)/2 with c_max the largest |c| of both
 // sides, or HLLE (c_R F^- + c_L F^+ - c_R c_L (U^+ - U^-))/(c_L + c_R) with
 // c_R = max(c, 0), c_L = max(-c, 0) over both sides (Section 2.4.2);
-// L: the left state P^-, R: the right state P^+.
-__device__ __forceinline__ void riemann_flux(int kind, const double FL[NV], const double FR[NV], const double UL[NV],
-                                             const double UR[NV], double cminL, double cmaxL, double cminR,
-                                             double cmaxR, double* out, long long plane) {
+// L: the left state P^-, R: the right state P^+.  Written as float64.
+template <typename T>
+__device__ __forceinline__ void riemann_flux(int kind, const T FL[NV], const T FR[NV], const T UL[NV], const T UR[NV],
+                                             T cminL, T cmaxL, T cminR, T cmaxR, double* out, long long plane) {
   if (kind == 1) {
-    const double cR = fmax(fmax(cmaxL, cmaxR), 0.0), cL = fmax(-fmin(cminL, cminR), 0.0);
-    const double iw = 1.0 / (cL + cR);
+    const T cR = fmax(fmax(cmaxL, cmaxR), tconst<T>(0.0)), cL = fmax(-fmin(cminL, cminR), tconst<T>(0.0));
+    const T iw = nr_rcp(cL + cR);
 #pragma unroll
-    for (int v = 0; v < NV; v++) out[v * plane] = (cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) * iw;
+    for (int v = 0; v < NV; v++) out[v * plane] = as_double((cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) * iw);
   } else {
-    const double cm = fmax(fmax(cmaxL, -cminL), fmax(cmaxR, -cminR));
+    const T cm = fmax(fmax(cmaxL, -cminL), fmax(cmaxR, -cminR));
 #pragma unroll
-    for (int v = 0; v < NV; v++) out[v * plane] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+    for (int v = 0; v < NV; v++)
+      out[v * plane] = as_double(tconst<T>(0.5) * (FL[v] + FR[v]) - tconst<T>(0.5) * cm * (UR[v] - UL[v]));
   }
 }
 
@@ -143,10 +147,14 @@ struct ExpArgs {
   // with a learned start: the ten increment features -r_a(P_n) of each zone
   // (float32 [10][N]), from the constants computed here
   float* feat;
+  // float-float copies of gamma, gamma-1, sqrt(phi gamma), sqrt(psi gamma),
+  // kappa gamma and the limiter theta (hi, lo pairs), for the float-float
+  // face states and slopes
+  float ffc[12];
 };
 constexpr int NCACHE = NV + 2;
 
-template <int D, int RECON>
+template <int D, int RECON, typename S>
 __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a, int i, int j, double* out,
                                               long long plane) {
   constexpr int di = (D == 0), dj = (D == 1);
@@ -158,38 +166,59 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   bool fa[6], fb[6];
 #pragma unroll
   for (int t = o0; t <= o1; t++) zz[t + 3] = zone_at(p, i + t * di, j + t * dj, fa[t + 3], fb[t + 3]);
-  double L[NV], R[NV];
+  // reconstruction in float64 (its limiter decisions are those of the
+  // float64 path), then the face values in the state precision
+  S Ls[NV], Rs[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    double s[6];
+    double s[6], L, R;
 #pragma unroll
     for (int t = o0; t <= o1; t++) s[t + 3] = load_comp(a.PE, N, zz[t + 3], v, fa[t + 3], fb[t + 3]);
     if (RECON == RECON_WENO5) {
-      L[v] = weno5v(s[0], s[1], s[2], s[3], s[4]);
-      R[v] = weno5v(s[5], s[4], s[3], s[2], s[1]);
+      L = weno5v(s[0], s[1], s[2], s[3], s[4]);
+      R = weno5v(s[5], s[4], s[3], s[2], s[1]);
     } else if (RECON == RECON_PPM) {
       double lo, hi;
       ppm_zone(p.theta, s[0], s[1], s[2], s[3], s[4], lo, hi);  // zone left of the face
-      L[v] = hi;
+      L = hi;
       ppm_zone(p.theta, s[1], s[2], s[3], s[4], s[5], lo, hi);  // zone right of the face
-      R[v] = lo;
+      R = lo;
     } else {
-      L[v] = fma(0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
-      R[v] = fma(-0.5, gm_slope(p.theta, s[2], s[3], s[4]), s[3]);
+      L = fma(0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
+      R = fma(-0.5, gm_slope(p.theta, s[2], s[3], s[4]), s[3]);
     }
+    Ls[v] = from_double<S>(L);
+    Rs[v] = from_double<S>(R);
   }
-  const RC<double> c = make_rc<double>(p);
-  Z<double> zl, zr;
-  z_load(zl, L, c);
-  z_load(zr, R, c);
-  double UL[NV], FL[NV], UR[NV], FR[NV];
-  double cminL, cmaxL, cminR, cmaxR;
-  side_flux<D + 1>(zl, p.gamma, a.kappa, UL, FL, cminL, cmaxL);
-  side_flux<D + 1>(zr, p.gamma, a.kappa, UR, FR, cminR, cmaxR);
-  riemann_flux(p.riemann, FL, FR, UL, UR, cminL, cmaxL, cminR, cmaxR, out, plane);
+  // face states and fluxes in the state precision S (float64, or
+  // float-float for the mixed solver); the reconstruction above is float64
+  RC<S> c;
+  S gam, kg;
+  if constexpr (std::is_same<S, double>::value) {
+    c = make_rc<S>(p);
+    gam = S(p.gamma);
+    kg = S(a.kappa * p.gamma);
+  } else {
+    c.gam = S(a.ffc[0], a.ffc[1]);
+    c.gm1 = S(a.ffc[2], a.ffc[3]);
+    c.sphig = S(a.ffc[4], a.ffc[5]);
+    c.spsig = S(a.ffc[6], a.ffc[7]);
+    c.cond = p.cond;
+    c.visc = p.visc;
+    gam = c.gam;
+    kg = S(a.ffc[8], a.ffc[9]);
+  }
+  Z<S> zl, zr;
+  z_load(zl, Ls, c);
+  z_load(zr, Rs, c);
+  S UL[NV], FL[NV], UR[NV], FR[NV];
+  S cminL, cmaxL, cminR, cmaxR;
+  side_flux<D + 1>(zl, gam, kg, UL, FL, cminL, cmaxL);
+  side_flux<D + 1>(zr, gam, kg, UR, FR, cminR, cmaxR);
+  riemann_flux<S>(p.riemann, FL, FR, UL, UR, cminL, cmaxL, cminR, cmaxR, out, plane);
 }
 
-template <int BS>
+template <int BS, typename S>
 __global__ void __launch_bounds__(BS) face_flux_2d(const __grid_constant__ Params p,
                                                   const __grid_constant__ ExpArgs a) {
   const long long nf1 = (long long)(p.n1 + 1) * (p.n2 + 2);
@@ -199,16 +228,16 @@ __global__ void __launch_bounds__(BS) face_flux_2d(const __grid_constant__ Param
   if (f < nf1) {
     const int i = (int)(f % (p.n1 + 1)), j = (int)(f / (p.n1 + 1)) - 1;
     double* out = a.F1 + (long long)(j + 1) * (p.n1 + 1) + i;
-    if (p.recon == RECON_WENO5) face_flux_dir<0, RECON_WENO5>(p, a, i, j, out, nf1);
-    else if (p.recon == RECON_PPM) face_flux_dir<0, RECON_PPM>(p, a, i, j, out, nf1);
-    else face_flux_dir<0, RECON_MC>(p, a, i, j, out, nf1);
+    if (p.recon == RECON_WENO5) face_flux_dir<0, RECON_WENO5, S>(p, a, i, j, out, nf1);
+    else if (p.recon == RECON_PPM) face_flux_dir<0, RECON_PPM, S>(p, a, i, j, out, nf1);
+    else face_flux_dir<0, RECON_MC, S>(p, a, i, j, out, nf1);
   } else {
     const long long g = f - nf1;
     const int i = (int)(g % (p.n1 + 2)) - 1, j = (int)(g / (p.n1 + 2));
     double* out = a.F2 + (long long)j * (p.n1 + 2) + (i + 1);
-    if (p.recon == RECON_WENO5) face_flux_dir<1, RECON_WENO5>(p, a, i, j, out, nf2);
-    else if (p.recon == RECON_PPM) face_flux_dir<1, RECON_PPM>(p, a, i, j, out, nf2);
-    else face_flux_dir<1, RECON_MC>(p, a, i, j, out, nf2);
+    if (p.recon == RECON_WENO5) face_flux_dir<1, RECON_WENO5, S>(p, a, i, j, out, nf2);
+    else if (p.recon == RECON_PPM) face_flux_dir<1, RECON_PPM, S>(p, a, i, j, out, nf2);
+    else face_flux_dir<1, RECON_MC, S>(p, a, i, j, out, nf2);
   }
 }
 
@@ -225,7 +254,30 @@ __device__ __forceinline__ void derived_at(const Params& p, const double* PE, in
   u[1] = v1; u[2] = v2; u[3] = v3;
 }
 
-template <int BS>
+// The same in float-float (the mixed solver's slopes): inputs split
+// without float64 instructions.
+__device__ __forceinline__ void derived_at_ff(const Params& p, const ExpArgs& a, int i, int j, ff& th, ff u[4]) {
+  bool f1, f2;
+  const long long z = zone_at(p, i, j, f1, f2);
+  const long long N = p.N;
+  const ff rho = ff_split(__ldg(a.PE + z)), uu = ff_split(__ldg(a.PE + N + z));
+  const ff v1 = ff_split(load_comp(a.PE, N, z, 2, f1, f2)), v2 = ff_split(load_comp(a.PE, N, z, 3, f1, f2));
+  const ff v3 = ff_split(__ldg(a.PE + 4 * N + z));
+  th = ff(a.ffc[2], a.ffc[3]) * uu * nr_rcp(rho);
+  u[0] = -sqr_root(tconst<ff>(1.0) + v1 * v1 + v2 * v2 + v3 * v3);
+  u[1] = v1; u[2] = v2; u[3] = v3;
+}
+// Generalized minmod slope in float-float (the float64 form is gm_slope).
+__device__ __forceinline__ ff gm_slope_ff(ff theta, ff vm, ff v0, ff vp) {
+  const ff a = v0 - vm, c = vp - v0;
+  if (!((a.hi > 0.f && c.hi > 0.f) || (a.hi < 0.f && c.hi < 0.f))) return ff(0.f, 0.f);
+  const ff m = fmin(theta * fmin(fabs(a), fabs(c)), tconst<ff>(0.5) * fabs(a + c));
+  return a.hi > 0.f ? m : -m;
+}
+
+// FFS: the limited slopes of Theta and u_mu in float-float (the mixed
+// solver); everything else of the kernel is float64 either way.
+template <int BS, bool FFS>
 __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Params p,
                                                    const __grid_constant__ ExpArgs a) {
   const long long N = p.N;
@@ -307,7 +359,7 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
 
   // limited slopes at P^E of Theta and u_mu; the spatial part of nabla_mu u^mu
   double dTh[2], du[2][4], divu_sp = 0.0;
-  {
+  if (!FFS) {
     double th0 = ze.theta, u0[4] = {-ze.ut, ze.v[0], ze.v[1], ze.v[2]};
 #pragma unroll
     for (int d = 0; d < 2; d++) {
@@ -318,6 +370,21 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
       dTh[d] = gm_slope(p.theta, thm, th0, thp) * ih;
 #pragma unroll
       for (int m = 0; m < 4; m++) du[d][m] = gm_slope(p.theta, um[m], u0[m], up[m]) * ih;
+      divu_sp += du[d][1 + d];
+    }
+  } else {
+    const ff theta(a.ffc[10], a.ffc[11]);
+    const ff th0 = ff_split(ze.theta);
+    const ff u0[4] = {ff_split(-ze.ut), ff_split(ze.v[0]), ff_split(ze.v[1]), ff_split(ze.v[2])};
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      ff thm, thp, um[4], up[4];
+      derived_at_ff(p, a, i - (d == 0), j - (d == 1), thm, um);
+      derived_at_ff(p, a, i + (d == 0), j + (d == 1), thp, up);
+      const double ih = (d == 0) ? idx1 : idx2;
+      dTh[d] = ff_join(gm_slope_ff(theta, thm, th0, thp)) * ih;
+#pragma unroll
+      for (int m = 0; m < 4; m++) du[d][m] = ff_join(gm_slope_ff(theta, um[m], u0[m], up[m])) * ih;
       divu_sp += du[d][1 + d];
     }
   }
@@ -442,46 +509,64 @@ void explicit_args(const Params& p, const double* Pn, const double* PE, const do
                    double* P0, double* faces, ExpArgs& a) {
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.kappa = closure_kappa(p);
   a.cache = nullptr; a.mode = 0; a.feat = nullptr;
+  const double cv[6] = {p.gamma, p.gamma - 1.0, sqrt(p.phi * p.gamma), sqrt(p.psi * p.gamma), a.kappa * p.gamma,
+                        p.theta};
+  for (int k = 0; k < 6; k++) {
+    a.ffc[2 * k] = (float)cv[k];
+    a.ffc[2 * k + 1] = (float)(cv[k] - (double)(float)cv[k]);
+  }
   a.K = K; a.P0 = P0;
   a.F1 = faces;
   a.F2 = faces + (long long)NV * (p.n1 + 1) * (p.n2 + 2);
 }
 
-// bs: threads per block, 64, 128 or 256.
-cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, cudaStream_t st) {
+template <typename S>
+static cudaError_t launch_faces_s(const Params& p, const ExpArgs& a, unsigned nb, int bs, cudaStream_t st) {
+  switch (bs) {
+    case 64: face_flux_2d<64, S><<<nb, 64, 0, st>>>(p, a); break;
+    case 128: face_flux_2d<128, S><<<nb, 128, 0, st>>>(p, a); break;
+    case 256: face_flux_2d<256, S><<<nb, 256, 0, st>>>(p, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// bs: threads per block, 64, 128 or 256.  ffstates: face states and fluxes
+// in float-float (the mixed solver) instead of float64.
+cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, int ffstates, cudaStream_t st) {
   ExpArgs a;
   explicit_args(p, nullptr, PE, nullptr, 1.0, nullptr, nullptr, faces, a);
   const long long nf = (long long)(p.n1 + 1) * (p.n2 + 2) + (long long)(p.n1 + 2) * (p.n2 + 1);
   const unsigned nb = (unsigned)((nf + bs - 1) / bs);
-  switch (bs) {
-    case 64: face_flux_2d<64><<<nb, 64, 0, st>>>(p, a); break;
-    case 128: face_flux_2d<128><<<nb, 128, 0, st>>>(p, a); break;
-    case 256: face_flux_2d<256><<<nb, 256, 0, st>>>(p, a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return ffstates ? launch_faces_s<ff>(p, a, nb, bs, st) : launch_faces_s<double>(p, a, nb, bs, st);
 }
 
 long long pn_cache_doubles(long long N) { return (long long)NCACHE * N; }
 
 // mode: 0 general stage, 1 half step (P_E == P_n; fills cache), 2 full step
 // of the same step (reads cache and K_U).
+template <bool FFS>
+static cudaError_t launch_zone_const_s(const Params& p, const ExpArgs& a, unsigned nb, int bs, cudaStream_t st) {
+  switch (bs) {
+    case 64: zone_const_2d<64, FFS><<<nb, 64, 0, st>>>(p, a); break;
+    case 128: zone_const_2d<128, FFS><<<nb, 128, 0, st>>>(p, a); break;
+    case 256: zone_const_2d<256, FFS><<<nb, 256, 0, st>>>(p, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ffslopes: the limited slopes in float-float (the mixed solver).
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
                               double* K, double* P0, double* faces, double* cache, int mode, int bs, float* feat,
-                              cudaStream_t st) {
+                              int ffslopes, cudaStream_t st) {
   ExpArgs a;
   explicit_args(p, Pn, PE, guess, dts, K, P0, faces, a);
   a.cache = cache;
   a.mode = cache ? mode : 0;
   a.feat = feat;
   const unsigned nb = (unsigned)((p.N + bs - 1) / bs);
-  switch (bs) {
-    case 64: zone_const_2d<64><<<nb, 64, 0, st>>>(p, a); break;
-    case 128: zone_const_2d<128><<<nb, 128, 0, st>>>(p, a); break;
-    case 256: zone_const_2d<256><<<nb, 256, 0, st>>>(p, a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return ffslopes ? launch_zone_const_s<true>(p, a, nb, bs, st) : launch_zone_const_s<false>(p, a, nb, bs, st);
 }
 
 }  // namespace grim

@@ -1,0 +1,142 @@
+// Float-float arithmetic: a value is the unevaluated sum hi + lo of two
+// floats (about 48 significant bits, relative rounding ~2^-47), built from
+// error-free transformations (Knuth's two-sum, Dekker's split via FMA).  On
+// B300 a float-float operation costs 4-20 float32 instructions on a pipe 64
+// times wider than the float64 one, so face states and fluxes evaluated this
+// way cost a fraction of their float64 time at an accuracy far below the
+// solver tolerances.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace grim {
+
+struct ff {
+  float hi, lo;
+  ff() = default;
+  __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit ff(double d) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+  }
+  __device__ __forceinline__ explicit ff(int i) : hi((float)i), lo(0.f) {}
+};
+
+__device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// A compile-time constant in the working precision (for float-float: the
+// pair of the nearest float and the float nearest to the remainder), so that
+// literals cost no float64 conversion at run time.
+template <typename T> __host__ __device__ constexpr T tconst(double x) { return T(x); }
+template <> __host__ __device__ constexpr ff tconst<ff>(double x) {
+  return ff(static_cast<float>(x), static_cast<float>(x - static_cast<double>(static_cast<float>(x))));
+}
+template <> __host__ __device__ constexpr double tconst<double>(double x) { return x; }
+__device__ __forceinline__ double ff_join(ff a);
+__device__ __forceinline__ double as_double(ff a) { return ff_join(a); }
+__device__ __forceinline__ double as_double(double a) { return a; }
+
+// s + e with |s| >= |e| (or s = 0): normalised pair.
+__device__ __forceinline__ ff ff_quick(float s, float e) {
+  const float h = s + e;
+  return ff(h, e - (h - s));
+}
+// Exact sum a + b = s + err.
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float v = s - a;
+  return ff(s, (a - (s - v)) + (b - v));
+}
+
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator+(ff x, ff y) {
+  const ff s = ff_two_sum(x.hi, y.hi);
+  const ff t = ff_two_sum(x.lo, y.lo);
+  const ff u = ff_quick(s.hi, s.lo + t.hi);
+  return ff_quick(u.hi, u.lo + t.lo);
+}
+__device__ __forceinline__ ff operator-(ff x, ff y) { return x + (-y); }
+__device__ __forceinline__ ff operator*(ff x, ff y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return ff_quick(p, e);
+}
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) { a = a + b; return a; }
+__device__ __forceinline__ ff& operator-=(ff& a, ff b) { a = a - b; return a; }
+__device__ __forceinline__ ff& operator*=(ff& a, ff b) { a = a * b; return a; }
+
+__device__ __forceinline__ bool operator>(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator<(ff a, ff b) { return b > a; }
+
+// The float64 forms stay visible beside the float-float overloads below.
+__device__ __forceinline__ double fabs(double a) { return ::fabs(a); }
+__device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
+__device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float fabs(float a) { return ::fabsf(a); }
+__device__ __forceinline__ float fmax(float a, float b) { return ::fmaxf(a, b); }
+__device__ __forceinline__ float fmin(float a, float b) { return ::fminf(a, b); }
+
+__device__ __forceinline__ ff fabs(ff a) { return (a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f)) ? -a : a; }
+__device__ __forceinline__ ff fmax(ff a, ff b) { return a > b ? a : b; }
+__device__ __forceinline__ ff fmin(ff a, ff b) { return a > b ? b : a; }
+__device__ __forceinline__ ff fma(ff a, ff b, ff c) { return a * b + c; }
+
+// 1/y: the float reciprocal refined by one Newton step in float-float.
+__device__ __forceinline__ ff nr_rcp(ff y) {
+  const ff x(__frcp_rn(y.hi), 0.f);
+  const ff one(1.f, 0.f);
+  return x + x * (one - y * x);
+}
+// sqrt(a), a >= 0: the float root corrected by (a - s^2)/(2 s).
+__device__ __forceinline__ ff sqr_root(ff a) {
+  if (!(a.hi > 0.f)) return ff(0.f, 0.f);
+  const float s = __fsqrt_rn(a.hi);
+  const ff S(s, 0.f);
+  const ff r = a - S * S;
+  return ff_quick(s, r.hi * (0.5f / s));
+}
+// a^(-1/2), a > 0: the float estimate refined by one Newton step in
+// float-float, y <- y + y (1 - a y^2)/2.
+__device__ __forceinline__ ff rsq(ff a) {
+  const ff y(rsqrtf(a.hi), 0.f);
+  const ff one(1.f, 0.f), half(0.5f, 0.f);
+  return y + (y * half) * (one - a * (y * y));
+}
+
+// Conversions by integer bit manipulation (no float64 instruction): a double
+// split into its leading 24 significant bits (hi, truncated) and the float
+// nearest to the remaining 29 (lo); a float widened exactly to double.
+// Values outside the normal float range take the float64 route.
+__device__ __forceinline__ ff ff_split(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return ff(0.f, 0.f);
+  // fast path for 2^-74 <= |d| < 2^100: the scale of lo stays a normal float
+  if (e < 1075 - 126 || e > 1023 + 100) return ff(d);
+  const unsigned sign = (unsigned)(b >> 63);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const float hi = __uint_as_float((sign << 31) | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+  // low 29 bits: an integer below 2^29 times 2^(e - 1075)
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
+  float lo = __uint2float_rn((unsigned)(m & 0x1fffffffull)) * scale;
+  return ff(hi, sign ? -lo : lo);
+}
+__device__ __forceinline__ double f_widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xff;
+  if (ef == 0) return 0.0;  // zero or a float denormal (below 1e-38)
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long e = (unsigned long long)(ef - 127 + 1023) << 52;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(s | e | m));
+}
+__device__ __forceinline__ double ff_join(ff a) { return f_widen(a.hi) + f_widen(a.lo); }
+
+// Input in the working precision: float64 as is, float-float by the split.
+template <typename T> __device__ __forceinline__ T from_double(double d);
+template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }
+template <> __device__ __forceinline__ ff from_double<ff>(double d) { return ff_split(d); }
+
+}  // namespace grim

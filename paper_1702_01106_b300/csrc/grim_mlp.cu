@@ -569,8 +569,8 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
     layer_mma<NT>(out, afr, 8, &S.w3[0][0], IWH, lane);
     {
       const int ar = lane >> 2, ac = (lane & 3) * 2;
-#pragma unroll
       const float* hb = S.b + 3 * MLP_H;
+#pragma unroll
       for (int j = 0; j < NT; j++) {
         const float b0 = hb[j * 8 + ac], b1 = hb[j * 8 + ac + 1];
         S.y[warp][ar][j * 8 + ac] = out[j][0] + b0;
