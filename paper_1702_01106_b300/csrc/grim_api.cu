@@ -35,7 +35,8 @@ long long gr_geometry_doubles(const Params& p);
 long long gr_face_doubles(const Params& p);
 cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double h, const double x0[3],
                                double* geo, cudaStream_t st);
-cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo, double* faces, cudaStream_t st);
+cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo, double* faces, int ffstates,
+                            cudaStream_t st);
 cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
                                  const double* geo, double* faces, double* K, double* P0, cudaStream_t st);
 cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K, const double* Pn,
@@ -243,7 +244,7 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
   if (ctx->gr) {
     {
       KernelMark m(ctx, GRIM_K_FACES, ctx->p.dim);
-      GRIM_CUDA(grim::launch_gr_faces(ctx->p, PE, ctx->geo, ctx->faces, ctx->cur), "face kernel");
+      GRIM_CUDA(grim::launch_gr_faces(ctx->p, PE, ctx->geo, ctx->faces, ctx->precision == GRIM_MIXED, ctx->cur), "face kernel");
     }
     KernelMark m(ctx, GRIM_K_ZONECONST);
     GRIM_CUDA(grim::launch_gr_zone_const(ctx->p, Pn, PE, guess, dts, ctx->geo, ctx->faces, ctx->K, Pout, ctx->cur),

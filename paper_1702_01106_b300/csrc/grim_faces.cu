@@ -49,10 +49,12 @@ __device__ __forceinline__ long long zone_at(const Params& p, int i, int j, bool
   const int gj = map_idx(j, p.n2, p.bc[1][0], p.bc[1][1], f2);
   return (long long)gj * p.n1 + gi;
 }
+__device__ __forceinline__ bool comp_flips(int v, bool f1, bool f2) {
+  return (f1 && (v == 2 || v == 5)) || (f2 && (v == 3 || v == 6));
+}
 __device__ __forceinline__ double load_comp(const double* P, long long N, long long z, int v, bool f1, bool f2) {
-  double x = __ldg(P + v * N + z);
-  if ((f1 && (v == 2 || v == 5)) || (f2 && (v == 3 || v == 6))) x = -x;
-  return x;
+  const double x = __ldg(P + v * N + z);
+  return comp_flips(v, f1, f2) ? -x : x;
 }
 
 // Conserved variables U and flux F^j (j = 1, 2, 3) of a face state (Eqs.
@@ -166,32 +168,46 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   bool fa[6], fb[6];
 #pragma unroll
   for (int t = o0; t <= o1; t++) zz[t + 3] = zone_at(p, i + t * di, j + t * dj, fa[t + 3], fb[t + 3]);
-  // reconstruction in float64 (its limiter decisions are those of the
-  // float64 path), then the face values in the state precision
+  // reconstruction, then the face states in the state precision.  MC runs
+  // in the state precision (the limiter is continuous in its arguments, so
+  // a decision that differs from float64 at a near-tie moves the face value
+  // by no more than the rounding); WENO5 and PPM run in float64.
   S Ls[NV], Rs[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    double s[6], L, R;
+    if constexpr (!std::is_same<S, double>::value && RECON == RECON_MC) {
+      const ff theta(a.ffc[10], a.ffc[11]);
+      ff t[4];
 #pragma unroll
-    for (int t = o0; t <= o1; t++) s[t + 3] = load_comp(a.PE, N, zz[t + 3], v, fa[t + 3], fb[t + 3]);
-    if (RECON == RECON_WENO5) {
-      L = weno5v(s[0], s[1], s[2], s[3], s[4]);
-      R = weno5v(s[5], s[4], s[3], s[2], s[1]);
-    } else if (RECON == RECON_PPM) {
-      double lo, hi;
-      ppm_zone(p.theta, s[0], s[1], s[2], s[3], s[4], lo, hi);  // zone left of the face
-      L = hi;
-      ppm_zone(p.theta, s[1], s[2], s[3], s[4], s[5], lo, hi);  // zone right of the face
-      R = lo;
+      for (int k = 0; k < 4; k++) {
+        t[k] = ff_split(__ldg(a.PE + v * N + zz[k + 1]));
+        if (comp_flips(v, fa[k + 1], fb[k + 1])) t[k] = -t[k];
+      }
+      Ls[v] = t[1] + scale2(gm_slope(theta, t[0], t[1], t[2]), 0.5f);
+      Rs[v] = t[2] - scale2(gm_slope(theta, t[1], t[2], t[3]), 0.5f);
     } else {
-      L = fma(0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
-      R = fma(-0.5, gm_slope(p.theta, s[2], s[3], s[4]), s[3]);
+      double s[6], L, R;
+#pragma unroll
+      for (int t = o0; t <= o1; t++) s[t + 3] = load_comp(a.PE, N, zz[t + 3], v, fa[t + 3], fb[t + 3]);
+      if (RECON == RECON_WENO5) {
+        L = weno5v(s[0], s[1], s[2], s[3], s[4]);
+        R = weno5v(s[5], s[4], s[3], s[2], s[1]);
+      } else if (RECON == RECON_PPM) {
+        double lo, hi;
+        ppm_zone(p.theta, s[0], s[1], s[2], s[3], s[4], lo, hi);  // zone left of the face
+        L = hi;
+        ppm_zone(p.theta, s[1], s[2], s[3], s[4], s[5], lo, hi);  // zone right of the face
+        R = lo;
+      } else {
+        L = fma(0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
+        R = fma(-0.5, gm_slope(p.theta, s[2], s[3], s[4]), s[3]);
+      }
+      Ls[v] = from_double<S>(L);
+      Rs[v] = from_double<S>(R);
     }
-    Ls[v] = from_double<S>(L);
-    Rs[v] = from_double<S>(R);
   }
   // face states and fluxes in the state precision S (float64, or
-  // float-float for the mixed solver); the reconstruction above is float64
+  // float-float for the mixed solver)
   RC<S> c;
   S gam, kg;
   if constexpr (std::is_same<S, double>::value) {
@@ -218,8 +234,11 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   riemann_flux<S>(p.riemann, FL, FR, UL, UR, cminL, cmaxL, cminR, cmaxR, out, plane);
 }
 
-template <int BS, typename S>
-__global__ void __launch_bounds__(BS) face_flux_2d(const __grid_constant__ Params p,
+// One kernel per reconstruction, so that each holds only its own registers.
+// The float-float form is held to 128 registers a thread (16 warps per SM),
+// for the latency of its dependent float chains.
+template <int BS, typename S, int RECON>
+__global__ void __launch_bounds__(BS, std::is_same<S, ff>::value ? 65536 / (BS * 128) : 1) face_flux_2d(const __grid_constant__ Params p,
                                                   const __grid_constant__ ExpArgs a) {
   const long long nf1 = (long long)(p.n1 + 1) * (p.n2 + 2);
   const long long nf2 = (long long)(p.n1 + 2) * (p.n2 + 1);
@@ -228,16 +247,12 @@ __global__ void __launch_bounds__(BS) face_flux_2d(const __grid_constant__ Param
   if (f < nf1) {
     const int i = (int)(f % (p.n1 + 1)), j = (int)(f / (p.n1 + 1)) - 1;
     double* out = a.F1 + (long long)(j + 1) * (p.n1 + 1) + i;
-    if (p.recon == RECON_WENO5) face_flux_dir<0, RECON_WENO5, S>(p, a, i, j, out, nf1);
-    else if (p.recon == RECON_PPM) face_flux_dir<0, RECON_PPM, S>(p, a, i, j, out, nf1);
-    else face_flux_dir<0, RECON_MC, S>(p, a, i, j, out, nf1);
+    face_flux_dir<0, RECON, S>(p, a, i, j, out, nf1);
   } else {
     const long long g = f - nf1;
     const int i = (int)(g % (p.n1 + 2)) - 1, j = (int)(g / (p.n1 + 2));
     double* out = a.F2 + (long long)j * (p.n1 + 2) + (i + 1);
-    if (p.recon == RECON_WENO5) face_flux_dir<1, RECON_WENO5, S>(p, a, i, j, out, nf2);
-    else if (p.recon == RECON_PPM) face_flux_dir<1, RECON_PPM, S>(p, a, i, j, out, nf2);
-    else face_flux_dir<1, RECON_MC, S>(p, a, i, j, out, nf2);
+    face_flux_dir<1, RECON, S>(p, a, i, j, out, nf2);
   }
 }
 
@@ -266,13 +281,6 @@ __device__ __forceinline__ void derived_at_ff(const Params& p, const ExpArgs& a,
   th = ff(a.ffc[2], a.ffc[3]) * uu * nr_rcp(rho);
   u[0] = -sqr_root(tconst<ff>(1.0) + v1 * v1 + v2 * v2 + v3 * v3);
   u[1] = v1; u[2] = v2; u[3] = v3;
-}
-// Generalized minmod slope in float-float (the float64 form is gm_slope).
-__device__ __forceinline__ ff gm_slope_ff(ff theta, ff vm, ff v0, ff vp) {
-  const ff a = v0 - vm, c = vp - v0;
-  if (!((a.hi > 0.f && c.hi > 0.f) || (a.hi < 0.f && c.hi < 0.f))) return ff(0.f, 0.f);
-  const ff m = fmin(theta * fmin(fabs(a), fabs(c)), tconst<ff>(0.5) * fabs(a + c));
-  return a.hi > 0.f ? m : -m;
 }
 
 // FFS: the limited slopes of Theta and u_mu in float-float (the mixed
@@ -382,9 +390,9 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
       derived_at_ff(p, a, i - (d == 0), j - (d == 1), thm, um);
       derived_at_ff(p, a, i + (d == 0), j + (d == 1), thp, up);
       const double ih = (d == 0) ? idx1 : idx2;
-      dTh[d] = ff_join(gm_slope_ff(theta, thm, th0, thp)) * ih;
+      dTh[d] = ff_join(gm_slope(theta, thm, th0, thp)) * ih;
 #pragma unroll
-      for (int m = 0; m < 4; m++) du[d][m] = ff_join(gm_slope_ff(theta, um[m], u0[m], up[m])) * ih;
+      for (int m = 0; m < 4; m++) du[d][m] = ff_join(gm_slope(theta, um[m], u0[m], up[m])) * ih;
       divu_sp += du[d][1 + d];
     }
   }
@@ -520,15 +528,21 @@ void explicit_args(const Params& p, const double* Pn, const double* PE, const do
   a.F2 = faces + (long long)NV * (p.n1 + 1) * (p.n2 + 2);
 }
 
-template <typename S>
-static cudaError_t launch_faces_s(const Params& p, const ExpArgs& a, unsigned nb, int bs, cudaStream_t st) {
+template <typename S, int RECON>
+static cudaError_t launch_faces_r(const Params& p, const ExpArgs& a, unsigned nb, int bs, cudaStream_t st) {
   switch (bs) {
-    case 64: face_flux_2d<64, S><<<nb, 64, 0, st>>>(p, a); break;
-    case 128: face_flux_2d<128, S><<<nb, 128, 0, st>>>(p, a); break;
-    case 256: face_flux_2d<256, S><<<nb, 256, 0, st>>>(p, a); break;
+    case 64: face_flux_2d<64, S, RECON><<<nb, 64, 0, st>>>(p, a); break;
+    case 128: face_flux_2d<128, S, RECON><<<nb, 128, 0, st>>>(p, a); break;
+    case 256: face_flux_2d<256, S, RECON><<<nb, 256, 0, st>>>(p, a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+template <typename S>
+static cudaError_t launch_faces_s(const Params& p, const ExpArgs& a, unsigned nb, int bs, cudaStream_t st) {
+  if (p.recon == RECON_WENO5) return launch_faces_r<S, RECON_WENO5>(p, a, nb, bs, st);
+  if (p.recon == RECON_PPM) return launch_faces_r<S, RECON_PPM>(p, a, nb, bs, st);
+  return launch_faces_r<S, RECON_MC>(p, a, nb, bs, st);
 }
 
 // bs: threads per block, 64, 128 or 256.  ffstates: face states and fluxes

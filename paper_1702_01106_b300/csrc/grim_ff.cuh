@@ -7,6 +7,7 @@
 // solver tolerances.
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace grim {
 
@@ -69,14 +70,12 @@ __device__ __forceinline__ ff& operator*=(ff& a, ff b) { a = a * b; return a; }
 __device__ __forceinline__ bool operator>(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 __device__ __forceinline__ bool operator<(ff a, ff b) { return b > a; }
 
-// The float64 forms stay visible beside the float-float overloads below.
-__device__ __forceinline__ double fabs(double a) { return ::fabs(a); }
-__device__ __forceinline__ double fmax(double a, double b) { return ::fmax(a, b); }
-__device__ __forceinline__ double fmin(double a, double b) { return ::fmin(a, b); }
-__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
-__device__ __forceinline__ float fabs(float a) { return ::fabsf(a); }
-__device__ __forceinline__ float fmax(float a, float b) { return ::fmaxf(a, b); }
-__device__ __forceinline__ float fmin(float a, float b) { return ::fminf(a, b); }
+// The float64 and float forms stay visible beside the float-float overloads
+// below.
+using ::fabs;
+using ::fmax;
+using ::fmin;
+using ::fma;
 
 __device__ __forceinline__ ff fabs(ff a) { return (a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f)) ? -a : a; }
 __device__ __forceinline__ ff fmax(ff a, ff b) { return a > b ? a : b; }
@@ -98,12 +97,25 @@ __device__ __forceinline__ ff sqr_root(ff a) {
   return ff_quick(s, r.hi * (0.5f / s));
 }
 // a^(-1/2), a > 0: the float estimate refined by one Newton step in
-// float-float, y <- y + y (1 - a y^2)/2.
+// float-float, y <- y + y (1 - (a y) y)/2 (a y first, so that y^2 cannot
+// overflow for a small a).
 __device__ __forceinline__ ff rsq(ff a) {
   const ff y(rsqrtf(a.hi), 0.f);
   const ff one(1.f, 0.f), half(0.5f, 0.f);
-  return y + (y * half) * (one - a * (y * y));
+  return y + (y * half) * (one - (a * y) * y);
 }
+
+// A power of two s with s m in [1, 2) for a float m (s = 1 for m = 0; s and
+// its inverse r kept normal floats), and a float-float value scaled by a
+// power of two.  Used where the square of a small quantity (b^2 of a weak
+// field) would leave the float range.
+__device__ __forceinline__ void pow2_scale(float m, float& s, float& r) {
+  int eb = m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xff) : 127;
+  eb = eb < 1 ? 1 : (eb > 253 ? 253 : eb);
+  s = __uint_as_float((unsigned)(254 - eb) << 23);
+  r = __uint_as_float((unsigned)eb << 23);
+}
+__device__ __forceinline__ ff scale2(ff a, float s) { return ff(a.hi * s, a.lo * s); }
 
 // Conversions by integer bit manipulation (no float64 instruction): a double
 // split into its leading 24 significant bits (hi, truncated) and the float
@@ -137,6 +149,16 @@ __device__ __forceinline__ double ff_join(ff a) { return f_widen(a.hi) + f_widen
 // Input in the working precision: float64 as is, float-float by the split.
 template <typename T> __device__ __forceinline__ T from_double(double d);
 template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }
+template <> __device__ __forceinline__ float from_double<float>(double d) { return (float)d; }
 template <> __device__ __forceinline__ ff from_double<ff>(double d) { return ff_split(d); }
+
+// Generalized minmod slope (Section 2.4.1) of vm, v0, vp in float-float, for
+// the limited slopes of the mixed solver (sign tests on the leading parts).
+__device__ __forceinline__ ff gm_slope(ff theta, ff vm, ff v0, ff vp) {
+  const ff a = v0 - vm, c = vp - v0;
+  if (!((a.hi > 0.f && c.hi > 0.f) || (a.hi < 0.f && c.hi < 0.f))) return ff(0.f, 0.f);
+  const ff m = fmin(theta * fmin(fabs(a), fabs(c)), tconst<ff>(0.5) * fabs(a + c));
+  return a.hi > 0.f ? m : -m;
+}
 
 }  // namespace grim

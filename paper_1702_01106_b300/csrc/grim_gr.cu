@@ -5,6 +5,8 @@
 // constants of the residual.  Also the post-stage floors and a residual
 // evaluation.  Used for 3-D grids and for the modified Kerr-Schild metric;
 // 2-D Minkowski grids take the specialised kernels of grim_faces.cu.
+#include <type_traits>
+
 #include "grim_gr.cuh"
 
 namespace grim {
@@ -173,6 +175,9 @@ struct GrArgs {
   double* F[3];
   const double* gc;
   const double* gf[2];
+  // float-float copies of gamma, gamma-1, sqrt(phi gamma), sqrt(psi gamma)
+  // and kappa gamma (hi, lo pairs), for the float-float face states
+  float ffc[10];
 };
 
 // Extents and offsets of the face array of direction D: along D the faces
@@ -187,6 +192,7 @@ struct FaceBox {
 __host__ __device__ inline FaceBox face_box(const Params& p, int D) {
   FaceBox b;
   const int n[3] = {p.n1, p.n2, p.n3};
+#pragma unroll
   for (int d = 0; d < 3; d++) {
     const bool act = d < p.dim;
     b.e[d] = (d == D) ? n[d] + 1 : (act ? n[d] + 2 : 1);
@@ -246,11 +252,37 @@ static double gr_kappa(const Params& p) {
 }
 
 // ---------------------------------------------------------------- faces
-// LLF flux (Section 2.4.2) on the face at the low side of zone (i,j,k) in
-// direction D, from MC or WENO5 face states of P^E.  The stencil's zone
-// indices and reflection flips are resolved once; the fields are then loaded
-// and reconstructed one at a time.
-template <int D, int RECON>
+// Physical constants in the working precision: float64 from the parameters,
+// float-float from the host-split copies; kk is kappa in float64 and kappa
+// gamma in float-float (the argument each form of the speeds takes).
+template <typename S> __device__ __forceinline__ void gr_consts(const Params& p, const GrArgs& a, RC<S>& c, S& kk) {
+  if constexpr (std::is_same<S, double>::value) {
+    c = make_rc<double>(p);
+    kk = a.kappa;
+  } else {
+    c.gam = S(a.ffc[0], a.ffc[1]);
+    c.gm1 = S(a.ffc[2], a.ffc[3]);
+    c.sphig = S(a.ffc[4], a.ffc[5]);
+    c.spsig = S(a.ffc[6], a.ffc[7]);
+    c.cond = p.cond;
+    c.visc = p.visc;
+    kk = S(a.ffc[8], a.ffc[9]);
+  }
+}
+template <typename S>
+__device__ __forceinline__ void face_speeds(const ZG<S>& z, S gtt, S gtj, S gjj, int j, const RC<S>& c, S kk, S& cmin,
+                                            S& cmax) {
+  if constexpr (std::is_same<S, double>::value) zg_speeds(z, gtt, gtj, gjj, j, c.gam, kk, cmin, cmax);
+  else zg_speeds_kg(z, gtt, gtj, gjj, j, c.gam, kk, cmin, cmax);
+}
+
+// LLF or HLLE flux (Section 2.4.2) on the face at the low side of zone
+// (i,j,k) in direction D, from MC, WENO5 or PPM face states of P^E.  The
+// stencil's zone indices and reflection flips are resolved once; the fields
+// are then loaded and reconstructed one at a time, in float64.  The face
+// states, fluxes and speeds are evaluated in S: float64, or float-float for
+// the mixed solver.
+template <int D, int RECON, typename S>
 __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int i, int j, int k, const GT& g,
                                           double* out, long long plane) {
   constexpr bool WIDE = RECON != RECON_MC;
@@ -264,7 +296,7 @@ __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int 
     fl[t] = (f[0] ? 1 : 0) | (f[1] ? 2 : 0) | (f[2] ? 4 : 0);
   }
   const long long N = p.N;
-  double L[NV], R[NV];
+  S L[NV], R[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     // u~^d and B^d change sign in a zone mirrored across a boundary of direction d
@@ -275,57 +307,78 @@ __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int 
       const double x = __ldg(a.PE + v * N + zz[t]);
       s[t] = (fl[t] & bit) ? -x : x;
     }
+    double lv, rv;
     if (RECON == RECON_WENO5) {
-      L[v] = weno5v(s[0], s[1], s[2], s[3], s[4]);
-      R[v] = weno5v(s[5], s[4], s[3], s[2], s[1]);
+      lv = weno5v(s[0], s[1], s[2], s[3], s[4]);
+      rv = weno5v(s[5], s[4], s[3], s[2], s[1]);
     } else if (RECON == RECON_PPM) {
       double lo, hi;
       ppm_zone(p.theta, s[0], s[1], s[2], s[3], s[4], lo, hi);
-      L[v] = hi;
+      lv = hi;
       ppm_zone(p.theta, s[1], s[2], s[3], s[4], s[5], lo, hi);
-      R[v] = lo;
+      rv = lo;
     } else {
-      L[v] = fma(0.5, gm_slope(p.theta, s[0], s[1], s[2]), s[1]);
-      R[v] = fma(-0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
+      lv = fma(0.5, gm_slope(p.theta, s[0], s[1], s[2]), s[1]);
+      rv = fma(-0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
     }
+    L[v] = from_double<S>(lv);
+    R[v] = from_double<S>(rv);
   }
-  Met<double> m;
+  Met<S> m;
   met_load(m, g);
-  const RC<double> c = make_rc<double>(p);
-  double FL[NV], FR[NV], UL[NV], UR[NV], cminL, cmaxL, cminR, cmaxR;
-  const double gtt = g(G_CON + sym(0, 0)), gtj = g(G_CON + sym(0, D + 1)), gjj = g(G_CON + sym(D + 1, D + 1));
+  RC<S> c;
+  S kk;
+  gr_consts(p, a, c, kk);
+  S FL[NV], FR[NV], UL[NV], UR[NV], cminL, cmaxL, cminR, cmaxR;
+  const S gtt = from_double<S>(g(G_CON + sym(0, 0))), gtj = from_double<S>(g(G_CON + sym(0, D + 1)));
+  const S gjj = from_double<S>(g(G_CON + sym(D + 1, D + 1)));
   {
-    ZG<double> z;
+    ZG<S> z;
     zg_load(z, L, m, c);
     zg_conserved(z, UL);
     zg_flux(z, D + 1, FL);
-    zg_speeds(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa, cminL, cmaxL);
+    face_speeds(z, gtt, gtj, gjj, D + 1, c, kk, cminL, cmaxL);
   }
   {
-    ZG<double> z;
+    ZG<S> z;
     zg_load(z, R, m, c);
     zg_conserved(z, UR);
     zg_flux(z, D + 1, FR);
-    zg_speeds(z, gtt, gtj, gjj, D + 1, p.gamma, a.kappa, cminR, cmaxR);
+    face_speeds(z, gtt, gtj, gjj, D + 1, c, kk, cminR, cmaxR);
   }
-  const double sg = g(G_SQRTG);
-  double Fv[NV];
-  if (p.riemann == 1) {  // HLLE (Section 2.4.2)
-    const double cR = fmax(fmax(cmaxL, cmaxR), 0.0), cL = fmax(-fmin(cminL, cminR), 0.0);
-    const double iw = 1.0 / (cL + cR);
+  const S sg = from_double<S>(g(G_SQRTG));
+  if constexpr (std::is_same<S, double>::value) {
+    double Fv[NV];
+    if (p.riemann == 1) {  // HLLE (Section 2.4.2)
+      const double cR = fmax(fmax(cmaxL, cmaxR), 0.0), cL = fmax(-fmin(cminL, cminR), 0.0);
+      const double iw = 1.0 / (cL + cR);
 #pragma unroll
-    for (int v = 0; v < NV; v++) Fv[v] = (cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) * iw;
+      for (int v = 0; v < NV; v++) Fv[v] = (cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) * iw;
+    } else {               // LLF
+      const double cm = fmax(fmax(cmaxL, -cminL), fmax(cmaxR, -cminR));
+#pragma unroll
+      for (int v = 0; v < NV; v++) Fv[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) out[v * plane] = sg * Fv[v];
+  } else if (p.riemann == 1) {
+    const S cR = fmax(fmax(cmaxL, cmaxR), tconst<S>(0.0)), cL = fmax(-fmin(cminL, cminR), tconst<S>(0.0));
+    const S iw = sg * nr_rcp(cL + cR);
+#pragma unroll
+    for (int v = 0; v < NV; v++) out[v * plane] = as_double((cR * FL[v] + cL * FR[v] - cR * cL * (UR[v] - UL[v])) * iw);
   } else {               // LLF
-    const double cm = fmax(fmax(cmaxL, -cminL), fmax(cmaxR, -cminR));
+    const S cm = fmax(fmax(cmaxL, -cminL), fmax(cmaxR, -cminR));
+    const S h = tconst<S>(0.5) * sg;
 #pragma unroll
-    for (int v = 0; v < NV; v++) Fv[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * cm * (UR[v] - UL[v]);
+    for (int v = 0; v < NV; v++) out[v * plane] = as_double(h * ((FL[v] + FR[v]) - cm * (UR[v] - UL[v])));
   }
-#pragma unroll
-  for (int v = 0; v < NV; v++) out[v * plane] = sg * Fv[v];
 }
 
-template <int D>
-__global__ void __launch_bounds__(128) face_flux_gr(const __grid_constant__ Params p,
+// One kernel per direction and reconstruction, so that each holds only its
+// own registers; the float-float form is held to three blocks of 128 threads
+// per SM (168 registers), for the latency of its dependent float chains.
+template <int D, typename S, int RECON>
+__global__ void __launch_bounds__(128, std::is_same<S, ff>::value ? 3 : 1) face_flux_gr(const __grid_constant__ Params p,
                                                     const __grid_constant__ GrArgs a) {
   const FaceBox fb = face_box(p, D);
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -345,9 +398,7 @@ __global__ void __launch_bounds__(128) face_flux_gr(const __grid_constant__ Para
     for (int v = 0; v < NV; v++) out[v * fb.size] = 0.0;
     return;
   }
-  if (p.recon == RECON_WENO5) face_body<D, RECON_WENO5>(p, a, i, j, k, g, out, fb.size);
-  else if (p.recon == RECON_PPM) face_body<D, RECON_PPM>(p, a, i, j, k, g, out, fb.size);
-  else face_body<D, RECON_MC>(p, a, i, j, k, g, out, fb.size);
+  face_body<D, RECON, S>(p, a, i, j, k, g, out, fb.size);
 }
 
 // ---------------------------------------------------------------- zone constants
@@ -357,6 +408,8 @@ __device__ void gr_derived(const Params& p, const GrArgs& a, int i, int j, int k
                            double ucov[4], double sgu[3]) {
   double P[NV];
   gr_prim(p, a.PE, i, j, k, P);
+#pragma unroll
+  for (int v = 5; v < NV; v++) P[v] = 0.0;  // B, q~, dP~ do not enter
   const GT g = centre_geo(p, a.gc, i, j);
   Met<double> m;
   met_load(m, g);
@@ -642,6 +695,11 @@ static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a
     if (d < p.dim) f += (long long)NV * face_box(p, d).size;
   }
   a.kappa = gr_kappa(p);
+  const double cv[5] = {p.gamma, p.gamma - 1.0, sqrt(p.phi * p.gamma), sqrt(p.psi * p.gamma), a.kappa * p.gamma};
+  for (int k = 0; k < 5; k++) {
+    a.ffc[2 * k] = (float)cv[k];
+    a.ffc[2 * k + 1] = (float)(cv[k] - (double)(float)cv[k]);
+  }
 }
 
 cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double h, const double x0[3],
@@ -663,20 +721,33 @@ cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo, double* faces, cudaStream_t st) {
-  GrArgs a{};
-  gr_args(p, geo, faces, a);
-  a.PE = PE;
+template <typename S, int RECON>
+static cudaError_t launch_gr_faces_r(const Params& p, const GrArgs& a, cudaStream_t st) {
   for (int d = 0; d < p.dim; d++) {
     const long long n = face_box(p, d).size;
     const unsigned nb = (unsigned)((n + 127) / 128);
-    if (d == 0) face_flux_gr<0><<<nb, 128, 0, st>>>(p, a);
-    else if (d == 1) face_flux_gr<1><<<nb, 128, 0, st>>>(p, a);
-    else face_flux_gr<2><<<nb, 128, 0, st>>>(p, a);
+    if (d == 0) face_flux_gr<0, S, RECON><<<nb, 128, 0, st>>>(p, a);
+    else if (d == 1) face_flux_gr<1, S, RECON><<<nb, 128, 0, st>>>(p, a);
+    else face_flux_gr<2, S, RECON><<<nb, 128, 0, st>>>(p, a);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+template <typename S>
+static cudaError_t launch_gr_faces_s(const Params& p, const GrArgs& a, cudaStream_t st) {
+  if (p.recon == RECON_WENO5) return launch_gr_faces_r<S, RECON_WENO5>(p, a, st);
+  if (p.recon == RECON_PPM) return launch_gr_faces_r<S, RECON_PPM>(p, a, st);
+  return launch_gr_faces_r<S, RECON_MC>(p, a, st);
+}
+
+// ffstates: face states and fluxes in float-float (the mixed solver).
+cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo, double* faces, int ffstates,
+                            cudaStream_t st) {
+  GrArgs a{};
+  gr_args(p, geo, faces, a);
+  a.PE = PE;
+  return ffstates ? launch_gr_faces_s<ff>(p, a, st) : launch_gr_faces_s<double>(p, a, st);
 }
 
 cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,

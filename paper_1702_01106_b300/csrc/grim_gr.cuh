@@ -8,12 +8,14 @@
 // u~^j)^(1/2) (equal to u^i in Minkowski space).
 #pragma once
 #include "grim_zone.cuh"
+#include "grim_ff.cuh"
 
 namespace grim {
 
 // Packed symmetric 4x4 index: (00,01,02,03,11,12,13,22,23,33).
 __host__ __device__ constexpr int sym(int m, int n) {
-  return m <= n ? (m == 0 ? n : m == 1 ? 3 + n : m == 2 ? 5 + n : 9) : sym(n, m);
+  const int a = m < n ? m : n, b = m < n ? n : m;
+  return a == 0 ? b : a == 1 ? 3 + b : a == 2 ? 5 + b : 9;
 }
 
 // Geometry-table planes.  Zone centres: [NGC][(n2+2)(n1+2)] (one ring of
@@ -38,10 +40,10 @@ template <typename T> struct Met {
 };
 template <typename T, class GA> __device__ __forceinline__ void met_load(Met<T>& m, const GA& g) {
 #pragma unroll
-  for (int a = 0; a < 10; a++) m.gcov[a] = T(g(G_COV + a));
-  m.alpha = T(g(G_ALPHA));
+  for (int a = 0; a < 10; a++) m.gcov[a] = from_double<T>(g(G_COV + a));
+  m.alpha = from_double<T>(g(G_ALPHA));
 #pragma unroll
-  for (int i = 0; i < 3; i++) m.gti[i] = T(g(G_CON + sym(0, i + 1)));
+  for (int i = 0; i < 3; i++) m.gti[i] = from_double<T>(g(G_CON + sym(0, i + 1)));
 }
 
 // Intermediates of a primitive state in a general metric.
@@ -97,6 +99,29 @@ __device__ __forceinline__ void zg_load(ZG<T>& z, const T* P, const Met<T>& m, c
 #pragma unroll
   for (int i = 0; i < 3; i++) z.bcon[i + 1] = (z.B[i] + bt * z.ucon[i + 1]) * iut;
   lower(m, z.bcon, z.bcov);
+  if constexpr (std::is_same<T, ff>::value) {
+    // b^2 of a weak field leaves the float range: b^2 and bhat from b scaled
+    // by a power of two
+    float mx = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; a++) mx = fmaxf(mx, fmaxf(fabsf(z.bcon[a].hi), fabsf(z.bcov[a].hi)));
+    float s, r;
+    pow2_scale(mx, s, r);
+    ff bc[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; a++) { bc[a] = scale2(z.bcon[a], s); bv[a] = scale2(z.bcov[a], s); }
+    const ff q = bc[0] * bv[0] + bc[1] * bv[1] + bc[2] * bv[2] + bc[3] * bv[3];
+    z.bsq = scale2(scale2(q, r), r);
+    if (q.hi > 0.f) {
+      const ff ib = rsq(q);
+#pragma unroll
+      for (int a = 0; a < 4; a++) { z.bhcon[a] = bc[a] * ib; z.bhcov[a] = bv[a] * ib; }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; a++) { z.bhcon[a] = T(0); z.bhcov[a] = T(0); }
+    }
+    return;
+  }
   z.bsq = z.bcon[0] * z.bcov[0] + z.bcon[1] * z.bcov[1] + z.bcon[2] * z.bcov[2] + z.bcon[3] * z.bcov[3];
   if (z.bsq > T(0)) {
     const T ib = rsq(z.bsq);
@@ -113,10 +138,10 @@ __device__ __forceinline__ void zg_load(ZG<T>& z, const T* P, const Met<T>& m, c
 // u^m u_nu)/3), w = rho + u + P_g + b^2, p_t = P_g + b^2/2.
 template <typename T> __device__ __forceinline__ void zg_stress_row(const ZG<T>& z, int m, T out[4]) {
   const T q = z.qt * z.qs, dp = z.dpt * z.ds;
-  const T third = dp * T(1.0 / 3.0);
+  const T third = dp * tconst<T>(1.0 / 3.0);
   const T um = z.ucon[m], bm = z.bcon[m], bhm = z.bhcon[m];
   const T A = (z.w0 + z.bsq + third) * um;
-  const T pt = z.pg + T(0.5) * z.bsq + third;
+  const T pt = z.pg + tconst<T>(0.5) * z.bsq + third;
 #pragma unroll
   for (int n = 0; n < 4; n++) {
     T v = A * z.ucov[n] - bm * z.bcov[n] + q * (bhm * z.ucov[n] + um * z.bhcov[n]) - dp * bhm * z.bhcov[n];
@@ -167,6 +192,27 @@ __device__ __forceinline__ void zg_speeds(const ZG<double>& z, double gtt, doubl
   const double sq = sqrt(disc);
   const double i2a = 0.5 / A;
   const double c1 = (-B + sq) * i2a, c2 = (-B - sq) * i2a;
+  cmin = fmin(c1, c2);
+  cmax = fmax(c1, c2);
+}
+// The same in float-float (the mixed solver's face states), division-free;
+// kg = kappa gamma.
+template <typename T>
+__device__ __forceinline__ void zg_speeds_kg(const ZG<T>& z, T gtt, T gtj, T gjj, int j, T gam, T kg, T& cmin,
+                                             T& cmax) {
+  const T den = z.rho + gam * z.u;
+  const T cs2t = kg * z.pg * nr_rcp(den);
+  const T vA2 = z.bsq * nr_rcp(den + z.bsq);
+  const T v2 = cs2t + vA2 - cs2t * vA2;
+  const T ut = z.ucon[0], uj = z.ucon[j];
+  const T w = tconst<T>(1.0) - v2;
+  const T A = w * ut * ut - v2 * gtt;
+  const T B = tconst<T>(-2.0) * (w * ut * uj - v2 * gtj);
+  const T C = w * uj * uj - v2 * gjj;
+  const T disc = fmax(B * B - tconst<T>(4.0) * A * C, tconst<T>(0.0));
+  const T sq = sqr_root(disc);
+  const T i2a = tconst<T>(0.5) * nr_rcp(A);
+  const T c1 = (sq - B) * i2a, c2 = -((sq + B) * i2a);
   cmin = fmin(c1, c2);
   cmax = fmax(c1, c2);
 }

@@ -3,6 +3,7 @@
 // (thermodynamic: rho, u; kinematic: u^i; magnetic: B^i with u^i).
 #pragma once
 #include "grim_dev.cuh"
+#include "grim_ff.cuh"
 
 namespace grim {
 
@@ -143,6 +144,25 @@ template <typename T> __device__ __forceinline__ void z_mag(Z<T>& z) {
   z.bt = z.B[0] * z.v[0] + z.B[1] * z.v[1] + z.B[2] * z.v[2];
 #pragma unroll
   for (int i = 0; i < 3; i++) z.bc[i] = (z.B[i] + z.bt * z.v[i]) * z.iut;
+  if constexpr (std::is_same<T, ff>::value) {
+    // b^2 of a weak field leaves the float range: b^2 and bhat from b scaled
+    // by a power of two
+    const float m = fmaxf(fmaxf(fabsf(z.bt.hi), fabsf(z.bc[0].hi)), fmaxf(fabsf(z.bc[1].hi), fabsf(z.bc[2].hi)));
+    float s, r;
+    pow2_scale(m, s, r);
+    const ff t = scale2(z.bt, s), c0 = scale2(z.bc[0], s), c1 = scale2(z.bc[1], s), c2 = scale2(z.bc[2], s);
+    const ff q = c0 * c0 + c1 * c1 + c2 * c2 - t * t;
+    z.bsq = scale2(scale2(q, r), r);
+    if (q.hi > 0.f) {
+      const ff ib = rsq(q);
+      z.bht = t * ib;
+      z.bh[0] = c0 * ib; z.bh[1] = c1 * ib; z.bh[2] = c2 * ib;
+    } else {
+      z.bht = T(0);
+      z.bh[0] = z.bh[1] = z.bh[2] = T(0);
+    }
+    return;
+  }
   z.bsq = z.bc[0] * z.bc[0] + z.bc[1] * z.bc[1] + z.bc[2] * z.bc[2] - z.bt * z.bt;
   if (z.bsq > T(0)) {
     const T ib = rsq(z.bsq);
