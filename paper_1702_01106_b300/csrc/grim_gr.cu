@@ -173,6 +173,7 @@ struct GrArgs {
   double* K;
   double* P0;
   double* F[3];
+  double* Dv;  // [ND][ghost-ring grid]: derived P^E quantities of every centre
   const double* gc;
   const double* gf[2];
   // float-float copies of gamma, gamma-1, sqrt(phi gamma), sqrt(psi gamma)
@@ -404,8 +405,8 @@ __global__ void __launch_bounds__(128, std::is_same<S, ff>::value ? 3 : 1) face_
 // ---------------------------------------------------------------- zone constants
 // Theta, u_mu and sqrt(-g) u^d of the P^E state of zone (i,j,k) (ghosts by the
 // boundary rules, geometry of the ghost centre itself).
-__device__ void gr_derived(const Params& p, const GrArgs& a, int i, int j, int k, const RC<double>& c, double& th,
-                           double ucov[4], double sgu[3]) {
+__device__ __forceinline__ void gr_derived(const Params& p, const GrArgs& a, int i, int j, int k,
+                                           const RC<double>& c, double& th, double ucov[4], double sgu[3]) {
   double P[NV];
   gr_prim(p, a.PE, i, j, k, P);
 #pragma unroll
@@ -421,6 +422,56 @@ __device__ void gr_derived(const Params& p, const GrArgs& a, int i, int j, int k
   for (int q = 0; q < 4; q++) ucov[q] = z.ucov[q];
 #pragma unroll
   for (int d = 0; d < 3; d++) sgu[d] = sg * z.ucon[d + 1];
+}
+
+// The derived quantities of every zone and ghost centre (one ring along each
+// active direction), [ND][e1 e2 e3] with e1 = n1+2, e2 = n2+2 or 1, e3 = n3+2
+// or 1: computed once a stage here, read by the limited slopes of up to seven
+// zones.
+constexpr int ND = 8;  // Theta, u_mu (4), sqrt(-g) u^d (3)
+struct GhostBox {
+  int e1, e2, e3, o2, o3;
+  long long size;
+  __device__ __host__ long long at(int i, int j, int k) const {
+    return ((long long)(k + o3) * e2 + (j + o2)) * e1 + (i + 1);
+  }
+};
+__host__ __device__ inline GhostBox ghost_box(const Params& p) {
+  GhostBox b;
+  b.o2 = p.dim >= 2;
+  b.o3 = p.dim >= 3;
+  b.e1 = p.n1 + 2;
+  b.e2 = b.o2 ? p.n2 + 2 : 1;
+  b.e3 = b.o3 ? p.n3 + 2 : 1;
+  b.size = (long long)b.e1 * b.e2 * b.e3;
+  return b;
+}
+
+__global__ void __launch_bounds__(128) derived_gr(const __grid_constant__ Params p, const __grid_constant__ GrArgs a) {
+  const GhostBox gb = ghost_box(p);
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= gb.size) return;
+  const int i = (int)(q % gb.e1) - 1;
+  const int j = (int)((q / gb.e1) % gb.e2) - gb.o2;
+  const int k = (int)(q / ((long long)gb.e1 * gb.e2)) - gb.o3;
+  const RC<double> c = make_rc<double>(p);
+  double th, u[4], s[3];
+  gr_derived(p, a, i, j, k, c, th, u, s);
+  double* D = a.Dv + q;
+  D[0] = th;
+#pragma unroll
+  for (int m = 0; m < 4; m++) D[(1 + m) * gb.size] = u[m];
+#pragma unroll
+  for (int d = 0; d < 3; d++) D[(5 + d) * gb.size] = s[d];
+}
+__device__ __forceinline__ void derived_load(const GrArgs& a, const GhostBox& gb, int i, int j, int k, double& th,
+                                             double u[4], double s[3]) {
+  const double* D = a.Dv + gb.at(i, j, k);
+  th = __ldg(D);
+#pragma unroll
+  for (int m = 0; m < 4; m++) u[m] = __ldg(D + (1 + m) * gb.size);
+#pragma unroll
+  for (int d = 0; d < 3; d++) s[d] = __ldg(D + (5 + d) * gb.size);
 }
 
 __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Params p,
@@ -516,14 +567,15 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
 #pragma unroll
     for (int q = 0; q < 4; q++) du[d][q] = 0.0;
   {
+    const GhostBox gb = ghost_box(p);
     double th0, u0[4], s0[3];
-    gr_derived(p, a, i, j, k, c, th0, u0, s0);
+    derived_load(a, gb, i, j, k, th0, u0, s0);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       if (d >= p.dim) continue;
       double thm, thp, um[4], up[4], sm[3], sp[3];
-      gr_derived(p, a, i - (d == 0), j - (d == 1), k - (d == 2), c, thm, um, sm);
-      gr_derived(p, a, i + (d == 0), j + (d == 1), k + (d == 2), c, thp, up, sp);
+      derived_load(a, gb, i - (d == 0), j - (d == 1), k - (d == 2), thm, um, sm);
+      derived_load(a, gb, i + (d == 0), j + (d == 1), k + (d == 2), thp, up, sp);
       dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
 #pragma unroll
       for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
@@ -679,10 +731,12 @@ long long gr_geometry_doubles(const Params& p) {
   return (long long)NGC * (p.n1 + 2) * (p.n2 + 2) + (long long)NGF * (p.n1 + 1) * (p.n2 + 2) +
          (long long)NGF * (p.n1 + 2) * (p.n2 + 1);
 }
+// The explicit-stage scratch: face fluxes of every active direction, then
+// the derived quantities of the ghost-ring grid.
 long long gr_face_doubles(const Params& p) {
   long long s = 0;
   for (int d = 0; d < p.dim; d++) s += (long long)NV * face_box(p, d).size;
-  return s;
+  return s + (long long)ND * ghost_box(p).size;
 }
 
 static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a) {
@@ -694,6 +748,7 @@ static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a
     a.F[d] = f;
     if (d < p.dim) f += (long long)NV * face_box(p, d).size;
   }
+  a.Dv = f;
   a.kappa = gr_kappa(p);
   const double cv[5] = {p.gamma, p.gamma - 1.0, sqrt(p.phi * p.gamma), sqrt(p.psi * p.gamma), a.kappa * p.gamma};
   for (int k = 0; k < 5; k++) {
@@ -755,6 +810,9 @@ cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double
   GrArgs a{};
   gr_args(p, geo, faces, a);
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.K = K; a.P0 = P0;
+  derived_gr<<<(unsigned)((ghost_box(p).size + 127) / 128), 128, 0, st>>>(p, a);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   zone_const_gr<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, a);
   return cudaGetLastError();
 }
