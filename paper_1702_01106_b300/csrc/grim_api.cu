@@ -246,7 +246,7 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
       KernelMark m(ctx, GRIM_K_FACES, ctx->p.dim);
       GRIM_CUDA(grim::launch_gr_faces(ctx->p, PE, ctx->geo, ctx->faces, ctx->precision == GRIM_MIXED, ctx->cur), "face kernel");
     }
-    KernelMark m(ctx, GRIM_K_ZONECONST, 2);
+    KernelMark m(ctx, GRIM_K_ZONECONST, 3);
     GRIM_CUDA(grim::launch_gr_zone_const(ctx->p, Pn, PE, guess, dts, ctx->geo, ctx->faces, ctx->K, Pout, ctx->cur),
               "zone-constant kernel");
     return GRIM_OK;

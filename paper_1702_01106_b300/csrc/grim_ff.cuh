@@ -117,22 +117,28 @@ __device__ __forceinline__ void pow2_scale(float m, float& s, float& r) {
 }
 __device__ __forceinline__ ff scale2(ff a, float s) { return ff(a.hi * s, a.lo * s); }
 
-// Conversions by integer bit manipulation (no float64 instruction): a double
-// split into its leading 24 significant bits (hi, truncated) and the float
-// nearest to the remaining 29 (lo); a float widened exactly to double.
-// Values outside the normal float range take the float64 route.
+// Conversions by bit manipulation and float arithmetic (no float64 and no
+// integer-to-float conversion instruction, which share the narrow float64
+// pipe): a double split into its leading 24 significant bits (hi, truncated)
+// and the float nearest to the remaining 29 (lo); a float widened exactly
+// to double.  Values outside the normal float range take the float64 route.
 __device__ __forceinline__ ff ff_split(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const int e = (int)((b >> 52) & 0x7ff);
   if (e == 0) return ff(0.f, 0.f);
-  // fast path for 2^-74 <= |d| < 2^100: the scale of lo stays a normal float
+  // fast path for 2^-74 <= |d| < 2^100: every float below stays normal
   if (e < 1075 - 126 || e > 1023 + 100) return ff(d);
   const unsigned sign = (unsigned)(b >> 63);
   const unsigned long long m = b & 0xfffffffffffffull;
   const float hi = __uint_as_float((sign << 31) | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
-  // low 29 bits: an integer below 2^29 times 2^(e - 1075)
-  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);
-  float lo = __uint2float_rn((unsigned)(m & 0x1fffffffull)) * scale;
+  // the low 29 bits x = 64 xh + xl are worth x 2^(e - 1075): each part is
+  // made exact as (2^23 + part) 2^k - 2^23 2^k from its bits, and one float
+  // addition rounds their sum
+  const unsigned x = (unsigned)(m & 0x1fffffffull);
+  const unsigned eh = (unsigned)(e - 1069 + 150) << 23, el = (unsigned)(e - 1075 + 150) << 23;
+  const float ph = __uint_as_float(eh | (x >> 6)) - __uint_as_float(eh);
+  const float pl = __uint_as_float(el | (x & 63u)) - __uint_as_float(el);
+  const float lo = ph + pl;
   return ff(hi, sign ? -lo : lo);
 }
 __device__ __forceinline__ double f_widen(float f) {

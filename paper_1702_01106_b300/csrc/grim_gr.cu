@@ -173,7 +173,8 @@ struct GrArgs {
   double* K;
   double* P0;
   double* F[3];
-  double* Dv;  // [ND][ghost-ring grid]: derived P^E quantities of every centre
+  double* Dv;   // [ND][ghost-ring grid]: derived P^E quantities of every centre
+  double* Src;  // [NSRC][N]: sources at P^E of every zone
   const double* gc;
   const double* gf[2];
   // float-float copies of gamma, gamma-1, sqrt(phi gamma), sqrt(psi gamma)
@@ -474,6 +475,126 @@ __device__ __forceinline__ void derived_load(const GrArgs& a, const GhostBox& gb
   for (int d = 0; d < 3; d++) s[d] = __ldg(D + (5 + d) * gb.size);
 }
 
+// Sources at P^E of every zone: the geometric source sqrt(-g) T^k_l
+// Gamma^l_{nu k} (rows 1..4), the closure coefficients of q~ and dP~ (with
+// the limited slopes of Theta, u_mu and sqrt(-g) u^d from the derived
+// quantities) and the spatial part of nabla_mu u^mu; NSRC doubles a zone.
+constexpr int NSRC = 17;  // Sg (4), Aq, Bq, Cq (4), Ad, Dd (4), Ed, divu_sp
+__global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params p, const __grid_constant__ GrArgs a) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const int i = (int)(z % p.n1), j = (int)((z / p.n1) % p.n2), k = (int)(z / ((long long)p.n1 * p.n2));
+  const GT g = centre_geo(p, a.gc, i, j);
+  const double sg = g(G_SQRTG), tau = g(G_TAUR);
+  double PEz[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) PEz[v] = __ldg(a.PE + v * N + z);
+  // --- limited slopes at P^E of Theta, u_mu and sqrt(-g) u^d
+  double dTh[3] = {0.0, 0.0, 0.0}, du[3][4], divu_sp = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; d++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) du[d][q] = 0.0;
+  {
+    const GhostBox gb = ghost_box(p);
+    double th0, u0[4], s0[3];
+    derived_load(a, gb, i, j, k, th0, u0, s0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      if (d >= p.dim) continue;
+      double thm, thp, um[4], up[4], sm[3], sp[3];
+      derived_load(a, gb, i - (d == 0), j - (d == 1), k - (d == 2), thm, um, sm);
+      derived_load(a, gb, i + (d == 0), j + (d == 1), k + (d == 2), thp, up, sp);
+      dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
+#pragma unroll
+      for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
+      divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
+    }
+    divu_sp /= sg;
+  }
+  // --- sources at P^E
+  const RC<double> c = make_rc<double>(p);
+  Met<double> m;
+  met_load(m, g);
+  ZG<double> ze;
+  zg_load(ze, PEz, m, c);
+  // --- geometric source at P^E: sqrt(-g) T^k_l Gamma^l_{nu k} (rows 1..4)
+  double Sg[4] = {0.0, 0.0, 0.0, 0.0};
+  {
+    double T[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) zg_stress_row(ze, r, T[r]);
+#pragma unroll
+    for (int n = 0; n < 4; n++) {
+      double s = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++)
+#pragma unroll
+        for (int l = 0; l < 4; l++) s += T[kk][l] * g(G_GAM + 10 * l + sym(n, kk));
+      Sg[n] = sg * s;
+    }
+  }
+  const double cs2E = p.gamma * ze.pg / (ze.rho + p.gamma * ze.u);
+  const double* bh = ze.bhcon;
+  // sum over nu, l of Gamma^l_{nu mu} u^nu u_l at P^E, for each mu
+  double Gu[4];
+  #pragma unroll
+  for (int mu = 0; mu < 4; mu++) {
+    double s = 0.0;
+    #pragma unroll
+    for (int l = 0; l < 4; l++)
+      for (int nu = 0; nu < 4; nu++) s += g(G_GAM + 10 * l + sym(nu, mu)) * ze.ucon[nu] * ze.ucov[l];
+    Gu[mu] = s;
+  }
+  // heat flux: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
+  double Aq = 0.0, Bq = 0.0, Cq[4] = {0.0, 0.0, 0.0, 0.0};
+  if (p.cond) {
+    const double chi = p.phi * cs2E * tau;
+    const double pre = -sqrt(tau * ze.rho * chi) / ze.theta;
+    double acc = 0.0;
+    #pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      double a_sp = -Gu[mu];
+      #pragma unroll
+      for (int d = 0; d < 3; d++) a_sp += ze.ucon[d + 1] * du[d][mu];
+      acc += bh[mu] * a_sp;
+    }
+    Aq = pre * (bh[1] * dTh[0] + bh[2] * dTh[1] + bh[3] * dTh[2] + ze.theta * acc);
+    Bq = pre * bh[0];
+    #pragma unroll
+    for (int mu = 0; mu < 4; mu++) Cq[mu] = pre * ze.theta * bh[mu] * ze.ucon[0];
+  }
+  // anisotropy: dP~_0 = Ad + Dd^nu (u_nu - u_nu,n)/dt_s + Ed (u^t - u^t_n)/dt_s
+  double Ad = 0.0, Dd[4] = {0.0, 0.0, 0.0, 0.0}, Ed = 0.0;
+  if (p.visc) {
+    const double nu = p.psi * cs2E * tau;
+    const double pre = 3.0 * sqrt(tau * ze.rho * nu / ze.theta);
+    double sp = 0.0;
+    #pragma unroll
+    for (int mu = 0; mu < 4; mu++)
+      #pragma unroll
+      for (int nn = 0; nn < 4; nn++) {
+        double nab = 0.0;
+        if (mu >= 1) nab = du[mu - 1][nn];
+        #pragma unroll
+        for (int l = 0; l < 4; l++) nab -= g(G_GAM + 10 * l + sym(mu, nn)) * ze.ucov[l];
+        sp += bh[mu] * bh[nn] * nab;
+      }
+    Ad = pre * (sp - divu_sp * (1.0 / 3.0));
+    #pragma unroll
+    for (int nn = 0; nn < 4; nn++) Dd[nn] = pre * bh[0] * bh[nn];
+    Ed = -pre * (1.0 / 3.0);
+  }
+  double* Sz = a.Src + z;
+  const double x[NSRC] = {Sg[0], Sg[1], Sg[2], Sg[3], Aq, Bq, Cq[0], Cq[1], Cq[2], Cq[3],
+                          Ad, Dd[0], Dd[1], Dd[2], Dd[3], Ed, divu_sp};
+#pragma unroll
+  for (int q = 0; q < NSRC; q++) Sz[q * N] = x[q];
+}
+
+// The stage constants of every zone (float64): flux divergence with flux-CT,
+// U(P_n), the row scales, and the sources from sources_gr.
 __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Params p,
                                                      const __grid_constant__ GrArgs a) {
   const long long N = p.N;
@@ -528,7 +649,7 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
       divF[5 + B] += (0.5 * (E[1][0] + E[1][1]) - 0.5 * (E[0][0] + E[0][1])) * p.idx[A];
       divF[5 + A] += (-0.5 * (E[0][1] + E[1][1]) + 0.5 * (E[0][0] + E[1][0])) * p.idx[B];
     }
-  // --- states at P^E and P_n, geometry of the zone
+  // --- state at P_n and the conserved variables U(P_n) (float64)
   const RC<double> c = make_rc<double>(p);
   const GT g = centre_geo(p, a.gc, i, j);
   Met<double> m;
@@ -537,51 +658,22 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
   double PEz[NV], Pnz[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) { PEz[v] = __ldg(a.PE + v * N + z); Pnz[v] = __ldg(a.Pn + v * N + z); }
-  ZG<double> ze, zn;
-  zg_load(ze, PEz, m, c);
+  ZG<double> zn;
   zg_load(zn, Pnz, m, c);
   double Un[NV];
   zg_conserved(zn, Un);
 #pragma unroll
   for (int v = 0; v < NV; v++) Un[v] *= sg;
-  // --- geometric source at P^E: sqrt(-g) T^k_l Gamma^l_{nu k} (rows 1..4)
-  double Sg[4] = {0.0, 0.0, 0.0, 0.0};
+  // --- sources at P^E (geometric source, closure coefficients)
+  double Sg[4], Aq, Bq, Cq[4], Ad, Dd[4], Ed, divu_sp;
   {
-    double T[4][4];
+    const double* Sz = a.Src + z;
+    double x[NSRC];
 #pragma unroll
-    for (int r = 0; r < 4; r++) zg_stress_row(ze, r, T[r]);
+    for (int q = 0; q < NSRC; q++) x[q] = __ldg(Sz + q * N);
 #pragma unroll
-    for (int n = 0; n < 4; n++) {
-      double s = 0.0;
-#pragma unroll
-      for (int kk = 0; kk < 4; kk++)
-#pragma unroll
-        for (int l = 0; l < 4; l++) s += T[kk][l] * g(G_GAM + 10 * l + sym(n, kk));
-      Sg[n] = sg * s;
-    }
-  }
-  // --- limited slopes at P^E of Theta, u_mu and sqrt(-g) u^d
-  double dTh[3] = {0.0, 0.0, 0.0}, du[3][4], divu_sp = 0.0;
-#pragma unroll
-  for (int d = 0; d < 3; d++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) du[d][q] = 0.0;
-  {
-    const GhostBox gb = ghost_box(p);
-    double th0, u0[4], s0[3];
-    derived_load(a, gb, i, j, k, th0, u0, s0);
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-      if (d >= p.dim) continue;
-      double thm, thp, um[4], up[4], sm[3], sp[3];
-      derived_load(a, gb, i - (d == 0), j - (d == 1), k - (d == 2), thm, um, sm);
-      derived_load(a, gb, i + (d == 0), j + (d == 1), k + (d == 2), thp, up, sp);
-      dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
-#pragma unroll
-      for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
-      divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
-    }
-    divu_sp /= sg;
+    for (int q = 0; q < 4; q++) { Sg[q] = x[q]; Cq[q] = x[6 + q]; Dd[q] = x[11 + q]; }
+    Aq = x[4]; Bq = x[5]; Ad = x[10]; Ed = x[15]; divu_sp = x[16];
   }
   // --- stage constants (row scale folded in; sqrt(-g) folded into kU)
   const double dts = a.dts, idts = 1.0 / dts, it = 1.0 / tau;
@@ -591,40 +683,10 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
   for (int v = 0; v < NV; v++) {
     sr[v] = 1.0 / (fabs(Un[v]) + fabs(Un[0]));
     Kz[(K_U + v) * N] = sr[v] * sg;
-    const double S = (v >= 1 && v <= 4) ? Sg[v - 1] : 0.0;
-    Kz[(K_C + v) * N] = sr[v] * (dts * (divF[v] - S) - Un[v]);
+    const double src = (v >= 1 && v <= 4) ? Sg[v - 1] : 0.0;
+    Kz[(K_C + v) * N] = sr[v] * (dts * (divF[v] - src) - Un[v]);
   }
-  const double cs2E = p.gamma * ze.pg / (ze.rho + p.gamma * ze.u);
-  const double* bh = ze.bhcon;
-  // sum over nu, l of Gamma^l_{nu mu} u^nu u_l at P^E, for each mu
-  double Gu[4];
-  #pragma unroll
-  for (int mu = 0; mu < 4; mu++) {
-    double s = 0.0;
-    #pragma unroll
-    for (int l = 0; l < 4; l++)
-      for (int nu = 0; nu < 4; nu++) s += g(G_GAM + 10 * l + sym(nu, mu)) * ze.ucon[nu] * ze.ucov[l];
-    Gu[mu] = s;
-  }
-  const double hoq = p.ho ? 0.5 * ze.qt : 0.0, hod = p.ho ? 0.5 * ze.dpt : 0.0;
-  // heat flux: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
-  double Aq = 0.0, Bq = 0.0, Cq[4] = {0.0, 0.0, 0.0, 0.0};
-  if (p.cond) {
-    const double chi = p.phi * cs2E * tau;
-    const double pre = -sqrt(tau * ze.rho * chi) / ze.theta;
-    double acc = 0.0;
-    #pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-      double a_sp = -Gu[mu];
-      #pragma unroll
-      for (int d = 0; d < 3; d++) a_sp += ze.ucon[d + 1] * du[d][mu];
-      acc += bh[mu] * a_sp;
-    }
-    Aq = pre * (bh[1] * dTh[0] + bh[2] * dTh[1] + bh[3] * dTh[2] + ze.theta * acc);
-    Bq = pre * bh[0];
-    #pragma unroll
-    for (int mu = 0; mu < 4; mu++) Cq[mu] = pre * ze.theta * bh[mu] * ze.ucon[0];
-  }
+  const double hoq = p.ho ? 0.5 * PEz[8] : 0.0, hod = p.ho ? 0.5 * PEz[9] : 0.0;
   {
     const double s8 = sr[8] * dts;
     double cst = -Un[8] * idts + divF[8];
@@ -639,27 +701,6 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
     #pragma unroll
     for (int mu = 0; mu < 4; mu++) Kz[(K_Q + 2 + mu) * N] = -sg * s8 * Cq[mu] * idts * it;
     Kz[(K_Q + 6) * N] = -sg * s8 * hoq * idts;
-  }
-  // anisotropy: dP~_0 = Ad + Dd^nu (u_nu - u_nu,n)/dt_s + Ed (u^t - u^t_n)/dt_s
-  double Ad = 0.0, Dd[4] = {0.0, 0.0, 0.0, 0.0}, Ed = 0.0;
-  if (p.visc) {
-    const double nu = p.psi * cs2E * tau;
-    const double pre = 3.0 * sqrt(tau * ze.rho * nu / ze.theta);
-    double sp = 0.0;
-    #pragma unroll
-    for (int mu = 0; mu < 4; mu++)
-      #pragma unroll
-      for (int nn = 0; nn < 4; nn++) {
-        double nab = 0.0;
-        if (mu >= 1) nab = du[mu - 1][nn];
-        #pragma unroll
-        for (int l = 0; l < 4; l++) nab -= g(G_GAM + 10 * l + sym(mu, nn)) * ze.ucov[l];
-        sp += bh[mu] * bh[nn] * nab;
-      }
-    Ad = pre * (sp - divu_sp * (1.0 / 3.0));
-    #pragma unroll
-    for (int nn = 0; nn < 4; nn++) Dd[nn] = pre * bh[0] * bh[nn];
-    Ed = -pre * (1.0 / 3.0);
   }
   {
     const double s9 = sr[9] * dts;
@@ -731,12 +772,12 @@ long long gr_geometry_doubles(const Params& p) {
   return (long long)NGC * (p.n1 + 2) * (p.n2 + 2) + (long long)NGF * (p.n1 + 1) * (p.n2 + 2) +
          (long long)NGF * (p.n1 + 2) * (p.n2 + 1);
 }
-// The explicit-stage scratch: face fluxes of every active direction, then
-// the derived quantities of the ghost-ring grid.
+// The explicit-stage scratch: face fluxes of every active direction, the
+// derived quantities of the ghost-ring grid, the sources of every zone.
 long long gr_face_doubles(const Params& p) {
   long long s = 0;
   for (int d = 0; d < p.dim; d++) s += (long long)NV * face_box(p, d).size;
-  return s + (long long)ND * ghost_box(p).size;
+  return s + (long long)ND * ghost_box(p).size + (long long)NSRC * p.N;
 }
 
 static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a) {
@@ -749,6 +790,7 @@ static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a
     if (d < p.dim) f += (long long)NV * face_box(p, d).size;
   }
   a.Dv = f;
+  a.Src = f + (long long)ND * ghost_box(p).size;
   a.kappa = gr_kappa(p);
   const double cv[5] = {p.gamma, p.gamma - 1.0, sqrt(p.phi * p.gamma), sqrt(p.psi * p.gamma), a.kappa * p.gamma};
   for (int k = 0; k < 5; k++) {
@@ -811,9 +853,12 @@ cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double
   gr_args(p, geo, faces, a);
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.K = K; a.P0 = P0;
   derived_gr<<<(unsigned)((ghost_box(p).size + 127) / 128), 128, 0, st>>>(p, a);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  zone_const_gr<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, a);
+  const unsigned nb = (unsigned)((p.N + 127) / 128);
+  sources_gr<<<nb, 128, 0, st>>>(p, a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  zone_const_gr<<<nb, 128, 0, st>>>(p, a);
   return cudaGetLastError();
 }
 
