@@ -34,10 +34,12 @@ N_SIDE = 1024
 MLP_FLOPS_PER_ZONE = 2 * (32 * 128 + 2 * 128 * 128 + 128 * 80)
 MLP_TRAIN_STEPS = 24000   # Adam steps of the learned start (untimed, about 20 s)
 MLP_SAMPLE_STRIDE = 6     # training stages from every 6th of the first 48 steps (the timed stretch)
-# DRAM bytes read + written per launch at 1024^2 from the ncu captures in
-# profiles/explicit_turbulent_box_1024.md and profiles/newton_turbulent_box_1024.md
-# (None while a kernel has changed since its capture).
-NCU_TRAFFIC_BYTES = {"faces": 296.5e6, "zone_const": 641.5e6, "newton64": 428.0e6, "newton32": None}
+# DRAM bytes read + written per launch at 1024^2 (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of each kernel on this workload;
+# newton32 captured on the plain-start arm; None while a kernel has changed
+# since its capture).
+NCU_TRAFFIC_BYTES = {"faces": 297.8e6, "zone_const": 642.0e6, "newton64": 428.0e6, "newton32": 424.5e6,
+                     "mlp": 158.0e6}
 TOL = 1e-10
 
 
@@ -261,7 +263,7 @@ def profile_case(args, dev, torch):
         b = torch.empty_like(a)
         out[nm + "_tuning"] = g.autotune(a, dt)[0]
         ms, st, kt, _ = time_device(g, a, b, dt, args.steps, args.warmup, 1, torch)
-        out[nm] = {"ms_per_step": ms, "kernel_ms": {k: v[0] / v[1] for k, v in kt.items()},
+        out[nm] = {"ms_per_step": ms, "kernel_ms_per_stage": {k: v[0] / (2 * args.steps) for k, v in kt.items()},
                    "iters_per_zone_stage": st["iters"] / max(1, st["zones"]), "failed": st["failed"]}
         g.close()
     print(json.dumps(out))
@@ -391,7 +393,9 @@ def bench_kerr(dev, torch, world, steps=3, warmup=2):
         kt = g.kernel_times()
         out[name] = {"value": aggregate_rate(prob.zones, ms * 1e-3, world), "ms_per_step": ms,
                      "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]), "failed": s["failed"],
-                     "max_res": s["max_res"], "kernel_ms_per_stage": {k: v[0] / v[1] for k, v in kt.items()}}
+                     "max_res": s["max_res"],
+                     # per stage (zone_const: derived + sources + stage constants, and the floors)
+                     "kernel_ms_per_stage": {k: v[0] / (2 * steps) for k, v in kt.items()}}
         g.close()
         del a, b
         torch.cuda.empty_cache()

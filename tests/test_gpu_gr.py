@@ -38,14 +38,18 @@ def _torus(n1, n2, n3, tol=1e-14):
     return prob, inputs.torus_state(prob)
 
 
-def test_gr_residual_parity_kerr(dev, orc):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gr_residual_parity_kerr(dev, orc, precision):
+    """The stage residual on the torus against the oracle's; the mixed
+    solver's float-float face states and fluxes (about 48 significant bits)
+    meet the same bound as float64."""
     from paper_1702_01106_b300.grim import Grim
     prob, Pn = _torus(20, 16, 1)
     rng = np.random.default_rng(5)
     PE = Pn * (1 + 1e-3 * rng.standard_normal(Pn.shape))
     Pk = Pn * (1 + 1e-3 * rng.standard_normal(Pn.shape))
     dts = 0.5 * inputs.torus_dt(prob)
-    g = Grim(prob)
+    g = Grim(prob, precision=precision)
     R = torch.empty_like(_t(Pn, dev))
     g.residual(_t(Pn, dev), _t(PE, dev), dts, _t(Pk, dev), R)
     ref = orc.residual(prob, Pn, PE, dts, Pk)
