@@ -26,7 +26,7 @@ cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* P
 long long pn_cache_doubles(long long N);
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                             int* qcount, cudaStream_t st);
+                             int* qcount, double* rq, cudaStream_t st);
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
@@ -43,7 +43,7 @@ cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K
                              const uint8_t* status, double* P, cudaStream_t st);
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
-                             int* qcount, cudaStream_t st);
+                             int* qcount, double* rq, cudaStream_t st);
 cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,
                                double dts, double* R, cudaStream_t st);
 }  // namespace grim
@@ -71,7 +71,8 @@ struct grim_ctx {
   bool gr = false;            // general-metric kernels (3-D or Kerr)
   double* geo = nullptr;      // geometry tables of the general-metric path
   double* K = nullptr;        // NK x N stage constants
-  double* faces = nullptr;    // face fluxes of one stage
+  double* faces = nullptr;    // face fluxes of one stage; during the Newton solve,
+                              // the residuals of the zones handed to the queue kernel
   double* pncache = nullptr;  // P_n quantities shared by the two stages of a step
   double* Ph = nullptr;       // half-step state
   uint8_t* iters = nullptr;   // per-zone Newton updates of the last stage
@@ -280,7 +281,7 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
       KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64, cfg.kcut < ctx->p.kmax ? 2 : 1);
       GRIM_CUDA(grim::launch_newton_gr(ctx->p, ctx->precision, ctx->K, ctx->geo, Pout, iters ? iters : ctx->iters,
                                        status ? status : ctx->status, ctx->cnt, cfg, ctx->queue, ctx->qcount,
-                                       ctx->cur),
+                                       ctx->faces, ctx->cur),
                 "newton kernel");
     }
     if (ctx->p.floors) {
@@ -295,7 +296,7 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
     KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64, cfg.kcut < ctx->p.kmax ? 2 : 1);
     GRIM_CUDA(grim::launch_newton_fb(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
                                      status ? status : ctx->status, ctx->cnt, learned ? Pn : nullptr, ctx->accept,
-                                     cfg, ctx->queue, ctx->qcount, ctx->cur),
+                                     cfg, ctx->queue, ctx->qcount, ctx->faces, ctx->cur),
               "newton kernel");
   }
   return GRIM_OK;

@@ -309,21 +309,30 @@ struct ZoneResult {
 // shared memory (stride BS); kf: their float copies.  Pfb (non-NULL with a
 // learned start): the plain start P_n, whose magnetic components are those
 // of P; if the learned start's max|r| exceeds accept_bits the plain start is
-// evaluated too and the smaller |r|^2 wins.
+// evaluated too and the smaller |r|^2 wins.  rq (stride rs, may be NULL):
+// the zone's residual slot for the queue: a call that stops pending stores
+// r(P) there, and a resumed call (k0 > 0) reads it instead of evaluating it
+// again.
 template <bool MIXED, int BS>
 __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double* kd, const float* kf, double P[NV],
                                                   void* jac, const double* Pfb, long long fb_stride,
                                                   unsigned long long accept_bits, bool& fellback, int k0,
-                                                  int kstop) {
+                                                  int kstop, double* rq, long long rs) {
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
   const RC<double> c64 = make_rc<double>(p);
   const KSm<double, BS> k64{kd};
   const unsigned long long tol_bits = abits(p.tol);
   Z<double> z;
-  z_load(z, P, c64);
   double r[NV];
-  r_all(z, k64, r);
-  o.evals64++;
+  if (rq && k0 > 0) {
+    if (!MIXED) z_load(z, P, c64);  // the float64 Jacobian differentiates from z
+#pragma unroll
+    for (int a = 0; a < NV; a++) r[a] = rq[a * rs];
+  } else {
+    z_load(z, P, c64);
+    r_all(z, k64, r);
+    o.evals64++;
+  }
   double f = sum_sq10(r);
   fellback = false;
   if (Pfb && !(max_abits10(r) <= accept_bits)) {
@@ -414,6 +423,10 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
   unsigned long long mb = max_abits10(r);
   o.res = __longlong_as_double((long long)mb);
   if (!(P[0] > 0.0) || !(P[1] > 0.0)) o.status |= ST_INADMISSIBLE;
+  if (o.pending && rq) {
+#pragma unroll
+    for (int a = 0; a < NV; a++) rq[a * rs] = r[a];
+  }
   return o;
 }
 
@@ -479,7 +492,8 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
                                                    const double* __restrict__ Pfb, double accept, int kstop,
-                                                   int* __restrict__ queue, int* __restrict__ qcount) {
+                                                   int* __restrict__ queue, int* __restrict__ qcount,
+                                                   double* __restrict__ rq) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -501,7 +515,7 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
     o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, Pfb ? Pfb + z : nullptr, N, abits(accept), fellback, 0,
-                               kstop < p.kmax ? kstop : p.kmax);
+                               kstop < p.kmax ? kstop : p.kmax, queue && rq ? rq + z : nullptr, N);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -518,7 +532,8 @@ template <bool MIXED, int BS>
 __global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Params p, const double* __restrict__ K,
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
-                                                   const int* __restrict__ queue, const int* __restrict__ qcount) {
+                                                   const int* __restrict__ queue, const int* __restrict__ qcount,
+                                                   double* __restrict__ rq) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -542,7 +557,8 @@ __global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Param
       double Pz[NV];
 #pragma unroll
       for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-      o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, nullptr, N, 0ull, fellback, iters[z], p.kmax);
+      o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, nullptr, N, 0ull, fellback, iters[z], p.kmax,
+                                 rq ? rq + z : nullptr, N);
 #pragma unroll
       for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
       iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -612,7 +628,7 @@ template <bool MIXED, int BS> struct NewtonKernels {
   }
   static cudaError_t launch(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                             Counters* cnt, const double* Pfb, double accept, int kcut, int* queue, int* qcount,
-                            cudaStream_t st) {
+                            double* rq, cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
@@ -621,9 +637,9 @@ template <bool MIXED, int BS> struct NewtonKernels {
     const long long nb = (p.N + BS - 1) / BS;
     newton_dense<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
                                                                  compact ? kcut : p.kmax, compact ? queue : nullptr,
-                                                                 qcount);
+                                                                 qcount, rq);
     if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
-    newton_queue<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue, qcount);
+    newton_queue<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue, qcount, rq);
     return cudaGetLastError();
   }
 };
@@ -631,28 +647,30 @@ template <bool MIXED, int BS> struct NewtonKernels {
 template <bool MIXED>
 static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                                    Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                                   int* qcount, cudaStream_t st) {
+                                   int* qcount, double* rq, cudaStream_t st) {
   switch (cfg.bs) {
-    case 32: return NewtonKernels<MIXED, 32>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, st);
-    case 64: return NewtonKernels<MIXED, 64>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, st);
-    case 128: return NewtonKernels<MIXED, 128>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, st);
+    case 32: return NewtonKernels<MIXED, 32>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, rq, st);
+    case 64: return NewtonKernels<MIXED, 64>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, rq, st);
+    case 128: return NewtonKernels<MIXED, 128>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, rq, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // Newton solves of one stage: the in-order kernel, then (cfg.kcut < k_max)
 // the queue kernel over the zones still unconverged after kcut updates.
+// rq: scratch of NV x N doubles for the residuals of the zones handed to the
+// queue kernel (may be NULL: the queue kernel then re-evaluates them).
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                             int* qcount, cudaStream_t st) {
-  if (mixed) return launch_newton_bs<true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, st);
-  return launch_newton_bs<false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, st);
+                             int* qcount, double* rq, cudaStream_t st) {
+  if (mixed) return launch_newton_bs<true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
+  return launch_newton_bs<false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
 }
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                           Counters* cnt, cudaStream_t st) {
   const NewtonCfg cfg{64, 1 << 30};
-  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, st);
+  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, nullptr, st);
 }
 
 cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, int scaled, double dts, double* R,
@@ -761,19 +779,25 @@ __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], con
   }
 }
 
+// rq, rs: the zone's residual slot for the queue, as in newton_zone.
 template <bool MIXED, int BS>
 __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const float* kf, const double* md,
-                                     double P[NV], void* jac, int k0, int kstop) {
+                                     double P[NV], void* jac, int k0, int kstop, double* rq, long long rs) {
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
   const RC<double> c64 = make_rc<double>(p);
   const KSm<double, BS> k64{kd};
   const Met<double> m64 = met_smem<double, BS>(md);
   const unsigned long long tol_bits = abits(p.tol);
   ZG<double> z;
-  zg_load(z, P, m64, c64);
   double r[NV];
-  r_all_gr(z, k64, r);
-  o.evals64++;
+  if (rq && k0 > 0) {
+#pragma unroll
+    for (int a = 0; a < NV; a++) r[a] = rq[a * rs];
+  } else {
+    zg_load(z, P, m64, c64);
+    r_all_gr(z, k64, r);
+    o.evals64++;
+  }
   double f = sum_sq10(r);
   int k = k0;
   for (;;) {
@@ -843,6 +867,10 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
   o.done = k - k0;
   o.res = __longlong_as_double((long long)max_abits10(r));
   if (!(P[0] > 0.0) || !(P[1] > 0.0)) o.status |= ST_INADMISSIBLE;
+  if (o.pending && rq) {
+#pragma unroll
+    for (int a = 0; a < NV; a++) rq[a * rs] = r[a];
+  }
   return o;
 }
 
@@ -880,7 +908,7 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
                                                       const double* __restrict__ gc, double* __restrict__ P,
                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
                                                       Counters* __restrict__ cnt, int kstop, int* __restrict__ queue,
-                                                      int* __restrict__ qcount) {
+                                                      int* __restrict__ qcount, double* __restrict__ rq) {
   using S = NewtonSmemGr<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -896,7 +924,8 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
     double Pz[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-    o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax);
+    o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax,
+                                  queue && rq ? rq + z : nullptr, N);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -911,7 +940,7 @@ __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Pa
                                                       const double* __restrict__ gc, double* __restrict__ P,
                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
                                                       Counters* __restrict__ cnt, const int* __restrict__ queue,
-                                                      const int* __restrict__ qcount) {
+                                                      const int* __restrict__ qcount, double* __restrict__ rq) {
   using S = NewtonSmemGr<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -930,7 +959,7 @@ __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Pa
       double Pz[NV];
 #pragma unroll
       for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-      o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, iters[z], p.kmax);
+      o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, iters[z], p.kmax, rq ? rq + z : nullptr, N);
 #pragma unroll
       for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
       iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -996,7 +1025,8 @@ template <bool MIXED, int BS> struct NewtonKernelsGr {
     return cudaSuccess;
   }
   static cudaError_t launch(const Params& p, const double* K, const double* gc, double* P, uint8_t* iters,
-                            uint8_t* status, Counters* cnt, int kcut, int* queue, int* qcount, cudaStream_t st) {
+                            uint8_t* status, Counters* cnt, int kcut, int* queue, int* qcount, double* rq,
+                            cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
@@ -1005,25 +1035,26 @@ template <bool MIXED, int BS> struct NewtonKernelsGr {
     const long long nb = (p.N + BS - 1) / BS;
     newton_dense_gr<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
                                                                     compact ? kcut : p.kmax,
-                                                                    compact ? queue : nullptr, qcount);
+                                                                    compact ? queue : nullptr, qcount, rq);
     if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
     newton_queue_gr<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt, queue,
-                                                                      qcount);
+                                                                      qcount, rq);
     return cudaGetLastError();
   }
 };
 
 // Newton solves of one stage in a general metric (block size 32 or 64).
+// rq: as in launch_newton_fb.
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
-                             int* qcount, cudaStream_t st) {
+                             int* qcount, double* rq, cudaStream_t st) {
   const bool b32 = cfg.bs == 32;
   if (mixed) {
-    if (b32) return NewtonKernelsGr<true, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
-    return NewtonKernelsGr<true, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
+    if (b32) return NewtonKernelsGr<true, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
+    return NewtonKernelsGr<true, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
   }
-  if (b32) return NewtonKernelsGr<false, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
-  return NewtonKernelsGr<false, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, st);
+  if (b32) return NewtonKernelsGr<false, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
+  return NewtonKernelsGr<false, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
 }
 
 cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,
