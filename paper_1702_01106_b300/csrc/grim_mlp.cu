@@ -91,6 +91,10 @@ __device__ __forceinline__ float tanh_fast(float x) {
 }
 __device__ __forceinline__ float sigm(float x) { return fmaf(0.5f, tanh_fast(0.5f * x), 0.5f); }
 __device__ __forceinline__ float silu(float x) { return x * sigm(x); }
+// SiLU(x) from h = x/2: x sigmoid(x) = h (1 + tanh(h)), one FMA after the
+// special-function operation (the inference epilogue forms h = acc/2 + b/2
+// in one FMA from halved biases).
+__device__ __forceinline__ float silu_of_half(float h) { return fmaf(h, tanh_fast(h), h); }
 __device__ __forceinline__ float silu_grad(float x) {
   const float s = sigm(x);
   return s * (1.0f + x * (1.0f - s));
@@ -466,18 +470,19 @@ __device__ __forceinline__ void layer_mma(float acc[][4], const unsigned (*afr)[
   }
 }
 
-// SiLU(acc + b) of 16 n8 tiles -> 8 k16 A fragments.
-__device__ __forceinline__ void to_afrag(float acc[16][4], const float* b, unsigned afr[8][4], int lane) {
+// SiLU(acc + b) of 16 n8 tiles -> 8 k16 A fragments; hb: the halved biases.
+__device__ __forceinline__ void to_afrag(float acc[16][4], const float* hb, unsigned afr[8][4], int lane) {
   const int ac = (lane & 3) * 2;
+  auto act = [](float a, float h) { return silu_of_half(fmaf(a, 0.5f, h)); };
 #pragma unroll
   for (int ks = 0; ks < 8; ks++) {
     const int c0 = ks * 16 + ac, c1 = c0 + 8;
     const float* lo = acc[2 * ks];
     const float* hi = acc[2 * ks + 1];
-    afr[ks][0] = pack_bf16(silu(lo[0] + b[c0]), silu(lo[1] + b[c0 + 1]));
-    afr[ks][1] = pack_bf16(silu(lo[2] + b[c0]), silu(lo[3] + b[c0 + 1]));
-    afr[ks][2] = pack_bf16(silu(hi[0] + b[c1]), silu(hi[1] + b[c1 + 1]));
-    afr[ks][3] = pack_bf16(silu(hi[2] + b[c1]), silu(hi[3] + b[c1 + 1]));
+    afr[ks][0] = pack_bf16(act(lo[0], hb[c0]), act(lo[1], hb[c0 + 1]));
+    afr[ks][1] = pack_bf16(act(lo[2], hb[c0]), act(lo[3], hb[c0 + 1]));
+    afr[ks][2] = pack_bf16(act(hi[0], hb[c1]), act(hi[1], hb[c1 + 1]));
+    afr[ks][3] = pack_bf16(act(hi[2], hb[c1]), act(hi[3], hb[c1 + 1]));
   }
 }
 
@@ -499,13 +504,15 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
     S.w2[i / MLP_H][i % MLP_H] = wb[o2 + i];
   }
   for (int i = tid; i < MLP_HEAD * MLP_H; i += NT) S.w3[i / MLP_H][i % MLP_H] = wb[o3 + i];
-  for (int i = tid; i < MLP_H; i += NT) {
-    S.b[i] = params[mlp_boff(0) + i];
-    S.b[MLP_H + i] = params[mlp_boff(1) + i];
-    S.b[2 * MLP_H + i] = params[mlp_boff(2) + i];
+  for (int i = tid; i < MLP_H; i += NT) {  // hidden biases halved for the SiLU epilogue
+    S.b[i] = 0.5f * params[mlp_boff(0) + i];
+    S.b[MLP_H + i] = 0.5f * params[mlp_boff(1) + i];
+    S.b[2 * MLP_H + i] = 0.5f * params[mlp_boff(2) + i];
   }
   if (tid < MLP_HEAD) S.b[3 * MLP_H + tid] = params[mlp_boff(3) + tid];
-  if (tid < 2 * MLP_IN + 2 * MLP_Y) S.norm[tid] = norm[tid];
+  // the feature deviations as reciprocals (one multiply a feature below)
+  if (tid < 2 * MLP_IN + 2 * MLP_Y)
+    S.norm[tid] = (tid >= MLP_IN && tid < 2 * MLP_IN) ? 1.0f / norm[tid] : norm[tid];
   __syncthreads();
   const long long N = p.N;
   const float g[10] = {-1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f};
@@ -538,7 +545,7 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
       }
 #pragma unroll
       for (int a = 0; a < MLP_IN; a++) {
-        const float xs = (xf[a] - S.norm[a]) / S.norm[MLP_IN + a];
+        const float xs = (xf[a] - S.norm[a]) * S.norm[MLP_IN + a];
         S.x[warp][lane][a] = __float2bfloat16(xs);
         if (a < MLP_XU) S.xh[warp][lane][a] = xs;
       }
