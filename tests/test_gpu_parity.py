@@ -206,3 +206,26 @@ def test_mixed_residual_float_float_faces(dev, orc, recon):
     ref = orc.residual(prob, Pn, PE, dts, Pk)
     assert np.abs(R.cpu().numpy() - ref).max() < 1e-12
     g.close()
+
+
+@pytest.mark.parametrize("bscale", [1e-20, 1e-34, 0.0])
+def test_mixed_residual_weak_field(dev, orc, bscale):
+    """A field far below the float range's square root (b^2 underflows a
+    float) or zero: the float-float face states form b-hat from b scaled by
+    a power of two, so the mixed solver's residual still agrees with the
+    float64 oracle's to 1e-12 (an unscaled b-hat overflowed to ~1e41)."""
+    prob, Pn = _ragged_turbulent()
+    Pn = Pn.copy()
+    Pn[5:8] *= bscale
+    rng = np.random.default_rng(3)
+    PE = Pn * (1 + 1e-3 * rng.standard_normal(Pn.shape))
+    Pk = Pn * (1 + 1e-3 * rng.standard_normal(Pn.shape))
+    dts = 0.25 / 32
+    g = _g(prob, precision=1)
+    R = torch.empty_like(_t(Pn, dev))
+    g.residual(_t(Pn, dev), _t(PE, dev), dts, _t(Pk, dev), R)
+    ref = orc.residual(prob, Pn, PE, dts, Pk)
+    got = R.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() < 1e-12
+    g.close()
