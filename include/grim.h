@@ -53,7 +53,13 @@ extern "C" {
 #define GRIM_FLUX_HLLE 1   /* HLLE with the bounds c_R = max(c, 0), c_L = max(-c, 0) (Section 2.4.2) */
 
 #define GRIM_FP64 0        /* Jacobian, LU, residual all in float64 */
-#define GRIM_MIXED 1       /* Jacobian and LU in float32; residual, update and test in float64 */
+/* Jacobian and LU in float32; residual, update and test in float64; the
+ * explicit stage's face states, fluxes and wave speeds (and, on 2-D
+ * Minkowski grids, the MC reconstruction and the limited slopes) in
+ * float-float, pairs of floats with about 48 significant bits, joined back
+ * into float64 before they are stored; U(P_n), the flux divergence, flux-CT
+ * and the stage constants stay float64. */
+#define GRIM_MIXED 1
 
 /* Grid (Section 2.1): uniform in X^i, dX^i = (x_end - x_start)/n_i. */
 typedef struct {
