@@ -154,6 +154,27 @@ __device__ __forceinline__ double f_widen(float f) {
 }
 __device__ __forceinline__ double ff_join(ff a) { return f_widen(a.hi) + f_widen(a.lo); }
 
+// Conversions for the float32 Jacobian by bit manipulation, without a branch
+// and without the conversion instructions of the narrow float64 pipe:
+// double to float with the significand truncated to 24 bits (magnitudes
+// below the normal float range become signed zeros, above it infinities),
+// and float to double exactly (float denormals become zero).
+__device__ __forceinline__ float d2f_jac(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff) - 896;
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned mag = (unsigned)e << 23 | (unsigned)((b & 0xfffffffffffffull) >> 29);
+  const unsigned r = e < 1 ? sign : (e > 254 ? (sign | 0x7f800000u) : (sign | mag));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ double f2d_jac(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xff;
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long v = s | (unsigned long long)(ef + 896) << 52 | (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(ef == 0 ? s : v));
+}
+
 // Input in the working precision: float64 as is, float-float by the split.
 template <typename T> __device__ __forceinline__ T from_double(double d);
 template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }

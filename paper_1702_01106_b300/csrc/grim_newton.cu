@@ -376,7 +376,7 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       float* b = J + NV * NV * BS;
       float Pf[NV], rf[NV];
 #pragma unroll
-      for (int a = 0; a < NV; a++) Pf[a] = (float)P[a];
+      for (int a = 0; a < NV; a++) Pf[a] = d2f_jac(P[a]);
       Z<float> zf;
       z_load(zf, Pf, c32);
       r_all(zf, k32, rf);
@@ -388,11 +388,11 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
         o.evals32 += 7 + 1;
       }
 #pragma unroll
-      for (int i = 0; i < NV; i++) b[i * BS] = (float)(-r[i]);
+      for (int i = 0; i < NV; i++) b[i * BS] = d2f_jac(-r[i]);
       float df[NV];
       ok = lu_solve7_smem<float, BS>(J, b, df);
 #pragma unroll
-      for (int i = 0; i < NV; i++) dP[i] = (double)df[i];
+      for (int i = 0; i < NV; i++) dP[i] = f2d_jac(df[i]);
       o.lu32++;
     }
     if (!ok) { o.status |= ST_SINGULAR; break; }
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
     for (int a = 0; a < NK; a++) {
       const double x = __ldg(K + a * N + z);
       kd[a * BS] = x;
-      if (MIXED) kf[a * BS] = (float)x;
+      if (MIXED) kf[a * BS] = d2f_jac(x);
     }
     double Pz[NV];
 #pragma unroll
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Param
       for (int a = 0; a < NK; a++) {
         const double x = __ldg(K + a * N + z);
         kd[a * BS] = x;
-        if (MIXED) kf[a * BS] = (float)x;
+        if (MIXED) kf[a * BS] = d2f_jac(x);
       }
       double Pz[NV];
 #pragma unroll
@@ -824,7 +824,7 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       float* b = J + NV * NV * BS;
       float Pf[NV], rf[NV];
 #pragma unroll
-      for (int a = 0; a < NV; a++) Pf[a] = (float)P[a];
+      for (int a = 0; a < NV; a++) Pf[a] = d2f_jac(P[a]);
       ZG<float> zf;
       zg_load(zf, Pf, m32, c32);
       r_all_gr(zf, k32, rf);
@@ -836,11 +836,11 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
         o.evals32 += 7 + 1;
       }
 #pragma unroll
-      for (int i = 0; i < NV; i++) b[i * BS] = (float)(-r[i]);
+      for (int i = 0; i < NV; i++) b[i * BS] = d2f_jac(-r[i]);
       float df[NV];
       ok = lu_solve7_smem<float, BS>(J, b, df);
 #pragma unroll
-      for (int i = 0; i < NV; i++) dP[i] = (double)df[i];
+      for (int i = 0; i < NV; i++) dP[i] = f2d_jac(df[i]);
       o.lu32++;
     }
     if (!ok) { o.status |= ST_SINGULAR; break; }
@@ -891,7 +891,7 @@ __device__ __forceinline__ void load_zone_gr(const Params& p, const double* K, c
   for (int a = 0; a < NK; a++) {
     const double x = __ldg(K + a * N + z);
     kd[a * BS] = x;
-    if (MIXED) kf[a * BS] = (float)x;
+    if (MIXED) kf[a * BS] = d2f_jac(x);
   }
   const int i = (int)(z % p.n1), j = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
   const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
