@@ -175,10 +175,11 @@ __device__ __forceinline__ double f2d_jac(float f) {
   return __longlong_as_double((long long)(ef == 0 ? s : v));
 }
 
-// Input in the working precision: float64 as is, float-float by the split.
+// Input in the working precision: float64 as is, float-float by the split,
+// float (the float32 Jacobian's) by truncation.
 template <typename T> __device__ __forceinline__ T from_double(double d);
 template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }
-template <> __device__ __forceinline__ float from_double<float>(double d) { return (float)d; }
+template <> __device__ __forceinline__ float from_double<float>(double d) { return d2f_jac(d); }
 template <> __device__ __forceinline__ ff from_double<ff>(double d) { return ff_split(d); }
 
 // Generalized minmod slope (Section 2.4.1) of vm, v0, vp in float-float, for

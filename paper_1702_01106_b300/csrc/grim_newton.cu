@@ -703,10 +703,10 @@ constexpr int NMET = 14;  // g_{mu nu} (10), alpha, g^{ti} (3)
 template <typename T, int BS> __device__ __forceinline__ Met<T> met_smem(const double* md) {
   Met<T> m;
 #pragma unroll
-  for (int a = 0; a < 10; a++) m.gcov[a] = T(md[a * BS]);
-  m.alpha = T(md[10 * BS]);
+  for (int a = 0; a < 10; a++) m.gcov[a] = from_double<T>(md[a * BS]);
+  m.alpha = from_double<T>(md[10 * BS]);
 #pragma unroll
-  for (int i = 0; i < 3; i++) m.gti[i] = T(md[(11 + i) * BS]);
+  for (int i = 0; i < 3; i++) m.gti[i] = from_double<T>(md[(11 + i) * BS]);
   return m;
 }
 
