@@ -135,6 +135,7 @@ struct ExpArgs {
   const double* PE;
   const double* guess;
   double dts;
+  double idts, itau;  // 1/dt_s and 1/tau_R, once on the host
   double kappa;
   double* K;
   double* P0;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
       divu_sp += du[d][1 + d];
     }
   }
-  const double tau = p.tauR, dts = a.dts, idts = 1.0 / dts;
+  const double tau = p.tauR, dts = a.dts, idts = a.idts, it = a.itau, git = idts * it;
   double* Kz = a.K + z;
   double kU[NV];
   // the learned start's features x_a = -r_a(P_n) (the scaled residual of this
@@ -436,17 +437,17 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
     for (int m = 0; m < 4; m++) Cq[m] = pre * ze.theta * bhu[m] * ze.ut;
   }
   {
-    const double s8 = kU[8] * dts, it = 1.0 / tau;
-    double cst = -Un[8] * idts + divF[8] + 0.5 * qt_n * it - Aq * it + Bq * th_n * idts * it;
+    const double s8 = kU[8] * dts;
+    double cst = -Un[8] * idts + divF[8] + 0.5 * qt_n * it - Aq * it + Bq * th_n * git;
 #pragma unroll
-    for (int m = 0; m < 4; m++) cst += Cq[m] * ucovn[m] * idts * it;
+    for (int m = 0; m < 4; m++) cst += Cq[m] * ucovn[m] * git;
     cst -= hoq * (divu_sp - ut_n * idts);
     double kQ[7];
     const double kc = s8 * cst;
     kQ[0] = 0.5 * s8 * it;
-    kQ[1] = -s8 * Bq * idts * it;
+    kQ[1] = -s8 * git * Bq;
 #pragma unroll
-    for (int m = 0; m < 4; m++) kQ[2 + m] = -s8 * Cq[m] * idts * it;
+    for (int m = 0; m < 4; m++) kQ[2 + m] = -s8 * git * Cq[m];
     kQ[6] = -s8 * hoq * idts;
     Kz[(K_C + 8) * N] = kc;
 #pragma unroll
@@ -471,17 +472,17 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
     Ed = -pre * (1.0 / 3.0);
   }
   {
-    const double s9 = kU[9] * dts, it = 1.0 / tau;
-    double cst = -Un[9] * idts + divF[9] + 0.5 * dpt_n * it - Ad * it + Ed * ut_n * idts * it;
+    const double s9 = kU[9] * dts;
+    double cst = -Un[9] * idts + divF[9] + 0.5 * dpt_n * it - Ad * it + Ed * ut_n * git;
 #pragma unroll
-    for (int m = 0; m < 4; m++) cst += Dd[m] * ucovn[m] * idts * it;
+    for (int m = 0; m < 4; m++) cst += Dd[m] * ucovn[m] * git;
     cst -= hod * (divu_sp - ut_n * idts);
     double kD[6];
     const double kc = s9 * cst;
     kD[0] = 0.5 * s9 * it;
 #pragma unroll
-    for (int m = 0; m < 4; m++) kD[1 + m] = -s9 * Dd[m] * idts * it;
-    kD[5] = -s9 * (Ed * idts * it + hod * idts);
+    for (int m = 0; m < 4; m++) kD[1 + m] = -s9 * git * Dd[m];
+    kD[5] = -s9 * (Ed * git + hod * idts);
     Kz[(K_C + 9) * N] = kc;
 #pragma unroll
     for (int q = 0; q < 6; q++) Kz[(K_D + q) * N] = kD[q];
@@ -516,6 +517,8 @@ static double closure_kappa(const Params& p) {
 void explicit_args(const Params& p, const double* Pn, const double* PE, const double* guess, double dts, double* K,
                    double* P0, double* faces, ExpArgs& a) {
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.kappa = closure_kappa(p);
+  a.idts = 1.0 / dts;
+  a.itau = 1.0 / p.tauR;
   a.cache = nullptr; a.mode = 0; a.feat = nullptr;
   const double cv[6] = {p.gamma, p.gamma - 1.0, sqrt(p.phi * p.gamma), sqrt(p.psi * p.gamma), a.kappa * p.gamma,
                         p.theta};

@@ -170,6 +170,7 @@ struct GrArgs {
   const double* PE;
   const double* guess;
   double dts, kappa;
+  double idts;  // 1/dt_s, once on the host
   double* K;
   double* P0;
   double* F[3];
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
     Aq = x[4]; Bq = x[5]; Ad = x[10]; Ed = x[15]; divu_sp = x[16];
   }
   // --- stage constants (row scale folded in; sqrt(-g) folded into kU)
-  const double dts = a.dts, idts = 1.0 / dts, it = 1.0 / tau;
+  const double dts = a.dts, idts = a.idts, it = 1.0 / tau;
   double* Kz = a.K + z;
   double sr[NV];  // 1/(|U_v(P_n)| + |U_0(P_n)|)
 #pragma unroll
@@ -852,6 +853,7 @@ cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double
   GrArgs a{};
   gr_args(p, geo, faces, a);
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.K = K; a.P0 = P0;
+  a.idts = 1.0 / dts;
   derived_gr<<<(unsigned)((ghost_box(p).size + 127) / 128), 128, 0, st>>>(p, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
