@@ -258,7 +258,7 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
               "face kernel");
   }
   {
-    KernelMark m(ctx, GRIM_K_ZONECONST);
+    KernelMark m(ctx, GRIM_K_ZONECONST, ctx->precision == GRIM_MIXED ? 1 : 2);
     GRIM_CUDA(grim::launch_zone_const(ctx->p, Pn, PE, guess, dts, ctx->K, Pout, ctx->faces, ctx->pncache, mode,
                                       ctx->tune.zone_bs, feat, ctx->precision == GRIM_MIXED, ctx->cur),
               "zone-constant kernel");

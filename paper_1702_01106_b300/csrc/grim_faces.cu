@@ -141,6 +141,7 @@ struct ExpArgs {
   double* P0;
   double* F1;  // [10][(n2+2)][(n1+1)]
   double* F2;  // [10][(n2+1)][(n1+2)]
+  double* Dv;  // [2][N]: Theta and u^t of P^E at every zone (derived_2d)
   // P_n cache shared by the two stages of a step: U(P_n) [10], Theta_n, u^t_n.
   // mode 0: general stage (no cache); 1: half step (P^E = P_n; writes the
   // cache); 2: full step (reads the cache and the row weights K_U the half
@@ -257,21 +258,36 @@ __global__ void __launch_bounds__(BS, std::is_same<S, ff>::value ? 65536 / (BS *
   }
 }
 
+// Theta = (gamma-1) u/rho and u^t = (1 + u^i u^i)^(1/2) of P^E at every
+// zone, once a stage: the limited slopes of the zone kernel read them for
+// four neighbours of each zone.  Both are even under the reflections of the
+// boundary rules, so a ghost takes the values of the zone it maps to.
+template <int BS>
+__global__ void __launch_bounds__(BS) derived_2d(const __grid_constant__ Params p, const __grid_constant__ ExpArgs a) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * BS + threadIdx.x;
+  if (z >= N) return;
+  const double rho = __ldg(a.PE + z), uu = __ldg(a.PE + N + z);
+  const double v1 = __ldg(a.PE + 2 * N + z), v2 = __ldg(a.PE + 3 * N + z), v3 = __ldg(a.PE + 4 * N + z);
+  a.Dv[z] = (p.gamma - 1.0) * uu * nr_rcp(rho);
+  a.Dv[N + z] = sqrt(1.0 + v1 * v1 + v2 * v2 + v3 * v3);
+}
+
 // Theta and u_mu of the state at zone (i, j) of P^E (for the limited slopes).
-__device__ __forceinline__ void derived_at(const Params& p, const double* PE, int i, int j, double& th, double u[4]) {
+__device__ __forceinline__ void derived_at(const Params& p, const ExpArgs& a, int i, int j, double& th, double u[4]) {
   bool f1, f2;
   const long long z = zone_at(p, i, j, f1, f2);
   const long long N = p.N;
-  const double rho = __ldg(PE + z), uu = __ldg(PE + N + z);
-  const double v1 = load_comp(PE, N, z, 2, f1, f2), v2 = load_comp(PE, N, z, 3, f1, f2);
-  const double v3 = __ldg(PE + 4 * N + z);
-  th = (p.gamma - 1.0) * uu * nr_rcp(rho);
-  u[0] = -sqrt(1.0 + v1 * v1 + v2 * v2 + v3 * v3);
-  u[1] = v1; u[2] = v2; u[3] = v3;
+  th = __ldg(a.Dv + z);
+  u[0] = -__ldg(a.Dv + N + z);
+  u[1] = load_comp(a.PE, N, z, 2, f1, f2);
+  u[2] = load_comp(a.PE, N, z, 3, f1, f2);
+  u[3] = __ldg(a.PE + 4 * N + z);
 }
 
-// The same in float-float (the mixed solver's slopes): inputs split
-// without float64 instructions.
+// The same computed in float-float from P^E (the mixed solver's slopes;
+// there the float pipes make the recomputation cheaper than the pre-pass),
+// inputs split without float64 instructions.
 __device__ __forceinline__ void derived_at_ff(const Params& p, const ExpArgs& a, int i, int j, ff& th, ff u[4]) {
   bool f1, f2;
   const long long z = zone_at(p, i, j, f1, f2);
@@ -373,8 +389,8 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
 #pragma unroll
     for (int d = 0; d < 2; d++) {
       double thm, thp, um[4], up[4];
-      derived_at(p, a.PE, i - (d == 0), j - (d == 1), thm, um);
-      derived_at(p, a.PE, i + (d == 0), j + (d == 1), thp, up);
+      derived_at(p, a, i - (d == 0), j - (d == 1), thm, um);
+      derived_at(p, a, i + (d == 0), j + (d == 1), thp, up);
       const double ih = (d == 0) ? idx1 : idx2;
       dTh[d] = gm_slope(p.theta, thm, th0, thp) * ih;
 #pragma unroll
@@ -501,9 +517,11 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
   }
 }
 
-// Face arrays needed for an n1 x n2 grid, in doubles.
+// Explicit-stage scratch for an n1 x n2 grid, in doubles: the face arrays,
+// then Theta and u^t of every zone.
 long long face_scratch_doubles(int n1, int n2) {
-  return (long long)NV * ((long long)(n1 + 1) * (n2 + 2) + (long long)(n1 + 2) * (n2 + 1));
+  return (long long)NV * ((long long)(n1 + 1) * (n2 + 2) + (long long)(n1 + 2) * (n2 + 1)) +
+         2LL * n1 * n2;
 }
 
 // cs~^2 / c_s^2 under the closure chi = phi c_s^2 tau_R, nu = psi c_s^2 tau_R
@@ -529,6 +547,7 @@ void explicit_args(const Params& p, const double* Pn, const double* PE, const do
   a.K = K; a.P0 = P0;
   a.F1 = faces;
   a.F2 = faces + (long long)NV * (p.n1 + 1) * (p.n2 + 2);
+  a.Dv = a.F2 + (long long)NV * (p.n1 + 2) * (p.n2 + 1);
 }
 
 template <typename S, int RECON>
@@ -562,12 +581,14 @@ long long pn_cache_doubles(long long N) { return (long long)NCACHE * N; }
 
 // mode: 0 general stage, 1 half step (P_E == P_n; fills cache), 2 full step
 // of the same step (reads cache and K_U).
+// The float64 form first runs derived_2d; the float-float form recomputes
+// the neighbours' Theta and u^t itself.
 template <bool FFS>
 static cudaError_t launch_zone_const_s(const Params& p, const ExpArgs& a, unsigned nb, int bs, cudaStream_t st) {
   switch (bs) {
-    case 64: zone_const_2d<64, FFS><<<nb, 64, 0, st>>>(p, a); break;
-    case 128: zone_const_2d<128, FFS><<<nb, 128, 0, st>>>(p, a); break;
-    case 256: zone_const_2d<256, FFS><<<nb, 256, 0, st>>>(p, a); break;
+    case 64: if (!FFS) derived_2d<64><<<nb, 64, 0, st>>>(p, a); zone_const_2d<64, FFS><<<nb, 64, 0, st>>>(p, a); break;
+    case 128: if (!FFS) derived_2d<128><<<nb, 128, 0, st>>>(p, a); zone_const_2d<128, FFS><<<nb, 128, 0, st>>>(p, a); break;
+    case 256: if (!FFS) derived_2d<256><<<nb, 256, 0, st>>>(p, a); zone_const_2d<256, FFS><<<nb, 256, 0, st>>>(p, a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
