@@ -20,7 +20,6 @@
 #include <type_traits>
 
 #include "grim_zone.cuh"
-#include "grim_ff.cuh"
 
 namespace grim {
 

@@ -8,7 +8,6 @@
 // u~^j)^(1/2) (equal to u^i in Minkowski space).
 #pragma once
 #include "grim_zone.cuh"
-#include "grim_ff.cuh"
 
 namespace grim {
 
