@@ -538,14 +538,22 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
   }
   const double cs2E = p.gamma * ze.pg / (ze.rho + p.gamma * ze.u);
   const double* bh = ze.bhcon;
-  // sum over nu, l of Gamma^l_{nu mu} u^nu u_l at P^E, for each mu
+  // Gl[sym(mu, nu)] = sum_l Gamma^l_{mu nu} u_l at P^E (symmetric in mu, nu),
+  // and from it the sum over nu, l of Gamma^l_{nu mu} u^nu u_l for each mu
+  double Gl[10];
+#pragma unroll
+  for (int a = 0; a < 10; a++) {
+    double s = 0.0;
+#pragma unroll
+    for (int l = 0; l < 4; l++) s += g(G_GAM + 10 * l + a) * ze.ucov[l];
+    Gl[a] = s;
+  }
   double Gu[4];
-  #pragma unroll
+#pragma unroll
   for (int mu = 0; mu < 4; mu++) {
     double s = 0.0;
-    #pragma unroll
-    for (int l = 0; l < 4; l++)
-      for (int nu = 0; nu < 4; nu++) s += g(G_GAM + 10 * l + sym(nu, mu)) * ze.ucon[nu] * ze.ucov[l];
+#pragma unroll
+    for (int nu = 0; nu < 4; nu++) s += Gl[sym(nu, mu)] * ze.ucon[nu];
     Gu[mu] = s;
   }
   // heat flux: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
@@ -578,8 +586,7 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
       for (int nn = 0; nn < 4; nn++) {
         double nab = 0.0;
         if (mu >= 1) nab = du[mu - 1][nn];
-        #pragma unroll
-        for (int l = 0; l < 4; l++) nab -= g(G_GAM + 10 * l + sym(mu, nn)) * ze.ucov[l];
+        nab -= Gl[sym(mu, nn)];
         sp += bh[mu] * bh[nn] * nab;
       }
     Ad = pre * (sp - divu_sp * (1.0 / 3.0));
