@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
       for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
       divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
     }
-    divu_sp /= sg;
+    divu_sp *= nr_rcp(sg);
   }
   // --- sources at P^E
   const RC<double> c = make_rc<double>(p);
@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
       Sg[n] = sg * s;
     }
   }
-  const double cs2E = p.gamma * ze.pg / (ze.rho + p.gamma * ze.u);
+  const double cs2E = p.gamma * ze.pg * nr_rcp(ze.rho + p.gamma * ze.u);
+  const double ith = nr_rcp(ze.theta);
   const double* bh = ze.bhcon;
   // Gl[sym(mu, nu)] = sum_l Gamma^l_{mu nu} u_l at P^E (symmetric in mu, nu),
   // and from it the sum over nu, l of Gamma^l_{nu mu} u^nu u_l for each mu
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
   double Aq = 0.0, Bq = 0.0, Cq[4] = {0.0, 0.0, 0.0, 0.0};
   if (p.cond) {
     const double chi = p.phi * cs2E * tau;
-    const double pre = -sqrt(tau * ze.rho * chi) / ze.theta;
+    const double pre = -sqrt(tau * ze.rho * chi) * ith;
     double acc = 0.0;
     #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
@@ -578,7 +579,7 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
   double Ad = 0.0, Dd[4] = {0.0, 0.0, 0.0, 0.0}, Ed = 0.0;
   if (p.visc) {
     const double nu = p.psi * cs2E * tau;
-    const double pre = 3.0 * sqrt(tau * ze.rho * nu / ze.theta);
+    const double pre = 3.0 * sqrt(tau * ze.rho * nu * ith);
     double sp = 0.0;
     #pragma unroll
     for (int mu = 0; mu < 4; mu++)
@@ -684,12 +685,12 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
     Aq = x[4]; Bq = x[5]; Ad = x[10]; Ed = x[15]; divu_sp = x[16];
   }
   // --- stage constants (row scale folded in; sqrt(-g) folded into kU)
-  const double dts = a.dts, idts = a.idts, it = 1.0 / tau;
+  const double dts = a.dts, idts = a.idts, it = nr_rcp(tau), isg = nr_rcp(sg);
   double* Kz = a.K + z;
   double sr[NV];  // 1/(|U_v(P_n)| + |U_0(P_n)|)
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    sr[v] = 1.0 / (fabs(Un[v]) + fabs(Un[0]));
+    sr[v] = nr_rcp(fabs(Un[v]) + fabs(Un[0]));
     Kz[(K_U + v) * N] = sr[v] * sg;
     const double src = (v >= 1 && v <= 4) ? Sg[v - 1] : 0.0;
     Kz[(K_C + v) * N] = sr[v] * (dts * (divF[v] - src) - Un[v]);
@@ -728,7 +729,7 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     double x = a.guess ? __ldg(a.guess + v * N + z) : Pnz[v];
-    if (v >= 5 && v <= 7) x = (Un[v] - dts * divF[v]) / sg;
+    if (v >= 5 && v <= 7) x = (Un[v] - dts * divF[v]) * isg;
     a.P0[v * N + z] = x;
   }
 }
