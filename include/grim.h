@@ -132,8 +132,7 @@ typedef struct grim_ctx grim_ctx;
  * flat-space kernels; 3-D grids and the Kerr metric run the general-metric
  * kernels, whose geometry tables (metric, inverse, sqrt(-g), lapse,
  * connection and tau_R at zone centres and faces; axisymmetric, so n1 x n2
- * only) are computed here once, on the stream.  The learned start
- * (grim_set_guess) is for 2-D Minkowski grids only.
+ * only) are computed here once, on the stream.
  * Errors: GRIM_EINVAL (dim not 2 or 3, n3 != 1 in 2-D, sizes < 1, unsupported
  * metric or reconstruction), GRIM_ENOMEM, GRIM_ECUDA.  *out is NULL on
  * failure. */
@@ -347,8 +346,9 @@ int grim_mlp_sample(grim_ctx* ctx, const double* P_n, const double* P_conv, floa
  * the plain start P_n is evaluated too and the smaller |r|^2 wins (counted
  * in grim_stats.fallbacks).  The MLP must outlive its use by ctx.  The first
  * call with an MLP allocates a feature buffer (10 floats per zone), which the
- * zone-constant kernel fills each stage.  GRIM_EINVAL on a 3-D or Kerr
- * context; GRIM_ENOMEM. */
+ * zone-constant kernel fills each stage on 2-D Minkowski grids and a feature
+ * kernel (the stage's residual at P_n) in a general metric, where the metric
+ * features are the zone's g_{mu nu}.  GRIM_ENOMEM. */
 int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept);
 
 /* Self-check of the float64 reciprocal the kernels use for finite-difference

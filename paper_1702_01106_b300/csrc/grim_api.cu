@@ -30,7 +30,9 @@ cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
-                             cudaStream_t st);
+                             const double* gc, cudaStream_t st);
+cudaError_t launch_features_gr(const Params& p, const double* K, const double* gc, const double* Pn, const double* Pc,
+                               float* X, float* Y, float* feat, cudaStream_t st);
 long long gr_geometry_doubles(const Params& p);
 long long gr_face_doubles(const Params& p);
 cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double h, const double x0[3],
@@ -43,7 +45,7 @@ cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K
                              const uint8_t* status, double* P, cudaStream_t st);
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, cudaStream_t st);
+                             int* qcount, double* rq, const double* Pfb, double accept, cudaStream_t st);
 cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,
                                double dts, double* R, cudaStream_t st);
 }  // namespace grim
@@ -268,12 +270,18 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
 
 static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
                      double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
-  const bool learned = ctx->mlp && !guess && !ctx->gr;
-  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode, learned ? ctx->feat : nullptr);
+  const bool learned = ctx->mlp && !guess;
+  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode, learned && !ctx->gr ? ctx->feat : nullptr);
   if (rc) return rc;
   if (learned) {
-    KernelMark m(ctx, GRIM_K_MLP);
-    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->cur), "mlp kernel");
+    // the flat zone kernel wrote the increment features; in a general metric
+    // a feature kernel evaluates the stage's residual at P_n
+    KernelMark m(ctx, GRIM_K_MLP, ctx->gr ? 2 : 1);
+    if (ctx->gr)
+      GRIM_CUDA(grim::launch_features_gr(ctx->p, ctx->K, ctx->geo, Pn, nullptr, nullptr, nullptr, ctx->feat, ctx->cur),
+                "feature kernel");
+    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->gr ? ctx->geo : nullptr, ctx->cur),
+              "mlp kernel");
   }
   if (ctx->gr) {
     const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
@@ -281,7 +289,7 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
       KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64, cfg.kcut < ctx->p.kmax ? 2 : 1);
       GRIM_CUDA(grim::launch_newton_gr(ctx->p, ctx->precision, ctx->K, ctx->geo, Pout, iters ? iters : ctx->iters,
                                        status ? status : ctx->status, ctx->cnt, cfg, ctx->queue, ctx->qcount,
-                                       ctx->faces, ctx->cur),
+                                       ctx->faces, learned ? Pn : nullptr, ctx->accept, ctx->cur),
                 "newton kernel");
     }
     if (ctx->p.floors) {
@@ -566,7 +574,6 @@ int grim_get_stats(grim_ctx* ctx, grim_stats* out) {
 
 int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept) {
   if (!ctx || !(accept >= 0.0)) return GRIM_EINVAL;
-  if (mlp && ctx->gr) return fail(ctx, GRIM_EINVAL, "grim_set_guess: the learned start is for 2-D Minkowski grids");
   if (mlp && !ctx->feat) {
     const cudaError_t e = cudaMalloc(&ctx->feat, sizeof(float) * grim::NV * (size_t)ctx->p.N);
     if (e != cudaSuccess) return fail(ctx, GRIM_ENOMEM, "grim_set_guess: feature buffer", e);
@@ -578,10 +585,13 @@ int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept) {
 
 int grim_mlp_sample(grim_ctx* ctx, const double* P_n, const double* P_conv, float* X, float* Y) {
   if (!ctx || !P_n || !X || (Y && !P_conv)) return GRIM_EINVAL;
-  if (ctx->gr) return fail(ctx, GRIM_EINVAL, "grim_mlp_sample: the learned start is for 2-D Minkowski grids");
   {
     KernelMark m(ctx, GRIM_K_MLP);
-    GRIM_CUDA(grim::launch_mlp_features(ctx->p, ctx->K, P_n, P_conv, X, Y, ctx->stream), "feature kernel");
+    if (ctx->gr)
+      GRIM_CUDA(grim::launch_features_gr(ctx->p, ctx->K, ctx->geo, P_n, P_conv, X, Y, nullptr, ctx->stream),
+                "feature kernel");
+    else
+      GRIM_CUDA(grim::launch_mlp_features(ctx->p, ctx->K, P_n, P_conv, X, Y, ctx->stream), "feature kernel");
   }
   return GRIM_OK;
 }

@@ -491,7 +491,8 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
                                                              const double* __restrict__ Pn,
                                                              const __nv_bfloat16* __restrict__ wb,
                                                              const float* __restrict__ params,
-                                                             const float* __restrict__ norm, double* __restrict__ P0) {
+                                                             const float* __restrict__ norm, double* __restrict__ P0,
+                                                             const double* __restrict__ gc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smraw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -529,8 +530,16 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
       if (z < N) {
 #pragma unroll
         for (int a = 0; a < NV; a++) xf[a] = __ldg(feat + a * N + z);
+        if (gc) {  // the zone's g_{mu nu} from the centre table of a general metric
+          const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+          const int zi = (int)(z % p.n1), zj = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
+          const double* gz = gc + (long long)(zj + 1) * (p.n1 + 2) + (zi + 1);
 #pragma unroll
-        for (int a = 0; a < 10; a++) xf[NV + a] = g[a];
+          for (int a = 0; a < 10; a++) xf[NV + a] = (float)__ldg(gz + a * nc);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 10; a++) xf[NV + a] = g[a];
+        }
 #pragma unroll
         for (int a = 0; a < NV; a++) {
           const double x = __ldg(Pn + a * N + z);
@@ -858,8 +867,10 @@ cudaError_t launch_mlp_features(const Params& p, const double* K, const double* 
   return cudaGetLastError();
 }
 
+// gc: the centre geometry table of a general metric (its first ten planes
+// are g_{mu nu}), or NULL for Minkowski space.
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
-                             cudaStream_t st) {
+                             const double* gc, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(mlp_guess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(InferSmem));
@@ -872,7 +883,8 @@ cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* P
   long long tiles = (p.N + 16 * INF_WARPS - 1) / (16 * INF_WARPS);
   long long grid = sms;  // persistent: one block (and one copy of the weights) per SM
   if (grid > tiles) grid = tiles;
-  mlp_guess<<<(unsigned)grid, INF_WARPS * 32, sizeof(InferSmem), st>>>(p, feat, Pn, m->wb, m->params, m->norm, P0);
+  mlp_guess<<<(unsigned)grid, INF_WARPS * 32, sizeof(InferSmem), st>>>(p, feat, Pn, m->wb, m->params, m->norm, P0,
+                                                                        gc);
   return cudaGetLastError();
 }
 }  // namespace grim

@@ -779,10 +779,13 @@ __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], con
   }
 }
 
-// rq, rs: the zone's residual slot for the queue, as in newton_zone.
+// rq, rs: the zone's residual slot for the queue; Pfb, accept_bits,
+// fellback: the plain start of a learned start; both as in newton_zone.
 template <bool MIXED, int BS>
 __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const float* kf, const double* md,
-                                     double P[NV], void* jac, int k0, int kstop, double* rq, long long rs) {
+                                     double P[NV], void* jac, int k0, int kstop, double* rq, long long rs,
+                                     const double* Pfb, long long fb_stride, unsigned long long accept_bits,
+                                     bool& fellback) {
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
   const RC<double> c64 = make_rc<double>(p);
   const KSm<double, BS> k64{kd};
@@ -799,6 +802,23 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
     o.evals64++;
   }
   double f = sum_sq10(r);
+  fellback = false;
+  if (Pfb && !(max_abits10(r) <= accept_bits)) {
+    double Pp[NV], rp[NV];
+#pragma unroll
+    for (int a = 0; a < NV; a++) Pp[a] = (a >= 5 && a <= 7) ? P[a] : Pfb[a * fb_stride];
+    ZG<double> zp;
+    zg_load(zp, Pp, m64, c64);
+    r_all_gr(zp, k64, rp);
+    o.evals64++;
+    const double fp = sum_sq10(rp);
+    if (!(f <= fp)) {
+      fellback = true;
+#pragma unroll
+      for (int a = 0; a < NV; a++) { P[a] = Pp[a]; r[a] = rp[a]; }
+      f = fp;
+    }
+  }
   int k = k0;
   for (;;) {
     if (!finite_bits(f)) { o.status |= ST_NONFINITE; break; }
@@ -908,7 +928,8 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
                                                       const double* __restrict__ gc, double* __restrict__ P,
                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
                                                       Counters* __restrict__ cnt, int kstop, int* __restrict__ queue,
-                                                      int* __restrict__ qcount, double* __restrict__ rq) {
+                                                      int* __restrict__ qcount, double* __restrict__ rq,
+                                                      const double* __restrict__ Pfb, double accept) {
   using S = NewtonSmemGr<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -919,20 +940,22 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
   const long long z = (long long)blockIdx.x * BS + threadIdx.x;
   const bool active = z < N;
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
+  bool fellback = false;
   if (active) {
     load_zone_gr<MIXED, BS>(p, K, gc, z, kd, kf, md);
     double Pz[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
     o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax,
-                                  queue && rq ? rq + z : nullptr, N);
+                                  queue && rq ? rq + z : nullptr, N, Pfb ? Pfb + z : nullptr, N, abits(accept),
+                                  fellback);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
     status[z] = (uint8_t)o.status;
   }
   if (queue) enqueue(queue, qcount, active && o.pending, z);
-  accumulate(cnt, o, active, false);
+  accumulate(cnt, o, active, fellback);
 }
 
 template <bool MIXED, int BS>
@@ -959,7 +982,9 @@ __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Pa
       double Pz[NV];
 #pragma unroll
       for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-      o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, iters[z], p.kmax, rq ? rq + z : nullptr, N);
+      bool fb = false;
+      o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, iters[z], p.kmax, rq ? rq + z : nullptr, N, nullptr, N,
+                                    0ull, fb);
 #pragma unroll
       for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
       iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -1026,7 +1051,7 @@ template <bool MIXED, int BS> struct NewtonKernelsGr {
   }
   static cudaError_t launch(const Params& p, const double* K, const double* gc, double* P, uint8_t* iters,
                             uint8_t* status, Counters* cnt, int kcut, int* queue, int* qcount, double* rq,
-                            cudaStream_t st) {
+                            const double* Pfb, double accept, cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
@@ -1035,7 +1060,7 @@ template <bool MIXED, int BS> struct NewtonKernelsGr {
     const long long nb = (p.N + BS - 1) / BS;
     newton_dense_gr<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
                                                                     compact ? kcut : p.kmax,
-                                                                    compact ? queue : nullptr, qcount, rq);
+                                                                    compact ? queue : nullptr, qcount, rq, Pfb, accept);
     if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
     newton_queue_gr<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt, queue,
                                                                       qcount, rq);
@@ -1044,17 +1069,82 @@ template <bool MIXED, int BS> struct NewtonKernelsGr {
 };
 
 // Newton solves of one stage in a general metric (block size 32 or 64).
-// rq: as in launch_newton_fb.
+// rq, Pfb, accept: as in launch_newton_fb.
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, cudaStream_t st) {
+                             int* qcount, double* rq, const double* Pfb, double accept, cudaStream_t st) {
   const bool b32 = cfg.bs == 32;
   if (mixed) {
-    if (b32) return NewtonKernelsGr<true, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
-    return NewtonKernelsGr<true, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
+    if (b32)
+      return NewtonKernelsGr<true, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
+                                               accept, st);
+    return NewtonKernelsGr<true, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
+                                             accept, st);
   }
-  if (b32) return NewtonKernelsGr<false, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
-  return NewtonKernelsGr<false, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, st);
+  if (b32)
+    return NewtonKernelsGr<false, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
+                                              accept, st);
+  return NewtonKernelsGr<false, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
+                                            accept, st);
+}
+
+// Learned-start features in a general metric, in the flat path's layout:
+// x_a = -r_a(P_n) (the scaled residual of the stage at its start, from the
+// stage constants K), the zone's g_{mu nu} (10, packed), P_n (10), two
+// zeros.  X (row-major [N][32]) and, with Y, the targets P_conv - P_n of
+// the predicted fields ([N][16]) for training; or the ten x_a alone into
+// feat ([10][N]) for inference.
+__global__ void features_gr(const __grid_constant__ Params p, const double* __restrict__ K,
+                            const double* __restrict__ gc, const double* __restrict__ Pn,
+                            const double* __restrict__ Pc, float* __restrict__ X, float* __restrict__ Y,
+                            float* __restrict__ feat) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const KGl kg{K + z, N};
+  const RC<double> c = make_rc<double>(p);
+  const int i = (int)(z % p.n1), j = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
+  const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+  const double* g = gc + (long long)(j + 1) * (p.n1 + 2) + (i + 1);
+  Met<double> m;
+#pragma unroll
+  for (int a = 0; a < 10; a++) m.gcov[a] = __ldg(g + (G_COV + a) * nc);
+  m.alpha = __ldg(g + G_ALPHA * nc);
+#pragma unroll
+  for (int q = 0; q < 3; q++) m.gti[q] = __ldg(g + (G_CON + sym(0, q + 1)) * nc);
+  double P[NV], r[NV];
+#pragma unroll
+  for (int a = 0; a < NV; a++) P[a] = __ldg(Pn + a * N + z);
+  ZG<double> zz;
+  zg_load(zz, P, m, c);
+  r_all_gr(zz, kg, r);
+  if (feat) {
+#pragma unroll
+    for (int a = 0; a < NV; a++) feat[a * N + z] = (float)(-r[a]);
+  }
+  if (X) {
+    float* x = X + z * 32;
+#pragma unroll
+    for (int a = 0; a < NV; a++) {
+      x[a] = (float)(-r[a]);
+      x[NV + a] = (float)m.gcov[a];
+      x[2 * NV + a] = (float)P[a];
+    }
+    x[30] = 0.f;
+    x[31] = 0.f;
+    if (Y) {
+      float* y = Y + z * 16;
+#pragma unroll
+      for (int o = 0; o < 16; o++)
+        y[o] = (o < NV && !(o >= 5 && o <= 7)) ? (float)(__ldg(Pc + o * N + z) - P[o]) : 0.f;
+    }
+  }
+}
+
+cudaError_t launch_features_gr(const Params& p, const double* K, const double* gc, const double* Pn, const double* Pc,
+                               float* X, float* Y, float* feat, cudaStream_t st) {
+  features_gr<<<(unsigned)((p.N + 127) / 128), 128, 0, st>>>(p, K, gc, Pn, Pc, X, Y, feat);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,

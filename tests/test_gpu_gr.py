@@ -240,3 +240,89 @@ def test_gr_odd_grids_minkowski(dev, orc, shape):
     assert st.max() == 0 and g.stats()["failed"] == 0
     assert rel_field_err(out.cpu().numpy(), ref).max() < 1e-12
     g.close()
+
+
+def test_gr_learned_start_equals_reference_prediction(dev):
+    """The learned start in a general metric (the torus, floors off): with
+    k_max = 0 a stage returns its start, P_n + the network's output on the
+    stage's features (the residual at P_n, the zone's g_{mu nu}, P_n), with
+    the magnetic components from flux-CT.  The few atmosphere zones whose
+    start is inadmissible (u ~ 1e-10 there) fall back to P_n; the rest
+    carry the prediction."""
+    from paper_1702_01106_b300.grim import MLP, Grim
+    from oracle import mlp_ref
+    prob, P = _torus(20, 16, 1)
+    prob = prob.with_(k_max=0, floors=False)
+    a = _t(P, dev)
+    out = torch.empty_like(a)
+    dts = 0.5 * inputs.torus_dt(prob)
+    g = Grim(prob, precision=1)
+    g.stage(a, a, dts, out)                      # the stage's constants, plain start
+    X = torch.empty((prob.zones, 32), dtype=torch.float32, device=dev)
+    g.mlp_sample(a, None, X)
+    Xh = X.cpu().numpy()
+    assert np.ptp(Xh[:, 10:20], axis=0).max() > 0   # the metric varies over the torus
+    m = MLP(seed=7)
+    params, _ = m.get_params()
+    norm = np.zeros(96, np.float32)
+    norm[:32] = Xh.mean(axis=0)
+    norm[32:64] = np.maximum(Xh.std(axis=0), 1e-6)
+    norm[80:96] = 1e-9    # small corrections keep every start admissible
+    m.set_params(params, norm)
+    g.set_guess(m, accept=1e30)
+    g.reset_stats()
+    g.stage(a, a, dts, out)
+    nfb = g.stats()["fallbacks"]
+    pred = mlp_ref.predict(params, norm, Xh, bf16_round=True)
+    got = out.cpu().numpy().reshape(10, -1)
+    Pn = P.reshape(10, -1)
+    fields = [0, 1, 2, 3, 4, 8, 9]
+    kept = ~np.all(got[fields] == Pn[fields], axis=0)
+    assert (~kept).sum() == nfb and nfb <= 0.02 * prob.zones, nfb
+    for o in fields:
+        scale = np.abs(pred[kept, o]).max() + 1e-30
+        diff = np.abs(got[o, kept] - Pn[o, kept] - pred[kept, o]) / scale
+        assert diff.max() <= 3e-2, o
+        assert np.median(diff) <= 3e-3, o
+    g.close()
+    m.close()
+
+
+def test_gr_trained_guess_keeps_the_answer(dev, orc):
+    """Trained on converged stages of a small 3-D torus, the learned start
+    leaves the answer where the plain start puts it: the Newton updates stay
+    within a tenth of the plain start's, as few zones fail (torus-surface
+    zones without an admissible root), and the result stays within 1e-9 of
+    the oracle (sampled zones inside the torus).  On this grid the learned
+    start does not save updates (the benchmark reports the full-size
+    torus)."""
+    from paper_1702_01106_b300 import guess
+    from paper_1702_01106_b300.grim import Grim, GRIM_MIXED
+    prob, P = _torus(24, 24, 8, tol=1e-12)   # as test_gr_step_3d_kerr's mixed case
+    dt = inputs.torus_dt(prob)
+    X, Y, P1 = guess.collect(prob, P, dt, 4, dev)
+    P1 = P1.cpu().numpy()
+    m, losses = guess.train(X, Y, steps=4000)
+    assert losses[-1] < 0.9 * losses[0]
+    iters, outs, fails = {}, {}, {}
+    for learned in (False, True):
+        g = Grim(prob, precision=GRIM_MIXED)
+        if learned:
+            g.set_guess(m, accept=1e-3)
+        a = torch.from_numpy(P1).to(dev)
+        out = torch.empty_like(a)
+        g.step(a, out, dt)
+        s = g.stats()
+        assert s["failed"] <= 0.02 * s["zones"], s
+        iters[learned] = s["iters"] / s["zones"]
+        fails[learned] = s["failed"]
+        outs[learned] = out.cpu().numpy()
+        g.close()
+    assert iters[True] < iters[False] + 0.1, iters
+    assert fails[True] <= fails[False] + 0.005 * prob.zones, fails
+    rho = P1.reshape(10, -1)[0]
+    inside = np.nonzero(rho > 0.05 * rho.max())[0]
+    zs = np.random.default_rng(10).choice(inside, 48, replace=False)
+    ref, _, _, _ = orc.step_sampled(prob.with_(tol=1e-14), P1, dt, zs)
+    assert rel_field_err(outs[True].reshape(10, -1)[:, zs], ref).max() < 1e-9
+    m.close()
