@@ -360,16 +360,29 @@ def bench_batched(dev, mlp, torch, world, steps=3):
 def bench_kerr(dev, torch, world, steps=3, warmup=2):
     """3-D Fishbone-Moncrief torus around a Kerr black hole (a = 0.9375,
     modified Kerr-Schild, 192 x 192 x 128, floors on), dt fixed at CFL 0.5 of
-    the light-speed bound: zone-updates/s of the float64 and mixed arms."""
-    from paper_1702_01106_b300 import inputs
+    the light-speed bound: zone-updates/s of the float64 and mixed arms, and
+    of the mixed arm with a learned start trained (untimed) on both stages
+    of the first four float64 steps (8 stages of 4.7 M zones)."""
+    from paper_1702_01106_b300 import inputs, guess
     from paper_1702_01106_b300.grim import Grim, GRIM_FP64, GRIM_MIXED
     prob = inputs.torus_problem(192, 192, 128)
     P = torch.from_numpy(inputs.torus_state(prob))
     dt = inputs.torus_dt(prob)
     out = {"workload": "3-D Kerr torus a=0.9375 MKS 192x192x128, FM r_in=6 r_max=12, beta=100, floors, tol 1e-10",
            "zones": prob.zones, "dt": dt, "steps": steps}
-    for name, prec in (("fp64", GRIM_FP64), ("mixed", GRIM_MIXED)):
+    t0 = time.perf_counter()
+    X, Y, _ = guess.collect(prob, P.numpy(), dt, 4, dev)
+    mlp, losses = guess.train(X, Y, steps=MLP_TRAIN_STEPS)
+    torch.cuda.synchronize()
+    out["learned_training"] = {"samples": int(X.shape[0]), "adam_steps": MLP_TRAIN_STEPS,
+                               "loss_per_quarter": losses, "seconds": time.perf_counter() - t0}
+    del X, Y
+    torch.cuda.empty_cache()
+    for name, prec, learned in (("fp64", GRIM_FP64, False), ("mixed", GRIM_MIXED, False),
+                                ("mixed_learned", GRIM_MIXED, True)):
         g = Grim(prob, precision=prec)
+        if learned:
+            g.set_guess(mlp, accept=1e-3)
         a = P.to(dev)
         b = torch.empty_like(a)
         for _ in range(warmup):
@@ -393,13 +406,15 @@ def bench_kerr(dev, torch, world, steps=3, warmup=2):
         kt = g.kernel_times()
         out[name] = {"value": aggregate_rate(prob.zones, ms * 1e-3, world), "ms_per_step": ms,
                      "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]), "failed": s["failed"],
-                     "max_res": s["max_res"],
+                     "max_res": s["max_res"], "fallbacks": s["fallbacks"],
                      # per stage (zone_const: derived + sources + stage constants, and the floors)
                      "kernel_ms_per_stage": {k: v[0] / (2 * steps) for k, v in kt.items()}}
         g.close()
         del a, b
         torch.cuda.empty_cache()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed_learned"]["ms_per_step"]
+    mlp.close()
     return out
 
 
