@@ -41,6 +41,7 @@ MLP_SAMPLE_STRIDE = 6     # training stages from every 6th of the first 48 steps
 NCU_TRAFFIC_BYTES = {"faces": 296.6e6, "zone_const": None, "newton64": 428.0e6, "newton32": 424.9e6,
                      "mlp": 158.0e6}
 TOL = 1e-10
+KERR_OUTLIER_LIMIT = 50.0  # training rows of the torus kept within this many robust deviations
 
 
 def read_flop_counts():
@@ -372,9 +373,12 @@ def bench_kerr(dev, torch, world, steps=3, warmup=2):
            "zones": prob.zones, "dt": dt, "steps": steps}
     t0 = time.perf_counter()
     X, Y, _ = guess.collect(prob, P.numpy(), dt, 4, dev)
+    n_all = int(X.shape[0])
+    X, Y = guess.drop_outliers(X, Y, KERR_OUTLIER_LIMIT)
     mlp, losses = guess.train(X, Y, steps=MLP_TRAIN_STEPS)
     torch.cuda.synchronize()
-    out["learned_training"] = {"samples": int(X.shape[0]), "adam_steps": MLP_TRAIN_STEPS,
+    out["learned_training"] = {"samples": int(X.shape[0]), "samples_before_outliers": n_all,
+                               "outlier_limit_robust_devs": KERR_OUTLIER_LIMIT, "adam_steps": MLP_TRAIN_STEPS,
                                "loss_per_quarter": losses, "seconds": time.perf_counter() - t0}
     del X, Y
     torch.cuda.empty_cache()

@@ -38,6 +38,26 @@ def collect(prob, P, dt: float, steps: int, device, tol: float = 1e-12, stride: 
     return X, Y, a
 
 
+def drop_outliers(X, Y, limit: float, sample: int = 1 << 20, seed: int = 1):
+    """Rows of (X, Y) whose every feature and target lies within `limit`
+    robust deviations (1.4826 x the median absolute deviation, over a seeded
+    sample of rows) of its column's median.  Zones far outside the bulk (the
+    surface of a torus, whose stage residuals reach 1e3) would otherwise set
+    the standardisation and leave the bulk's features below bfloat16
+    resolution; at run time such zones fall back to the plain start."""
+    g = torch.Generator(device=X.device).manual_seed(seed)
+    idx = torch.randint(0, X.shape[0], (min(sample, X.shape[0]),), device=X.device, generator=g)
+    keep = torch.ones(X.shape[0], dtype=torch.bool, device=X.device)
+    for A in (X, Y):
+        S = A[idx].double()
+        med = S.median(dim=0).values
+        mad = (S - med).abs().median(dim=0).values * 1.4826
+        live = mad > 0
+        dev = ((A.double() - med).abs() / torch.where(live, mad, torch.ones_like(mad)))[:, live]
+        keep &= (dev <= limit).all(dim=1)
+    return X[keep].contiguous(), Y[keep].contiguous()
+
+
 def train(X, Y, steps: int = 6000, batch: int = 4096, lr: float = 3e-3, halvings: int = 3, seed: int = 1):
     """A freshly initialised MLP trained with Adam; the learning rate halves
     `halvings` times at equal intervals.  Returns (mlp, losses per interval)."""
