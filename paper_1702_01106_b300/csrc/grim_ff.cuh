@@ -1,10 +1,10 @@
 // Float-float arithmetic: a value is the unevaluated sum hi + lo of two
-// floats (about 48 significant bits, rounding ~2^-47 of the operands), built from
-// error-free transformations (Knuth's two-sum, Dekker's split via FMA).  On
-// B300 a float-float operation costs 4-20 float32 instructions on a pipe 64
-// times wider than the float64 one, so face states and fluxes evaluated this
-// way cost a fraction of their float64 time at an accuracy far below the
-// solver tolerances.
+// floats (about 48 significant bits, rounding ~2^-47 of the operands), built
+// from error-free transformations (Knuth's two-sum; the exact product error
+// by FMA, as in Dekker's product).  On B300 a float-float operation costs
+// 4-11 float32 instructions on a pipe 64 times wider than the float64 one,
+// so face states and fluxes evaluated this way cost a fraction of their
+// float64 time at an accuracy far below the solver tolerances.
 #pragma once
 #include <cuda_runtime.h>
 #include <type_traits>
@@ -21,8 +21,6 @@ struct ff {
   }
   __device__ __forceinline__ explicit ff(int i) : hi((float)i), lo(0.f) {}
 };
-
-__device__ __forceinline__ double to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
 // A compile-time constant in the working precision (for float-float: the
 // pair of the nearest float and the float nearest to the remainder), so that
