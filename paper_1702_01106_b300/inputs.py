@@ -47,7 +47,10 @@ class Problem:
     psi: float = 1.0
     tau_R: float = 1.0
     tol: float = 1e-10
-    eps_fd: float = 2.0 ** -26
+    # Section 3.1's epsilon for the float64 Jacobian: relative perturbations at
+    # |P_j| >= 5 eps, so the smallest step is 5 eps^2 (1.1e-12 here), well
+    # above the residual's rounding
+    eps_fd: float = 2.0 ** -21
     k_max: int = 30
     ls_max: int = 10
     spin: float = 0.0

@@ -183,9 +183,33 @@ def test_fd_jacobian_matches_complex_step(orc):
         Jfd = orc.zone_jacobian(prob, zc, P, "fd")
         Jcs = orc.zone_jacobian(prob, zc, P, "cs")
         scale = np.abs(Jcs).max()
-        assert np.abs(Jfd - Jcs).max() < 1e-6 * scale
+        # one-sided differences: truncation error O(eps) of the column scale
+        assert np.abs(Jfd - Jcs).max() < 8 * prob.eps_fd * scale
         # the magnetic rows depend only on B (and linearly)
         assert np.all(Jcs[5:8, :5] == 0) and np.all(Jcs[5:8, 8:] == 0)
+
+
+def test_fd_column_of_a_small_component(orc):
+    """small() (Section 3.1) perturbs a component just above 5 eps by eps of
+    itself, i.e. by 5 eps^2: with the default eps that column still stands
+    far enough above the residual's rounding to match the complex-step
+    column to 1e-4 of the Jacobian's scale (at eps = 2^-26 the same columns
+    were off by 1-2 % of it)."""
+    prob = inputs.linear_mode_problem(8)
+    eps = prob.eps_fd
+    rng = np.random.default_rng(13)
+    for sgn in (1.0, -1.0):
+        Pn = random_zone_state(rng)
+        Pn[8] = sgn * 6 * eps
+        Pn[9] = -sgn * 6 * eps
+        PE = Pn.copy()
+        zc = zone_vector(orc, prob, Pn, PE, 0.01, divF=rng.normal(0, 0.1, 10),
+                         dTh=np.r_[0, rng.normal(0, 0.1, 3)], du=np.vstack([np.zeros(4), rng.normal(0, 0.1, (3, 4))]),
+                         divu=0.05)
+        Jfd = orc.zone_jacobian(prob, zc, Pn, "fd")
+        Jcs = orc.zone_jacobian(prob, zc, Pn, "cs")
+        scale = np.abs(Jcs).max()
+        assert np.abs(Jfd[:, 8:] - Jcs[:, 8:]).max() < 1e-4 * scale
 
 
 def test_complex_step_matches_central_differences(orc):
