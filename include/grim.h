@@ -78,7 +78,12 @@ typedef struct {
 
 /* Physics (Section 4): gamma-law gas, closure chi = phi c_s^2 tau_R,
  * nu = psi c_s^2 tau_R, switches for conduction, viscosity and the
- * higher-order terms of Eqs. q_evol_eqn_rescaled and dP_evol_eqn_rescaled. */
+ * higher-order terms of Eqs. q_evol_eqn_rescaled and dP_evol_eqn_rescaled.
+ * Each zone's Newton update solves the 7x7 block of rho, u, u^i, q~, dP~
+ * (B is explicit, Section 8.2); with conduction and viscosity both off
+ * (ideal MHD), a zone whose q~, dP~ and their residual rows are zero solves
+ * the 5x5 block of rho, u, u^i: the same root at 5 instead of 7 Jacobian
+ * columns. */
 typedef struct {
   double gamma, tau_R, phi, psi;
   int conduction, viscosity, higher_order;

@@ -163,35 +163,50 @@ __device__ __forceinline__ void fd_column(const Z<T>& z, const T r[NV], const KA
 // formed: the B rows are linear in B alone (r_B = kU_B B + kC_B) and the
 // start already holds their root, the flux-CT field, so the Newton update of
 // B is zero to round-off and the system reduces to the 7x7 block of the
-// other components (the paper's EMHD solve, Section 8.2).
+// other components (the paper's EMHD solve, Section 8.2).  five: ideal MHD
+// (see ideal_zone), where the q~ and dP~ columns are not formed either and
+// the block is 5x5.
 template <typename T, bool CENTRAL, int BS, class KA>
 __device__ __forceinline__ void fd_jacobian(const Z<T>& z, const T r[NV], const KA& k, const RC<T>& c, T eps,
-                                            T* J) {
+                                            T* J, bool five = false) {
   fd_column<0, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<1, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<2, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<3, CENTRAL, T, BS>(z, r, k, c, eps, J);
   fd_column<4, CENTRAL, T, BS>(z, r, k, c, eps, J);
-  fd_column<8, CENTRAL, T, BS>(z, r, k, c, eps, J);
-  fd_column<9, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  if (!five) {
+    fd_column<8, CENTRAL, T, BS>(z, r, k, c, eps, J);
+    fd_column<9, CENTRAL, T, BS>(z, r, k, c, eps, J);
+  }
+}
+
+// Ideal MHD (conduction and viscosity off, Section 8.2's 5x5 solve): in a
+// zone whose q~ and dP~ and their residual rows are zero, those rows stay
+// exactly zero for any rho, u, u^i (every term of them carries q~, dP~ or a
+// closure coefficient), so their Newton update is zero and the system
+// reduces to the 5x5 block of rho, u, u^i.  Other zones keep the 7x7 block.
+__device__ __forceinline__ bool ideal_zone(const Params& p, const double P[NV], const double r[NV]) {
+  return !p.cond && !p.visc && P[8] == 0.0 && P[9] == 0.0 && r[8] == 0.0 && r[9] == 0.0;
 }
 
 // Index of the m-th non-magnetic component (rho, u, u^1..3, q~, dP~).
 __host__ __device__ constexpr int nb7(int m) { return m < 5 ? m : m + 3; }
 
-// Partial-pivot LU solve of the 7x7 non-magnetic block of J (rows and columns
-// nb7(0..6) of the 10x10 layout in shared memory, stride BS); x[5..7] = 0.
+// Partial-pivot LU solve of the NB x NB block of J (NB = 7: rows and columns
+// nb7(0..6), the non-magnetic components; NB = 5: rho, u, u^i) in the 10x10
+// layout in shared memory, stride BS; the other components of x are 0.
 // Pivot: largest |a_ik|, lowest row on ties.  Returns false on a zero pivot.
-template <typename T, int BS>
-__device__ __forceinline__ bool lu_solve7_smem(T* J, T* b, T x[NV]) {
-  T inv[7];
+template <typename T, int BS, int NB = 7>
+__device__ __forceinline__ bool lu_solve_block_smem(T* J, T* b, T x[NV]) {
+  static_assert(NB == 7 || NB == 5, "7x7 or 5x5 block");
+  T inv[NB];
 #pragma unroll
-  for (int k = 0; k < 7; k++) {
+  for (int k = 0; k < NB; k++) {
     const int kk = nb7(k);
     int piv = k;
     auto best = abits(J[(kk * NV + kk) * BS]);
 #pragma unroll
-    for (int i = k + 1; i < 7; i++) {
+    for (int i = k + 1; i < NB; i++) {
       const auto a = abits(J[(nb7(i) * NV + kk) * BS]);
       if (a > best) { best = a; piv = i; }
     }
@@ -199,7 +214,7 @@ __device__ __forceinline__ bool lu_solve7_smem(T* J, T* b, T x[NV]) {
     if (piv != k) {
       const int pp = nb7(piv);
 #pragma unroll
-      for (int c = k; c < 7; c++) {
+      for (int c = k; c < NB; c++) {
         const int cc = nb7(c);
         const T t = J[(kk * NV + cc) * BS];
         J[(kk * NV + cc) * BS] = J[(pp * NV + cc) * BS];
@@ -212,23 +227,24 @@ __device__ __forceinline__ bool lu_solve7_smem(T* J, T* b, T x[NV]) {
     inv[k] = nr_rcp(J[(kk * NV + kk) * BS]);
     const T bk = b[kk * BS];
 #pragma unroll
-    for (int i = k + 1; i < 7; i++) {
+    for (int i = k + 1; i < NB; i++) {
       const int ii = nb7(i);
       const T a = J[(ii * NV + kk) * BS];
       if (abits(a) == 0) continue;  // zero multiplier: row i is unchanged
       const T l = a * inv[k];
 #pragma unroll
-      for (int c = k + 1; c < 7; c++) J[(ii * NV + nb7(c)) * BS] -= l * J[(kk * NV + nb7(c)) * BS];
+      for (int c = k + 1; c < NB; c++) J[(ii * NV + nb7(c)) * BS] -= l * J[(kk * NV + nb7(c)) * BS];
       b[ii * BS] -= l * bk;
     }
   }
   x[5] = x[6] = x[7] = T(0);
+  if (NB == 5) x[8] = x[9] = T(0);
 #pragma unroll
-  for (int i = 6; i >= 0; i--) {
+  for (int i = NB - 1; i >= 0; i--) {
     const int ii = nb7(i);
     T acc = b[ii * BS];
 #pragma unroll
-    for (int c = i + 1; c < 7; c++) acc -= J[(ii * NV + nb7(c)) * BS] * x[nb7(c)];
+    for (int c = i + 1; c < NB; c++) acc -= J[(ii * NV + nb7(c)) * BS] * x[nb7(c)];
     x[ii] = acc * inv[i];
   }
   return true;
@@ -313,7 +329,7 @@ struct ZoneResult {
 // the zone's residual slot for the queue: a call that stops pending stores
 // r(P) there, and a resumed call (k0 > 0) reads it instead of evaluating it
 // again.
-template <bool MIXED, int BS>
+template <bool MIXED, int BS, bool IDEAL>
 __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double* kd, const float* kf, double P[NV],
                                                   void* jac, const double* Pfb, long long fb_stride,
                                                   unsigned long long accept_bits, bool& fellback, int k0,
@@ -352,6 +368,7 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       f = fp;
     }
   }
+  const bool five = IDEAL && ideal_zone(p, P, r);
   int k = k0;
   for (;;) {
     if (!finite_bits(f)) { o.status |= ST_NONFINITE; break; }
@@ -363,11 +380,11 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
     if (!MIXED) {
       double* J = (double*)jac + threadIdx.x;
       double* b = J + NV * NV * BS;
-      fd_jacobian<double, false, BS>(z, r, k64, c64, p.eps64, J);
-      o.evals64 += 7;
+      fd_jacobian<double, false, BS>(z, r, k64, c64, p.eps64, J, five);
+      o.evals64 += five ? 5 : 7;
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
-      ok = lu_solve7_smem<double, BS>(J, b, dP);
+      ok = five ? lu_solve_block_smem<double, BS, 5>(J, b, dP) : lu_solve_block_smem<double, BS, 7>(J, b, dP);
       o.lu64++;
     } else {
       const RC<float> c32 = make_rc<float>(p);
@@ -380,17 +397,18 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       Z<float> zf;
       z_load(zf, Pf, c32);
       r_all(zf, k32, rf);
+      const int ncol = five ? 5 : 7;
       if (p.fd32c) {
-        fd_jacobian<float, true, BS>(zf, rf, k32, c32, p.eps32, J);
-        o.evals32 += 2 * 7 + 1;
+        fd_jacobian<float, true, BS>(zf, rf, k32, c32, p.eps32, J, five);
+        o.evals32 += 2 * ncol + 1;
       } else {
-        fd_jacobian<float, false, BS>(zf, rf, k32, c32, p.eps32, J);
-        o.evals32 += 7 + 1;
+        fd_jacobian<float, false, BS>(zf, rf, k32, c32, p.eps32, J, five);
+        o.evals32 += ncol + 1;
       }
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = d2f_jac(-r[i]);
       float df[NV];
-      ok = lu_solve7_smem<float, BS>(J, b, df);
+      ok = five ? lu_solve_block_smem<float, BS, 5>(J, b, df) : lu_solve_block_smem<float, BS, 7>(J, b, df);
 #pragma unroll
       for (int i = 0; i < NV; i++) dP[i] = f2d_jac(df[i]);
       o.lu32++;
@@ -487,7 +505,7 @@ template <bool MIXED, int BS> struct NewtonSmem {
 // One thread per zone, zones in order; each zone runs to convergence or to
 // kstop updates, after which it is appended to the queue (kstop >= k_max:
 // no queue).
-template <bool MIXED, int BS>
+template <bool MIXED, int BS, bool IDEAL>
 __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Params p, const double* __restrict__ K,
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
@@ -514,7 +532,7 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
     double Pz[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-    o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, Pfb ? Pfb + z : nullptr, N, abits(accept), fellback, 0,
+    o = newton_zone<MIXED, BS, IDEAL>(p, kd, kf, Pz, jac, Pfb ? Pfb + z : nullptr, N, abits(accept), fellback, 0,
                                kstop < p.kmax ? kstop : p.kmax, queue && rq ? rq + z : nullptr, N);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
@@ -528,7 +546,7 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
 // The zones queued by newton_dense, packed densely into warps: a persistent
 // grid strides over the queue and continues each zone from its state and
 // update count to convergence or k_max.
-template <bool MIXED, int BS>
+template <bool MIXED, int BS, bool IDEAL>
 __global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Params p, const double* __restrict__ K,
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
@@ -557,7 +575,7 @@ __global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Param
       double Pz[NV];
 #pragma unroll
       for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-      o = newton_zone<MIXED, BS>(p, kd, kf, Pz, jac, nullptr, N, 0ull, fellback, iters[z], p.kmax,
+      o = newton_zone<MIXED, BS, IDEAL>(p, kd, kf, Pz, jac, nullptr, N, 0ull, fellback, iters[z], p.kmax,
                                  rq ? rq + z : nullptr, N);
 #pragma unroll
       for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
@@ -604,21 +622,22 @@ __global__ void rcp_check(int n, unsigned long long seed, double* worst) {
   atomicMax((unsigned long long*)worst, (unsigned long long)__double_as_longlong(rel));
 }
 
-template <bool MIXED, int BS> struct NewtonKernels {
+template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
   using S = NewtonSmem<MIXED, BS>;
   static cudaError_t configure(int& qgrid) {
     static bool done = false;
     static int grid = 0;
     if (!done) {
-      cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)S::bytes);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(newton_queue<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+        e = cudaFuncSetAttribute(newton_queue<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)S::bytes);
       int dev = 0, sms = 0, per_sm = 0;
       if (e == cudaSuccess) e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue<MIXED, BS>, BS, S::bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue<MIXED, BS, IDEAL>, BS, S::bytes);
       if (e != cudaSuccess) return e;
       grid = sms * (per_sm > 0 ? per_sm : 1);
       done = true;
@@ -635,23 +654,30 @@ template <bool MIXED, int BS> struct NewtonKernels {
     const bool compact = queue && qcount && kcut < p.kmax;
     if (compact && (e = cudaMemsetAsync(qcount, 0, sizeof(int), st)) != cudaSuccess) return e;
     const long long nb = (p.N + BS - 1) / BS;
-    newton_dense<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
+    newton_dense<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
                                                                  compact ? kcut : p.kmax, compact ? queue : nullptr,
                                                                  qcount, rq);
     if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
-    newton_queue<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue, qcount, rq);
+    newton_queue<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue, qcount,
+                                                                        rq);
     return cudaGetLastError();
   }
 };
 
-template <bool MIXED>
+template <bool MIXED, bool IDEAL>
 static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                                    Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
                                    int* qcount, double* rq, cudaStream_t st) {
   switch (cfg.bs) {
-    case 32: return NewtonKernels<MIXED, 32>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, rq, st);
-    case 64: return NewtonKernels<MIXED, 64>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, rq, st);
-    case 128: return NewtonKernels<MIXED, 128>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue, qcount, rq, st);
+    case 32:
+      return NewtonKernels<MIXED, 32, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
+                                                     qcount, rq, st);
+    case 64:
+      return NewtonKernels<MIXED, 64, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
+                                                     qcount, rq, st);
+    case 128:
+      return NewtonKernels<MIXED, 128, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
+                                                      qcount, rq, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -663,8 +689,13 @@ static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P,
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
                              int* qcount, double* rq, cudaStream_t st) {
-  if (mixed) return launch_newton_bs<true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
-  return launch_newton_bs<false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
+  // ideal MHD: the kernels that may take the 5x5 block (ideal_zone)
+  if (!p.cond && !p.visc) {
+    if (mixed) return launch_newton_bs<true, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
+    return launch_newton_bs<false, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
+  }
+  if (mixed) return launch_newton_bs<true, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
+  return launch_newton_bs<false, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
 }
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
@@ -738,11 +769,11 @@ template <typename T, class KA> __device__ __forceinline__ void r_all_gr(const Z
 // (field-like: they enter the stress as squares over rho).
 template <typename T, bool CENTRAL, bool SCALED, int BS, class KA>
 __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], const KA& k, const Met<T>& m,
-                                               const RC<T>& c, T eps, T* J) {
+                                               const RC<T>& c, T eps, T* J, bool five = false) {
   T sfield = T(0);
   if (SCALED) sfield = sqr_root(fabs(P[0]));
 #pragma unroll 1
-  for (int mc = 0; mc < 7; mc++) {  // the non-magnetic columns (7x7 solve, see fd_jacobian)
+  for (int mc = 0; mc < (five ? 5 : 7); mc++) {  // the non-magnetic columns (see fd_jacobian)
     const int col = nb7(mc);
     T Pe[NV];
 #pragma unroll
@@ -781,7 +812,7 @@ __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], con
 
 // rq, rs: the zone's residual slot for the queue; Pfb, accept_bits,
 // fellback: the plain start of a learned start; both as in newton_zone.
-template <bool MIXED, int BS>
+template <bool MIXED, int BS, bool IDEAL>
 __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const float* kf, const double* md,
                                      double P[NV], void* jac, int k0, int kstop, double* rq, long long rs,
                                      const double* Pfb, long long fb_stride, unsigned long long accept_bits,
@@ -819,6 +850,7 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       f = fp;
     }
   }
+  const bool five = IDEAL && ideal_zone(p, P, r);
   int k = k0;
   for (;;) {
     if (!finite_bits(f)) { o.status |= ST_NONFINITE; break; }
@@ -830,11 +862,11 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
     if (!MIXED) {
       double* J = (double*)jac + threadIdx.x;
       double* b = J + NV * NV * BS;
-      fd_jacobian_gr<double, false, false, BS>(P, r, k64, m64, c64, p.eps64, J);
-      o.evals64 += 7;
+      fd_jacobian_gr<double, false, false, BS>(P, r, k64, m64, c64, p.eps64, J, five);
+      o.evals64 += five ? 5 : 7;
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
-      ok = lu_solve7_smem<double, BS>(J, b, dP);
+      ok = five ? lu_solve_block_smem<double, BS, 5>(J, b, dP) : lu_solve_block_smem<double, BS, 7>(J, b, dP);
       o.lu64++;
     } else {
       const RC<float> c32 = make_rc<float>(p);
@@ -848,17 +880,18 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       ZG<float> zf;
       zg_load(zf, Pf, m32, c32);
       r_all_gr(zf, k32, rf);
+      const int ncol = five ? 5 : 7;
       if (p.fd32c) {
-        fd_jacobian_gr<float, true, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J);
-        o.evals32 += 2 * 7 + 1;
+        fd_jacobian_gr<float, true, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J, five);
+        o.evals32 += 2 * ncol + 1;
       } else {
-        fd_jacobian_gr<float, false, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J);
-        o.evals32 += 7 + 1;
+        fd_jacobian_gr<float, false, true, BS>(Pf, rf, k32, m32, c32, p.eps32, J, five);
+        o.evals32 += ncol + 1;
       }
 #pragma unroll
       for (int i = 0; i < NV; i++) b[i * BS] = d2f_jac(-r[i]);
       float df[NV];
-      ok = lu_solve7_smem<float, BS>(J, b, df);
+      ok = five ? lu_solve_block_smem<float, BS, 5>(J, b, df) : lu_solve_block_smem<float, BS, 7>(J, b, df);
 #pragma unroll
       for (int i = 0; i < NV; i++) dP[i] = f2d_jac(df[i]);
       o.lu32++;
@@ -923,7 +956,7 @@ __device__ __forceinline__ void load_zone_gr(const Params& p, const double* K, c
   for (int q = 0; q < 3; q++) md[(11 + q) * BS] = __ldg(g + (G_CON + sym(0, q + 1)) * nc);
 }
 
-template <bool MIXED, int BS>
+template <bool MIXED, int BS, bool IDEAL>
 __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Params p, const double* __restrict__ K,
                                                       const double* __restrict__ gc, double* __restrict__ P,
                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
@@ -946,7 +979,7 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
     double Pz[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
-    o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax,
+    o = newton_zone_gr<MIXED, BS, IDEAL>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax,
                                   queue && rq ? rq + z : nullptr, N, Pfb ? Pfb + z : nullptr, N, abits(accept),
                                   fellback);
 #pragma unroll
@@ -958,7 +991,7 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
   accumulate(cnt, o, active, fellback);
 }
 
-template <bool MIXED, int BS>
+template <bool MIXED, int BS, bool IDEAL>
 __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Params p, const double* __restrict__ K,
                                                       const double* __restrict__ gc, double* __restrict__ P,
                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
@@ -983,7 +1016,8 @@ __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Pa
 #pragma unroll
       for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
       bool fb = false;
-      o = newton_zone_gr<MIXED, BS>(p, kd, kf, md, Pz, jac, iters[z], p.kmax, rq ? rq + z : nullptr, N, nullptr, N,
+      o = newton_zone_gr<MIXED, BS, IDEAL>(p, kd, kf, md, Pz, jac, iters[z], p.kmax, rq ? rq + z : nullptr, N, nullptr,
+                                           N,
                                     0ull, fb);
 #pragma unroll
       for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
@@ -1026,22 +1060,23 @@ __global__ void residual_once_gr(const __grid_constant__ Params p, const double*
   }
 }
 
-template <bool MIXED, int BS> struct NewtonKernelsGr {
+template <bool MIXED, int BS, bool IDEAL> struct NewtonKernelsGr {
   using S = NewtonSmemGr<MIXED, BS>;
   static cudaError_t configure(int& qgrid) {
     static bool done = false;
     static int grid = 0;
     if (!done) {
-      cudaError_t e = cudaFuncSetAttribute(newton_dense_gr<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaError_t e = cudaFuncSetAttribute(newton_dense_gr<MIXED, BS, IDEAL>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)S::bytes);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(newton_queue_gr<MIXED, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(newton_queue_gr<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)S::bytes);
       int dev = 0, sms = 0, per_sm = 0;
       if (e == cudaSuccess) e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue_gr<MIXED, BS>, BS, S::bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue_gr<MIXED, BS, IDEAL>, BS, S::bytes);
       if (e != cudaSuccess) return e;
       grid = sms * (per_sm > 0 ? per_sm : 1);
       done = true;
@@ -1058,11 +1093,11 @@ template <bool MIXED, int BS> struct NewtonKernelsGr {
     const bool compact = queue && qcount && kcut < p.kmax;
     if (compact && (e = cudaMemsetAsync(qcount, 0, sizeof(int), st)) != cudaSuccess) return e;
     const long long nb = (p.N + BS - 1) / BS;
-    newton_dense_gr<MIXED, BS><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
+    newton_dense_gr<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
                                                                     compact ? kcut : p.kmax,
                                                                     compact ? queue : nullptr, qcount, rq, Pfb, accept);
     if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
-    newton_queue_gr<MIXED, BS><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt, queue,
+    newton_queue_gr<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt, queue,
                                                                       qcount, rq);
     return cudaGetLastError();
   }
@@ -1070,22 +1105,33 @@ template <bool MIXED, int BS> struct NewtonKernelsGr {
 
 // Newton solves of one stage in a general metric (block size 32 or 64).
 // rq, Pfb, accept: as in launch_newton_fb.
-cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
-                             uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, const double* Pfb, double accept, cudaStream_t st) {
+template <bool IDEAL>
+static cudaError_t launch_newton_gr_i(const Params& p, int mixed, const double* K, const double* gc, double* P,
+                                     uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg,
+                                     int* queue, int* qcount, double* rq, const double* Pfb, double accept,
+                                     cudaStream_t st) {
   const bool b32 = cfg.bs == 32;
   if (mixed) {
     if (b32)
-      return NewtonKernelsGr<true, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
-                                               accept, st);
-    return NewtonKernelsGr<true, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
-                                             accept, st);
+      return NewtonKernelsGr<true, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+                                                      Pfb, accept, st);
+    return NewtonKernelsGr<true, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+                                                    Pfb, accept, st);
   }
   if (b32)
-    return NewtonKernelsGr<false, 32>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
-                                              accept, st);
-  return NewtonKernelsGr<false, 64>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq, Pfb,
-                                            accept, st);
+    return NewtonKernelsGr<false, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+                                                     Pfb, accept, st);
+  return NewtonKernelsGr<false, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+                                                   Pfb, accept, st);
+}
+
+cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
+                             uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
+                             int* qcount, double* rq, const double* Pfb, double accept, cudaStream_t st) {
+  // ideal MHD: the kernels that may take the 5x5 block (ideal_zone)
+  if (!p.cond && !p.visc)
+    return launch_newton_gr_i<true>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, st);
+  return launch_newton_gr_i<false>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, st);
 }
 
 // Learned-start features in a general metric, in the flat path's layout:
