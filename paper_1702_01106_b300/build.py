@@ -1,7 +1,9 @@
 """Build libgrim.so (all CUDA sources, sm_103a) in the package directory."""
+import concurrent.futures
 import glob
 import os
 import subprocess
+import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -18,11 +20,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
         os.path.join(os.path.dirname(HERE), "include", "grim.h")]
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
         return LIB
-    cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "--expt-relaxed-constexpr", "-o", LIB + ".tmp", *sources()]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.insert(0, "-Xptxas=-v")
+    # one nvcc process per source file, in parallel, then one link
+    with tempfile.TemporaryDirectory() as tmp:
+        objs = [os.path.join(tmp, os.path.basename(src) + ".o") for src in sources()]
+        jobs = [["nvcc", *flags, "-c", src, "-o", obj] for src, obj in zip(sources(), objs)]
+        workers = max(1, min(len(jobs), os.cpu_count() or 1))
+        with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+            for res in ex.map(lambda c: subprocess.run(c, check=False), jobs):
+                if res.returncode != 0:
+                    raise subprocess.CalledProcessError(res.returncode, res.args)
+        subprocess.run(["nvcc", *ARCH, "-shared", "-o", LIB + ".tmp", *objs], check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 
