@@ -88,6 +88,13 @@ template <typename T, class KA> __device__ __forceinline__ void r_all(const Z<T>
   r[9] = r_aniso(z, k);
 }
 
+// The non-magnetic block of the Jacobian: its m-th component is nb7(m)
+// (rho, u, u^1..3, q~, dP~), and component i sits in slot jslot(i) (-1 for
+// B).  Shared memory holds only this NJ x NJ block and its right-hand side.
+constexpr int NJ = 7;
+__host__ __device__ constexpr int nb7(int m) { return m < 5 ? m : m + 3; }
+__host__ __device__ constexpr int jslot(int i) { return i < 5 ? i : (i >= 8 ? i - 3 : -1); }
+
 // Perturbed component of the FD Jacobian (Section 3.1): (1 + eps) x, or
 // x + eps when |x| < 5 eps (small() read as an absolute step, so the divisor
 // never approaches zero).
@@ -134,8 +141,9 @@ template <int C, typename T> __device__ __forceinline__ T component(const Z<T>& 
   else return z.dpt;
 }
 
-// Column C of the FD Jacobian, written to shared memory (element (i, C) at
-// Jc[(i*10 + C)*BS]).  One-sided (Section 3.1):
+// Column C of the FD Jacobian, written to shared memory in the compact 7x7
+// layout of the non-magnetic block (element (i, C) at
+// Jc[(jslot(i)*NJ + jslot(C))*BS]; the B rows are not stored).  One-sided (Section 3.1):
 // J_iC = (r_i(P_eps) - r_i(P)) / (P_eps,C - P_C).  Centred (float32 option):
 // J_iC = (r_i(P + h e_C) - r_i(P - h e_C)) / (2h) with h = P_eps,C - P_C.
 template <int C, bool CENTRAL, typename T, int BS, class KA>
@@ -149,13 +157,15 @@ __device__ __forceinline__ void fd_column(const Z<T>& z, const T r[NV], const KA
   if constexpr (!CENTRAL) {
     const T ih = nr_rcp(h);
 #pragma unroll
-    for (int i = 0; i < NV; i++) Jc[(i * NV + C) * BS] = row_depends<C>(i) ? (rp[i] - r[i]) * ih : T(0);
+    for (int i = 0; i < NV; i++)
+      if (jslot(i) >= 0) Jc[(jslot(i) * NJ + jslot(C)) * BS] = row_depends<C>(i) ? (rp[i] - r[i]) * ih : T(0);
   } else {
     T rm[NV];
     perturbed_rows<C>(z, pj - h, r, k, c, rm);
     const T ih = T(0.5) * nr_rcp(h);
 #pragma unroll
-    for (int i = 0; i < NV; i++) Jc[(i * NV + C) * BS] = row_depends<C>(i) ? (rp[i] - rm[i]) * ih : T(0);
+    for (int i = 0; i < NV; i++)
+      if (jslot(i) >= 0) Jc[(jslot(i) * NJ + jslot(C)) * BS] = row_depends<C>(i) ? (rp[i] - rm[i]) * ih : T(0);
   }
 }
 
@@ -189,112 +199,57 @@ __device__ __forceinline__ bool ideal_zone(const Params& p, const double P[NV], 
   return !p.cond && !p.visc && P[8] == 0.0 && P[9] == 0.0 && r[8] == 0.0 && r[9] == 0.0;
 }
 
-// Index of the m-th non-magnetic component (rho, u, u^1..3, q~, dP~).
-__host__ __device__ constexpr int nb7(int m) { return m < 5 ? m : m + 3; }
 
-// Partial-pivot LU solve of the NB x NB block of J (NB = 7: rows and columns
-// nb7(0..6), the non-magnetic components; NB = 5: rho, u, u^i) in the 10x10
-// layout in shared memory, stride BS; the other components of x are 0.
-// Pivot: largest |a_ik|, lowest row on ties.  Returns false on a zero pivot.
+// Partial-pivot LU solve of the leading NB x NB block of the compact
+// Jacobian (NB = 7: the non-magnetic components nb7(0..6); NB = 5: rho, u,
+// u^i) in shared memory at stride BS, with the right-hand side b in slots
+// 0..NB-1; the other components of x are 0.  Pivot: largest |a_ik|, lowest
+// row on ties.  Returns false on a zero pivot.
 template <typename T, int BS, int NB = 7>
 __device__ __forceinline__ bool lu_solve_block_smem(T* J, T* b, T x[NV]) {
   static_assert(NB == 7 || NB == 5, "7x7 or 5x5 block");
   T inv[NB];
 #pragma unroll
   for (int k = 0; k < NB; k++) {
-    const int kk = nb7(k);
     int piv = k;
-    auto best = abits(J[(kk * NV + kk) * BS]);
+    auto best = abits(J[(k * NJ + k) * BS]);
 #pragma unroll
     for (int i = k + 1; i < NB; i++) {
-      const auto a = abits(J[(nb7(i) * NV + kk) * BS]);
+      const auto a = abits(J[(i * NJ + k) * BS]);
       if (a > best) { best = a; piv = i; }
     }
     if (best == 0) return false;
     if (piv != k) {
-      const int pp = nb7(piv);
 #pragma unroll
       for (int c = k; c < NB; c++) {
-        const int cc = nb7(c);
-        const T t = J[(kk * NV + cc) * BS];
-        J[(kk * NV + cc) * BS] = J[(pp * NV + cc) * BS];
-        J[(pp * NV + cc) * BS] = t;
+        const T t = J[(k * NJ + c) * BS];
+        J[(k * NJ + c) * BS] = J[(piv * NJ + c) * BS];
+        J[(piv * NJ + c) * BS] = t;
       }
-      const T t = b[kk * BS];
-      b[kk * BS] = b[pp * BS];
-      b[pp * BS] = t;
+      const T t = b[k * BS];
+      b[k * BS] = b[piv * BS];
+      b[piv * BS] = t;
     }
-    inv[k] = nr_rcp(J[(kk * NV + kk) * BS]);
-    const T bk = b[kk * BS];
+    inv[k] = nr_rcp(J[(k * NJ + k) * BS]);
+    const T bk = b[k * BS];
 #pragma unroll
     for (int i = k + 1; i < NB; i++) {
-      const int ii = nb7(i);
-      const T a = J[(ii * NV + kk) * BS];
+      const T a = J[(i * NJ + k) * BS];
       if (abits(a) == 0) continue;  // zero multiplier: row i is unchanged
       const T l = a * inv[k];
 #pragma unroll
-      for (int c = k + 1; c < NB; c++) J[(ii * NV + nb7(c)) * BS] -= l * J[(kk * NV + nb7(c)) * BS];
-      b[ii * BS] -= l * bk;
+      for (int c = k + 1; c < NB; c++) J[(i * NJ + c) * BS] -= l * J[(k * NJ + c) * BS];
+      b[i * BS] -= l * bk;
     }
   }
   x[5] = x[6] = x[7] = T(0);
   if (NB == 5) x[8] = x[9] = T(0);
 #pragma unroll
   for (int i = NB - 1; i >= 0; i--) {
-    const int ii = nb7(i);
-    T acc = b[ii * BS];
-#pragma unroll
-    for (int c = i + 1; c < NB; c++) acc -= J[(ii * NV + nb7(c)) * BS] * x[nb7(c)];
-    x[ii] = acc * inv[i];
-  }
-  return true;
-}
-
-// Partial-pivot LU solve J x = b with J, b in shared memory at stride BS
-// (element (i,j) at J[(i*10+j)*BS], b[i] at b[i*BS]); x returned in registers.
-// Pivot: largest |a_ik|, lowest row on ties.  Returns false on a zero pivot.
-template <typename T, int BS>
-__device__ __forceinline__ bool lu_solve_smem(T* J, T* b, T x[NV]) {
-  T inv[NV];
-#pragma unroll
-  for (int k = 0; k < NV; k++) {
-    int piv = k;
-    auto best = abits(J[(k * NV + k) * BS]);
-#pragma unroll
-    for (int i = k + 1; i < NV; i++) {
-      const auto a = abits(J[(i * NV + k) * BS]);
-      if (a > best) { best = a; piv = i; }
-    }
-    if (best == 0) return false;
-    if (piv != k) {
-#pragma unroll
-      for (int c = k; c < NV; c++) {
-        const T t = J[(k * NV + c) * BS];
-        J[(k * NV + c) * BS] = J[(piv * NV + c) * BS];
-        J[(piv * NV + c) * BS] = t;
-      }
-      const T t = b[k * BS];
-      b[k * BS] = b[piv * BS];
-      b[piv * BS] = t;
-    }
-    inv[k] = nr_rcp(J[(k * NV + k) * BS]);
-    const T bk = b[k * BS];
-#pragma unroll
-    for (int i = k + 1; i < NV; i++) {
-      const T a = J[(i * NV + k) * BS];
-      if (abits(a) == 0) continue;  // zero multiplier: row i is unchanged
-      const T l = a * inv[k];
-#pragma unroll
-      for (int c = k + 1; c < NV; c++) J[(i * NV + c) * BS] -= l * J[(k * NV + c) * BS];
-      b[i * BS] -= l * bk;
-    }
-  }
-#pragma unroll
-  for (int i = NV - 1; i >= 0; i--) {
     T acc = b[i * BS];
 #pragma unroll
-    for (int c = i + 1; c < NV; c++) acc -= J[(i * NV + c) * BS] * x[c];
-    x[i] = acc * inv[i];
+    for (int c = i + 1; c < NB; c++) acc -= J[(i * NJ + c) * BS] * x[nb7(c)];
+    x[nb7(i)] = acc * inv[i];
   }
   return true;
 }
@@ -379,18 +334,18 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
     bool ok;
     if (!MIXED) {
       double* J = (double*)jac + threadIdx.x;
-      double* b = J + NV * NV * BS;
+      double* b = J + NJ * NJ * BS;
       fd_jacobian<double, false, BS>(z, r, k64, c64, p.eps64, J, five);
       o.evals64 += five ? 5 : 7;
 #pragma unroll
-      for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
+      for (int m = 0; m < NJ; m++) b[m * BS] = -r[nb7(m)];
       ok = five ? lu_solve_block_smem<double, BS, 5>(J, b, dP) : lu_solve_block_smem<double, BS, 7>(J, b, dP);
       o.lu64++;
     } else {
       const RC<float> c32 = make_rc<float>(p);
       const KSm<float, BS> k32{kf};
       float* J = (float*)jac + threadIdx.x;
-      float* b = J + NV * NV * BS;
+      float* b = J + NJ * NJ * BS;
       float Pf[NV], rf[NV];
 #pragma unroll
       for (int a = 0; a < NV; a++) Pf[a] = d2f_jac(P[a]);
@@ -406,7 +361,7 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
         o.evals32 += ncol + 1;
       }
 #pragma unroll
-      for (int i = 0; i < NV; i++) b[i * BS] = d2f_jac(-r[i]);
+      for (int m = 0; m < NJ; m++) b[m * BS] = d2f_jac(-r[nb7(m)]);
       float df[NV];
       ok = five ? lu_solve_block_smem<float, BS, 5>(J, b, df) : lu_solve_block_smem<float, BS, 7>(J, b, df);
 #pragma unroll
@@ -498,7 +453,7 @@ __device__ __forceinline__ void enqueue(int* queue, int* qcount, bool pending, l
 template <bool MIXED, int BS> struct NewtonSmem {
   static constexpr size_t kd = sizeof(double) * NK * BS;
   static constexpr size_t kf = MIXED ? sizeof(float) * NK * BS : 0;
-  static constexpr size_t jac = (MIXED ? sizeof(float) : sizeof(double)) * (NV * NV + NV) * BS;
+  static constexpr size_t jac = (MIXED ? sizeof(float) : sizeof(double)) * (NJ * NJ + NJ) * BS;
   static constexpr size_t bytes = kd + kf + jac;
 };
 
@@ -797,7 +752,8 @@ __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], con
     if (!CENTRAL) {
       const T ih = nr_rcp(hstep);
 #pragma unroll
-      for (int i = 0; i < NV; i++) J[(i * NV + col) * BS] = (rp[i] - r[i]) * ih;
+      for (int i = 0; i < NV; i++)
+        if (jslot(i) >= 0) J[(jslot(i) * NJ + mc) * BS] = (rp[i] - r[i]) * ih;
     } else {
       Pe[col] = pj - hstep;
       zg_load(z, Pe, m, c);
@@ -805,7 +761,8 @@ __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], con
       r_all_gr(z, k, rm);
       const T ih = T(0.5) * nr_rcp(hstep);
 #pragma unroll
-      for (int i = 0; i < NV; i++) J[(i * NV + col) * BS] = (rp[i] - rm[i]) * ih;
+      for (int i = 0; i < NV; i++)
+        if (jslot(i) >= 0) J[(jslot(i) * NJ + mc) * BS] = (rp[i] - rm[i]) * ih;
     }
   }
 }
@@ -861,11 +818,11 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
     bool ok;
     if (!MIXED) {
       double* J = (double*)jac + threadIdx.x;
-      double* b = J + NV * NV * BS;
+      double* b = J + NJ * NJ * BS;
       fd_jacobian_gr<double, false, false, BS>(P, r, k64, m64, c64, p.eps64, J, five);
       o.evals64 += five ? 5 : 7;
 #pragma unroll
-      for (int i = 0; i < NV; i++) b[i * BS] = -r[i];
+      for (int m = 0; m < NJ; m++) b[m * BS] = -r[nb7(m)];
       ok = five ? lu_solve_block_smem<double, BS, 5>(J, b, dP) : lu_solve_block_smem<double, BS, 7>(J, b, dP);
       o.lu64++;
     } else {
@@ -873,7 +830,7 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       const KSm<float, BS> k32{kf};
       const Met<float> m32 = met_smem<float, BS>(md);
       float* J = (float*)jac + threadIdx.x;
-      float* b = J + NV * NV * BS;
+      float* b = J + NJ * NJ * BS;
       float Pf[NV], rf[NV];
 #pragma unroll
       for (int a = 0; a < NV; a++) Pf[a] = d2f_jac(P[a]);
@@ -889,7 +846,7 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
         o.evals32 += ncol + 1;
       }
 #pragma unroll
-      for (int i = 0; i < NV; i++) b[i * BS] = d2f_jac(-r[i]);
+      for (int m = 0; m < NJ; m++) b[m * BS] = d2f_jac(-r[nb7(m)]);
       float df[NV];
       ok = five ? lu_solve_block_smem<float, BS, 5>(J, b, df) : lu_solve_block_smem<float, BS, 7>(J, b, df);
 #pragma unroll
@@ -931,7 +888,7 @@ template <bool MIXED, int BS> struct NewtonSmemGr {
   static constexpr size_t kd = sizeof(double) * NK * BS;
   static constexpr size_t md = sizeof(double) * NMET * BS;
   static constexpr size_t kf = MIXED ? sizeof(float) * NK * BS : 0;
-  static constexpr size_t jac = (MIXED ? sizeof(float) : sizeof(double)) * (NV * NV + NV) * BS;
+  static constexpr size_t jac = (MIXED ? sizeof(float) : sizeof(double)) * (NJ * NJ + NJ) * BS;
   static constexpr size_t bytes = kd + md + kf + jac;
 };
 
