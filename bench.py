@@ -38,7 +38,7 @@ MLP_SAMPLE_STRIDE = 6     # training stages from every 6th of the first 48 steps
 # dram__bytes_write.sum of one ncu capture of each kernel on this workload;
 # newton32 captured on the plain-start arm; None while a kernel has changed
 # since its capture).
-NCU_TRAFFIC_BYTES = {"faces": 296.6e6, "zone_const": None, "newton64": 428.0e6, "newton32": 424.9e6,
+NCU_TRAFFIC_BYTES = {"faces": 296.6e6, "zone_const": None, "newton64": 428.1e6, "newton32": 424.4e6,
                      "mlp": None}
 TOL = 1e-10
 KERR_OUTLIER_LIMIT = 50.0  # training rows of the torus kept within this many robust deviations
