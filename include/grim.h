@@ -120,8 +120,8 @@ typedef struct {
   unsigned long long iters;     /* Newton updates */
   unsigned long long evals64;   /* float64 residual evaluations */
   unsigned long long evals32;   /* float32 residual evaluations */
-  unsigned long long lu64;      /* float64 10x10 LU solves */
-  unsigned long long lu32;      /* float32 10x10 LU solves */
+  unsigned long long lu64;      /* float64 LU solves (7x7 block; 5x5 in ideal MHD) */
+  unsigned long long lu32;      /* float32 LU solves (7x7 block; 5x5 in ideal MHD) */
   unsigned long long hist[32];  /* zone solves by number of Newton updates (31 = 31 or more) */
   double max_res;               /* largest final max_a |r_a| over zone solves */
   unsigned long long launches;  /* kernels launched by the library */

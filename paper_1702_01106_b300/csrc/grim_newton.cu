@@ -1,5 +1,6 @@
 // Per-zone Newton solve of the stage residual (Section 3): FD Jacobian
-// (Section 3.1), 10x10 partial-pivot LU, quadratic backtracking line search
+// (Section 3.1), partial-pivot LU of the non-magnetic 7x7 block (5x5 in ideal
+// MHD), quadratic backtracking line search
 // (Section 3.2), convergence test max_a |r_a| <= tol before each Jacobian.
 //
 // One thread owns one zone.  The zone constants, the Jacobian and the
