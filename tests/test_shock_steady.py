@@ -65,3 +65,20 @@ def test_shock_steady_gpu(orc):
     assert rel_field_err(b.cpu().numpy(), ref).max() < 1e-11
     g.close()
     g2.close()
+
+
+def test_ideal_rows_vanish_for_any_fluid_state(orc):
+    """The premise of the ideal-MHD 5x5 Newton block: with conduction and
+    viscosity off and q~ = dP~ = 0 everywhere, the q~ and dP~ rows of the
+    stage residual are exactly zero whatever rho, u and u^i are, so their
+    Newton update is zero."""
+    prob = shock_problem(32)
+    Pn, _ = shock_state(prob)
+    rng = np.random.default_rng(5)
+    PE = Pn * (1 + 1e-2 * rng.standard_normal(Pn.shape))
+    PE[5:] = Pn[5:]
+    for _ in range(3):
+        Pk = Pn * (1 + 1e-1 * rng.standard_normal(Pn.shape))
+        Pk[5:] = Pn[5:]
+        R = orc.residual(prob, Pn, PE, 0.01, Pk).reshape(10, -1)
+        assert np.all(R[8:] == 0.0) and np.abs(R[:5]).max() > 0
