@@ -1,5 +1,5 @@
-"""Hydrostatic conducting atmosphere (Section 8.2), the case in thermal
-equilibrium: a static gas around a Schwarzschild black hole (M = 1) with a
+"""Hydrostatic conducting atmosphere (Section 8.2), in thermal equilibrium
+and with a radial heat flux: a static gas around a Schwarzschild black hole (M = 1) with a
 radial field, 200 <= r <= 300, held up by its pressure with no heat flux.
 Written here from the equilibrium conditions of that section; nothing comes
 from the oracle or the CUDA path.
@@ -29,6 +29,7 @@ fluid is u~^1 = 2 u^t / (r^2 + 2 r), u^t = 1/alpha_t (Kerr-Schild, a = 0).
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -73,6 +74,102 @@ def pressure_ode(r):
                     dense_output=True)
     assert sol.status == 0
     return sol.sol(np.asarray(r, dtype=float))[0]
+
+
+# ---------------------------------------------------------------- with a heat flux
+# The second case: heat flowing outwards.  For the static fluid the
+# relaxation equation leaves q = q_0 (its advection and nabla_mu u^mu vanish),
+# so q_0 = -rho chi b-hat^r (dTheta/dr + Theta d ln alpha_t/dr) fixes dTheta/dr.
+# The Killing energy flux sqrt(-g) T^r_t = sqrt(-g) q b-hat^r u_t is constant
+# (the field carries none: b_t = 0 for a static fluid and a radial field), which
+# fixes q(r) = F / (r^2 b-hat^r (-u_t)).  The radial momentum balance
+# d(sqrt(-g) T^r_r)/dr = sqrt(-g) T^k_l Gamma^l_{r k}, with T^r_r = P + q b-hat^r u_r
+# (u_r = g_rt u^t is not zero in Kerr-Schild coordinates) and T^k_l = w u^k u_l
+# + P delta^k_l + q (b-hat^k u_l + u^k b-hat_l), fixes dP/dr.  Gamma of the
+# Kerr-Schild metric (a = 0) comes from sympy, here; with F = 0 the balance
+# reduces to the closed form above.
+
+
+@functools.lru_cache(maxsize=None)
+def _kerr_schild_r_connection():
+    """(g_{mu nu}(r), Gamma^l_{r k}(r)) on the equator, Kerr-Schild, a = 0."""
+    import sympy as sp
+    r, th = sp.symbols("r theta", positive=True)
+    t, ph = sp.symbols("t phi")
+    X = [t, r, th, ph]
+    g = sp.zeros(4)
+    g[0, 0] = -(1 - 2 / r)
+    g[0, 1] = g[1, 0] = 2 / r
+    g[1, 1] = 1 + 2 / r
+    g[2, 2] = r ** 2
+    g[3, 3] = r ** 2 * sp.sin(th) ** 2
+    gi = g.inv()
+    gam = [[sp.simplify(sum(gi[l, m] * (sp.diff(g[m, 1], X[k]) + sp.diff(g[m, k], X[1]) - sp.diff(g[1, k], X[m]))
+                            for m in range(4)) / 2).subs(th, sp.pi / 2) for k in range(4)] for l in range(4)]
+    return sp.lambdify(r, g.subs(th, sp.pi / 2), "numpy"), sp.lambdify(r, sp.Matrix(gam), "numpy")
+
+
+def _static_frame(r):
+    """u^mu, u_mu, b-hat^mu, b-hat_mu of the static fluid with a radial field."""
+    gfun, _ = _kerr_schild_r_connection()
+    gm = np.array(gfun(r), dtype=float)
+    ucon = np.array([1.0 / alpha_t(r), 0.0, 0.0, 0.0])
+    ucov = gm @ ucon
+    v = np.array([-ucov[1] / ucov[0], 1.0, 0.0, 0.0])   # in the (t, r) plane, orthogonal to u
+    bh = v / math.sqrt(v @ gm @ v)
+    return ucon, ucov, bh, gm @ bh
+
+
+def heat_flux(r, F):
+    _, ucov, bh, _ = _static_frame(r)
+    return F / (r * r * bh[1] * (-ucov[0]))
+
+
+def _conducting_rhs(r, y, F, phi):
+    Pg, th = y
+    rho, u = Pg / th, Pg / (GAMMA - 1.0)
+    w = rho + u + Pg
+    ucon, ucov, bh, bhc = _static_frame(r)
+    q = heat_flux(r, F)
+    chi = phi * GAMMA * Pg / w * TAU0 * r ** 1.5
+    dth = -q / (rho * chi * bh[1]) - th * dlnalpha_dr(r)
+    T = w * np.outer(ucon, ucov) + Pg * np.eye(4) + q * (np.outer(bh, ucov) + np.outer(ucon, bhc))
+    _, gam = _kerr_schild_r_connection()
+    G = np.array(gam(r), dtype=float)                      # G[l, k] = Gamma^l_{r k}
+    S = float(np.sum(T * G.T))                             # T^k_l Gamma^l_{r k}
+
+    def qbu(x):
+        _, uv, b, _ = _static_frame(x)
+        return heat_flux(x, F) * b[1] * uv[1]
+
+    h = 1e-3 * r
+    dqbu = (qbu(r + h) - qbu(r - h)) / (2.0 * h)
+    return [S - (2.0 / r) * (Pg + qbu(r)) - dqbu, dth]
+
+
+@functools.lru_cache(maxsize=None)
+def conducting_solution(F, phi=1.0):
+    """Dense solution (P, Theta)(r) of the conducting atmosphere with energy
+    flux F (F = 0: thermal equilibrium)."""
+    from scipy.integrate import solve_ivp
+    sol = solve_ivp(lambda x, y: _conducting_rhs(x, y, F, phi), (R_IN, R_OUT), [RHO0 * THETA0, THETA0],
+                    method="DOP853", rtol=1e-12, atol=1e-16, dense_output=True)
+    assert sol.status == 0
+    return sol
+
+
+def conducting_state(prob, F):
+    """Primitives of the conducting atmosphere (q~ = q (tau_R/(chi rho Theta^2))^(1/2))."""
+    x1, _, _ = inputs.zone_centers(prob)
+    r = np.exp(x1[0, 0])
+    Pg, th = conducting_solution(F, prob.phi).sol(r)
+    rho, u = Pg / th, Pg / (GAMMA - 1.0)
+    cs2 = GAMMA * Pg / (rho + u + Pg)
+    q = np.array([heat_flux(x, F) for x in r])
+    P, _ = atmosphere_state(prob)
+    P[0], P[1] = rho, u
+    P[8] = q / (th * np.sqrt(prob.phi * cs2 * rho))
+    return P, r
 
 
 def atmosphere_problem(n1, n2=4, tol=1e-12, conduction=True, viscosity=True):

@@ -1,7 +1,10 @@
-"""Hydrostatic conducting atmosphere in thermal equilibrium (Section 8.2):
-a static gas at 200 <= r <= 300 around a Schwarzschild black hole, radial
-field, conduction and viscosity on, whose redshifted temperature Theta
-alpha_t is uniform, so that no heat flows although Theta falls outwards.
+"""Hydrostatic conducting atmosphere (Section 8.2), in thermal equilibrium
+and with a radial heat flux.  In thermal equilibrium: a static gas at
+200 <= r <= 300 around a Schwarzschild black hole, radial field, conduction
+and viscosity on, whose redshifted temperature Theta alpha_t is uniform, so
+that no heat flows although Theta falls outwards.  With a heat flux: the same
+gas carrying a constant energy flux outwards, its temperature set by
+q = q_0 and its pressure by the momentum balance with the flux's stress.
 The scheme must hold it: the heat flux stays at truncation level only if the
 Theta a_mu term of Eq. q0def is there, and the density drift falls with
 resolution.  The state is the closed-form solution in tests/atmosphere.py;
@@ -111,3 +114,47 @@ def test_gpu_atmosphere(orc, precision):
         d.append(_interior_drift(a.cpu().numpy(), P0, r))
         g.close()
     assert d[0][0] > 3.5 * d[1][0] and d[1][0] > 3.5 * d[2][0], d
+
+
+F_HEAT = 0.04   # energy flux sqrt(-g) T^r_t / sin(theta): q = 1e-6 at r = 200, Theta falls 16 %
+
+
+def test_conducting_balance_reduces_to_the_closed_form():
+    """With no heat flux the general balance (momentum with the Kerr-Schild
+    connection, temperature from q = q_0) gives the closed-form atmosphere;
+    with F = 0.04 the heat flux lowers Theta at r = 300 by 15 % more than the
+    redshift law does."""
+    r = np.linspace(at.R_IN, at.R_OUT, 21)
+    P0, T0 = at.conducting_solution(0.0).sol(r)
+    assert np.abs(P0 / at.pressure(r) - 1).max() < 1e-11
+    assert np.abs(T0 / at.theta_of_r(r) - 1).max() < 1e-12
+    _, T1 = at.conducting_solution(F_HEAT).sol(r)
+    assert T1[-1] < 0.86 * at.theta_of_r(r[-1])
+
+
+def test_oracle_holds_the_conducting_atmosphere(orc):
+    """Heat flowing outwards through the static atmosphere (q~ about 9e-4):
+    the oracle's steady residual falls 2.5x or more per doubling in every
+    row, and after t = 10 the interior drift of rho and the relative drift of
+    q~ fall 3.5x or more per doubling (32 x 4 to 128 x 16)."""
+    prev = None
+    d = []
+    for n1, n2 in GRIDS:
+        prob = at.atmosphere_problem(n1, n2)
+        P0, r = at.conducting_state(prob, F_HEAT)
+        dt = at.atmosphere_dt(prob)
+        R = orc.residual(prob, P0, P0, 0.5 * dt, P0).reshape(10, n2, n1)[:, :, 3:n1 - 3]
+        m = np.abs(R).max(axis=(1, 2))[[0, 1, 2, 3, 8]] / (0.5 * dt)
+        if prev is not None:
+            assert np.all(prev > 2.5 * m), (prev, m)
+        prev = m
+        P = P0.copy()
+        for _ in range(int(round(10.0 / dt))):
+            P, _, st, _ = orc.step(prob, P, dt)
+            assert st.max() == 0
+        inner = (r > 220) & (r < 280)
+        d.append((float(np.abs(P[0, 0][:, inner] / P0[0, 0][:, inner] - 1).mean()),
+                  float(np.abs(P[8, 0][:, inner] / P0[8, 0][:, inner] - 1).mean())))
+    for k in range(2):
+        assert d[k][0] > 3.5 * d[k + 1][0] and d[k][1] > 3.5 * d[k + 1][1], d
+    assert d[2][1] < 1e-5
