@@ -466,3 +466,68 @@ def test_flop_count_file_matches_oracle():
             k, v = line.split()
             stored[k] = int(v)
     assert stored == make_flop_counts.counts()
+
+
+# ---------------------------------------------------------------- HLLE (Section 2.4.2)
+def _zigzag_line(n, base, amp):
+    """States of n zones along X1 alternating base + amp, base - amp: every
+    zone is a local extremum of every field, so the limited reconstruction
+    is flat and the face states are the neighbouring zone values."""
+    P = np.zeros((10, 1, 1, n))
+    sgn = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    for v in range(10):
+        P[v, 0, 0] = base[v] + amp[v] * sgn
+    return P
+
+
+def test_hlle_equals_llf_when_the_bounds_are_symmetric(orc):
+    """With no flow along either direction the grid-frame speeds of each face
+    state are +-c, so the HLLE bounds are c_R = c_L = max c, the LLF speed; the
+    HLLE flux (c_R F^- + c_L F^+ - c_R c_L (U^+ - U^-))/(c_R + c_L) then is the
+    LLF flux (F^- + F^+)/2 - c (U^+ - U^-)/2.  Random rest-frame states
+    (u^1 = u^2 = 0, everything else varying, both closures on) on a ragged
+    2-D grid, flux-CT included."""
+    rng = np.random.default_rng(31)
+    prob = inputs.linear_mode_problem(8).with_(n=(9, 6, 1))
+    P = np.zeros((10, 1, 6, 9))
+    P[0] = rng.uniform(0.5, 2.0, P[0].shape)
+    P[1] = rng.uniform(0.2, 3.0, P[1].shape)
+    P[4] = rng.normal(0.0, 0.4, P[4].shape)
+    P[5:8] = rng.normal(0.0, 0.3, P[5:8].shape)
+    P[8:10] = rng.normal(0.0, 0.1, P[8:10].shape)
+    F_llf = orc.fluxes(prob, P)
+    F_hlle = orc.fluxes(prob.with_(riemann=inputs.FLUX_HLLE), P)
+    scale = np.abs(F_llf).max(axis=(2, 3, 4), keepdims=True) + 1e-300
+    assert (np.abs(F_hlle - F_llf) / scale).max() < 1e-14
+    # the pin has teeth: a dissipation term of the wrong sign would differ
+    assert np.abs(F_llf[0, 0]).max() > 1e-3
+
+
+@pytest.mark.parametrize("direction", [+1, -1])
+def test_hlle_is_the_upwind_flux_of_a_supersonic_face(orc, direction):
+    """When every wave at a face moves the same way (all c^+- > 0), c_L = 0
+    and HLLE returns the flux of the upwind state, F(P^-) (left state); for
+    flow to -X1 it returns F(P^+).  Zig-zag data make the face states the
+    zone values themselves, so the expected flux is the pointwise flux of
+    the upwind zone.  Cold, fast flow (|u~^1| = 3, v ~ 0.95) with the
+    closures on keeps every speed of one sign (checked)."""
+    n = 8
+    base = np.array([1.0, 0.01, 3.0 * direction, 0.2, -0.1, 0.05, 0.02, -0.03, 0.01, -0.02])
+    amp = np.array([0.1, 0.002, 0.1, 0.05, 0.03, 0.0, 0.01, 0.01, 0.005, 0.004])
+    prob = inputs.Problem(dim=1, n=(n, 1, 1), riemann=inputs.FLUX_HLLE)
+    P = _zigzag_line(n, base, amp)
+    F = orc.fluxes(prob, P)[0]                  # [10, 1, 1, n], low face of each zone
+    Pz = P.reshape(10, n)
+    for i in range(n):
+        up = Pz[:, (i - 1) % n] if direction > 0 else Pz[:, i]
+        dn = Pz[:, i] if direction > 0 else Pz[:, (i - 1) % n]
+        _, Fup, cup = orc.point(prob, up)
+        _, Fdn, cdn = orc.point(prob, dn)
+        c = np.r_[cup[0], cdn[0]]
+        assert (c > 0).all() if direction > 0 else (c < 0).all()
+        want = Fup[0].copy()
+        want[5] = 0.0                           # F^1[B^1] = 0 (flux-CT)
+        got = F[:, 0, 0, i]
+        assert np.abs(got - want).max() <= 1e-14 * np.abs(want).max(), (i, got - want)
+        # and not the downstream state's flux: the face states differ
+        assert np.abs(Fdn[0][:5] - Fup[0][:5]).max() > 1e-3
