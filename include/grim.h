@@ -9,8 +9,8 @@
  * Eq. half_step_residual (and its full-step analogue, Eq. full_step) to zero
  * with Newton iterations on a finite-difference Jacobian (Section 3.1) and a
  * quadratic backtracking line search (Section 3.2).  Fluxes are local
- * Lax-Friedrichs (Section 2.4.2) on generalized-minmod or WENO5 states
- * (Section 2.4.1) with flux-CT for the magnetic field (Section 4.2).
+ * Lax-Friedrichs or HLLE (Section 2.4.2) on generalized-minmod, WENO5 or PPM
+ * states (Section 2.4.1) with flux-CT for the magnetic field (Section 4.2).
  *
  * Conventions shared by every entry point:
  *  - A state is a caller-owned DEVICE buffer of float64, structure of arrays
@@ -22,8 +22,15 @@
  *    traps, aborts or waits on the device.  Zones whose Newton solve does not
  *    converge keep their last iterate and are counted in grim_stats.
  *  - The library owns its scratch (stage constants, status bytes, counters),
- *    allocated once by grim_init and freed by grim_destroy.
- *  - Minkowski space, 2-D grids (dim = 2, n3 = 1) in this version.
+ *    allocated once by grim_init and freed by grim_destroy (grim_step_static
+ *    uses a static device array instead).
+ *  - Grids: 2-D (n3 = 1) or 3-D, in Minkowski space or in the Kerr metric in
+ *    modified Kerr-Schild coordinates (Section 2.1); 2-D Minkowski grids run
+ *    specialised flat-space kernels, everything else the general-metric
+ *    kernels.
+ *  - Reconstruction: generalized minmod (MC), WENO5 or PPM (Section 2.4.1);
+ *    Riemann solver: LLF or HLLE (Section 2.4.2).
+ *  - Precision: float64 throughout, or the mixed solver (GRIM_MIXED).
  */
 #ifndef GRIM_H
 #define GRIM_H
@@ -58,7 +65,11 @@ extern "C" {
  * Minkowski grids, the MC reconstruction and the limited slopes) in
  * float-float, pairs of floats with about 48 significant bits, joined back
  * into float64 before they are stored; U(P_n), the flux divergence, flux-CT
- * and the stage constants stay float64. */
+ * and the stage constants stay float64.  A zone whose float32-Jacobian
+ * iteration ends with a non-zero status (the float32 Jacobian of a cold zone
+ * can lose the internal-energy column to rounding) is solved again with the
+ * float64 Jacobian from P_n, or from P^E when the stage's output overwrites
+ * P_n (grim_stats.rescued); with k_max = 0 there is no second solve. */
 #define GRIM_MIXED 1
 
 /* Grid (Section 2.1): uniform in X^i, dX^i = (x_end - x_start)/n_i. */
@@ -126,6 +137,9 @@ typedef struct {
   double max_res;               /* largest final max_a |r_a| over zone solves */
   unsigned long long launches;  /* kernels launched by the library */
   unsigned long long fallbacks; /* zone solves whose learned start lost to P_n (grim_set_guess) */
+  unsigned long long rescued;   /* GRIM_MIXED: zone solves whose float32-Jacobian iteration ended with a
+                                   non-zero status and were solved again with the float64 Jacobian from
+                                   P_n (their status is the float64 solve's) */
 } grim_stats;
 
 typedef struct grim_ctx grim_ctx;
@@ -222,10 +236,23 @@ void grim_destroy(grim_ctx* ctx);
  *    before any stream capture.
  *  - All calls share the one array: calls that overlap on the GPU (other
  *    streams, other threads) race and must be serialised by the caller.
+ *  - Accepts 2-D Minkowski grids (dim = 2, n3 = 1) with MC or WENO5
+ *    reconstruction and the LLF flux; anything else returns GRIM_EINVAL.
+ *  - Zones whose Newton solve does not converge keep their last iterate, as
+ *    in grim_step; grim_step_static_stats reports how many.
  *  - Returns 0, GRIM_EINVAL (bad configuration or pointer), GRIM_ESIZE or
  *    GRIM_ECUDA; asynchronous on the stream like grim_step. */
 int grim_step_static(const grim_grid* grid, const grim_metric* metric, const grim_physics* phys,
                      const grim_solver* solver, void* stream, const double* P_in, double* P_out, double dt);
+
+/* Counters of the last grim_step_static call on the current device (its two
+ * stages: zone solves, failures, Newton updates, residual evaluations, the
+ * update histogram, the largest final max_a |r_a|), read from the shared
+ * static array into *out.  Waits for `stream` (the stream of that call) to
+ * finish; allocates nothing.  A call made since on another stream or
+ * thread may have overwritten them (the array is shared).  Returns 0,
+ * GRIM_EINVAL or GRIM_ECUDA. */
+int grim_step_static_stats(void* stream, grim_stats* out);
 
 /* Measure the float64 and float32 FMA throughput of the current device with
  * dependent FMA chains (no memory traffic): writes TFLOP/s (2 flops per

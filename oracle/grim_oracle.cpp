@@ -898,8 +898,11 @@ static NewtonOut newton(const ZoneConst& z, const Params& p, double P[10]) {
       double lim = 1.0 - ebt * lam;
       if (fin && ft < f * lim * lim) break;
       if (t >= p.lsmax) { o.status |= ST_LSSTALL; break; }
-      if (!fin) lam = 0.5 * lam;
-      else lam = f * lam * lam / (ft + (2.0 * lam - 1.0) * f);
+      // the minimiser of the quadratic model; where it is not a positive
+      // finite number (a non-finite trial, or a denominator that overflowed
+      // to leave 0 and then 0/0), lambda is halved instead
+      const double ln = fin ? f * lam * lam / (ft + (2.0 * lam - 1.0) * f) : 0.0;
+      lam = (ln > 0.0 && std::isfinite(ln)) ? ln : 0.5 * lam;
     }
     std::memcpy(P, Pt, sizeof(Pt));
     std::memcpy(r, rt, sizeof(rt));

@@ -26,7 +26,7 @@ cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* P
 long long pn_cache_doubles(long long N);
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, cudaStream_t st);
+                             int* qcount, double* rq, const Rescue& rs, cudaStream_t st);
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
@@ -45,7 +45,8 @@ cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K
                              const uint8_t* status, double* P, cudaStream_t st);
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, const double* Pfb, double accept, cudaStream_t st);
+                             int* qcount, double* rq, const double* Pfb, double accept, const Rescue& rs,
+                             cudaStream_t st);
 cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,
                                double dts, double* R, cudaStream_t st);
 }  // namespace grim
@@ -60,7 +61,8 @@ struct grim_ctx {
   cudaStream_t cap = nullptr; // private stream for graph capture
   grim_tuning tune{64, 2, 128, 128};
   int* queue = nullptr;       // zones left for the queue kernel
-  int* qcount = nullptr;      // their number
+  int* qcount = nullptr;      // their number, then the rescue queue's length
+  int* rqueue = nullptr;      // mixed-solver zones handed to the float64 rescue
   bool graphs = false, warmed = false;
   grim_tuning warm_tune{};    // launch shape and guess of the last eager step: every
   bool warm_mlp = false;      // kernel a capture records has been configured
@@ -166,6 +168,7 @@ void grim_destroy(grim_ctx* ctx) {
   cudaFree(ctx->dev_out);
   cudaFree(ctx->queue);
   cudaFree(ctx->qcount);
+  cudaFree(ctx->rqueue);
   cudaFree(ctx->feat);
   for (auto& g : ctx->gcache) cudaGraphExecDestroy(g.exec);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -226,7 +229,8 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
       (e = cudaMalloc(&ctx->iters, N)) != cudaSuccess || (e = cudaMalloc(&ctx->status, N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->cnt, sizeof(grim::Counters))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->queue, sizeof(int) * N)) != cudaSuccess ||
-      (e = cudaMalloc(&ctx->qcount, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->qcount, 2 * sizeof(int))) != cudaSuccess ||
+      (solver->precision == GRIM_MIXED && (e = cudaMalloc(&ctx->rqueue, sizeof(int) * N)) != cudaSuccess) ||
       (e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking)) != cudaSuccess) {
     grim_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? GRIM_ENOMEM : GRIM_ECUDA;
@@ -268,6 +272,14 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
   return GRIM_OK;
 }
 
+// The mixed solver hands the zones its float32-Jacobian iteration cannot
+// solve to the float64 kernel, which starts from P_n; when the stage writes
+// over P_n (an in-place full step), from P^E instead.
+static grim::Rescue rescue(grim_ctx* ctx, const double* Pn, const double* PE, const double* Pout) {
+  if (ctx->precision != GRIM_MIXED || !ctx->rqueue || ctx->p.kmax < 1) return grim::Rescue{nullptr, nullptr, nullptr};
+  return grim::Rescue{ctx->rqueue, ctx->qcount + 1, Pout == Pn ? PE : Pn};
+}
+
 static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
                      double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
   const bool learned = ctx->mlp && !guess;
@@ -286,10 +298,11 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
   if (ctx->gr) {
     const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
     {
-      KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64, cfg.kcut < ctx->p.kmax ? 2 : 1);
+      KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64,
+                   (cfg.kcut < ctx->p.kmax ? 2 : 1) + (rescue(ctx, Pn, PE, Pout).queue ? 1 : 0));
       GRIM_CUDA(grim::launch_newton_gr(ctx->p, ctx->precision, ctx->K, ctx->geo, Pout, iters ? iters : ctx->iters,
                                        status ? status : ctx->status, ctx->cnt, cfg, ctx->queue, ctx->qcount,
-                                       ctx->faces, learned ? Pn : nullptr, ctx->accept, ctx->cur),
+                                       ctx->faces, learned ? Pn : nullptr, ctx->accept, rescue(ctx, Pn, PE, Pout), ctx->cur),
                 "newton kernel");
     }
     if (ctx->p.floors) {
@@ -301,10 +314,11 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
   }
   {
     const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
-    KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64, cfg.kcut < ctx->p.kmax ? 2 : 1);
+    KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64,
+                 (cfg.kcut < ctx->p.kmax ? 2 : 1) + (rescue(ctx, Pn, PE, Pout).queue ? 1 : 0));
     GRIM_CUDA(grim::launch_newton_fb(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
                                      status ? status : ctx->status, ctx->cnt, learned ? Pn : nullptr, ctx->accept,
-                                     cfg, ctx->queue, ctx->qcount, ctx->faces, ctx->cur),
+                                     cfg, ctx->queue, ctx->qcount, ctx->faces, rescue(ctx, Pn, PE, Pout), ctx->cur),
               "newton kernel");
   }
   return GRIM_OK;
@@ -569,6 +583,7 @@ int grim_get_stats(grim_ctx* ctx, grim_stats* out) {
   out->max_res = mr;
   out->launches = ctx->launches;
   out->fallbacks = c.fallbacks;
+  out->rescued = c.rescued;
   return GRIM_OK;
 }
 
@@ -810,6 +825,7 @@ int grim_batch_get_stats(grim_batch* b, grim_stats* out) {
     for (int i = 0; i < 32; i++) t.hist[i] += s.hist[i];
     t.max_res = std::max(t.max_res, s.max_res);
     t.fallbacks += s.fallbacks;
+    t.rescued += s.rescued;
   }
   t.launches = b->launches;
   *out = t;

@@ -10,7 +10,36 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace grim {
+
+// One-time set-up per device, safe between host threads.  Kernel attributes
+// (the dynamic shared-memory limit) and occupancy-derived grid sizes belong
+// to a device, so each is set up once for every device that launches the
+// kernel: the first call with a device current runs f(&value) under a lock
+// and keeps value; a failing f is tried again on the next call.
+struct PerDevice {
+  static constexpr int kMaxDevices = 64;
+  std::mutex m;
+  bool done[kMaxDevices] = {};
+  int value[kMaxDevices] = {};
+  template <class F> cudaError_t get(F f, int* out = nullptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(m);
+    if (!done[dev]) {
+      int v = 0;
+      if ((e = f(&v)) != cudaSuccess) return e;
+      value[dev] = v;
+      done[dev] = true;
+    }
+    if (out) *out = value[dev];
+    return cudaSuccess;
+  }
+};
 
 constexpr int NV = 10;
 
@@ -73,6 +102,17 @@ struct Counters {
   unsigned long long hist[32];  // Newton updates per zone
   unsigned long long maxres_bits;  // max over zones of max_a |r_a|, as ordered bits
   unsigned long long fallbacks;    // zones whose learned start lost to the plain start
+  unsigned long long rescued;      // mixed-solver zones re-solved by the float64 kernel
+};
+
+// Zones whose mixed-precision Newton iteration ended with a non-zero status
+// are handed to the float64 Newton kernel, which solves them again from the
+// stage's start (queue of zone indices, its length, and P_n).  All NULL:
+// no rescue (the zone keeps its status).
+struct Rescue {
+  int* queue;
+  int* count;
+  const double* Pn;
 };
 
 // ----------------------------------------------------------------------------

@@ -141,10 +141,10 @@ __device__ __forceinline__ void face_states(const double* sP, const Params& p, i
 
 template <int TX, int TY, int H>
 __global__ void __launch_bounds__(TX* TY) explicit_stage_2d(const __grid_constant__ Params p,
-                                                            const double* __restrict__ Pn,
+                                                            const double* Pn,
                                                             const double* __restrict__ PE,
-                                                            const double* __restrict__ guess, double dts,
-                                                            double* __restrict__ K, double* __restrict__ P0) {
+                                                            const double* guess, double dts,
+                                                            double* __restrict__ K, double* P0) {
   using S = ExpSmem<TX, TY, H>;
   extern __shared__ double smem[];
   double* sP = smem;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(TX* TY) explicit_stage_2d(const __grid_constan
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     PEz[v] = sP[v * S::PX * S::PY + se];
-    Pnz[v] = __ldg(Pn + v * N + z);
+    Pnz[v] = Pn[v * N + z];  // plain load: P0 may be Pn (an in-place step)
   }
   Pt<double> sE_, sn;
   point_state(PEz, p, sE_);
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(TX* TY) explicit_stage_2d(const __grid_constan
   // initial guess: P_n (or the given guess) with B from the explicit flux-CT update
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    double x = guess ? __ldg(guess + v * N + z) : Pnz[v];
+    double x = guess ? guess[v * N + z] : Pnz[v];
     if (v >= 5 && v <= 7) x = Pnz[v] - dts * divF[v];
     P0[v * N + z] = x;
   }
@@ -372,13 +372,12 @@ template <int TX, int TY, int H>
 static cudaError_t launch_explicit_t(const Params& p, const double* Pn, const double* PE, const double* guess,
                                      double dts, double* K, double* P0, cudaStream_t st) {
   using S = ExpSmem<TX, TY, H>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(explicit_stage_2d<TX, TY, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::bytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static PerDevice once;
+  cudaError_t e = once.get([](int*) {
+    return cudaFuncSetAttribute(explicit_stage_2d<TX, TY, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)S::bytes);
+  });
+  if (e != cudaSuccess) return e;
   dim3 grid((p.n1 + TX - 1) / TX, (p.n2 + TY - 1) / TY);
   explicit_stage_2d<TX, TY, H><<<grid, TX * TY, S::bytes, st>>>(p, Pn, PE, guess, dts, K, P0);
   return cudaGetLastError();

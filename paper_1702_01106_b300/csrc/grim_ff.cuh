@@ -157,19 +157,25 @@ __device__ __forceinline__ double ff_join(ff a) { return f_widen(a.hi) + f_widen
 // double to float with the significand truncated to 24 bits (magnitudes
 // below the normal float range become signed zeros, above it infinities),
 // and float to double exactly (float denormals become zero).
+// Infinities stay infinite and NaNs stay NaN (a quiet NaN) both ways, so a
+// float32 solve that overflowed is seen as such by the caller.
 __device__ __forceinline__ float d2f_jac(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const int e = (int)((b >> 52) & 0x7ff) - 896;
+  const int ed = (int)((b >> 52) & 0x7ff);
+  const int e = ed - 896;
   const unsigned sign = (unsigned)(b >> 63) << 31;
-  const unsigned mag = (unsigned)e << 23 | (unsigned)((b & 0xfffffffffffffull) >> 29);
-  const unsigned r = e < 1 ? sign : (e > 254 ? (sign | 0x7f800000u) : (sign | mag));
+  const unsigned long long md = b & 0xfffffffffffffull;
+  const unsigned mag = (unsigned)e << 23 | (unsigned)(md >> 29);
+  const unsigned special = sign | 0x7f800000u | (md != 0ull ? 0x400000u : 0u);  // inf or NaN
+  const unsigned r = ed == 0x7ff ? special : (e < 1 ? sign : (e > 254 ? (sign | 0x7f800000u) : (sign | mag)));
   return __uint_as_float(r);
 }
 __device__ __forceinline__ double f2d_jac(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ef = (u >> 23) & 0xff;
   const unsigned long long s = (unsigned long long)(u >> 31) << 63;
-  const unsigned long long v = s | (unsigned long long)(ef + 896) << 52 | (unsigned long long)(u & 0x7fffffu) << 29;
+  const unsigned long long ed = ef == 0xffu ? 0x7ffull : (unsigned long long)(ef + 896);
+  const unsigned long long v = s | ed << 52 | (unsigned long long)(u & 0x7fffffu) << 29;
   return __longlong_as_double((long long)(ef == 0 ? s : v));
 }
 

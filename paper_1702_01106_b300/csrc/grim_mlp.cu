@@ -871,15 +871,19 @@ cudaError_t launch_mlp_features(const Params& p, const double* K, const double* 
 // are g_{mu nu}), or NULL for Minkowski space.
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
                              const double* gc, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_guess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(InferSmem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static PerDevice once;
+  int sms = 0;
+  cudaError_t e = once.get(
+      [](int* v) {
+        cudaError_t r = cudaFuncSetAttribute(mlp_guess, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(InferSmem));
+        int dev = 0;
+        if (r == cudaSuccess) r = cudaGetDevice(&dev);
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev);
+        return r;
+      },
+      &sms);
+  if (e != cudaSuccess) return e;
   long long tiles = (p.N + 16 * INF_WARPS - 1) / (16 * INF_WARPS);
   long long grid = sms;  // persistent: one block (and one copy of the weights) per SM
   if (grid > tiles) grid = tiles;

@@ -365,6 +365,10 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       for (int m = 0; m < NJ; m++) b[m * BS] = d2f_jac(-r[nb7(m)]);
       float df[NV];
       ok = five ? lu_solve_block_smem<float, BS, 5>(J, b, df) : lu_solve_block_smem<float, BS, 7>(J, b, df);
+      // a float32 solve that overflowed or met a NaN pivot has no direction:
+      // the zone is reported singular, not moved by a huge step
+#pragma unroll
+      for (int i = 0; i < NV; i++) ok = ok && isfinite(df[i]);
 #pragma unroll
       for (int i = 0; i < NV; i++) dP[i] = f2d_jac(df[i]);
       o.lu32++;
@@ -384,7 +388,11 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
       const double lim = 1.0 - 1e-4 * lam;
       if (fin && ft < f * lim * lim) break;
       if (t >= p.lsmax) { o.status |= ST_LSSTALL; break; }
-      lam = fin ? f * lam * lam / (ft + (2.0 * lam - 1.0) * f) : 0.5 * lam;
+      // the quadratic model's minimiser when it is a positive finite number,
+      // else half the step (a non-finite trial, or an overflowed denominator
+      // that would leave lambda = 0 and then 0/0)
+      const double ln = fin ? f * lam * lam / (ft + (2.0 * lam - 1.0) * f) : 0.0;
+      lam = (ln > 0.0 && finite_bits(ln)) ? ln : 0.5 * lam;
     }
 #pragma unroll
     for (int a = 0; a < NV; a++) { P[a] = Pt[a]; r[a] = rt[a]; }
@@ -448,6 +456,16 @@ __device__ __forceinline__ void enqueue(int* queue, int* qcount, bool pending, l
   if (pending) queue[base + __popc(m & ((1u << lane) - 1u))] = (int)z;
 }
 
+// A mixed-precision zone solve that ended with a non-zero status (no
+// convergence, a stalled line search, a singular or non-finite float32
+// solve) goes to the rescue queue, and counts as unfinished here: the
+// float64 kernel solves it again and finishes it.
+__device__ __forceinline__ void to_rescue(int* rqueue, int* rcount, ZoneResult& o, bool active, long long z) {
+  const bool resc = active && !o.pending && o.status != 0;
+  enqueue(rqueue, rcount, resc, z);
+  o.pending = o.pending || resc;
+}
+
 // Shared memory per thread: zone constants (NK doubles, plus NK floats for
 // MIXED), the Jacobian and the right-hand side (110 elements of the Jacobian
 // precision).
@@ -467,7 +485,8 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
                                                    const double* __restrict__ Pfb, double accept, int kstop,
                                                    int* __restrict__ queue, int* __restrict__ qcount,
-                                                   double* __restrict__ rq) {
+                                                   double* __restrict__ rq, int* __restrict__ rqueue,
+                                                   int* __restrict__ rcount) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -496,6 +515,7 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
     status[z] = (uint8_t)o.status;
   }
   if (queue) enqueue(queue, qcount, active && o.pending, z);
+  if (MIXED && rqueue) to_rescue(rqueue, rcount, o, active, z);
   accumulate(cnt, o, active, fellback);
 }
 
@@ -507,7 +527,8 @@ __global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Param
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
                                                    const int* __restrict__ queue, const int* __restrict__ qcount,
-                                                   double* __restrict__ rq) {
+                                                   double* __restrict__ rq, int* __restrict__ rqueue,
+                                                   int* __restrict__ rcount) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -538,9 +559,78 @@ __global__ void __launch_bounds__(BS) newton_queue(const __grid_constant__ Param
       iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
       status[z] = (uint8_t)o.status;
     }
+    if (MIXED && rqueue) to_rescue(rqueue, rcount, o, active, active ? queue[q] : 0);
     accumulate(cnt, o, active, fellback);
   }
 }
+
+// The mixed solver's rescue: the zones of the rescue queue solved again with
+// the float64 Jacobian, from the stage's start (P_n; the magnetic components
+// are still the start's, since no update changes them), to convergence or
+// k_max.  Persistent grid over the queue; the zone's counters are finished
+// here.
+template <int BS, bool IDEAL>
+__global__ void __launch_bounds__(BS) newton_rescue(const __grid_constant__ Params p, const double* __restrict__ K,
+                                                    const double* __restrict__ Pn, double* __restrict__ P,
+                                                    uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
+                                                    Counters* __restrict__ cnt, const int* __restrict__ rqueue,
+                                                    const int* __restrict__ rcount) {
+  using S = NewtonSmem<false, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* kd = (double*)smem_raw + threadIdx.x;
+  void* jac = smem_raw + S::kd;
+  const long long N = p.N;
+  const int count = *rcount;
+  for (int base = blockIdx.x * BS; base < count; base += gridDim.x * BS) {
+    const int q = base + (int)threadIdx.x;
+    const bool active = q < count;
+    ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
+    bool fb = false;
+    if (active) {
+      const long long z = rqueue[q];
+#pragma unroll
+      for (int a = 0; a < NK; a++) kd[a * BS] = __ldg(K + a * N + z);
+      double Pz[NV];
+#pragma unroll
+      for (int a = 0; a < NV; a++) Pz[a] = (a >= 5 && a <= 7) ? P[a * N + z] : __ldg(Pn + a * N + z);
+      o = newton_zone<false, BS, IDEAL>(p, kd, nullptr, Pz, jac, nullptr, N, 0ull, fb, 0, p.kmax, nullptr, N);
+#pragma unroll
+      for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
+      iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
+      status[z] = (uint8_t)o.status;
+    }
+    accumulate(cnt, o, active, false);
+    const unsigned m = __ballot_sync(0xffffffffu, active);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt->rescued, (unsigned long long)__popc(m));
+  }
+}
+
+// Launch the rescue kernel over the queue filled by the mixed kernels.
+template <int BS, bool IDEAL> struct RescueKernels {
+  using S = NewtonSmem<false, BS>;
+  static cudaError_t launch(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
+                            Counters* cnt, const Rescue& rs, cudaStream_t st) {
+    static PerDevice once;
+    int grid = 0;
+    cudaError_t e = once.get(
+        [](int* g) {
+          cudaError_t r = cudaFuncSetAttribute(newton_rescue<BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)S::bytes);
+          int dev = 0, sms = 0, per_sm = 0;
+          if (r == cudaSuccess) r = cudaGetDevice(&dev);
+          if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_rescue<BS, IDEAL>, BS,
+                                                                                  S::bytes);
+          if (r == cudaSuccess) *g = sms * (per_sm > 0 ? per_sm : 1);
+          return r;
+        },
+        &grid);
+    if (e != cudaSuccess) return e;
+    newton_rescue<BS, IDEAL><<<(unsigned)grid, BS, S::bytes, st>>>(p, K, rs.Pn, P, iters, status, cnt, rs.queue,
+                                                                    rs.count);
+    return cudaGetLastError();
+  }
+};
 
 // Evaluate the scaled (or raw) residual at Pk once per zone.
 __global__ void residual_once(const __grid_constant__ Params p, const double* __restrict__ K,
@@ -580,60 +670,64 @@ __global__ void rcp_check(int n, unsigned long long seed, double* worst) {
 
 template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
   using S = NewtonSmem<MIXED, BS>;
+  // the kernels' shared-memory limit and the queue kernel's persistent grid
+  // (SMs x resident blocks), once per device
   static cudaError_t configure(int& qgrid) {
-    static bool done = false;
-    static int grid = 0;
-    if (!done) {
-      cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)S::bytes);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(newton_queue<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)S::bytes);
-      int dev = 0, sms = 0, per_sm = 0;
-      if (e == cudaSuccess) e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue<MIXED, BS, IDEAL>, BS, S::bytes);
-      if (e != cudaSuccess) return e;
-      grid = sms * (per_sm > 0 ? per_sm : 1);
-      done = true;
-    }
-    qgrid = grid;
-    return cudaSuccess;
+    static PerDevice once;
+    return once.get(
+        [](int* grid) {
+          cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(newton_queue<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+          int dev = 0, sms = 0, per_sm = 0;
+          if (e == cudaSuccess) e = cudaGetDevice(&dev);
+          if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue<MIXED, BS, IDEAL>, BS, S::bytes);
+          if (e == cudaSuccess) *grid = sms * (per_sm > 0 ? per_sm : 1);
+          return e;
+        },
+        &qgrid);
   }
   static cudaError_t launch(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                             Counters* cnt, const double* Pfb, double accept, int kcut, int* queue, int* qcount,
-                            double* rq, cudaStream_t st) {
+                            double* rq, const Rescue& rs, cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
     const bool compact = queue && qcount && kcut < p.kmax;
+    const bool rescue = MIXED && rs.queue && rs.count && rs.Pn;
     if (compact && (e = cudaMemsetAsync(qcount, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if (rescue && (e = cudaMemsetAsync(rs.count, 0, sizeof(int), st)) != cudaSuccess) return e;
+    int* rqueue = rescue ? rs.queue : nullptr;
     const long long nb = (p.N + BS - 1) / BS;
     newton_dense<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
                                                                  compact ? kcut : p.kmax, compact ? queue : nullptr,
-                                                                 qcount, rq);
-    if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
-    newton_queue<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue, qcount,
-                                                                        rq);
-    return cudaGetLastError();
+                                                                 qcount, rq, rqueue, rs.count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (compact) {
+      newton_queue<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue,
+                                                                          qcount, rq, rqueue, rs.count);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (rescue) return RescueKernels<BS, IDEAL>::launch(p, K, P, iters, status, cnt, rs, st);
+    return cudaSuccess;
   }
 };
 
 template <bool MIXED, bool IDEAL>
 static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                                    Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                                   int* qcount, double* rq, cudaStream_t st) {
+                                   int* qcount, double* rq, const Rescue& rs, cudaStream_t st) {
   switch (cfg.bs) {
     case 32:
       return NewtonKernels<MIXED, 32, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
-                                                     qcount, rq, st);
+                                                     qcount, rq, rs, st);
     case 64:
       return NewtonKernels<MIXED, 64, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
-                                                     qcount, rq, st);
+                                                     qcount, rq, rs, st);
     case 128:
       return NewtonKernels<MIXED, 128, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
-                                                      qcount, rq, st);
+                                                      qcount, rq, rs, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -642,22 +736,26 @@ static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P,
 // the queue kernel over the zones still unconverged after kcut updates.
 // rq: scratch of NV x N doubles for the residuals of the zones handed to the
 // queue kernel (may be NULL: the queue kernel then re-evaluates them).
+// rs: the mixed solver's rescue (Rescue{} for none).
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, cudaStream_t st) {
+                             int* qcount, double* rq, const Rescue& rs, cudaStream_t st) {
   // ideal MHD: the kernels that may take the 5x5 block (ideal_zone)
   if (!p.cond && !p.visc) {
-    if (mixed) return launch_newton_bs<true, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
-    return launch_newton_bs<false, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
+    if (mixed)
+      return launch_newton_bs<true, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
+    return launch_newton_bs<false, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
   }
-  if (mixed) return launch_newton_bs<true, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
-  return launch_newton_bs<false, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, st);
+  if (mixed)
+    return launch_newton_bs<true, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
+  return launch_newton_bs<false, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
 }
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                           Counters* cnt, cudaStream_t st) {
   const NewtonCfg cfg{64, 1 << 30};
-  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, nullptr, st);
+  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, nullptr, Rescue{},
+                          st);
 }
 
 cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, int scaled, double dts, double* R,
@@ -850,6 +948,10 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       for (int m = 0; m < NJ; m++) b[m * BS] = d2f_jac(-r[nb7(m)]);
       float df[NV];
       ok = five ? lu_solve_block_smem<float, BS, 5>(J, b, df) : lu_solve_block_smem<float, BS, 7>(J, b, df);
+      // a float32 solve that overflowed or met a NaN pivot has no direction:
+      // the zone is reported singular, not moved by a huge step
+#pragma unroll
+      for (int i = 0; i < NV; i++) ok = ok && isfinite(df[i]);
 #pragma unroll
       for (int i = 0; i < NV; i++) dP[i] = f2d_jac(df[i]);
       o.lu32++;
@@ -867,7 +969,11 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
       const double lim = 1.0 - 1e-4 * lam;
       if (fin && ft < f * lim * lim) break;
       if (t >= p.lsmax) { o.status |= ST_LSSTALL; break; }
-      lam = fin ? f * lam * lam / (ft + (2.0 * lam - 1.0) * f) : 0.5 * lam;
+      // the quadratic model's minimiser when it is a positive finite number,
+      // else half the step (a non-finite trial, or an overflowed denominator
+      // that would leave lambda = 0 and then 0/0)
+      const double ln = fin ? f * lam * lam / (ft + (2.0 * lam - 1.0) * f) : 0.0;
+      lam = (ln > 0.0 && finite_bits(ln)) ? ln : 0.5 * lam;
     }
 #pragma unroll
     for (int a = 0; a < NV; a++) { P[a] = Pt[a]; r[a] = rt[a]; }
@@ -920,7 +1026,8 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
                                                       Counters* __restrict__ cnt, int kstop, int* __restrict__ queue,
                                                       int* __restrict__ qcount, double* __restrict__ rq,
-                                                      const double* __restrict__ Pfb, double accept) {
+                                                      const double* __restrict__ Pfb, double accept,
+                                                      int* __restrict__ rqueue, int* __restrict__ rcount) {
   using S = NewtonSmemGr<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -946,6 +1053,7 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
     status[z] = (uint8_t)o.status;
   }
   if (queue) enqueue(queue, qcount, active && o.pending, z);
+  if (MIXED && rqueue) to_rescue(rqueue, rcount, o, active, z);
   accumulate(cnt, o, active, fellback);
 }
 
@@ -954,7 +1062,8 @@ __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Pa
                                                       const double* __restrict__ gc, double* __restrict__ P,
                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
                                                       Counters* __restrict__ cnt, const int* __restrict__ queue,
-                                                      const int* __restrict__ qcount, double* __restrict__ rq) {
+                                                      const int* __restrict__ qcount, double* __restrict__ rq,
+                                                      int* __restrict__ rqueue, int* __restrict__ rcount) {
   using S = NewtonSmemGr<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -982,9 +1091,74 @@ __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Pa
       iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
       status[z] = (uint8_t)o.status;
     }
+    if (MIXED && rqueue) to_rescue(rqueue, rcount, o, active, active ? queue[q] : 0);
     accumulate(cnt, o, active, false);
   }
 }
+
+// The rescue of the general-metric mixed solver (see newton_rescue).
+template <int BS, bool IDEAL>
+__global__ void __launch_bounds__(BS) newton_rescue_gr(const __grid_constant__ Params p,
+                                                       const double* __restrict__ K, const double* __restrict__ gc,
+                                                       const double* __restrict__ Pn, double* __restrict__ P,
+                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
+                                                       Counters* __restrict__ cnt, const int* __restrict__ rqueue,
+                                                       const int* __restrict__ rcount) {
+  using S = NewtonSmemGr<false, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* kd = (double*)smem_raw + threadIdx.x;
+  double* md = (double*)(smem_raw + S::kd) + threadIdx.x;
+  void* jac = smem_raw + S::kd + S::md;
+  const long long N = p.N;
+  const int count = *rcount;
+  for (int base = blockIdx.x * BS; base < count; base += gridDim.x * BS) {
+    const int q = base + (int)threadIdx.x;
+    const bool active = q < count;
+    ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
+    if (active) {
+      const long long z = rqueue[q];
+      load_zone_gr<false, BS>(p, K, gc, z, kd, nullptr, md);
+      double Pz[NV];
+#pragma unroll
+      for (int a = 0; a < NV; a++) Pz[a] = (a >= 5 && a <= 7) ? P[a * N + z] : __ldg(Pn + a * N + z);
+      bool fb = false;
+      o = newton_zone_gr<false, BS, IDEAL>(p, kd, nullptr, md, Pz, jac, 0, p.kmax, nullptr, N, nullptr, N, 0ull, fb);
+#pragma unroll
+      for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
+      iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
+      status[z] = (uint8_t)o.status;
+    }
+    accumulate(cnt, o, active, false);
+    const unsigned m = __ballot_sync(0xffffffffu, active);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(&cnt->rescued, (unsigned long long)__popc(m));
+  }
+}
+
+template <int BS, bool IDEAL> struct RescueKernelsGr {
+  using S = NewtonSmemGr<false, BS>;
+  static cudaError_t launch(const Params& p, const double* K, const double* gc, double* P, uint8_t* iters,
+                            uint8_t* status, Counters* cnt, const Rescue& rs, cudaStream_t st) {
+    static PerDevice once;
+    int grid = 0;
+    cudaError_t e = once.get(
+        [](int* g) {
+          cudaError_t r = cudaFuncSetAttribute(newton_rescue_gr<BS, IDEAL>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+          int dev = 0, sms = 0, per_sm = 0;
+          if (r == cudaSuccess) r = cudaGetDevice(&dev);
+          if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          if (r == cudaSuccess)
+            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_rescue_gr<BS, IDEAL>, BS, S::bytes);
+          if (r == cudaSuccess) *g = sms * (per_sm > 0 ? per_sm : 1);
+          return r;
+        },
+        &grid);
+    if (e != cudaSuccess) return e;
+    newton_rescue_gr<BS, IDEAL><<<(unsigned)grid, BS, S::bytes, st>>>(p, K, gc, rs.Pn, P, iters, status, cnt,
+                                                                       rs.queue, rs.count);
+    return cudaGetLastError();
+  }
+};
 
 // Scaled (or raw) residual at Pk, general metric.
 __global__ void residual_once_gr(const __grid_constant__ Params p, const double* __restrict__ K,
@@ -1020,44 +1194,48 @@ __global__ void residual_once_gr(const __grid_constant__ Params p, const double*
 
 template <bool MIXED, int BS, bool IDEAL> struct NewtonKernelsGr {
   using S = NewtonSmemGr<MIXED, BS>;
+  // the kernels' shared-memory limit and the queue kernel's persistent grid
+  // (SMs x resident blocks), once per device
   static cudaError_t configure(int& qgrid) {
-    static bool done = false;
-    static int grid = 0;
-    if (!done) {
-      cudaError_t e = cudaFuncSetAttribute(newton_dense_gr<MIXED, BS, IDEAL>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)S::bytes);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(newton_queue_gr<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)S::bytes);
-      int dev = 0, sms = 0, per_sm = 0;
-      if (e == cudaSuccess) e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue_gr<MIXED, BS, IDEAL>, BS, S::bytes);
-      if (e != cudaSuccess) return e;
-      grid = sms * (per_sm > 0 ? per_sm : 1);
-      done = true;
-    }
-    qgrid = grid;
-    return cudaSuccess;
+    static PerDevice once;
+    return once.get(
+        [](int* grid) {
+          cudaError_t e = cudaFuncSetAttribute(newton_dense_gr<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(newton_queue_gr<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+          int dev = 0, sms = 0, per_sm = 0;
+          if (e == cudaSuccess) e = cudaGetDevice(&dev);
+          if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_queue_gr<MIXED, BS, IDEAL>, BS, S::bytes);
+          if (e == cudaSuccess) *grid = sms * (per_sm > 0 ? per_sm : 1);
+          return e;
+        },
+        &qgrid);
   }
   static cudaError_t launch(const Params& p, const double* K, const double* gc, double* P, uint8_t* iters,
                             uint8_t* status, Counters* cnt, int kcut, int* queue, int* qcount, double* rq,
-                            const double* Pfb, double accept, cudaStream_t st) {
+                            const double* Pfb, double accept, const Rescue& rs, cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
     const bool compact = queue && qcount && kcut < p.kmax;
+    const bool rescue = MIXED && rs.queue && rs.count && rs.Pn;
     if (compact && (e = cudaMemsetAsync(qcount, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if (rescue && (e = cudaMemsetAsync(rs.count, 0, sizeof(int), st)) != cudaSuccess) return e;
+    int* rqueue = rescue ? rs.queue : nullptr;
     const long long nb = (p.N + BS - 1) / BS;
     newton_dense_gr<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
                                                                     compact ? kcut : p.kmax,
-                                                                    compact ? queue : nullptr, qcount, rq, Pfb, accept);
-    if ((e = cudaGetLastError()) != cudaSuccess || !compact) return e;
-    newton_queue_gr<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt, queue,
-                                                                      qcount, rq);
-    return cudaGetLastError();
+                                                                    compact ? queue : nullptr, qcount, rq, Pfb, accept,
+                                                                    rqueue, rs.count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (compact) {
+      newton_queue_gr<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
+                                                                               queue, qcount, rq, rqueue, rs.count);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (rescue) return RescueKernelsGr<BS, IDEAL>::launch(p, K, gc, P, iters, status, cnt, rs, st);
+    return cudaSuccess;
   }
 };
 
@@ -1067,29 +1245,30 @@ template <bool IDEAL>
 static cudaError_t launch_newton_gr_i(const Params& p, int mixed, const double* K, const double* gc, double* P,
                                      uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg,
                                      int* queue, int* qcount, double* rq, const double* Pfb, double accept,
-                                     cudaStream_t st) {
+                                     const Rescue& rs, cudaStream_t st) {
   const bool b32 = cfg.bs == 32;
   if (mixed) {
     if (b32)
       return NewtonKernelsGr<true, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
-                                                      Pfb, accept, st);
+                                                      Pfb, accept, rs, st);
     return NewtonKernelsGr<true, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
-                                                    Pfb, accept, st);
+                                                    Pfb, accept, rs, st);
   }
   if (b32)
     return NewtonKernelsGr<false, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
-                                                     Pfb, accept, st);
+                                                     Pfb, accept, rs, st);
   return NewtonKernelsGr<false, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
-                                                   Pfb, accept, st);
+                                                   Pfb, accept, rs, st);
 }
 
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, const double* Pfb, double accept, cudaStream_t st) {
+                             int* qcount, double* rq, const double* Pfb, double accept, const Rescue& rs,
+                             cudaStream_t st) {
   // ideal MHD: the kernels that may take the 5x5 block (ideal_zone)
   if (!p.cond && !p.visc)
-    return launch_newton_gr_i<true>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, st);
-  return launch_newton_gr_i<false>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, st);
+    return launch_newton_gr_i<true>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, rs, st);
+  return launch_newton_gr_i<false>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, rs, st);
 }
 
 // Learned-start features in a general metric, in the flat path's layout:

@@ -113,3 +113,21 @@ extern "C" int grim_step_static(const grim_grid* grid, const grim_metric* metric
   if (grim::launch_newton(p, mixed, K, P_out, iters, status, cnt, st) != cudaSuccess) return GRIM_ECUDA;
   return GRIM_OK;
 }
+
+extern "C" int grim_step_static_stats(void* stream, grim_stats* out) {
+  if (!out) return GRIM_EINVAL;
+  double* base = nullptr;
+  if (scratch_address(&base) != cudaSuccess) return GRIM_ECUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  grim::Counters c;
+  if (cudaMemcpyAsync(&c, base + kOffCnt, sizeof(c), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GRIM_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GRIM_ECUDA;
+  std::memset(out, 0, sizeof(*out));
+  out->zones = c.zones; out->failed = c.failed; out->iters = c.iters;
+  out->evals64 = c.evals64; out->evals32 = c.evals32; out->lu64 = c.lu64; out->lu32 = c.lu32;
+  for (int i = 0; i < 32; i++) out->hist[i] = c.hist[i];
+  const long long bits = (long long)c.maxres_bits;
+  std::memcpy(&out->max_res, &bits, sizeof(bits));
+  out->launches = 4;
+  return GRIM_OK;
+}

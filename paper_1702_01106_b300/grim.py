@@ -22,7 +22,7 @@ _lib = None
 EXPORTS = (
     "grim_init", "grim_step", "grim_step_host", "grim_stage", "grim_residual", "grim_get_stats",
     "grim_reset_stats", "grim_last_error", "grim_strerror", "grim_destroy", "grim_peak_flops",
-    "grim_profile", "grim_kernel_times", "grim_step_static", "grim_math_selftest",
+    "grim_profile", "grim_kernel_times", "grim_step_static", "grim_step_static_stats", "grim_math_selftest",
     "grim_mlp_create", "grim_mlp_destroy", "grim_mlp_param_count", "grim_mlp_get_params", "grim_mlp_set_params",
     "grim_mlp_fit_norm", "grim_mlp_train", "grim_mlp_gradient", "grim_mlp_sample", "grim_set_guess",
     "grim_get_tuning", "grim_set_tuning", "grim_autotune", "grim_use_graphs",
@@ -68,7 +68,8 @@ class GrimStats(ctypes.Structure):
     _fields_ = [("zones", ctypes.c_ulonglong), ("failed", ctypes.c_ulonglong), ("iters", ctypes.c_ulonglong),
                 ("evals64", ctypes.c_ulonglong), ("evals32", ctypes.c_ulonglong), ("lu64", ctypes.c_ulonglong),
                 ("lu32", ctypes.c_ulonglong), ("hist", ctypes.c_ulonglong * 32), ("max_res", ctypes.c_double),
-                ("launches", ctypes.c_ulonglong), ("fallbacks", ctypes.c_ulonglong)]
+                ("launches", ctypes.c_ulonglong), ("fallbacks", ctypes.c_ulonglong),
+                ("rescued", ctypes.c_ulonglong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
@@ -103,6 +104,7 @@ def load():
     lib.grim_peak_flops.argtypes = [ctypes.POINTER(dp), ctypes.POINTER(dp)]
     lib.grim_step_static.argtypes = [ctypes.POINTER(GrimGrid), ctypes.POINTER(GrimMetric),
                                      ctypes.POINTER(GrimPhysics), ctypes.POINTER(GrimSolver), vp, vp, vp, dp]
+    lib.grim_step_static_stats.argtypes = [vp, ctypes.POINTER(GrimStats)]
     lib.grim_profile.argtypes = [vp, i]
     lib.grim_math_selftest.argtypes = [i, ctypes.POINTER(dp)]
     ll, ull, fp = ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)
@@ -179,6 +181,20 @@ def step_static(prob, P_in, P_out, dt: float, precision: int = GRIM_FP64, stream
         stream = torch.cuda.current_stream()
     return lib.grim_step_static(ctypes.byref(g), ctypes.byref(m), ctypes.byref(ph), ctypes.byref(sv),
                                 ctypes.c_void_p(stream.cuda_stream), _f64(P_in), _f64(P_out), dt)
+
+
+def step_static_stats(stream=None) -> dict:
+    """grim_step_static_stats: the counters of the last grim_step_static call
+    on the current device (waits for the stream)."""
+    import torch
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = GrimStats()
+    rc = lib.grim_step_static_stats(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(s))
+    if rc != 0:
+        raise RuntimeError(f"grim_step_static_stats: {lib.grim_strerror(rc).decode()}")
+    return s.as_dict()
 
 
 class Grim:

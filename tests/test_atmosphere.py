@@ -158,3 +158,66 @@ def test_oracle_holds_the_conducting_atmosphere(orc):
     for k in range(2):
         assert d[k][0] > 3.5 * d[k + 1][0] and d[k][1] > 3.5 * d[k + 1][1], d
     assert d[2][1] < 1e-5
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gpu_conducting_atmosphere(orc, precision):
+    """The heat-flux atmosphere through the CUDA path, float64 and mixed:
+    16 steps of the 64 x 8 band within 1e-9 of the oracle (float64 at tol
+    1e-12, mixed at tol 1e-10 after one step); the CUDA residual of the
+    steady state falls 2.5x or more per doubling in every row; and after
+    t = 10 the interior drift of rho and the relative drift of q~ fall 3.5x
+    or more per doubling (64 x 8 to 256 x 32, solved to 1e-13 in float64 and
+    1e-12 in mixed precision), as the oracle's do up to 128 x 16.  The
+    residual is measured where the drift is, 220 < r < 280: the density of
+    this atmosphere has a maximum near r = 215, where the limiter flattens
+    the reconstruction, so the largest residual over the whole interior
+    stops falling once that zone dominates (at 256 radial zones)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_01106_b300.grim import Grim
+    from tests.gpu_helpers import rel_field_err
+    dev = torch.device("cuda:0")
+    tol = 1e-12 if precision == 0 else 1e-10
+
+    prob = at.atmosphere_problem(64, 8, tol=tol)
+    P0, _ = at.conducting_state(prob, F_HEAT)
+    dt = at.atmosphere_dt(prob)
+    g = Grim(prob, precision=precision)
+    a = torch.from_numpy(P0).to(dev)
+    ref = P0.copy()
+    for _ in range(16 if precision == 0 else 1):
+        g.step(a, a, dt)
+        ref, _, st, _ = orc.step(prob.with_(tol=1e-13), ref, dt)
+        assert st.max() == 0
+    assert g.stats()["failed"] == 0
+    assert rel_field_err(a.cpu().numpy(), ref).max() < 1e-9
+    g.close()
+
+    prev = None
+    d = []
+    for n1, n2 in ((64, 8), (128, 16), (256, 32)):
+        prob = at.atmosphere_problem(n1, n2, tol=1e-13 if precision == 0 else 1e-12)
+        P0, r = at.conducting_state(prob, F_HEAT)
+        dt = at.atmosphere_dt(prob)
+        g = Grim(prob, precision=precision)
+        a = torch.from_numpy(P0).to(dev)
+        R = torch.empty_like(a)
+        g.residual(a, a, 0.5 * dt, a, R)
+        inner = (r > 220) & (r < 280)
+        R = R.cpu().numpy().reshape(10, n2, n1)[:, :, inner]
+        m = np.abs(R).max(axis=(1, 2))[[0, 1, 2, 3, 8]] / (0.5 * dt)
+        if prev is not None:
+            assert np.all(prev > 2.5 * m), (prev, m)
+        prev = m
+        for _ in range(int(round(10.0 / dt))):
+            g.step(a, a, dt)
+        assert g.stats()["failed"] == 0
+        P = a.cpu().numpy()
+        d.append((float(np.abs(P[0, 0][:, inner] / P0[0, 0][:, inner] - 1).mean()),
+                  float(np.abs(P[8, 0][:, inner] / P0[8, 0][:, inner] - 1).mean())))
+        g.close()
+    for k in range(2):
+        assert d[k][0] > 3.5 * d[k + 1][0] and d[k][1] > 3.5 * d[k + 1][1], d

@@ -288,7 +288,8 @@ def _paper_newton(orc, prob, zc, P):
             ft = rt @ rt
             if math.sqrt(ft) < math.sqrt(f) * (1 - 1e-4 * lam) or t == prob.ls_max:
                 break
-            lam = f / (ft + (2 * lam - 1) * f) * lam * lam
+            ln = f / (ft + (2 * lam - 1) * f) * lam * lam if math.isfinite(ft) else 0.0
+            lam = ln if (ln > 0 and math.isfinite(ln)) else 0.5 * lam
         P, r, f = Pt, rt, ft
         k += 1
     return P, k, evals
