@@ -858,6 +858,17 @@ static double sumsq(const double* r) {
 
 struct NewtonOut { int iters, status, evals; };
 
+// Perturbed component of the FD Jacobian (Section 3.1): (1 + eps) P_j, or
+// P_j + eps where |P_j| < 5 eps (small(), read as an absolute step so that the
+// divisor never vanishes).  The absolute floor is for components that pass
+// through zero; rho and u are positive, and their step stays relative at
+// every magnitude (the internal energy of a cold atmosphere, 1e-11, would
+// otherwise move by 1e4 times itself).
+static double fd_perturbed(double x, double eps, bool positive) {
+  if (positive && x > 0.0) return (1.0 + eps) * x;
+  return (std::fabs(x) < 5.0 * eps) ? x + eps : (1.0 + eps) * x;
+}
+
 // Newton iteration of Section 3 with the FD Jacobian of Section 3.1 and the
 // quadratic backtracking line search of Section 3.2.
 static NewtonOut newton(const ZoneConst& z, const Params& p, double P[10]) {
@@ -877,7 +888,7 @@ static NewtonOut newton(const ZoneConst& z, const Params& p, double P[10]) {
     for (int j = 0; j < 10; j++) {
       double Pe[10];
       std::memcpy(Pe, P, sizeof(Pe));
-      Pe[j] = (std::fabs(P[j]) < 5.0 * eps) ? P[j] + eps : (1.0 + eps) * P[j];
+      Pe[j] = fd_perturbed(P[j], eps, j <= 1);
       double re_[10];
       residual(z, p, Pe, re_);
       o.evals++;
@@ -1362,7 +1373,7 @@ int oracle_zone_jacobian_fd(const int* ip, const double* dp, const double* zc, c
   for (int j = 0; j < 10; j++) {
     double Pe[10], re_[10];
     std::memcpy(Pe, P, sizeof(Pe));
-    Pe[j] = (std::fabs(P[j]) < 5.0 * p.eps) ? P[j] + p.eps : (1.0 + p.eps) * P[j];
+    Pe[j] = fd_perturbed(P[j], p.eps, j <= 1);
     residual(z, p, Pe, re_);
     for (int i = 0; i < 10; i++) J[i * 10 + j] = (re_[i] - r[i]) / (Pe[j] - P[j]);
   }

@@ -40,7 +40,9 @@ cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double 
 cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo, double* faces, int ffstates,
                             cudaStream_t st);
 cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                                 const double* geo, double* faces, double* K, double* P0, cudaStream_t st);
+                                 const double* geo, double* faces, double* K, double* P0, double* cache, int mode,
+                                 float* feat, cudaStream_t st);
+long long gr_cache_doubles(long long N);
 cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K, const double* Pn,
                              const uint8_t* status, double* P, cudaStream_t st);
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
@@ -225,7 +227,8 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
                                                               : grim::face_scratch_doubles(p.n1, p.n2)))) !=
           cudaSuccess ||
       (ctx->gr && (e = cudaMalloc(&ctx->geo, sizeof(double) * grim::gr_geometry_doubles(p))) != cudaSuccess) ||
-      (e = cudaMalloc(&ctx->pncache, sizeof(double) * grim::pn_cache_doubles(p.N))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->pncache, sizeof(double) * (ctx->gr ? grim::gr_cache_doubles(p.N)
+                                                              : grim::pn_cache_doubles(p.N)))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->iters, N)) != cudaSuccess || (e = cudaMalloc(&ctx->status, N)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->cnt, sizeof(grim::Counters))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->queue, sizeof(int) * N)) != cudaSuccess ||
@@ -254,7 +257,8 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
       GRIM_CUDA(grim::launch_gr_faces(ctx->p, PE, ctx->geo, ctx->faces, ctx->precision == GRIM_MIXED, ctx->cur), "face kernel");
     }
     KernelMark m(ctx, GRIM_K_ZONECONST, 3);
-    GRIM_CUDA(grim::launch_gr_zone_const(ctx->p, Pn, PE, guess, dts, ctx->geo, ctx->faces, ctx->K, Pout, ctx->cur),
+    GRIM_CUDA(grim::launch_gr_zone_const(ctx->p, Pn, PE, guess, dts, ctx->geo, ctx->faces, ctx->K, Pout,
+                                         ctx->pncache, mode, feat, ctx->cur),
               "zone-constant kernel");
     return GRIM_OK;
   }
@@ -283,15 +287,11 @@ static grim::Rescue rescue(grim_ctx* ctx, const double* Pn, const double* PE, co
 static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
                      double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
   const bool learned = ctx->mlp && !guess;
-  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode, learned && !ctx->gr ? ctx->feat : nullptr);
+  int rc = run_explicit(ctx, Pn, PE, dts, guess, Pout, mode, learned ? ctx->feat : nullptr);
   if (rc) return rc;
   if (learned) {
-    // the flat zone kernel wrote the increment features; in a general metric
-    // a feature kernel evaluates the stage's residual at P_n
-    KernelMark m(ctx, GRIM_K_MLP, ctx->gr ? 2 : 1);
-    if (ctx->gr)
-      GRIM_CUDA(grim::launch_features_gr(ctx->p, ctx->K, ctx->geo, Pn, nullptr, nullptr, nullptr, ctx->feat, ctx->cur),
-                "feature kernel");
+    // the zone-constant kernel wrote the increment features beside the constants
+    KernelMark m(ctx, GRIM_K_MLP, 1);
     GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->gr ? ctx->geo : nullptr, ctx->cur),
               "mlp kernel");
   }

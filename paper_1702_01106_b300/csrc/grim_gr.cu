@@ -178,10 +178,22 @@ struct GrArgs {
   double* Src;  // [NSRC][N]: sources at P^E of every zone
   const double* gc;
   const double* gf[2];
+  // P_n quantities shared by the two stages of a step (NCACHE_GR planes):
+  // sqrt(-g) U(P_n) [10], Theta_n, u_mu,n [4], u^t_n.  mode 0: a general
+  // stage (no cache); 1: the half step (the sources kernel, whose P^E is
+  // P_n, writes the cache; the zone-constant kernel reads it); 2: the full
+  // step (reads the cache and the row weights K_U the half step wrote, which
+  // depend on P_n only).
+  double* cache;
+  int mode;
+  // with a learned start: the ten increment features -r_a(P_n) of each zone
+  // (float32 [10][N]), from the constants computed here
+  float* feat;
   // float-float copies of gamma, gamma-1, sqrt(phi gamma), sqrt(psi gamma)
   // and kappa gamma (hi, lo pairs), for the float-float face states
   float ffc[10];
 };
+constexpr int NCACHE_GR = NV + 6;
 
 // Extents and offsets of the face array of direction D: along D the faces
 // 0..n_D; across it one ring of ghost faces in every active direction.
@@ -521,34 +533,24 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
   met_load(m, g);
   ZG<double> ze;
   zg_load(ze, PEz, m, c);
-  // --- geometric source at P^E: sqrt(-g) T^k_l Gamma^l_{nu k} (rows 1..4)
-  double Sg[4] = {0.0, 0.0, 0.0, 0.0};
-  {
-    double T[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) zg_stress_row(ze, r, T[r]);
-#pragma unroll
-    for (int n = 0; n < 4; n++) {
-      double s = 0.0;
-#pragma unroll
-      for (int kk = 0; kk < 4; kk++)
-#pragma unroll
-        for (int l = 0; l < 4; l++) s += T[kk][l] * g(G_GAM + 10 * l + sym(n, kk));
-      Sg[n] = sg * s;
-    }
-  }
   const double cs2E = p.gamma * ze.pg * nr_rcp(ze.rho + p.gamma * ze.u);
   const double ith = nr_rcp(ze.theta);
   const double* bh = ze.bhcon;
-  // Gl[sym(mu, nu)] = sum_l Gamma^l_{mu nu} u_l at P^E (symmetric in mu, nu),
-  // and from it the sum over nu, l of Gamma^l_{nu mu} u^nu u_l for each mu
-  double Gl[10];
+  // Gl[sym(mu, nu)] = sum_l Gamma^l_{mu nu} u_l and Gb[sym(mu, nu)] = sum_l
+  // Gamma^l_{mu nu} bhat_l at P^E (symmetric in mu, nu), and from Gl the sum
+  // over nu, l of Gamma^l_{nu mu} u^nu u_l for each mu
+  double Gl[10], Gb[10];
 #pragma unroll
   for (int a = 0; a < 10; a++) {
-    double s = 0.0;
+    double s = 0.0, t = 0.0;
 #pragma unroll
-    for (int l = 0; l < 4; l++) s += g(G_GAM + 10 * l + a) * ze.ucov[l];
+    for (int l = 0; l < 4; l++) {
+      const double G = g(G_GAM + 10 * l + a);
+      s += G * ze.ucov[l];
+      t += G * ze.bhcov[l];
+    }
     Gl[a] = s;
+    Gb[a] = t;
   }
   double Gu[4];
 #pragma unroll
@@ -557,6 +559,27 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
 #pragma unroll
     for (int nu = 0; nu < 4; nu++) s += Gl[sym(nu, mu)] * ze.ucon[nu];
     Gu[mu] = s;
+  }
+  // --- geometric source at P^E: sqrt(-g) T^k_l Gamma^l_{nu k} (rows 1..4),
+  // with T^k_l of Eq. fullSEtens taken apart: (w + b^2 + dP/3) u^k u_l +
+  // p_t delta^k_l - b^2 bhat^k bhat_l + q (bhat^k u_l + u^k bhat_l) - dP
+  // bhat^k bhat_l, so that each part contracts Gamma with the vectors alone
+  double Sg[4];
+  {
+    const double q = ze.qt * ze.qs, dp = ze.dpt * ze.ds, third = dp * (1.0 / 3.0);
+    const double A = ze.w0 + ze.bsq + third, pt = ze.pg + 0.5 * ze.bsq + third;
+#pragma unroll
+    for (int n = 0; n < 4; n++) {
+      double bGl = 0.0, uGb = 0.0, bGb = 0.0, tr = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        bGl += bh[kk] * Gl[sym(n, kk)];
+        uGb += ze.ucon[kk] * Gb[sym(n, kk)];
+        bGb += bh[kk] * Gb[sym(n, kk)];
+        tr += g(G_GAM + 10 * kk + sym(n, kk));   // Gamma^k_{n k}
+      }
+      Sg[n] = sg * (A * Gu[n] + pt * tr + q * (bGl + uGb) - (ze.bsq + dp) * bGb);
+    }
   }
   // heat flux: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
   double Aq = 0.0, Bq = 0.0, Cq[4] = {0.0, 0.0, 0.0, 0.0};
@@ -601,6 +624,18 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
                           Ad, Dd[0], Dd[1], Dd[2], Dd[3], Ed, divu_sp};
 #pragma unroll
   for (int q = 0; q < NSRC; q++) Sz[q * N] = x[q];
+  if (a.mode == 1) {
+    // the half step's P^E is P_n: its quantities go to the step's P_n cache
+    // for the zone-constant kernels of both stages
+    double U[NV];
+    zg_conserved(ze, U);
+#pragma unroll
+    for (int v = 0; v < NV; v++) a.cache[v * N + z] = sg * U[v];
+    a.cache[NV * N + z] = ze.theta;
+#pragma unroll
+    for (int q = 0; q < 4; q++) a.cache[(NV + 1 + q) * N + z] = ze.ucov[q];
+    a.cache[(NV + 5) * N + z] = ze.ucon[0];
+  }
 }
 
 // The stage constants of every zone (float64): flux divergence with flux-CT,
@@ -659,23 +694,38 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
       divF[5 + B] += (0.5 * (E[1][0] + E[1][1]) - 0.5 * (E[0][0] + E[0][1])) * p.idx[A];
       divF[5 + A] += (-0.5 * (E[0][1] + E[1][1]) + 0.5 * (E[0][0] + E[1][0])) * p.idx[B];
     }
-  // --- state at P_n and the conserved variables U(P_n) (float64)
-  const RC<double> c = make_rc<double>(p);
+  // --- state at P_n and the conserved variables U(P_n) (float64); in a
+  // step of grim_step from the cache the half step's sources kernel wrote
   const GT g = centre_geo(p, a.gc, i, j);
-  Met<double> m;
-  met_load(m, g);
   const double sg = g(G_SQRTG), tau = g(G_TAUR);
-  double PEz[NV], Pnz[NV];
+  double Pnz[NV];
 #pragma unroll
-  for (int v = 0; v < NV; v++) { PEz[v] = __ldg(a.PE + v * N + z); Pnz[v] = __ldg(a.Pn + v * N + z); }
-  ZG<double> zn;
-  zg_load(zn, Pnz, m, c);
-  double Un[NV];
-  zg_conserved(zn, Un);
+  for (int v = 0; v < NV; v++) Pnz[v] = __ldg(a.Pn + v * N + z);
+  double Un[NV], th_n, ucn[4], ut_n;
+  if (a.mode != 0) {
 #pragma unroll
-  for (int v = 0; v < NV; v++) Un[v] *= sg;
+    for (int v = 0; v < NV; v++) Un[v] = __ldg(a.cache + v * N + z);
+    th_n = __ldg(a.cache + NV * N + z);
+#pragma unroll
+    for (int m = 0; m < 4; m++) ucn[m] = __ldg(a.cache + (NV + 1 + m) * N + z);
+    ut_n = __ldg(a.cache + (NV + 5) * N + z);
+  } else {
+    const RC<double> c = make_rc<double>(p);
+    Met<double> m;
+    met_load(m, g);
+    ZG<double> zn;
+    zg_load(zn, Pnz, m, c);
+    zg_conserved(zn, Un);
+#pragma unroll
+    for (int v = 0; v < NV; v++) Un[v] *= sg;
+    th_n = zn.theta;
+#pragma unroll
+    for (int q = 0; q < 4; q++) ucn[q] = zn.ucov[q];
+    ut_n = zn.ucon[0];
+  }
+  const double qt_n = Pnz[8], dpt_n = Pnz[9];
   // --- sources at P^E (geometric source, closure coefficients)
-  double Sg[4], Aq, Bq, Cq[4], Ad, Dd[4], Ed, divu_sp;
+  double Sg[4], Aq, Bq, Cq[4], Ad, Dd[4], Ed, divu_sp, hoq, hod;
   {
     const double* Sz = a.Src + z;
     double x[NSRC];
@@ -684,47 +734,68 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
 #pragma unroll
     for (int q = 0; q < 4; q++) { Sg[q] = x[q]; Cq[q] = x[6 + q]; Dd[q] = x[11 + q]; }
     Aq = x[4]; Bq = x[5]; Ad = x[10]; Ed = x[15]; divu_sp = x[16];
+    hoq = p.ho ? 0.5 * __ldg(a.PE + 8 * N + z) : 0.0;
+    hod = p.ho ? 0.5 * __ldg(a.PE + 9 * N + z) : 0.0;
   }
   // --- stage constants (row scale folded in; sqrt(-g) folded into kU)
   const double dts = a.dts, idts = a.idts, it = nr_rcp(tau), isg = nr_rcp(sg);
   double* Kz = a.K + z;
   double sr[NV];  // 1/(|U_v(P_n)| + |U_0(P_n)|)
+  double r[NV];   // the stage's scaled residual at P_n: the learned start's features
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    sr[v] = nr_rcp(fabs(Un[v]) + fabs(Un[0]));
-    Kz[(K_U + v) * N] = sr[v] * sg;
+    if (a.mode == 2) {
+      sr[v] = Kz[(K_U + v) * N] * isg;
+    } else {
+      sr[v] = nr_rcp(fabs(Un[v]) + fabs(Un[0]));
+      Kz[(K_U + v) * N] = sr[v] * sg;
+    }
     const double src = (v >= 1 && v <= 4) ? Sg[v - 1] : 0.0;
-    Kz[(K_C + v) * N] = sr[v] * (dts * (divF[v] - src) - Un[v]);
+    const double kc = sr[v] * (dts * (divF[v] - src) - Un[v]);
+    Kz[(K_C + v) * N] = kc;
+    r[v] = sr[v] * Un[v] + kc;
   }
-  const double hoq = p.ho ? 0.5 * PEz[8] : 0.0, hod = p.ho ? 0.5 * PEz[9] : 0.0;
   {
     const double s8 = sr[8] * dts;
     double cst = -Un[8] * idts + divF[8];
-    double src = 0.5 * zn.qt * it - Aq * it + Bq * zn.theta * idts * it;
+    double src = 0.5 * qt_n * it - Aq * it + Bq * th_n * idts * it;
     #pragma unroll
-    for (int mu = 0; mu < 4; mu++) src += Cq[mu] * zn.ucov[mu] * idts * it;
-    src -= hoq * (divu_sp - zn.ucon[0] * idts);
+    for (int mu = 0; mu < 4; mu++) src += Cq[mu] * ucn[mu] * idts * it;
+    src -= hoq * (divu_sp - ut_n * idts);
     cst += sg * src;
-    Kz[(K_C + 8) * N] = s8 * cst;
-    Kz[(K_Q + 0) * N] = sg * 0.5 * s8 * it;
-    Kz[(K_Q + 1) * N] = -sg * s8 * Bq * idts * it;
-    #pragma unroll
-    for (int mu = 0; mu < 4; mu++) Kz[(K_Q + 2 + mu) * N] = -sg * s8 * Cq[mu] * idts * it;
-    Kz[(K_Q + 6) * N] = -sg * s8 * hoq * idts;
+    const double kq[7] = {sg * 0.5 * s8 * it, -sg * s8 * Bq * idts * it, -sg * s8 * Cq[0] * idts * it,
+                          -sg * s8 * Cq[1] * idts * it, -sg * s8 * Cq[2] * idts * it, -sg * s8 * Cq[3] * idts * it,
+                          -sg * s8 * hoq * idts};
+    const double kc = s8 * cst;
+    Kz[(K_C + 8) * N] = kc;
+#pragma unroll
+    for (int q = 0; q < 7; q++) Kz[(K_Q + q) * N] = kq[q];
+    r[8] = sr[8] * Un[8] + kc + kq[0] * qt_n + kq[1] * th_n + kq[6] * ut_n;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) r[8] += kq[2 + mu] * ucn[mu];
   }
   {
     const double s9 = sr[9] * dts;
     double cst = -Un[9] * idts + divF[9];
-    double src = 0.5 * zn.dpt * it - Ad * it + Ed * zn.ucon[0] * idts * it;
+    double src = 0.5 * dpt_n * it - Ad * it + Ed * ut_n * idts * it;
     #pragma unroll
-    for (int nn = 0; nn < 4; nn++) src += Dd[nn] * zn.ucov[nn] * idts * it;
-    src -= hod * (divu_sp - zn.ucon[0] * idts);
+    for (int nn = 0; nn < 4; nn++) src += Dd[nn] * ucn[nn] * idts * it;
+    src -= hod * (divu_sp - ut_n * idts);
     cst += sg * src;
-    Kz[(K_C + 9) * N] = s9 * cst;
-    Kz[(K_D + 0) * N] = sg * 0.5 * s9 * it;
-    #pragma unroll
-    for (int nn = 0; nn < 4; nn++) Kz[(K_D + 1 + nn) * N] = -sg * s9 * Dd[nn] * idts * it;
-    Kz[(K_D + 5) * N] = -sg * s9 * (Ed * idts * it + hod * idts);
+    const double kd[6] = {sg * 0.5 * s9 * it, -sg * s9 * Dd[0] * idts * it, -sg * s9 * Dd[1] * idts * it,
+                          -sg * s9 * Dd[2] * idts * it, -sg * s9 * Dd[3] * idts * it,
+                          -sg * s9 * (Ed * idts * it + hod * idts)};
+    const double kc = s9 * cst;
+    Kz[(K_C + 9) * N] = kc;
+#pragma unroll
+    for (int q = 0; q < 6; q++) Kz[(K_D + q) * N] = kd[q];
+    r[9] = sr[9] * Un[9] + kc + kd[0] * dpt_n + kd[5] * ut_n;
+#pragma unroll
+    for (int nn = 0; nn < 4; nn++) r[9] += kd[1 + nn] * ucn[nn];
+  }
+  if (a.feat) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) a.feat[v * N + z] = (float)(-r[v]);
   }
   // --- initial guess: P_n (or the given guess), B from the flux-CT update
 #pragma unroll
@@ -736,8 +807,9 @@ __global__ void __launch_bounds__(128) zone_const_gr(const __grid_constant__ Par
 }
 
 // ---------------------------------------------------------------- floors
-// After the Newton solves of a stage: a zone whose iteration ended with a
-// non-zero status (no admissible root found) reverts to its start, P_n with
+// After the Newton solves of a stage, for the zones whose iteration ended
+// with a non-zero status (no admissible root found; the Newton kernels floor
+// the converged zones themselves): the zone reverts to its start, P_n with
 // the flux-CT field B = -kC/kU of its field rows; then rho >= 1e-5 r^{-3/2},
 // u >= 1e-7 r^{-5/2} (r = 1 in Minkowski space), and -b^2 <= dP <= b^2/2 on
 // the physical anisotropy dP = dP~ (psi c_s^2 P_g)^(1/2).
@@ -746,12 +818,12 @@ __global__ void floors_gr(const __grid_constant__ Params p, const double* __rest
                           const uint8_t* __restrict__ status, double* __restrict__ P) {
   const long long N = p.N;
   const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (z >= N) return;
+  if (z >= N || status[z] == 0) return;
   const int i = (int)(z % p.n1), j = (int)((z / p.n1) % p.n2);
   const GT g = centre_geo(p, gc, i, j);
   const double r = g(G_R);
   double Pz[NV];
-  const bool failed = status[z] != 0;
+  const bool failed = true;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     if (failed) Pz[v] = (v >= 5 && v <= 7) ? -__ldg(K + (K_C + v) * N + z) / __ldg(K + (K_U + v) * N + z)
@@ -857,12 +929,20 @@ cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo
   return ffstates ? launch_gr_faces_s<ff>(p, a, st) : launch_gr_faces_s<double>(p, a, st);
 }
 
+long long gr_cache_doubles(long long N) { return (long long)NCACHE_GR * N; }
+
+// mode, cache: the P_n cache of a step (mode 0: none); feat: the learned
+// start's increment features (NULL: not wanted).
 cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
-                                 const double* geo, double* faces, double* K, double* P0, cudaStream_t st) {
+                                 const double* geo, double* faces, double* K, double* P0, double* cache, int mode,
+                                 float* feat, cudaStream_t st) {
   GrArgs a{};
   gr_args(p, geo, faces, a);
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.K = K; a.P0 = P0;
   a.idts = 1.0 / dts;
+  a.cache = cache;
+  a.mode = cache ? mode : 0;
+  a.feat = feat;
   derived_gr<<<(unsigned)((ghost_box(p).size + 127) / 128), 128, 0, st>>>(p, a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -98,9 +98,11 @@ __host__ __device__ constexpr int jslot(int i) { return i < 5 ? i : (i >= 8 ? i 
 
 // Perturbed component of the FD Jacobian (Section 3.1): (1 + eps) x, or
 // x + eps when |x| < 5 eps (small() read as an absolute step, so the divisor
-// never approaches zero).
-template <typename T> __device__ __forceinline__ T fd_step(T x, T eps) {
-  return (fabs(x) < T(5) * eps) ? x + eps : (T(1) + eps) * x;
+// never approaches zero).  The absolute floor is for components that pass
+// through zero: the positive rho and u (positive = true) keep the relative
+// step at every magnitude.
+template <typename T> __device__ __forceinline__ T fd_step(T x, T eps, bool positive) {
+  return (fabs(x) < T(5) * eps && !(positive && x > T(0))) ? x + eps : (T(1) + eps) * x;
 }
 
 // Residual rows of the state z after its component C changed to x (groups
@@ -151,7 +153,7 @@ template <int C, bool CENTRAL, typename T, int BS, class KA>
 __device__ __forceinline__ void fd_column(const Z<T>& z, const T r[NV], const KA& k, const RC<T>& c, T eps,
                                           T* Jc) {
   const T pj = component<C>(z);
-  const T pe = fd_step(pj, eps);
+  const T pe = fd_step(pj, eps, C <= 1);
   const T h = pe - pj;
   T rp[NV];
   perturbed_rows<C>(z, pe, r, k, c, rp);
@@ -273,6 +275,7 @@ struct ZoneResult {
   int done;       // Newton updates made by this call (iters counts from the zone's first)
   bool pending;   // stopped at kstop, unconverged: the zone continues in the queue kernel
   double res;
+  double bsq, ds; // general metric with floors and viscosity: b^2 and dP / dP~ of the final state
 };
 
 // Newton on one zone, starting from P (updated in place) after k0 updates
@@ -616,12 +619,12 @@ template <int BS, bool IDEAL> struct RescueKernels {
         [](int* g) {
           cudaError_t r = cudaFuncSetAttribute(newton_rescue<BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)S::bytes);
-          int dev = 0, sms = 0, per_sm = 0;
+          int dev = 0, sms = 0;
           if (r == cudaSuccess) r = cudaGetDevice(&dev);
           if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-          if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_rescue<BS, IDEAL>, BS,
-                                                                                  S::bytes);
-          if (r == cudaSuccess) *g = sms * (per_sm > 0 ? per_sm : 1);
+          // rescued zones are rare: one block per SM keeps the launch of an
+          // empty queue cheap
+          if (r == cudaSuccess) *g = sms;
           return r;
         },
         &grid);
@@ -815,7 +818,7 @@ template <typename T, class KA> __device__ __forceinline__ void r_all_gr(const Z
 }
 
 // Column steps: the FP64 Jacobian uses the step rule of Section 3.1
-// (fd_step).  The float32 Jacobian (SCALED) takes h_j = eps (|P_j| + s_j)
+// (fd_step; relative for rho and u).  The float32 Jacobian (SCALED) takes h_j = eps (|P_j| + s_j)
 // with the natural scale of each component: s = 0 for rho and u (their step
 // is relative; the torus atmosphere holds rho ~ 1e-7, u ~ 1e-10, where an
 // absolute float32 step would jump by orders of magnitude), 1/sqrt(g_jj)
@@ -840,7 +843,7 @@ __device__ __forceinline__ void fd_jacobian_gr(const T P[NV], const T r[NV], con
       else if (col <= 4) s = rsq(m.gcov[sym(col - 1, col - 1)]);
       pe = pj + eps * (fabs(pj) + s);
     } else {
-      pe = fd_step(pj, eps);
+      pe = fd_step(pj, eps, col <= 1);
     }
     const T hstep = pe - pj;
     Pe[col] = pe;
@@ -880,11 +883,13 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
   const unsigned long long tol_bits = abits(p.tol);
   ZG<double> z;
   double r[NV];
+  bool zvalid = false;  // z holds the state of P
   if (rq && k0 > 0) {
 #pragma unroll
     for (int a = 0; a < NV; a++) r[a] = rq[a * rs];
   } else {
     zg_load(z, P, m64, c64);
+    zvalid = true;
     r_all_gr(z, k64, r);
     o.evals64++;
   }
@@ -901,6 +906,7 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
     const double fp = sum_sq10(rp);
     if (!(f <= fp)) {
       fellback = true;
+      zvalid = false;
 #pragma unroll
       for (int a = 0; a < NV; a++) { P[a] = Pp[a]; r[a] = rp[a]; }
       f = fp;
@@ -978,17 +984,53 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
 #pragma unroll
     for (int a = 0; a < NV; a++) { P[a] = Pt[a]; r[a] = rt[a]; }
     f = ft;
+    zvalid = true;
     k++;
   }
   o.iters = k;
   o.done = k - k0;
   o.res = __longlong_as_double((long long)max_abits10(r));
   if (!(P[0] > 0.0) || !(P[1] > 0.0)) o.status |= ST_INADMISSIBLE;
+  if (p.floors && p.visc && !o.pending && o.status == 0) {
+    // what the anisotropy clamp of the floors needs of the final state
+    if (!zvalid) zg_load(z, P, m64, c64);
+    o.bsq = z.bsq;
+    o.ds = z.ds;
+  }
   if (o.pending && rq) {
 #pragma unroll
     for (int a = 0; a < NV; a++) rq[a * rs] = r[a];
   }
   return o;
+}
+
+// The floors of a converged zone, in the kernel that finishes it (a failed
+// zone keeps its status and is reverted and floored by floors_gr): rho >=
+// 1e-5 r^{-3/2}, u >= 1e-7 r^{-5/2}, then -b^2 <= dP <= b^2/2 on the physical
+// anisotropy dP = dP~ ds, with b^2 and ds of the final state.  b^2 depends
+// on B and u^i only, so the floors of rho and u leave it; ds = (psi gamma)^(1/2)
+// P_g (rho + gamma u)^(-1/2) is recomputed where they moved rho or u.
+__device__ __forceinline__ void floors_converged(const Params& p, const double* gc, long long z, const ZoneResult& o,
+                                                 double P[NV]) {
+  const int i = (int)(z % p.n1), j = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
+  const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+  const double r = __ldg(gc + G_R * nc + (long long)(j + 1) * (p.n1 + 2) + (i + 1));
+  const double rho = fmax(P[0], 1e-5 / (r * sqrt(r)));
+  const double u = fmax(P[1], 1e-7 / (r * r * sqrt(r)));
+  const bool moved = rho != P[0] || u != P[1];
+  P[0] = rho;
+  P[1] = u;
+  if (!p.visc) return;
+  double f = o.ds;
+  if (moved) {
+    const RC<double> c = make_rc<double>(p);
+    f = c.spsig * (c.gm1 * u) * rsq(rho + c.gam * u);
+  }
+  if (f > 0.0) {
+    const double dP = P[9] * f, hi = 0.5 * o.bsq, lo = -o.bsq;
+    if (dP > hi) P[9] = hi / f;
+    else if (dP < lo) P[9] = lo / f;
+  }
 }
 
 template <bool MIXED, int BS> struct NewtonSmemGr {
@@ -1047,6 +1089,7 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
     o = newton_zone_gr<MIXED, BS, IDEAL>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax,
                                   queue && rq ? rq + z : nullptr, N, Pfb ? Pfb + z : nullptr, N, abits(accept),
                                   fellback);
+    if (p.floors && !o.pending && o.status == 0) floors_converged(p, gc, z, o, Pz);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -1084,8 +1127,8 @@ __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Pa
       for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
       bool fb = false;
       o = newton_zone_gr<MIXED, BS, IDEAL>(p, kd, kf, md, Pz, jac, iters[z], p.kmax, rq ? rq + z : nullptr, N, nullptr,
-                                           N,
-                                    0ull, fb);
+                                           N, 0ull, fb);
+      if (p.floors && o.status == 0) floors_converged(p, gc, z, o, Pz);
 #pragma unroll
       for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
       iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -1123,6 +1166,7 @@ __global__ void __launch_bounds__(BS) newton_rescue_gr(const __grid_constant__ P
       for (int a = 0; a < NV; a++) Pz[a] = (a >= 5 && a <= 7) ? P[a * N + z] : __ldg(Pn + a * N + z);
       bool fb = false;
       o = newton_zone_gr<false, BS, IDEAL>(p, kd, nullptr, md, Pz, jac, 0, p.kmax, nullptr, N, nullptr, N, 0ull, fb);
+      if (p.floors && o.status == 0) floors_converged(p, gc, z, o, Pz);
 #pragma unroll
       for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
       iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -1144,12 +1188,12 @@ template <int BS, bool IDEAL> struct RescueKernelsGr {
         [](int* g) {
           cudaError_t r = cudaFuncSetAttribute(newton_rescue_gr<BS, IDEAL>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-          int dev = 0, sms = 0, per_sm = 0;
+          int dev = 0, sms = 0;
           if (r == cudaSuccess) r = cudaGetDevice(&dev);
           if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-          if (r == cudaSuccess)
-            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_rescue_gr<BS, IDEAL>, BS, S::bytes);
-          if (r == cudaSuccess) *g = sms * (per_sm > 0 ? per_sm : 1);
+          // rescued zones are rare: one block per SM keeps the launch of an
+          // empty queue cheap
+          if (r == cudaSuccess) *g = sms;
           return r;
         },
         &grid);

@@ -212,6 +212,23 @@ def test_fd_column_of_a_small_component(orc):
         assert np.abs(Jfd[:, 8:] - Jcs[:, 8:]).max() < 1e-4 * scale
 
 
+def test_fd_columns_of_a_cold_zone(orc):
+    """A cold, tenuous zone (rho = 1e-7, u = 1e-11, as in the torus
+    atmosphere): the rho and u columns of the FD Jacobian (Section 3.1) match
+    the complex-step columns to 1e-4 of their scale.  An absolute step of
+    eps on u (small() taken for every component below 5 eps) moves u by
+    5e4 times itself, and that column is off by order one."""
+    prob = inputs.linear_mode_problem(8)
+    rng = np.random.default_rng(17)
+    Pn = np.array([1e-7, 1e-11, 0.01, -0.02, 0.005, 1e-6, 2e-6, 0.0, 1e-9, -1e-9])
+    zc = zone_vector(orc, prob, Pn, Pn.copy(), 0.01, divF=1e-8 * rng.normal(0, 1, 10))
+    Jfd = orc.zone_jacobian(prob, zc, Pn, "fd")
+    Jcs = orc.zone_jacobian(prob, zc, Pn, "cs")
+    for col in (0, 1):
+        scale = np.abs(Jcs[:, col]).max()
+        assert np.abs(Jfd[:, col] - Jcs[:, col]).max() < 1e-4 * scale, col
+
+
 def test_complex_step_matches_central_differences(orc):
     """Independent check of the complex-step Jacobian itself."""
     prob = inputs.linear_mode_problem(8)
