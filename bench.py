@@ -41,7 +41,7 @@ MLP_SAMPLE_STRIDE = 6     # training stages from every 6th of the first 48 steps
 NCU_TRAFFIC_BYTES = {"faces": 296.6e6, "zone_const": None, "newton64": 428.1e6, "newton32": 424.4e6,
                      "mlp": None}
 TOL = 1e-10
-KERR_OUTLIER_LIMIT = 50.0  # training rows of the torus kept within this many robust deviations
+KERR_OUTLIER_LIMIT = 10.0  # training rows of the torus kept within this many central-99.8% spans of each median
 
 
 def read_flop_counts():
@@ -425,7 +425,7 @@ def bench_kerr(dev, torch, world, steps=10, warmup=3, cpu=False):
     mlp, losses = guess.train(X, Y, steps=MLP_TRAIN_STEPS)
     torch.cuda.synchronize()
     out["learned_training"] = {"samples": int(X.shape[0]), "samples_before_outliers": n_all,
-                               "outlier_limit_robust_devs": KERR_OUTLIER_LIMIT, "adam_steps": MLP_TRAIN_STEPS,
+                               "outlier_limit_spans": KERR_OUTLIER_LIMIT, "adam_steps": MLP_TRAIN_STEPS,
                                "loss_per_quarter": losses, "seconds": time.perf_counter() - t0}
     del X, Y
     torch.cuda.empty_cache()

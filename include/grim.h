@@ -332,13 +332,19 @@ const char* grim_batch_last_error(grim_batch* batch);
  * residual of the stage at its start (a = 0..9: for the conserved rows the
  * explicit increment U* - U(P_n) in the residual's row scaling, for q~ and
  * dP~ the explicit part of their relaxation equations), the ten g_{mu nu},
- * P_n, two zeros.  The head's 80 outputs hold a 7x10 matrix M(x) (row-major)
- * and an offset c(x); the standardised prediction of the seven predicted
- * fields is y = M x_U + c, x_U the ten standardised increment features, so
- * that the network learns a state-dependent inverse Jacobian.  Targets
- * (float32 [16]): P_conv - P_n for rho, u, u^i, q~, dP~ at indices 0-4, 8, 9
- * (the magnetic field is the explicit flux-CT update, not predicted), zeros
- * elsewhere.  X and Y arrays are device, zone-major ([M][32], [M][16]). */
+ * P_n in the units below (log rho, log u, u^i, q~/(|q~| + rho),
+ * dP~/(|dP~| + rho)), two zeros.  The head's
+ * 80 outputs hold a 7x10 matrix M(x) (row-major) and an offset c(x); the
+ * standardised prediction of the seven predicted fields is y = M x_U + c,
+ * x_U the ten standardised increment features, so that the network learns a
+ * state-dependent inverse Jacobian.  Targets (float32 [16]): the stage's
+ * change P_conv - P_n of rho, u, u^i, q~, dP~ at indices 0-4, 8, 9 in units
+ * of P_n for rho and u, |X_n| + rho_n for q~ and dP~ and 1 for u^i (the
+ * magnetic field is the explicit flux-CT update, not predicted), zeros
+ * elsewhere; the start is P_n + y times that unit.  These are the units the
+ * scaled residual measures each field in, which keeps a torus and its
+ * tenuous atmosphere, many orders of magnitude apart, in one
+ * standardisation.  X and Y arrays are device, zone-major ([M][32], [M][16]). */
 typedef struct grim_mlp grim_mlp;
 
 /* Create an MLP with Kaiming-uniform weights from `seed`, zero biases, and an

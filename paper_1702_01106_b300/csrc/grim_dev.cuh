@@ -105,6 +105,28 @@ struct Counters {
   unsigned long long rescued;      // mixed-solver zones re-solved by the float64 kernel
 };
 
+// The learned start's variables, in the units the scaled residual measures
+// each field in (its rows divide by the conserved magnitudes, which carry the
+// rest-mass density): rho and u enter as logarithms and their stage change
+// is predicted relative to P_n, (P_conv - P_n)/P_n; q~ and dP~ enter and are
+// predicted in units of |X_n| + rho_n; the velocities as they are.  Across
+// the orders of magnitude between a torus and its atmosphere this keeps
+// features and targets of one size.
+__device__ __forceinline__ float mlp_pn_feature(int a, double x, double rho) {
+  if (a <= 1) return logf(fmaxf((float)x, 1e-37f));
+  if (a >= 8) return (float)(x / (fabs(x) + rho));
+  return (float)x;
+}
+__device__ __forceinline__ double mlp_unit(int a, double pn, double rho) {
+  return a <= 1 ? pn : (a >= 8 ? fabs(pn) + rho : 1.0);
+}
+__device__ __forceinline__ float mlp_target(int a, double pc, double pn, double rho) {
+  return (float)((pc - pn) / mlp_unit(a, pn, rho));
+}
+__device__ __forceinline__ double mlp_apply(int a, double pn, double d, double rho) {
+  return pn + d * mlp_unit(a, pn, rho);
+}
+
 // Zones whose mixed-precision Newton iteration ended with a non-zero status
 // are handed to the float64 Newton kernel, which solves them again from the
 // stage's start (queue of zone indices, its length, and P_n).  All NULL:

@@ -381,13 +381,13 @@ __global__ void mlp_features(const __grid_constant__ Params p, const double* __r
 #pragma unroll
   for (int a = 0; a < 10; a++) x[NV + a] = g[a];
 #pragma unroll
-  for (int a = 0; a < NV; a++) x[2 * NV + a] = (float)P[a];
+  for (int a = 0; a < NV; a++) x[2 * NV + a] = mlp_pn_feature(a, P[a], P[0]);
   x[30] = 0.f;
   x[31] = 0.f;
   if (Y) {
     float* y = Y + z * MLP_Y;
 #pragma unroll
-    for (int o = 0; o < MLP_Y; o++) y[o] = (o < NV && mlp_predicted(o)) ? (float)(__ldg(Pc + o * N + z) - P[o]) : 0.f;
+    for (int o = 0; o < MLP_Y; o++) y[o] = (o < NV && mlp_predicted(o)) ? mlp_target(o, __ldg(Pc + o * N + z), P[o], P[0]) : 0.f;
   }
 }
 
@@ -540,10 +540,11 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
 #pragma unroll
           for (int a = 0; a < 10; a++) xf[NV + a] = g[a];
         }
+        const double rho_n = __ldg(Pn + z);
 #pragma unroll
         for (int a = 0; a < NV; a++) {
           const double x = __ldg(Pn + a * N + z);
-          xf[2 * NV + a] = (float)x;
+          xf[2 * NV + a] = mlp_pn_feature(a, x, rho_n);
           if (a < 5) Pkeep[a] = x;
           else if (a >= 8) Pkeep[a - 3] = x;
         }
@@ -620,7 +621,7 @@ __global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constan
           for (int j = 0; j < MLP_XU; j++) yi = fmaf(yo[i * MLP_XU + j], x[j], yi);
           const int f = mlp_field(i);
           const double d = (double)(yi * S.norm[2 * MLP_IN + MLP_Y + f] + S.norm[2 * MLP_IN + f]);
-          P0[f * N + z] = Pkeep[i] + d;
+          P0[f * N + z] = mlp_apply(f, Pkeep[i], d, Pkeep[0]);
         }
       }
     }

@@ -1317,7 +1317,8 @@ cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const 
 
 // Learned-start features in a general metric, in the flat path's layout:
 // x_a = -r_a(P_n) (the scaled residual of the stage at its start, from the
-// stage constants K), the zone's g_{mu nu} (10, packed), P_n (10), two
+// stage constants K), the zone's g_{mu nu} (10, packed), P_n (10, in the
+// learned start's units: log rho, log u, q~ and dP~ over |X| + rho), two
 // zeros.  X (row-major [N][32]) and, with Y, the targets P_conv - P_n of
 // the predicted fields ([N][16]) for training; or the ten x_a alone into
 // feat ([10][N]) for inference.
@@ -1355,7 +1356,7 @@ __global__ void features_gr(const __grid_constant__ Params p, const double* __re
     for (int a = 0; a < NV; a++) {
       x[a] = (float)(-r[a]);
       x[NV + a] = (float)m.gcov[a];
-      x[2 * NV + a] = (float)P[a];
+      x[2 * NV + a] = mlp_pn_feature(a, P[a], P[0]);
     }
     x[30] = 0.f;
     x[31] = 0.f;
@@ -1363,7 +1364,7 @@ __global__ void features_gr(const __grid_constant__ Params p, const double* __re
       float* y = Y + z * 16;
 #pragma unroll
       for (int o = 0; o < 16; o++)
-        y[o] = (o < NV && !(o >= 5 && o <= 7)) ? (float)(__ldg(Pc + o * N + z) - P[o]) : 0.f;
+        y[o] = (o < NV && !(o >= 5 && o <= 7)) ? mlp_target(o, __ldg(Pc + o * N + z), P[o], P[0]) : 0.f;
     }
   }
 }

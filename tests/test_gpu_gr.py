@@ -251,10 +251,11 @@ def test_gr_odd_grids_minkowski(dev, orc, shape):
 
 def test_gr_learned_start_equals_reference_prediction(dev):
     """The learned start in a general metric (the torus, floors off): with
-    k_max = 0 a stage returns its start, P_n + the network's output on the
-    stage's features (the residual at P_n, the zone's g_{mu nu}, P_n), with
-    the magnetic components from flux-CT.  The few atmosphere zones whose
-    start is inadmissible (u ~ 1e-10 there) fall back to P_n; the rest
+    k_max = 0 a stage returns its start, P_n + y times the field's unit (P_n
+    for rho and u, |X_n| + rho_n for q~ and dP~, 1 for the velocities), y the
+    network's output on the stage's features (the residual at P_n, the
+    zone's g_{mu nu}, P_n in those units), with the magnetic components from
+    flux-CT.  Zones whose start is worse than P_n fall back to P_n; the rest
     carry the prediction."""
     from paper_1702_01106_b300.grim import MLP, Grim
     from oracle import mlp_ref
@@ -284,11 +285,14 @@ def test_gr_learned_start_equals_reference_prediction(dev):
     got = out.cpu().numpy().reshape(10, -1)
     Pn = P.reshape(10, -1)
     fields = [0, 1, 2, 3, 4, 8, 9]
+    from tests.gpu_helpers import learned_units
+    unit = learned_units(Pn)
     kept = ~np.all(got[fields] == Pn[fields], axis=0)
     assert (~kept).sum() == nfb and nfb <= 0.02 * prob.zones, nfb
     for o in fields:
         scale = np.abs(pred[kept, o]).max() + 1e-30
-        diff = np.abs(got[o, kept] - Pn[o, kept] - pred[kept, o]) / scale
+        dgot = (got[o, kept] - Pn[o, kept]) / unit[o, kept]
+        diff = np.abs(dgot - pred[kept, o]) / scale
         assert diff.max() <= 3e-2, o
         assert np.median(diff) <= 3e-3, o
     g.close()

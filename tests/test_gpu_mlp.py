@@ -67,14 +67,18 @@ def test_features_are_the_stage_increment(dev, orc):
         assert np.abs(X[:, f] + r[f]).max() <= 1e-6 * scale + 1e-30, f
     eta = np.array([-1, 0, 0, 0, 1, 0, 0, 1, 0, 1], np.float64)   # g_tt, g_tx, .., g_zz
     assert np.array_equal(X[:, 10:20], np.broadcast_to(eta, (prob.zones, 10)))
-    assert np.abs(X[:, 20:30] - P.reshape(10, -1).T).max() <= 1e-6 * np.abs(P).max()
+    from tests.gpu_helpers import learned_pn_features
+    Pf = learned_pn_features(P)           # log rho, log u, q~ and dP~ over |X| + rho
+    assert np.abs(X[:, 20:30] - Pf).max() <= 1e-6 * np.abs(Pf).max()
     assert not X[:, 30:].any()
     g.close()
 
 
 def test_learned_start_equals_reference_prediction(dev):
-    """With k_max = 0 the stage returns its start: P_n + the network's output
-    on the stage's features (magnetic components from flux-CT)."""
+    """With k_max = 0 the stage returns its start: P_n + y times the field's
+    unit (P_n for rho and u, |X_n| + rho_n for q~ and dP~, 1 for u^i), y the
+    network's output on the stage's features (magnetic components from
+    flux-CT)."""
     from paper_1702_01106_b300.grim import MLP, Grim
     from oracle import mlp_ref
     rng = np.random.default_rng(4)
@@ -98,14 +102,17 @@ def test_learned_start_equals_reference_prediction(dev):
     X = torch.empty((prob.zones, 32), dtype=torch.float32, device=dev)
     g.mlp_sample(a, None, X)
     pred = mlp_ref.predict(params, norm, X.cpu().numpy(), bf16_round=True)
+    from tests.gpu_helpers import learned_units
     got = out.cpu().numpy().reshape(10, -1)
     Pn = P.reshape(10, -1)
+    unit = learned_units(Pn)
     for o in (0, 1, 2, 3, 4, 8, 9):
         # the device SiLU uses the hardware tanh approximation (relative error
         # ~2^-11) and a different float32 summation order, which can flip the
         # bfloat16 rounding of an activation (one part in 2^8)
         scale = np.abs(pred[:, o]).max() + 1e-6
-        diff = np.abs(got[o] - Pn[o] - pred[:, o]) / scale
+        dgot = (got[o] - Pn[o]) / unit[o]
+        diff = np.abs(dgot - pred[:, o]) / scale
         assert diff.max() <= 3e-2, o
         assert np.median(diff) <= 3e-3, o
     g.close()
