@@ -140,6 +140,8 @@ typedef struct {
   unsigned long long rescued;   /* GRIM_MIXED: zone solves whose float32-Jacobian iteration ended with a
                                    non-zero status and were solved again with the float64 Jacobian from
                                    P_n (their status is the float64 solve's) */
+  unsigned long long mlp_stalls; /* learned-start launches that gave up waiting for their tensor-core
+                                    work (a bounded wait); the zones not reached keep the plain start */
 } grim_stats;
 
 typedef struct grim_ctx grim_ctx;

@@ -30,7 +30,7 @@ cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
-                             const double* gc, cudaStream_t st);
+                             const double* gc, unsigned long long* stalls, cudaStream_t st);
 cudaError_t launch_features_gr(const Params& p, const double* K, const double* gc, const double* Pn, const double* Pc,
                                float* X, float* Y, float* feat, cudaStream_t st);
 long long gr_geometry_doubles(const Params& p);
@@ -292,7 +292,8 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
   if (learned) {
     // the zone-constant kernel wrote the increment features beside the constants
     KernelMark m(ctx, GRIM_K_MLP, 1);
-    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->gr ? ctx->geo : nullptr, ctx->cur),
+    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->gr ? ctx->geo : nullptr,
+                                     &ctx->cnt->mlp_stalls, ctx->cur),
               "mlp kernel");
   }
   if (ctx->gr) {
@@ -584,6 +585,7 @@ int grim_get_stats(grim_ctx* ctx, grim_stats* out) {
   out->launches = ctx->launches;
   out->fallbacks = c.fallbacks;
   out->rescued = c.rescued;
+  out->mlp_stalls = c.mlp_stalls;
   return GRIM_OK;
 }
 
@@ -826,6 +828,7 @@ int grim_batch_get_stats(grim_batch* b, grim_stats* out) {
     t.max_res = std::max(t.max_res, s.max_res);
     t.fallbacks += s.fallbacks;
     t.rescued += s.rescued;
+    t.mlp_stalls += s.mlp_stalls;
   }
   t.launches = b->launches;
   *out = t;

@@ -103,6 +103,7 @@ struct Counters {
   unsigned long long maxres_bits;  // max over zones of max_a |r_a|, as ordered bits
   unsigned long long fallbacks;    // zones whose learned start lost to the plain start
   unsigned long long rescued;      // mixed-solver zones re-solved by the float64 kernel
+  unsigned long long mlp_stalls;   // learned-start launches that gave up waiting on the tensor cores
 };
 
 // The learned start's variables, in the units the scaled residual measures

@@ -5,7 +5,8 @@
 //
 // Network: 30 features -> 128 -> 128 -> 128 -> head, SiLU after each hidden
 // layer, bfloat16 weights and activations, float32 accumulation and biases,
-// on the tensor cores (mma.sync m16n8k16).  The head (80 outputs, 77 used)
+// on the tensor cores (inference: tcgen05 with TMEM accumulators; training
+// GEMMs: mma.sync m16n8k16).  The head (80 outputs, 77 used)
 // is a 7x10 matrix M and an offset c: the standardised prediction of the
 // seven predicted fields is y = M x_U + c, with x_U the ten standardised
 // conserved-increment features.  The prediction is therefore exactly linear
@@ -35,6 +36,7 @@
 #include <vector>
 #include <cuda_bf16.h>
 
+#include "grim_tc.cuh"
 #include "grim_zone.cuh"
 #include "../../include/grim.h"
 
@@ -413,24 +415,45 @@ __global__ void mlp_colstats(const float* __restrict__ X, long long M, int ncol,
 }
 
 // ---------------------------------------------------------------- fused inference
-// One warp runs 16 zones through the network with the activations kept in
-// mma fragments: the float32 accumulator of two adjacent n8 tiles of one
-// layer is exactly the bfloat16 A fragment of one k16 step of the next.
-// Weights live in shared memory (row stride padded by 8 to keep the
-// fragment loads conflict-free).  The result replaces the non-magnetic
-// components of the Newton initial guess: P0 = P_n + prediction.
-constexpr int IW1 = MLP_IN + 8, IWH = MLP_H + 8;
-constexpr int INF_WARPS = 12; // warps per block: one block per SM shares one copy of the weights
-struct InferSmem {
-  __nv_bfloat16 w0[MLP_H][IW1];
-  __nv_bfloat16 w1[MLP_H][IWH];
-  __nv_bfloat16 w2[MLP_H][IWH];
-  __nv_bfloat16 w3[MLP_HEAD][IWH];
-  float b[3 * MLP_H + MLP_HEAD];
-  float norm[2 * MLP_IN + 2 * MLP_Y];
-  __nv_bfloat16 x[INF_WARPS][16][IW1];   // per-warp input tile
-  __align__(16) float xh[INF_WARPS][16][12];  // per-warp head features (float32; 10 used)
-  __align__(16) float y[INF_WARPS][16][84];   // per-warp head output tile, bias added (80 used)
+// The learned start on the fifth-generation tensor cores (tcgen05): one
+// persistent CTA per SM keeps the bfloat16 weights in shared memory and runs
+// tiles of 128 zones through the network, in two independent streams of
+// tiles (one per warpgroup, each with its own buffers, mbarrier and TMEM
+// accumulator), so that one stream's epilogue overlaps the other's MMAs.  Each layer is a 128 x N x K
+// product issued by one thread as K/16 tcgen05.mma instructions (A: the
+// tile's activations, B: the layer's weights, both in shared memory; D:
+// float32 in tensor memory, one TMEM lane per zone); its completion arrives
+// on an mbarrier.  The epilogue reads each zone's row back from TMEM
+// (tcgen05.ld: warp w of a warpgroup reads lanes 32 (w % 4) ..), adds the
+// bias, applies SiLU and writes the bfloat16 activations into the next
+// layer's A tile.
+// The head's 80 outputs give y = M x_U + c per zone, and the start
+// P_n + y (in the learned start's units) replaces the non-magnetic
+// components of the Newton start P0.
+constexpr int TC_ROWS = 128;      // zones per tile: the MMA's M and the TMEM lanes
+constexpr int TC_STREAMS = 2;     // warpgroups, each with its own stream of tiles
+constexpr int TC_THREADS = 128 * TC_STREAMS;
+constexpr uint32_t TC_COLS = 128; // TMEM columns of one warpgroup's accumulator
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;  // mbarrier polls before the kernel gives up
+
+// What one warpgroup's tile stream owns.
+struct TcStream {
+  __align__(128) unsigned char x[TC_ROWS * MLP_IN * 2];    // standardised features of the tile
+  __align__(128) unsigned char h[TC_ROWS * MLP_H * 2];     // hidden activations of the tile
+  float xu[TC_ROWS][MLP_XU + 2];                           // standardised head features, float32
+  uint64_t mbar;                                           // completion of the stream's MMAs
+};
+struct TcSmem {
+  __align__(128) unsigned char w0[MLP_H * MLP_IN * 2];     // W_1 [128][32], core-matrix K-major
+  __align__(128) unsigned char w1[MLP_H * MLP_H * 2];      // W_2 [128][128]
+  __align__(128) unsigned char w2[MLP_H * MLP_H * 2];      // W_3 [128][128]
+  __align__(128) unsigned char w3[MLP_HEAD * MLP_H * 2];   // W_4 [80][128]
+  TcStream st[TC_STREAMS];
+  __align__(16) float hb[3 * MLP_H];                      // halved hidden biases
+  float b4[MLP_HEAD];                                      // head bias
+  float norm[2 * MLP_IN + 2 * MLP_Y];                      // x mean, 1/x std, y mean, y std
+  uint32_t taddr;
+  int abort[TC_STREAMS];
 };
 
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
@@ -438,194 +461,223 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   return *reinterpret_cast<unsigned*>(&h);
 }
 
-// B fragments of n-tiles j and j+1 for one k16 step from the row-major
-// [n][k] weights in shared memory with one ldmatrix.x4: matrix q (lanes
-// 8q..8q+7 give its row addresses) covers n-tile j + q/2, k half q%2, and the
-// m8n8 distribution (row lane/4, columns 2(lane%4), +1) is the mma B layout.
-__device__ __forceinline__ void ldsm_b2(const __nv_bfloat16* W, int ldw, int j, int ks, int lane, unsigned b[4]) {
-  const int q = lane >> 3, r = lane & 7;
-  const __nv_bfloat16* row = W + ((j + (q >> 1)) * 8 + r) * ldw + ks * 16 + (q & 1) * 8;
-  const unsigned addr = (unsigned)__cvta_generic_to_shared(row);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
-               : "r"(addr));
-}
-
-template <int NOUT_TILES>
-__device__ __forceinline__ void layer_mma(float acc[][4], const unsigned (*afr)[4], int ksteps,
-                                          const __nv_bfloat16* W, int ldw, int lane) {
-  static_assert(NOUT_TILES % 2 == 0, "n-tiles are loaded in pairs");
-#pragma unroll
-  for (int j = 0; j < NOUT_TILES; j++) {
-    acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  }
-  for (int ks = 0; ks < ksteps; ks++) {
-#pragma unroll
-    for (int j = 0; j < NOUT_TILES; j += 2) {
-      unsigned b[4];
-      ldsm_b2(W, ldw, j, ks, lane, b);
-      mma_bf16(acc[j], afr[ks], b);
-      mma_bf16(acc[j + 1], afr[ks], b + 2);
-    }
+// A row-major bfloat16 matrix [rows][kc] (global) into the core-matrix
+// K-major layout (shared), 16 bytes at a time.
+__device__ __forceinline__ void tc_load_tile(unsigned char* dst, const __nv_bfloat16* src, int rows, int kc) {
+  const int chunks = rows * (kc / 8);
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    const int r = c / (kc / 8), k8 = c % (kc / 8);
+    const uint4 v = *reinterpret_cast<const uint4*>(src + (long long)r * kc + k8 * 8);
+    *reinterpret_cast<uint4*>(dst + tc::kmajor_offset(r, k8 * 8, kc)) = v;
   }
 }
 
-// SiLU(acc + b) of 16 n8 tiles -> 8 k16 A fragments; hb: the halved biases.
-__device__ __forceinline__ void to_afrag(float acc[16][4], const float* hb, unsigned afr[8][4], int lane) {
-  const int ac = (lane & 3) * 2;
-  auto act = [](float a, float h) { return silu_of_half(fmaf(a, 0.5f, h)); };
-#pragma unroll
-  for (int ks = 0; ks < 8; ks++) {
-    const int c0 = ks * 16 + ac, c1 = c0 + 8;
-    const float* lo = acc[2 * ks];
-    const float* hi = acc[2 * ks + 1];
-    afr[ks][0] = pack_bf16(act(lo[0], hb[c0]), act(lo[1], hb[c0 + 1]));
-    afr[ks][1] = pack_bf16(act(lo[2], hb[c0]), act(lo[3], hb[c0 + 1]));
-    afr[ks][2] = pack_bf16(act(hi[0], hb[c1]), act(hi[1], hb[c1 + 1]));
-    afr[ks][3] = pack_bf16(act(hi[2], hb[c1]), act(hi[3], hb[c1 + 1]));
-  }
-}
-
-__global__ void __launch_bounds__(INF_WARPS * 32) mlp_guess(const __grid_constant__ Params p,
-                                                             const float* __restrict__ feat,
-                                                             const double* __restrict__ Pn,
-                                                             const __nv_bfloat16* __restrict__ wb,
-                                                             const float* __restrict__ params,
-                                                             const float* __restrict__ norm, double* __restrict__ P0,
-                                                             const double* __restrict__ gc) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  InferSmem& S = *reinterpret_cast<InferSmem*>(smraw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // weights to shared memory
-  constexpr int NT = INF_WARPS * 32;
-  for (int i = tid; i < MLP_H * MLP_IN; i += NT) S.w0[i / MLP_IN][i % MLP_IN] = wb[mlp_woff(0) - 0 + i];
-  const int o1 = MLP_H * MLP_IN, o2 = o1 + MLP_H * MLP_H, o3 = o2 + MLP_H * MLP_H;
-  for (int i = tid; i < MLP_H * MLP_H; i += NT) {
-    S.w1[i / MLP_H][i % MLP_H] = wb[o1 + i];
-    S.w2[i / MLP_H][i % MLP_H] = wb[o2 + i];
-  }
-  for (int i = tid; i < MLP_HEAD * MLP_H; i += NT) S.w3[i / MLP_H][i % MLP_H] = wb[o3 + i];
-  for (int i = tid; i < MLP_H; i += NT) {  // hidden biases halved for the SiLU epilogue
-    S.b[i] = 0.5f * params[mlp_boff(0) + i];
-    S.b[MLP_H + i] = 0.5f * params[mlp_boff(1) + i];
-    S.b[2 * MLP_H + i] = 0.5f * params[mlp_boff(2) + i];
-  }
-  if (tid < MLP_HEAD) S.b[3 * MLP_H + tid] = params[mlp_boff(3) + tid];
-  // the feature deviations as reciprocals (one multiply a feature below)
-  if (tid < 2 * MLP_IN + 2 * MLP_Y)
-    S.norm[tid] = (tid >= MLP_IN && tid < 2 * MLP_IN) ? 1.0f / norm[tid] : norm[tid];
-  __syncthreads();
+// The raw inputs of one zone, loaded a tile ahead so that their latency
+// overlaps the tensor-core work of the tile before: the ten increment
+// features, P_n, and in a general metric the zone's g_{mu nu}.
+struct TcRaw {
+  float f[NV];
+  double pn[NV];
+  double g[10];
+};
+__device__ __forceinline__ void tc_fetch(const Params& p, const float* feat, const double* Pn, const double* gc,
+                                         long long z, TcRaw& R) {
   const long long N = p.N;
-  const float g[10] = {-1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f};
-  // persistent over tiles of 16 zones per warp
-  for (long long base = (long long)blockIdx.x * (16 * INF_WARPS); base < N;
-       base += (long long)gridDim.x * (16 * INF_WARPS)) {
-    // features: lanes 0..15 of each warp build one zone each (the increment
-    // features come from the zone-constant kernel of this stage)
-    const long long zw = base + warp * 16;
-    double Pkeep[MLP_NP];
-    if (lane < 16) {
-      const long long z = zw + lane;
-      float xf[MLP_IN];
-      if (z < N) {
+  if (z >= N) return;
 #pragma unroll
-        for (int a = 0; a < NV; a++) xf[a] = __ldg(feat + a * N + z);
-        if (gc) {  // the zone's g_{mu nu} from the centre table of a general metric
-          const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
-          const int zi = (int)(z % p.n1), zj = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
-          const double* gz = gc + (long long)(zj + 1) * (p.n1 + 2) + (zi + 1);
+  for (int a = 0; a < NV; a++) R.f[a] = __ldg(feat + a * N + z);
 #pragma unroll
-          for (int a = 0; a < 10; a++) xf[NV + a] = (float)__ldg(gz + a * nc);
-        } else {
+  for (int a = 0; a < NV; a++) R.pn[a] = __ldg(Pn + a * N + z);
+  if (gc) {
+    const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+    const int zi = (int)(z % p.n1), zj = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
+    const double* gz = gc + (long long)(zj + 1) * (p.n1 + 2) + (zi + 1);
 #pragma unroll
-          for (int a = 0; a < 10; a++) xf[NV + a] = g[a];
-        }
-        const double rho_n = __ldg(Pn + z);
+    for (int a = 0; a < 10; a++) R.g[a] = __ldg(gz + a * nc);
+  }
+}
+
+// The 32 features of the zone (see the file header), standardised: the
+// first ten also as float32 for the head, all 32 as bfloat16 into row `row`
+// of the A tile.  Rows past the grid get the feature means (standardised
+// zeros).
+__device__ __forceinline__ void tc_features(const TcRaw& R, bool live, bool metric, const TcSmem& S, TcStream& T,
+                                            int row) {
+  float xf[MLP_IN];
+  if (live) {
 #pragma unroll
-        for (int a = 0; a < NV; a++) {
-          const double x = __ldg(Pn + a * N + z);
-          xf[2 * NV + a] = mlp_pn_feature(a, x, rho_n);
-          if (a < 5) Pkeep[a] = x;
-          else if (a >= 8) Pkeep[a - 3] = x;
-        }
-        xf[30] = xf[31] = 0.f;
-      } else {
+    for (int a = 0; a < NV; a++) xf[a] = R.f[a];
+    const float eta[10] = {-1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f};  // Minkowski g_{mu nu}
 #pragma unroll
-        for (int a = 0; a < MLP_IN; a++) xf[a] = S.norm[a];
+    for (int a = 0; a < 10; a++) xf[NV + a] = metric ? (float)R.g[a] : eta[a];
+#pragma unroll
+    for (int a = 0; a < NV; a++) xf[2 * NV + a] = mlp_pn_feature(a, R.pn[a], R.pn[0]);
+    xf[30] = xf[31] = 0.f;
+  } else {
+#pragma unroll
+    for (int a = 0; a < MLP_IN; a++) xf[a] = S.norm[a];
+  }
+  float xs[MLP_IN];
+#pragma unroll
+  for (int a = 0; a < MLP_IN; a++) xs[a] = (xf[a] - S.norm[a]) * S.norm[MLP_IN + a];
+#pragma unroll
+  for (int a = 0; a < MLP_XU; a++) T.xu[row][a] = xs[a];
+#pragma unroll
+  for (int c = 0; c < MLP_IN / 8; c++) {
+    uint4 v;
+    v.x = pack_bf16(xs[8 * c + 0], xs[8 * c + 1]);
+    v.y = pack_bf16(xs[8 * c + 2], xs[8 * c + 3]);
+    v.z = pack_bf16(xs[8 * c + 4], xs[8 * c + 5]);
+    v.w = pack_bf16(xs[8 * c + 6], xs[8 * c + 7]);
+    *reinterpret_cast<uint4*>(T.x + tc::kmajor_offset(row, 8 * c, MLP_IN)) = v;
+  }
+}
+
+// Issue the MMAs of layer l for the tile (one thread) and commit them to
+// the mbarrier.
+__device__ __forceinline__ void tc_issue_layer(const TcSmem& S, TcStream& T, int l, uint32_t tmem) {
+  const unsigned char* A = l == 0 ? T.x : T.h;
+  const unsigned char* B = l == 0 ? S.w0 : l == 1 ? S.w1 : l == 2 ? S.w2 : S.w3;
+  const uint32_t kc = l == 0 ? MLP_IN : MLP_H;
+  const uint32_t n = l == 3 ? MLP_HEAD : MLP_H;
+  const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B), sbo = kc * 16u;
+  const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, n);
+  for (uint32_t s = 0; s < kc / 16; s++)  // K = 16 per MMA: two core matrices along K
+    tc::mma_bf16(tmem, tc::smem_desc(a0 + 256u * s, 128u, sbo), tc::smem_desc(b0 + 256u * s, 128u, sbo), idesc,
+                 s > 0);
+  tc::commit(&T.mbar);
+}
+
+// Named barrier of one warpgroup (ids 1, 2; 0 is __syncthreads).
+__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+__global__ void __launch_bounds__(TC_THREADS, 1) mlp_guess_tc(const __grid_constant__ Params p,
+                                                               const float* __restrict__ feat,
+                                                               const double* __restrict__ Pn,
+                                                               const __nv_bfloat16* __restrict__ wb,
+                                                               const float* __restrict__ params,
+                                                               const float* __restrict__ norm,
+                                                               double* __restrict__ P0,
+                                                               const double* __restrict__ gc,
+                                                               unsigned long long* __restrict__ stalls) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  TcSmem& S = *reinterpret_cast<TcSmem*>(smraw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp >> 2;                   // warpgroup: the tile stream of this thread
+  const int row = (warp & 3) * 32 + lane;    // the tile row (zone) of this thread's TMEM lane
+  TcStream& T = S.st[g];
+  // weights, biases and standardisation into shared memory (all threads)
+  tc_load_tile(S.w0, wb, MLP_H, MLP_IN);
+  tc_load_tile(S.w1, wb + MLP_H * MLP_IN, MLP_H, MLP_H);
+  tc_load_tile(S.w2, wb + MLP_H * MLP_IN + MLP_H * MLP_H, MLP_H, MLP_H);
+  tc_load_tile(S.w3, wb + MLP_H * MLP_IN + 2 * MLP_H * MLP_H, MLP_HEAD, MLP_H);
+  for (int i = tid; i < MLP_H; i += TC_THREADS) {
+    S.hb[i] = 0.5f * params[mlp_boff(0) + i];
+    S.hb[MLP_H + i] = 0.5f * params[mlp_boff(1) + i];
+    S.hb[2 * MLP_H + i] = 0.5f * params[mlp_boff(2) + i];
+  }
+  if (tid < MLP_HEAD) S.b4[tid] = params[mlp_boff(3) + tid];
+  if (tid < 2 * MLP_IN + 2 * MLP_Y) S.norm[tid] = (tid >= MLP_IN && tid < 2 * MLP_IN) ? 1.0f / norm[tid] : norm[tid];
+  if (tid < TC_STREAMS) {
+    tc::mbar_init(&S.st[tid].mbar, 1);
+    S.abort[tid] = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&S.taddr, TC_COLS * TC_STREAMS);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = S.taddr + TC_COLS * (uint32_t)g;             // this stream's accumulator
+  const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lane quarter
+  const bool issuer = (tid & 127) == 0;
+  uint32_t phase = 0;
+  const long long N = p.N;
+  const long long tiles = (N + TC_ROWS - 1) / TC_ROWS;
+  const long long tstep = (long long)gridDim.x * TC_STREAMS;
+  TcRaw cur, nxt;
+  long long t = (long long)blockIdx.x * TC_STREAMS + g;
+  tc_fetch(p, feat, Pn, gc, t * TC_ROWS + row, cur);
+  for (; t < tiles; t += tstep) {
+    const long long z0 = t * TC_ROWS, z = z0 + row;
+    tc_features(cur, z < N, gc != nullptr, S, T, row);
+    tc_fetch(p, feat, Pn, gc, (t + tstep) * TC_ROWS + row, nxt);   // in flight during this tile's layers
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    wg_sync(g);
+    for (int l = 0; l < MLP_NLAYER; l++) {
+      if (issuer) {
+        tc::fence_after_sync();
+        tc_issue_layer(S, T, l, tmem);
       }
+      // warp-uniform, since the TMEM loads below are warp-collective
+      const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&T.mbar, phase, TC_WAIT_LIMIT));
+      phase ^= 1u;
+      if (!ok) S.abort[g] = 1;
+      tc::fence_after_sync();
+      if (ok && l < MLP_NLAYER - 1) {
+        // bias, SiLU, bfloat16 of this thread's zone, all 128 columns, 16 at
+        // a time: the load of the next 16 is in flight while these are
+        // processed
+        const float4* hb4 = reinterpret_cast<const float4*>(S.hb + l * MLP_H);
+        uint32_t r[2][16];
+        tc::ld_x16_issue(tlane, r[0]);
 #pragma unroll
-      for (int a = 0; a < MLP_IN; a++) {
-        const float xs = (xf[a] - S.norm[a]) * S.norm[MLP_IN + a];
-        S.x[warp][lane][a] = __float2bfloat16(xs);
-        if (a < MLP_XU) S.xh[warp][lane][a] = xs;
-      }
-    }
-    __syncwarp();
-    // layer 0: 16 x 32 input, two k16 steps
-    unsigned a0[2][4];
-    {
-      const int ar = lane >> 2, ac = (lane & 3) * 2;
+        for (int q = 0; q < MLP_H / 16; q++) {
+          tc::ld_wait16(r[q & 1]);
+          if (q + 1 < MLP_H / 16) tc::ld_x16_issue(tlane + (uint32_t)(16 * (q + 1)), r[(q + 1) & 1]);
+          uint32_t u[8];
 #pragma unroll
-      for (int ks = 0; ks < 2; ks++) {
-        a0[ks][0] = *reinterpret_cast<const unsigned*>(&S.x[warp][ar][ks * 16 + ac]);
-        a0[ks][1] = *reinterpret_cast<const unsigned*>(&S.x[warp][ar + 8][ks * 16 + ac]);
-        a0[ks][2] = *reinterpret_cast<const unsigned*>(&S.x[warp][ar][ks * 16 + ac + 8]);
-        a0[ks][3] = *reinterpret_cast<const unsigned*>(&S.x[warp][ar + 8][ks * 16 + ac + 8]);
-      }
-    }
-    float acc[16][4];
-    unsigned afr[8][4];
-    layer_mma<16>(acc, a0, 2, &S.w0[0][0], IW1, lane);
-    to_afrag(acc, S.b, afr, lane);
-    layer_mma<16>(acc, afr, 8, &S.w1[0][0], IWH, lane);
-    to_afrag(acc, S.b + MLP_H, afr, lane);
-    layer_mma<16>(acc, afr, 8, &S.w2[0][0], IWH, lane);
-    to_afrag(acc, S.b + 2 * MLP_H, afr, lane);
-    constexpr int NT = MLP_HEAD / 8;
-    float out[NT][4];
-    layer_mma<NT>(out, afr, 8, &S.w3[0][0], IWH, lane);
-    {
-      const int ar = lane >> 2, ac = (lane & 3) * 2;
-      const float* hb = S.b + 3 * MLP_H;
-#pragma unroll
-      for (int j = 0; j < NT; j++) {
-        const float b0 = hb[j * 8 + ac], b1 = hb[j * 8 + ac + 1];
-        S.y[warp][ar][j * 8 + ac] = out[j][0] + b0;
-        S.y[warp][ar][j * 8 + ac + 1] = out[j][1] + b1;
-        S.y[warp][ar + 8][j * 8 + ac] = out[j][2] + b0;
-        S.y[warp][ar + 8][j * 8 + ac + 1] = out[j][3] + b1;
-      }
-    }
-    __syncwarp();
-    // head: y_i = sum_j M_ij x_j + c_i, one zone per lane
-    if (lane < 16) {
-      const long long z = zw + lane;
-      if (z < N) {
-        float yo[80], x[12];
-        const float4* yv = reinterpret_cast<const float4*>(S.y[warp][lane]);
-        const float4* xv = reinterpret_cast<const float4*>(S.xh[warp][lane]);
-#pragma unroll
-        for (int q = 0; q < 20; q++) {
-          const float4 t = yv[q];
-          yo[4 * q] = t.x; yo[4 * q + 1] = t.y; yo[4 * q + 2] = t.z; yo[4 * q + 3] = t.w;
+          for (int e4 = 0; e4 < 4; e4++) {
+            const float4 b = hb4[4 * q + e4];
+            const uint32_t* v = r[q & 1] + 4 * e4;
+            u[2 * e4] = pack_bf16(silu_of_half(fmaf(__uint_as_float(v[0]), 0.5f, b.x)),
+                                  silu_of_half(fmaf(__uint_as_float(v[1]), 0.5f, b.y)));
+            u[2 * e4 + 1] = pack_bf16(silu_of_half(fmaf(__uint_as_float(v[2]), 0.5f, b.z)),
+                                      silu_of_half(fmaf(__uint_as_float(v[3]), 0.5f, b.w)));
+          }
+          *reinterpret_cast<uint4*>(T.h + tc::kmajor_offset(row, 16 * q, MLP_H)) = make_uint4(u[0], u[1], u[2], u[3]);
+          *reinterpret_cast<uint4*>(T.h + tc::kmajor_offset(row, 16 * q + 8, MLP_H)) =
+              make_uint4(u[4], u[5], u[6], u[7]);
         }
-#pragma unroll
-        for (int q = 0; q < 3; q++) {
-          const float4 t = xv[q];
-          x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
-        }
+      } else if (ok) {
+        // head: y_i = sum_j M_ij x_j + c_i, then the start of the zone (the
+        // loads are warp-collective: every lane takes part, rows past the
+        // grid write nothing)
+        float o[MLP_HEAD];
+        tc::ld_x32(tlane, o);
+        tc::ld_x32(tlane + 32u, o + 32);
+        tc::ld_x16(tlane + 64u, o + 64);
 #pragma unroll
         for (int i = 0; i < MLP_NP; i++) {
-          float yi = yo[MLP_NP * MLP_XU + i];
+          if (z >= N) break;
+          float y = o[MLP_NP * MLP_XU + i] + S.b4[MLP_NP * MLP_XU + i];
 #pragma unroll
-          for (int j = 0; j < MLP_XU; j++) yi = fmaf(yo[i * MLP_XU + j], x[j], yi);
+          for (int j = 0; j < MLP_XU; j++) y = fmaf(o[i * MLP_XU + j] + S.b4[i * MLP_XU + j], T.xu[row][j], y);
           const int f = mlp_field(i);
-          const double d = (double)(yi * S.norm[2 * MLP_IN + MLP_Y + f] + S.norm[2 * MLP_IN + f]);
-          P0[f * N + z] = mlp_apply(f, Pkeep[i], d, Pkeep[0]);
+          const double d = (double)(y * S.norm[2 * MLP_IN + MLP_Y + f] + S.norm[2 * MLP_IN + f]);
+          P0[f * N + z] = mlp_apply(f, cur.pn[f], d, cur.pn[0]);
         }
       }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      wg_sync(g);
+      if (S.abort[g]) break;
     }
-    __syncwarp();
+    if (S.abort[g]) break;
+    cur = nxt;
+  }
+  if (S.abort[g] && issuer) {
+    // a layer's MMAs did not complete in time: wait (bounded) for them once
+    // more before the tensor memory is released; the zones not reached keep
+    // the plain start the zone-constant kernel wrote
+    tc::mbar_wait(&T.mbar, phase ^ 1u, TC_WAIT_LIMIT);
+    atomicAdd(stalls, 1ull);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(S.taddr, TC_COLS * TC_STREAMS);
   }
 }
 
@@ -869,15 +921,16 @@ cudaError_t launch_mlp_features(const Params& p, const double* K, const double* 
 }
 
 // gc: the centre geometry table of a general metric (its first ten planes
-// are g_{mu nu}), or NULL for Minkowski space.
+// are g_{mu nu}), or NULL for Minkowski space.  stalls: a device counter
+// raised when the kernel gave up waiting for its tensor-core work.
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
-                             const double* gc, cudaStream_t st) {
+                             const double* gc, unsigned long long* stalls, cudaStream_t st) {
   static PerDevice once;
   int sms = 0;
   cudaError_t e = once.get(
       [](int* v) {
-        cudaError_t r = cudaFuncSetAttribute(mlp_guess, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(InferSmem));
+        cudaError_t r = cudaFuncSetAttribute(mlp_guess_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(TcSmem));
         int dev = 0;
         if (r == cudaSuccess) r = cudaGetDevice(&dev);
         if (r == cudaSuccess) r = cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev);
@@ -885,11 +938,11 @@ cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* P
       },
       &sms);
   if (e != cudaSuccess) return e;
-  long long tiles = (p.N + 16 * INF_WARPS - 1) / (16 * INF_WARPS);
-  long long grid = sms;  // persistent: one block (and one copy of the weights) per SM
-  if (grid > tiles) grid = tiles;
-  mlp_guess<<<(unsigned)grid, INF_WARPS * 32, sizeof(InferSmem), st>>>(p, feat, Pn, m->wb, m->params, m->norm, P0,
-                                                                        gc);
+  const long long tiles = (p.N + TC_ROWS - 1) / TC_ROWS;
+  long long grid = sms;  // persistent: one block (one copy of the weights, 256 TMEM columns) per SM
+  if (grid > (tiles + TC_STREAMS - 1) / TC_STREAMS) grid = (tiles + TC_STREAMS - 1) / TC_STREAMS;
+  mlp_guess_tc<<<(unsigned)grid, TC_THREADS, sizeof(TcSmem), st>>>(p, feat, Pn, m->wb, m->params, m->norm, P0, gc,
+                                                                   stalls);
   return cudaGetLastError();
 }
 }  // namespace grim

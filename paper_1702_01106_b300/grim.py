@@ -69,7 +69,7 @@ class GrimStats(ctypes.Structure):
                 ("evals64", ctypes.c_ulonglong), ("evals32", ctypes.c_ulonglong), ("lu64", ctypes.c_ulonglong),
                 ("lu32", ctypes.c_ulonglong), ("hist", ctypes.c_ulonglong * 32), ("max_res", ctypes.c_double),
                 ("launches", ctypes.c_ulonglong), ("fallbacks", ctypes.c_ulonglong),
-                ("rescued", ctypes.c_ulonglong)]
+                ("rescued", ctypes.c_ulonglong), ("mlp_stalls", ctypes.c_ulonglong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
