@@ -162,8 +162,11 @@ int grim_init(const grim_grid* grid, const grim_metric* metric, const grim_physi
 
 /* One time step (Section 2.3): the half step P_n -> P_{n+1/2} with P^E = P_n
  * and dt/2, then the full step P_n -> P_{n+1} with P^E = P_{n+1/2} and dt.
- * P_in, P_out: device states; P_out may equal P_in.  The initial guess of
- * each stage is P_n with B set to the explicit flux-CT update. */
+ * P_in, P_out: device states; P_out may equal P_in (the full stage then
+ * reads a copy of P_in: one more state-sized device buffer, allocated by the
+ * first such call, so make it before capturing the call into a graph).  The
+ * initial guess of each stage is P_n with B set to the explicit flux-CT
+ * update. */
 int grim_step(grim_ctx* ctx, const double* P_in, double* P_out, double dt);
 
 /* grim_step with HOST buffers: copies P_in_host to the device, steps, and
@@ -174,7 +177,9 @@ int grim_step_host(grim_ctx* ctx, const double* P_in_host, double* P_out_host, d
 /* One stage: solve R(P) = 0 with explicit state P_E, start-of-step state P_n
  * and stage time step dts (dt/2 for the half step, dt for the full step).
  * guess: optional device state to start Newton from (NULL = P_n); its B
- * components are replaced by the explicit flux-CT update.  Writes P_out and,
+ * components are replaced by the explicit flux-CT update.  P_out may equal
+ * P_n (the stage then reads a copy of P_n, as grim_step in place) but not
+ * P_E (GRIM_EINVAL: neighbouring zones read P_E).  Writes P_out and,
  * if non-NULL, the per-zone Newton update count and status bits
  * (1 max-iterations, 2 line-search stall, 4 singular, 8 non-finite,
  * 16 inadmissible rho or u) to device byte arrays of n1*n2*n3 entries. */

@@ -30,7 +30,8 @@ cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
-                             const double* gc, unsigned long long* stalls, cudaStream_t st);
+                             const float* gf, unsigned long long* stalls, cudaStream_t st);
+cudaError_t launch_mlp_metric_table(const Params& p, const double* gc, float* gf, cudaStream_t st);
 cudaError_t launch_features_gr(const Params& p, const double* K, const double* gc, const double* Pn, const double* Pc,
                                float* X, float* Y, float* feat, cudaStream_t st);
 long long gr_geometry_doubles(const Params& p);
@@ -81,6 +82,7 @@ struct grim_ctx {
                               // the residuals of the zones handed to the queue kernel
   double* pncache = nullptr;  // P_n quantities shared by the two stages of a step
   double* Ph = nullptr;       // half-step state
+  double* Pcopy = nullptr;    // copy of P_n for a stage written over P_n (allocated on first use)
   uint8_t* iters = nullptr;   // per-zone Newton updates of the last stage
   uint8_t* status = nullptr;  // per-zone status bits of the last stage
   grim::Counters* cnt = nullptr;
@@ -89,6 +91,7 @@ struct grim_ctx {
   unsigned long long launches = 0;
   grim_mlp* mlp = nullptr;    // learned initial guess (grim_set_guess)
   float* feat = nullptr;      // its increment features [10][N], written by the zone kernel
+  float* gfeat = nullptr;     // its metric features: float copy of g_{mu nu} at zone centres (general metric)
   double accept = 0.0;
   // per-kernel timing: (class, start, stop) event triples
   bool profile = false;
@@ -163,6 +166,7 @@ void grim_destroy(grim_ctx* ctx) {
   cudaFree(ctx->faces);
   cudaFree(ctx->pncache);
   cudaFree(ctx->Ph);
+  cudaFree(ctx->Pcopy);
   cudaFree(ctx->iters);
   cudaFree(ctx->status);
   cudaFree(ctx->cnt);
@@ -172,6 +176,7 @@ void grim_destroy(grim_ctx* ctx) {
   cudaFree(ctx->qcount);
   cudaFree(ctx->rqueue);
   cudaFree(ctx->feat);
+  cudaFree(ctx->gfeat);
   for (auto& g : ctx->gcache) cudaGraphExecDestroy(g.exec);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   for (auto& m : ctx->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
@@ -284,6 +289,29 @@ static grim::Rescue rescue(grim_ctx* ctx, const double* Pn, const double* PE, co
   return grim::Rescue{ctx->rqueue, ctx->qcount + 1, Pout == Pn ? PE : Pn};
 }
 
+// A stage whose output is its own P_n: the start written into P_out would
+// replace P_n while the learned start's fallback and the revert of failed
+// zones still read it, so the stage reads a copy of P_n instead.  The copy's
+// buffer is allocated here, before any capture (grim_step, grim_stage and
+// grim_batch_step call this ahead of their launches).
+static int ensure_copy(grim_ctx* ctx, const double* Pn, const double* Pout) {
+  if (Pn != Pout || ctx->Pcopy) return GRIM_OK;
+  if (cudaMalloc(&ctx->Pcopy, sizeof(double) * grim::NV * (size_t)ctx->p.N) != cudaSuccess) {
+    ctx->Pcopy = nullptr;
+    return fail(ctx, GRIM_ENOMEM, "copy of P_n for an in-place stage");
+  }
+  return GRIM_OK;
+}
+static int pn_of_stage(grim_ctx* ctx, const double* Pn, const double* Pout, const double** out) {
+  *out = Pn;
+  if (Pn != Pout) return GRIM_OK;
+  GRIM_CUDA(cudaMemcpyAsync(ctx->Pcopy, Pn, sizeof(double) * grim::NV * (size_t)ctx->p.N, cudaMemcpyDeviceToDevice,
+                            ctx->cur),
+            "in-place copy of P_n");
+  *out = ctx->Pcopy;
+  return GRIM_OK;
+}
+
 static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double dts, const double* guess,
                      double* Pout, uint8_t* iters, uint8_t* status, int mode = 0) {
   const bool learned = ctx->mlp && !guess;
@@ -292,7 +320,7 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
   if (learned) {
     // the zone-constant kernel wrote the increment features beside the constants
     KernelMark m(ctx, GRIM_K_MLP, 1);
-    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->gr ? ctx->geo : nullptr,
+    GRIM_CUDA(grim::launch_mlp_guess(ctx->p, ctx->feat, Pn, ctx->mlp, Pout, ctx->gfeat,
                                      &ctx->cnt->mlp_stalls, ctx->cur),
               "mlp kernel");
   }
@@ -330,15 +358,19 @@ int grim_stage(grim_ctx* ctx, const double* P_n, const double* P_E, double dts, 
   if (!ctx || !P_n || !P_E || !P_out || !(dts > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_stage: bad argument");
   // other CTAs read P_E around their tiles while P_out is written
   if (P_out == P_E) return fail(ctx, GRIM_EINVAL, "grim_stage: P_out must not alias P_E");
-  return run_stage(ctx, P_n, P_E, dts, guess, P_out, iters, status);
+  const double* Pn = nullptr;
+  int rc = ensure_copy(ctx, P_n, P_out);
+  if (!rc) rc = pn_of_stage(ctx, P_n, P_out, &Pn);
+  return rc ? rc : run_stage(ctx, Pn, P_E, dts, guess, P_out, iters, status);
 }
 
 static int step_launches(grim_ctx* ctx, const double* P_in, double* P_out, double dt) {
   // The half step (P^E = P_n) caches the P_n quantities the full step reuses.
   int rc = run_stage(ctx, P_in, P_in, 0.5 * dt, nullptr, ctx->Ph, nullptr, nullptr, 1);
   if (rc) return rc;
-  // The full stage reads P_n only at each zone itself, so P_out may alias P_in.
-  return run_stage(ctx, P_in, ctx->Ph, dt, nullptr, P_out, nullptr, nullptr, 2);
+  const double* Pn = nullptr;
+  if ((rc = pn_of_stage(ctx, P_in, P_out, &Pn))) return rc;
+  return run_stage(ctx, Pn, ctx->Ph, dt, nullptr, P_out, nullptr, nullptr, 2);
 }
 
 static bool same_tuning(const grim_tuning& a, const grim_tuning& b) {
@@ -368,6 +400,7 @@ static int capture_step(grim_ctx* ctx, const double* P_in, double* P_out, double
 
 int grim_step(grim_ctx* ctx, const double* P_in, double* P_out, double dt) {
   if (!ctx || !P_in || !P_out || !(dt > 0.0)) return fail(ctx, GRIM_EINVAL, "grim_step: bad argument");
+  if (const int rc = ensure_copy(ctx, P_in, P_out)) return rc;
   if (!ctx->graphs || ctx->profile || !ctx->warmed || !same_tuning(ctx->warm_tune, ctx->tune) ||
       ctx->warm_mlp != (ctx->mlp != nullptr)) {
     const int rc = step_launches(ctx, P_in, P_out, dt);
@@ -595,6 +628,15 @@ int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept) {
     const cudaError_t e = cudaMalloc(&ctx->feat, sizeof(float) * grim::NV * (size_t)ctx->p.N);
     if (e != cudaSuccess) return fail(ctx, GRIM_ENOMEM, "grim_set_guess: feature buffer", e);
   }
+  if (mlp && ctx->gr && !ctx->gfeat) {
+    cudaError_t e = cudaMalloc(&ctx->gfeat, sizeof(float) * 10 * (size_t)(ctx->p.n1 + 2) * (ctx->p.n2 + 2));
+    if (e != cudaSuccess) {
+      ctx->gfeat = nullptr;
+      return fail(ctx, GRIM_ENOMEM, "grim_set_guess: metric features", e);
+    }
+    if ((e = grim::launch_mlp_metric_table(ctx->p, ctx->geo, ctx->gfeat, ctx->stream)) != cudaSuccess)
+      return fail(ctx, GRIM_ECUDA, "grim_set_guess: metric features", e);
+  }
   ctx->mlp = mlp;
   ctx->accept = accept;
   return GRIM_OK;
@@ -768,6 +810,8 @@ int grim_batch_step(grim_batch* b, const double* const* P_in, double* const* P_o
   const size_t n = b->box.size();
   for (size_t i = 0; i < n; i++)
     if (!P_in[i] || !P_out[i] || !(dt[i] > 0.0)) return batch_fail(b, GRIM_EINVAL, "grim_batch_step: bad argument");
+  for (size_t i = 0; i < n; i++)
+    if (const int rc = ensure_copy(b->box[i], P_in[i], P_out[i])) return batch_fail(b, rc, b->box[i]->err);
   bool profiling = false;
   for (auto c : b->box) profiling = profiling || c->profile;
   if (!b->graphs || !b->warmed || profiling) {

@@ -118,6 +118,12 @@ __device__ __forceinline__ float mlp_pn_feature(int a, double x, double rho) {
   if (a >= 8) return (float)(x / (fabs(x) + rho));
   return (float)x;
 }
+// mlp_pn_feature in float, from the float values of x and rho.
+__device__ __forceinline__ float mlp_pn_feature_f(int a, float x, float rho) {
+  if (a <= 1) return logf(fmaxf(x, 1e-37f));
+  if (a >= 8) return x / (fabsf(x) + rho);
+  return x;
+}
 __device__ __forceinline__ double mlp_unit(int a, double pn, double rho) {
   return a <= 1 ? pn : (a >= 8 ? fabs(pn) + rho : 1.0);
 }

@@ -417,30 +417,33 @@ __global__ void mlp_colstats(const float* __restrict__ X, long long M, int ncol,
 // ---------------------------------------------------------------- fused inference
 // The learned start on the fifth-generation tensor cores (tcgen05): one
 // persistent CTA per SM keeps the bfloat16 weights in shared memory and runs
-// tiles of 128 zones through the network, in two independent streams of
-// tiles (one per warpgroup, each with its own buffers, mbarrier and TMEM
-// accumulator), so that one stream's epilogue overlaps the other's MMAs.  Each layer is a 128 x N x K
+// tiles of 128 zones through the network in four independent streams of
+// tiles, one per warpgroup, each with its own activation buffer, mbarrier
+// and 128 TMEM columns, so that the epilogues of some streams overlap the
+// MMAs and the global loads of the others.  Each layer is a 128 x N x K
 // product issued by one thread as K/16 tcgen05.mma instructions (A: the
 // tile's activations, B: the layer's weights, both in shared memory; D:
 // float32 in tensor memory, one TMEM lane per zone); its completion arrives
-// on an mbarrier.  The epilogue reads each zone's row back from TMEM
-// (tcgen05.ld: warp w of a warpgroup reads lanes 32 (w % 4) ..), adds the
-// bias, applies SiLU and writes the bfloat16 activations into the next
-// layer's A tile.
-// The head's 80 outputs give y = M x_U + c per zone, and the start
-// P_n + y (in the learned start's units) replaces the non-magnetic
-// components of the Newton start P0.
+// on the stream's mbarrier.  The epilogue reads each zone's row back from
+// TMEM (tcgen05.ld: warp w of a warpgroup reads lanes 32 (w % 4) ..), adds
+// the bias, applies SiLU and writes the bfloat16 activations over the
+// layer's own A operand (complete by then).  The thread of a TMEM lane is
+// the thread of that zone throughout, so the head's ten float32 inputs
+// x_U stay in its registers.  The head's 80 outputs give y = M x_U + c per
+// zone, and the start P_n + y (in the learned start's units) replaces the
+// non-magnetic components of the Newton start P0.
 constexpr int TC_ROWS = 128;      // zones per tile: the MMA's M and the TMEM lanes
-constexpr int TC_STREAMS = 2;     // warpgroups, each with its own stream of tiles
+constexpr int TC_STREAMS = 4;     // warpgroups, each with its own stream of tiles
 constexpr int TC_THREADS = 128 * TC_STREAMS;
 constexpr uint32_t TC_COLS = 128; // TMEM columns of one warpgroup's accumulator
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;  // mbarrier polls before the kernel gives up
 
-// What one warpgroup's tile stream owns.
+// What one warpgroup's tile stream owns: the activations of its tile, in
+// the core-matrix K-major layout.  The standardised features (the first
+// layer's A operand, 128 x 32) occupy the start of the same buffer: the
+// first epilogue overwrites them only after the first layer's MMAs are done.
 struct TcStream {
-  __align__(128) unsigned char x[TC_ROWS * MLP_IN * 2];    // standardised features of the tile
-  __align__(128) unsigned char h[TC_ROWS * MLP_H * 2];     // hidden activations of the tile
-  float xu[TC_ROWS][MLP_XU + 2];                           // standardised head features, float32
+  __align__(128) unsigned char h[TC_ROWS * MLP_H * 2];
   uint64_t mbar;                                           // completion of the stream's MMAs
 };
 struct TcSmem {
@@ -450,7 +453,7 @@ struct TcSmem {
   __align__(128) unsigned char w3[MLP_HEAD * MLP_H * 2];   // W_4 [80][128]
   TcStream st[TC_STREAMS];
   __align__(16) float hb[3 * MLP_H];                      // halved hidden biases
-  float b4[MLP_HEAD];                                      // head bias
+  __align__(16) float b4[MLP_HEAD];                       // head bias
   float norm[2 * MLP_IN + 2 * MLP_Y];                      // x mean, 1/x std, y mean, y std
   uint32_t taddr;
   int abort[TC_STREAMS];
@@ -472,46 +475,33 @@ __device__ __forceinline__ void tc_load_tile(unsigned char* dst, const __nv_bflo
   }
 }
 
-// The raw inputs of one zone, loaded a tile ahead so that their latency
-// overlaps the tensor-core work of the tile before: the ten increment
-// features, P_n, and in a general metric the zone's g_{mu nu}.
-struct TcRaw {
-  float f[NV];
-  double pn[NV];
-  double g[10];
-};
-__device__ __forceinline__ void tc_fetch(const Params& p, const float* feat, const double* Pn, const double* gc,
-                                         long long z, TcRaw& R) {
+// The 32 features of zone z (see the file header), standardised: all 32 as
+// bfloat16 into row `row` of the stream's A tile, the first ten also as
+// float32 into xu for the head.  Rows past the grid get the feature means
+// (standardised zeros).
+// Little float64 work here: the metric comes from a float copy of the
+// centre table, and the P_n features are formed in float.
+__device__ __forceinline__ void tc_features(const Params& p, const float* feat, const double* Pn, const float* gf,
+                                            long long z, const TcSmem& S, TcStream& T, int row, float xu[MLP_XU]) {
   const long long N = p.N;
-  if (z >= N) return;
-#pragma unroll
-  for (int a = 0; a < NV; a++) R.f[a] = __ldg(feat + a * N + z);
-#pragma unroll
-  for (int a = 0; a < NV; a++) R.pn[a] = __ldg(Pn + a * N + z);
-  if (gc) {
-    const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
-    const int zi = (int)(z % p.n1), zj = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
-    const double* gz = gc + (long long)(zj + 1) * (p.n1 + 2) + (zi + 1);
-#pragma unroll
-    for (int a = 0; a < 10; a++) R.g[a] = __ldg(gz + a * nc);
-  }
-}
-
-// The 32 features of the zone (see the file header), standardised: the
-// first ten also as float32 for the head, all 32 as bfloat16 into row `row`
-// of the A tile.  Rows past the grid get the feature means (standardised
-// zeros).
-__device__ __forceinline__ void tc_features(const TcRaw& R, bool live, bool metric, const TcSmem& S, TcStream& T,
-                                            int row) {
   float xf[MLP_IN];
-  if (live) {
+  if (z < N) {
 #pragma unroll
-    for (int a = 0; a < NV; a++) xf[a] = R.f[a];
-    const float eta[10] = {-1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f};  // Minkowski g_{mu nu}
+    for (int a = 0; a < NV; a++) xf[a] = __ldg(feat + a * N + z);
+    if (gf) {  // the zone's g_{mu nu} from the float centre table of a general metric
+      const long long nc = (long long)(p.n1 + 2) * (p.n2 + 2);
+      const int zi = (int)(z % p.n1), zj = p.dim >= 2 ? (int)((z / p.n1) % p.n2) : 0;
+      const float* gz = gf + (long long)(zj + 1) * (p.n1 + 2) + (zi + 1);
 #pragma unroll
-    for (int a = 0; a < 10; a++) xf[NV + a] = metric ? (float)R.g[a] : eta[a];
+      for (int a = 0; a < 10; a++) xf[NV + a] = __ldg(gz + a * nc);
+    } else {
+      const float eta[10] = {-1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0.f, 1.f};  // Minkowski g_{mu nu}
 #pragma unroll
-    for (int a = 0; a < NV; a++) xf[2 * NV + a] = mlp_pn_feature(a, R.pn[a], R.pn[0]);
+      for (int a = 0; a < 10; a++) xf[NV + a] = eta[a];
+    }
+    const float rho = (float)__ldg(Pn + z);
+#pragma unroll
+    for (int a = 0; a < NV; a++) xf[2 * NV + a] = mlp_pn_feature_f(a, a == 0 ? rho : (float)__ldg(Pn + a * N + z), rho);
     xf[30] = xf[31] = 0.f;
   } else {
 #pragma unroll
@@ -521,7 +511,7 @@ __device__ __forceinline__ void tc_features(const TcRaw& R, bool live, bool metr
 #pragma unroll
   for (int a = 0; a < MLP_IN; a++) xs[a] = (xf[a] - S.norm[a]) * S.norm[MLP_IN + a];
 #pragma unroll
-  for (int a = 0; a < MLP_XU; a++) T.xu[row][a] = xs[a];
+  for (int a = 0; a < MLP_XU; a++) xu[a] = xs[a];
 #pragma unroll
   for (int c = 0; c < MLP_IN / 8; c++) {
     uint4 v;
@@ -529,18 +519,17 @@ __device__ __forceinline__ void tc_features(const TcRaw& R, bool live, bool metr
     v.y = pack_bf16(xs[8 * c + 2], xs[8 * c + 3]);
     v.z = pack_bf16(xs[8 * c + 4], xs[8 * c + 5]);
     v.w = pack_bf16(xs[8 * c + 6], xs[8 * c + 7]);
-    *reinterpret_cast<uint4*>(T.x + tc::kmajor_offset(row, 8 * c, MLP_IN)) = v;
+    *reinterpret_cast<uint4*>(T.h + tc::kmajor_offset(row, 8 * c, MLP_IN)) = v;
   }
 }
 
 // Issue the MMAs of layer l for the tile (one thread) and commit them to
-// the mbarrier.
+// the stream's mbarrier.
 __device__ __forceinline__ void tc_issue_layer(const TcSmem& S, TcStream& T, int l, uint32_t tmem) {
-  const unsigned char* A = l == 0 ? T.x : T.h;
   const unsigned char* B = l == 0 ? S.w0 : l == 1 ? S.w1 : l == 2 ? S.w2 : S.w3;
   const uint32_t kc = l == 0 ? MLP_IN : MLP_H;
   const uint32_t n = l == 3 ? MLP_HEAD : MLP_H;
-  const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B), sbo = kc * 16u;
+  const uint32_t a0 = tc::smem_addr(T.h), b0 = tc::smem_addr(B), sbo = kc * 16u;
   const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, n);
   for (uint32_t s = 0; s < kc / 16; s++)  // K = 16 per MMA: two core matrices along K
     tc::mma_bf16(tmem, tc::smem_desc(a0 + 256u * s, 128u, sbo), tc::smem_desc(b0 + 256u * s, 128u, sbo), idesc,
@@ -548,7 +537,7 @@ __device__ __forceinline__ void tc_issue_layer(const TcSmem& S, TcStream& T, int
   tc::commit(&T.mbar);
 }
 
-// Named barrier of one warpgroup (ids 1, 2; 0 is __syncthreads).
+// Named barrier of one warpgroup (ids 1..4; 0 is __syncthreads).
 __device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) mlp_guess_tc(const __grid_constant__ Params p,
@@ -558,24 +547,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_guess_tc(const __grid_const
                                                                const float* __restrict__ params,
                                                                const float* __restrict__ norm,
                                                                double* __restrict__ P0,
-                                                               const double* __restrict__ gc,
+                                                               const float* __restrict__ gf,
                                                                unsigned long long* __restrict__ stalls) {
   extern __shared__ __align__(128) unsigned char smraw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smraw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = warp >> 2;                   // warpgroup: the tile stream of this thread
-  const int row = (warp & 3) * 32 + lane;    // the tile row (zone) of this thread's TMEM lane
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = warp >> 2;                           // warpgroup: the tile stream of this thread
+  const int row = (warp & 3) * 32 + (tid & 31);      // the tile row (zone) of this thread's TMEM lane
   TcStream& T = S.st[g];
   // weights, biases and standardisation into shared memory (all threads)
   tc_load_tile(S.w0, wb, MLP_H, MLP_IN);
   tc_load_tile(S.w1, wb + MLP_H * MLP_IN, MLP_H, MLP_H);
   tc_load_tile(S.w2, wb + MLP_H * MLP_IN + MLP_H * MLP_H, MLP_H, MLP_H);
   tc_load_tile(S.w3, wb + MLP_H * MLP_IN + 2 * MLP_H * MLP_H, MLP_HEAD, MLP_H);
-  for (int i = tid; i < MLP_H; i += TC_THREADS) {
-    S.hb[i] = 0.5f * params[mlp_boff(0) + i];
-    S.hb[MLP_H + i] = 0.5f * params[mlp_boff(1) + i];
-    S.hb[2 * MLP_H + i] = 0.5f * params[mlp_boff(2) + i];
-  }
+  for (int i = tid; i < 3 * MLP_H; i += TC_THREADS) S.hb[i] = 0.5f * params[mlp_boff(i / MLP_H) + i % MLP_H];
   if (tid < MLP_HEAD) S.b4[tid] = params[mlp_boff(3) + tid];
   if (tid < 2 * MLP_IN + 2 * MLP_Y) S.norm[tid] = (tid >= MLP_IN && tid < 2 * MLP_IN) ? 1.0f / norm[tid] : norm[tid];
   if (tid < TC_STREAMS) {
@@ -594,13 +579,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_guess_tc(const __grid_const
   const long long N = p.N;
   const long long tiles = (N + TC_ROWS - 1) / TC_ROWS;
   const long long tstep = (long long)gridDim.x * TC_STREAMS;
-  TcRaw cur, nxt;
-  long long t = (long long)blockIdx.x * TC_STREAMS + g;
-  tc_fetch(p, feat, Pn, gc, t * TC_ROWS + row, cur);
-  for (; t < tiles; t += tstep) {
-    const long long z0 = t * TC_ROWS, z = z0 + row;
-    tc_features(cur, z < N, gc != nullptr, S, T, row);
-    tc_fetch(p, feat, Pn, gc, (t + tstep) * TC_ROWS + row, nxt);   // in flight during this tile's layers
+  for (long long t = (long long)blockIdx.x * TC_STREAMS + g; t < tiles; t += tstep) {
+    const long long z = t * TC_ROWS + row;
+    float xu[MLP_XU];
+    tc_features(p, feat, Pn, gf, z, S, T, row, xu);
     tc::fence_async_smem();
     tc::fence_before_sync();
     wg_sync(g);
@@ -614,12 +596,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_guess_tc(const __grid_const
       phase ^= 1u;
       if (!ok) S.abort[g] = 1;
       tc::fence_after_sync();
+      uint32_t r[2][16];
       if (ok && l < MLP_NLAYER - 1) {
         // bias, SiLU, bfloat16 of this thread's zone, all 128 columns, 16 at
         // a time: the load of the next 16 is in flight while these are
         // processed
         const float4* hb4 = reinterpret_cast<const float4*>(S.hb + l * MLP_H);
-        uint32_t r[2][16];
         tc::ld_x16_issue(tlane, r[0]);
 #pragma unroll
         for (int q = 0; q < MLP_H / 16; q++) {
@@ -640,22 +622,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_guess_tc(const __grid_const
               make_uint4(u[4], u[5], u[6], u[7]);
         }
       } else if (ok) {
-        // head: y_i = sum_j M_ij x_j + c_i, then the start of the zone (the
-        // loads are warp-collective: every lane takes part, rows past the
-        // grid write nothing)
-        float o[MLP_HEAD];
-        tc::ld_x32(tlane, o);
-        tc::ld_x32(tlane + 32u, o + 32);
-        tc::ld_x16(tlane + 64u, o + 64);
+        // head: y_i = sum_j M_ij x_j + c_i (M_ij in column 10 i + j, c_i in
+        // column 70 + i), 16 columns at a time as above; then the start of
+        // the zone (the loads are warp-collective: every lane takes part,
+        // rows past the grid write nothing)
+        const float4* b44 = reinterpret_cast<const float4*>(S.b4);
+        float y[MLP_NP];
 #pragma unroll
-        for (int i = 0; i < MLP_NP; i++) {
-          if (z >= N) break;
-          float y = o[MLP_NP * MLP_XU + i] + S.b4[MLP_NP * MLP_XU + i];
+        for (int i = 0; i < MLP_NP; i++) y[i] = 0.f;
+        tc::ld_x16_issue(tlane, r[0]);
 #pragma unroll
-          for (int j = 0; j < MLP_XU; j++) y = fmaf(o[i * MLP_XU + j] + S.b4[i * MLP_XU + j], T.xu[row][j], y);
-          const int f = mlp_field(i);
-          const double d = (double)(y * S.norm[2 * MLP_IN + MLP_Y + f] + S.norm[2 * MLP_IN + f]);
-          P0[f * N + z] = mlp_apply(f, cur.pn[f], d, cur.pn[0]);
+        for (int q = 0; q < MLP_HEAD / 16; q++) {
+          tc::ld_wait16(r[q & 1]);
+          if (q + 1 < MLP_HEAD / 16) tc::ld_x16_issue(tlane + (uint32_t)(16 * (q + 1)), r[(q + 1) & 1]);
+#pragma unroll
+          for (int e4 = 0; e4 < 4; e4++) {
+            const float4 b = b44[4 * q + e4];
+            const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const int c = 16 * q + 4 * e4 + e;
+              const float o = __uint_as_float(r[q & 1][4 * e4 + e]) + bb[e];
+              if (c < MLP_NP * MLP_XU) y[c / MLP_XU] = fmaf(o, xu[c % MLP_XU], y[c / MLP_XU]);
+              else if (c < MLP_NP * (MLP_XU + 1)) y[c - MLP_NP * MLP_XU] += o;
+            }
+          }
+        }
+        if (z < N) {
+          const double rho = __ldg(Pn + z);
+#pragma unroll
+          for (int i = 0; i < MLP_NP; i++) {
+            const int f = mlp_field(i);
+            const double d = (double)(y[i] * S.norm[2 * MLP_IN + MLP_Y + f] + S.norm[2 * MLP_IN + f]);
+            P0[f * N + z] = mlp_apply(f, f == 0 ? rho : __ldg(Pn + f * N + z), d, rho);
+          }
         }
       }
       tc::fence_async_smem();
@@ -664,7 +664,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_guess_tc(const __grid_const
       if (S.abort[g]) break;
     }
     if (S.abort[g]) break;
-    cur = nxt;
   }
   if (S.abort[g] && issuer) {
     // a layer's MMAs did not complete in time: wait (bounded) for them once
@@ -920,11 +919,24 @@ cudaError_t launch_mlp_features(const Params& p, const double* K, const double* 
   return cudaGetLastError();
 }
 
-// gc: the centre geometry table of a general metric (its first ten planes
-// are g_{mu nu}), or NULL for Minkowski space.  stalls: a device counter
-// raised when the kernel gave up waiting for its tensor-core work.
+// float copy of the first n entries of a float64 table (the metric planes
+// the learned start reads)
+__global__ void mlp_table_f32(const double* __restrict__ in, long long n, float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+cudaError_t launch_mlp_metric_table(const Params& p, const double* gc, float* gf, cudaStream_t st) {
+  const long long n = 10LL * (p.n1 + 2) * (p.n2 + 2);
+  mlp_table_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gc, n, gf);
+  return cudaGetLastError();
+}
+
+// gf: float copy of the first ten planes (g_{mu nu}) of the centre geometry
+// table of a general metric (launch_mlp_metric_table), or NULL for
+// Minkowski space.  stalls: a device counter raised when the kernel gave up
+// waiting for its tensor-core work.
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
-                             const double* gc, unsigned long long* stalls, cudaStream_t st) {
+                             const float* gf, unsigned long long* stalls, cudaStream_t st) {
   static PerDevice once;
   int sms = 0;
   cudaError_t e = once.get(
@@ -941,7 +953,7 @@ cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* P
   const long long tiles = (p.N + TC_ROWS - 1) / TC_ROWS;
   long long grid = sms;  // persistent: one block (one copy of the weights, 256 TMEM columns) per SM
   if (grid > (tiles + TC_STREAMS - 1) / TC_STREAMS) grid = (tiles + TC_STREAMS - 1) / TC_STREAMS;
-  mlp_guess_tc<<<(unsigned)grid, TC_THREADS, sizeof(TcSmem), st>>>(p, feat, Pn, m->wb, m->params, m->norm, P0, gc,
+  mlp_guess_tc<<<(unsigned)grid, TC_THREADS, sizeof(TcSmem), st>>>(p, feat, Pn, m->wb, m->params, m->norm, P0, gf,
                                                                    stalls);
   return cudaGetLastError();
 }
