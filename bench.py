@@ -436,13 +436,14 @@ def bench_kerr(dev, torch, world, steps=10, warmup=3, cpu=False):
             g.set_guess(mlp, accept=1e-3)
         a = P.to(dev)
         b = torch.empty_like(a)
+        tuning = g.autotune(a, dt)[0]   # launch shapes, untimed
         ms, s, kt, _ = time_device(g, a, b, dt, steps, warmup, world, torch)
         ms = max_over_ranks(ms, world)
         out[name] = {"value": aggregate_rate(prob.zones, ms * 1e-3, world), "ms_per_step": ms,
                      "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]),
                      "fp64_residuals_per_zone_stage": s["evals64"] / max(1, s["zones"]),
                      "failed": s["failed"], "rescued": s["rescued"],
-                     "max_res": s["max_res"], "fallbacks": s["fallbacks"],
+                     "max_res": s["max_res"], "fallbacks": s["fallbacks"], "tuning": tuning,
                      # per stage, from the profile pass (zone_const: derived + sources +
                      # stage constants, and the floors)
                      "kernel_ms_per_stage": {k: v[0] / (2 * min(steps, 10)) for k, v in kt.items()}}

@@ -272,14 +272,20 @@ int grim_peak_flops(double* fp64_tflops, double* fp32_tflops);
  * kernels (32, 64 or 128).  newton_kcut: after this many Newton updates a
  * zone that has not converged leaves the in-order kernel for a queue that a
  * persistent kernel works through densely, so that a few slow zones do not
- * hold whole warps (>= k_max: no queue).  faces_bs, zone_bs: threads per
- * block of the face-flux and zone-constant kernels (64, 128 or 256). */
+ * hold whole warps (>= k_max: no queue).  newton_rounds: 1 = the in-order
+ * kernel makes one update per round and, between rounds, packs the block's
+ * unconverged zones into its lowest threads (their state moves through
+ * shared memory; the zone constants stay where they are), so that converged
+ * zones stop costing their warps issue slots; 0 = each thread runs its zone
+ * to convergence or newton_kcut updates in one pass.  Either way the
+ * results are the same bits.  faces_bs, zone_bs: threads per block of the
+ * face-flux and zone-constant kernels (64, 128 or 256). */
 typedef struct {
-  int newton_bs, newton_kcut, faces_bs, zone_bs;
+  int newton_bs, newton_kcut, faces_bs, zone_bs, newton_rounds;
 } grim_tuning;
 
 int grim_get_tuning(grim_ctx* ctx, grim_tuning* out);
-/* GRIM_EINVAL for a value outside the sets above (newton_kcut >= 1). */
+/* GRIM_EINVAL for a value outside the sets above (newton_kcut >= 1, newton_rounds 0 or 1). */
 int grim_set_tuning(grim_ctx* ctx, const grim_tuning* tuning);
 
 /* Choose the launch shape by timing grim_step from the device state P with

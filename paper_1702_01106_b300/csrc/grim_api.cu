@@ -62,7 +62,7 @@ struct grim_ctx {
   cudaStream_t stream;        // the caller's stream
   cudaStream_t cur;           // where launches go: stream, or cap while capturing
   cudaStream_t cap = nullptr; // private stream for graph capture
-  grim_tuning tune{64, 2, 128, 128};
+  grim_tuning tune{64, 2, 128, 128, 0};
   int* queue = nullptr;       // zones left for the queue kernel
   int* qcount = nullptr;      // their number, then the rescue queue's length
   int* rqueue = nullptr;      // mixed-solver zones handed to the float64 rescue
@@ -325,7 +325,7 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
               "mlp kernel");
   }
   if (ctx->gr) {
-    const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
+    const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut, ctx->tune.newton_rounds != 0};
     {
       KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64,
                    (cfg.kcut < ctx->p.kmax ? 2 : 1) + (rescue(ctx, Pn, PE, Pout).queue ? 1 : 0));
@@ -342,7 +342,7 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
     return GRIM_OK;
   }
   {
-    const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut};
+    const grim::NewtonCfg cfg{ctx->tune.newton_bs, ctx->tune.newton_kcut, ctx->tune.newton_rounds != 0};
     KernelMark m(ctx, ctx->precision ? GRIM_K_NEWTON32 : GRIM_K_NEWTON64,
                  (cfg.kcut < ctx->p.kmax ? 2 : 1) + (rescue(ctx, Pn, PE, Pout).queue ? 1 : 0));
     GRIM_CUDA(grim::launch_newton_fb(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
@@ -374,7 +374,8 @@ static int step_launches(grim_ctx* ctx, const double* P_in, double* P_out, doubl
 }
 
 static bool same_tuning(const grim_tuning& a, const grim_tuning& b) {
-  return a.newton_bs == b.newton_bs && a.newton_kcut == b.newton_kcut && a.faces_bs == b.faces_bs &&
+  return a.newton_bs == b.newton_bs && a.newton_kcut == b.newton_kcut && a.newton_rounds == b.newton_rounds &&
+         a.faces_bs == b.faces_bs &&
          a.zone_bs == b.zone_bs;
 }
 
@@ -439,7 +440,8 @@ int grim_use_graphs(grim_ctx* ctx, int enable) {
 
 static bool valid_tuning(const grim_tuning& t) {
   auto in = [](int v, std::initializer_list<int> s) { return std::find(s.begin(), s.end(), v) != s.end(); };
-  return in(t.newton_bs, {32, 64, 128}) && t.newton_kcut >= 1 && in(t.faces_bs, {64, 128, 256}) &&
+  return in(t.newton_bs, {32, 64, 128}) && t.newton_kcut >= 1 && in(t.newton_rounds, {0, 1}) &&
+         in(t.faces_bs, {64, 128, 256}) &&
          in(t.zone_bs, {64, 128, 256});
 }
 
@@ -481,8 +483,8 @@ static bool read_cached_tuning(const char* path, const std::string& key, grim_tu
     const char* q = std::strstr(line, "\"newton_bs\":");
     grim_tuning c;
     double m = 0.0;
-    if (q && std::sscanf(q, "\"newton_bs\": %d, \"newton_kcut\": %d, \"faces_bs\": %d, \"zone_bs\": %d, \"step_ms\": %lf",
-                         &c.newton_bs, &c.newton_kcut, &c.faces_bs, &c.zone_bs, &m) == 5 &&
+    if (q && std::sscanf(q, "\"newton_bs\": %d, \"newton_kcut\": %d, \"newton_rounds\": %d, \"faces_bs\": %d, \"zone_bs\": %d, \"step_ms\": %lf",
+                         &c.newton_bs, &c.newton_kcut, &c.newton_rounds, &c.faces_bs, &c.zone_bs, &m) == 6 &&
         valid_tuning(c)) {
       t = c; ms = m; found = true;
     }
@@ -503,8 +505,8 @@ static void write_cached_tuning(const char* path, const std::string& key, const 
   FILE* f = std::fopen(path, "w");
   if (!f) return;
   for (auto& l : keep) std::fputs(l.c_str(), f);
-  std::fprintf(f, "{%s, \"newton_bs\": %d, \"newton_kcut\": %d, \"faces_bs\": %d, \"zone_bs\": %d, \"step_ms\": %.6f}\n",
-               tag.c_str(), t.newton_bs, t.newton_kcut, t.faces_bs, t.zone_bs, ms);
+  std::fprintf(f, "{%s, \"newton_bs\": %d, \"newton_kcut\": %d, \"newton_rounds\": %d, \"faces_bs\": %d, \"zone_bs\": %d, \"step_ms\": %.6f}\n",
+               tag.c_str(), t.newton_bs, t.newton_kcut, t.newton_rounds, t.faces_bs, t.zone_bs, ms);
   std::fclose(f);
 }
 
@@ -542,11 +544,13 @@ int grim_autotune(grim_ctx* ctx, const double* P, double dt, const char* cache_p
     ctx->profile = false;
     int rc = time_steps(ctx, P, out_state, dt, best_ms);
     const int kmax = ctx->p.kmax;
-    const std::vector<int> sets[4] = {{32, 64, 128}, {1, 2, 3, kmax > 3 ? kmax : 4}, {64, 128, 256}, {64, 128, 256}};
-    for (int f = 0; f < 4 && !rc; f++) {
+    const std::vector<int> sets[5] = {{32, 64, 128}, {0, 1}, {1, 2, 3, 4, kmax > 4 ? kmax : 5}, {64, 128, 256},
+                                      {64, 128, 256}};
+    for (int f = 0; f < 5 && !rc; f++) {
       for (int v : sets[f]) {
         grim_tuning c = best;
-        int* field = f == 0 ? &c.newton_bs : f == 1 ? &c.newton_kcut : f == 2 ? &c.faces_bs : &c.zone_bs;
+        int* field = f == 0 ? &c.newton_bs : f == 1 ? &c.newton_rounds : f == 2 ? &c.newton_kcut
+                   : f == 3 ? &c.faces_bs : &c.zone_bs;
         if (*field == v) continue;
         *field = v;
         ctx->tune = c;

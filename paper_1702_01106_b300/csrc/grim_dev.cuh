@@ -82,6 +82,7 @@ struct Params {
 struct NewtonCfg {
   int bs;
   int kcut;
+  bool rounds;  // one update per round, unconverged zones packed between rounds
 };
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2 };

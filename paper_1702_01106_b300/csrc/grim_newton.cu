@@ -469,6 +469,87 @@ __device__ __forceinline__ void to_rescue(int* rqueue, int* rcount, ZoneResult& 
   o.pending = o.pending || resc;
 }
 
+// Per-thread tallies of a block's zone solves, added to the counters once,
+// at the end of the kernel (warp sums, one atomic per warp and counter); a
+// zone's histogram bin and residual maximum go in when it finishes.  Work
+// counts belong to whichever thread did the work, zone counts to the thread
+// that finished the zone.
+struct Tally {
+  unsigned e64 = 0, e32 = 0, l64 = 0, l32 = 0, it = 0, zn = 0, fl = 0, fb = 0;  // one thread's share: small
+  __device__ __forceinline__ void work(const ZoneResult& o) {
+    e64 += o.evals64; e32 += o.evals32; l64 += o.lu64; l32 += o.lu32; it += o.done;
+  }
+  __device__ __forceinline__ void finish(Counters* c, const ZoneResult& o) {
+    zn++;
+    fl += o.status != 0;
+    atomicAdd(&c->hist[o.iters < 31 ? o.iters : 31], 1ull);
+    if (finite_bits(o.res)) atomicMax(&c->maxres_bits, (unsigned long long)__double_as_longlong(o.res));
+  }
+  // every lane of the warp calls it
+  __device__ __forceinline__ void flush(Counters* c) {
+    using u64 = unsigned long long;
+    const u64 s64 = warp_sum(e64), s32 = warp_sum(e32), sl64 = warp_sum(l64), sl32 = warp_sum(l32);
+    const u64 sit = warp_sum(it), szn = warp_sum(zn), sfl = warp_sum(fl), sfb = warp_sum(fb);
+    if ((threadIdx.x & 31) == 0 && (s64 | s32 | szn | sit)) {
+      atomicAdd(&c->evals64, s64); atomicAdd(&c->evals32, s32);
+      atomicAdd(&c->lu64, sl64); atomicAdd(&c->lu32, sl32);
+      atomicAdd(&c->iters, sit);
+      if (szn) { atomicAdd(&c->failed, sfl); atomicAdd(&c->zones, szn); }
+      if (sfb) atomicAdd(&c->fallbacks, sfb);
+    }
+  }
+};
+
+// Rank of this thread among the threads of the block whose flag is set (in
+// thread order), and in `total` their number.  wsum: BS/32 ints of shared
+// memory.  Every thread of the block calls it; it holds a barrier, after
+// which every thread has passed its call.
+template <int BS>
+__device__ __forceinline__ int block_rank(bool flag, int* wsum, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) wsum[w] = __popc(m);
+  __syncthreads();
+  int base = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < BS / 32; i++) {
+    const int c = wsum[i];
+    base += i < w ? c : 0;
+    tot += c;
+  }
+  total = tot;
+  return base + __popc(m & ((1u << lane) - 1u));
+}
+
+// Compaction between updates.  Between two rounds of one update each, a
+// zone that goes on moves to the thread of its rank among the block's
+// unconverged zones, through the Jacobian area of shared memory (free
+// between updates): its state P, its residual r (the resumed solve reads r
+// instead of evaluating it again), the slot of its constants (they stay in
+// their column) and its update count.  The Jacobian area holds 20 doubles
+// and an int per thread at least (MIXED: 56 floats).
+struct Staging {
+  double* P;
+  double* r;
+  int* meta;
+  template <int BS> __device__ __forceinline__ static Staging at(void* jac) {
+    double* d = (double*)jac;
+    return Staging{d, d + NV * BS, (int*)(d + 2 * NV * BS)};
+  }
+  template <int BS> __device__ __forceinline__ void put(int i, const double P_[NV], const double r_[NV], int slot, int k) const {
+#pragma unroll
+    for (int a = 0; a < NV; a++) { P[a * BS + i] = P_[a]; r[a * BS + i] = r_[a]; }
+    meta[i] = slot | (k << 16);
+  }
+  template <int BS> __device__ __forceinline__ void get(int i, double P_[NV], double r_[NV], int& slot, int& k) const {
+#pragma unroll
+    for (int a = 0; a < NV; a++) { P_[a] = P[a * BS + i]; r_[a] = r[a * BS + i]; }
+    slot = meta[i] & 0xffff;
+    k = meta[i] >> 16;
+  }
+};
+static_assert(sizeof(float) * (NJ * NJ + NJ) >= 2 * NV * sizeof(double) + sizeof(int), "staging fits the Jacobian area");
+
 // Shared memory per thread: zone constants (NK doubles, plus NK floats for
 // MIXED), the Jacobian and the right-hand side (110 elements of the Jacobian
 // precision).
@@ -520,6 +601,98 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
   if (queue) enqueue(queue, qcount, active && o.pending, z);
   if (MIXED && rqueue) to_rescue(rqueue, rcount, o, active, z);
   accumulate(cnt, o, active, fellback);
+}
+
+// newton_dense in rounds of one update, with the block's unconverged zones
+// packed into its lowest threads between rounds (see Staging): a converged
+// zone stops costing its warp issue slots (a float64 warp instruction costs
+// the pipe the same whatever lanes are live).  A zone makes at most kstop
+// updates here, then goes on in the queue kernel (kstop >= k_max: no queue).
+// The zone solves are those of newton_dense, bit for bit.
+template <bool MIXED, int BS, bool IDEAL>
+__global__ void __launch_bounds__(BS) newton_rounds(const __grid_constant__ Params p, const double* __restrict__ K,
+                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
+                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
+                                                    const double* __restrict__ Pfb, double accept, int kstop,
+                                                    int* __restrict__ queue, int* __restrict__ qcount,
+                                                    double* __restrict__ rq, int* __restrict__ rqueue,
+                                                    int* __restrict__ rcount) {
+  using S = NewtonSmem<MIXED, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int wsum[BS / 32];
+  double* kd = (double*)smem_raw;
+  float* kf = (float*)(smem_raw + S::kd);
+  void* jac = smem_raw + S::kd + S::kf;
+  const Staging stg = Staging::at<BS>(jac);
+  const long long N = p.N;
+  const long long z0 = (long long)blockIdx.x * BS;
+  const int t = threadIdx.x;
+  const int ks = kstop < p.kmax ? kstop : p.kmax;
+  const unsigned long long acc = abits(accept);
+  bool own = z0 + t < N;
+  int sl = t, k = 0;
+  double Pz[NV], rz[NV];
+  if (own) {
+#pragma unroll
+    for (int a = 0; a < NK; a++) {
+      const double x = __ldg(K + a * N + z0 + t);
+      kd[a * BS + t] = x;
+      if (MIXED) kf[a * BS + t] = d2f_jac(x);
+    }
+#pragma unroll
+    for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z0 + t];
+  }
+  Tally tl;
+  for (int round = 0;; round++) {
+    const long long z = z0 + sl;
+    bool go = false, resc = false;
+    if (own) {
+      bool fb = false;
+      const ZoneResult o = newton_zone<MIXED, BS, IDEAL>(p, kd + sl, kf + sl, Pz, jac,
+                                                         round == 0 && Pfb ? Pfb + z : nullptr, N, acc, fb, k,
+                                                         k + 1, rz, 1);
+      tl.work(o);
+      tl.fb += fb;
+      k = o.iters;
+      go = o.pending;
+      if (!go) {
+#pragma unroll
+        for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
+        iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
+        status[z] = (uint8_t)o.status;
+        if (MIXED && rqueue && o.status != 0) resc = true;  // finished by the rescue kernel
+        else tl.finish(cnt, o);
+      }
+    }
+    if (MIXED && rqueue) enqueue(rqueue, rcount, resc, z);
+    int n = 0;
+    const int rank = block_rank<BS>(go, wsum, n);
+    if (n == 0) break;
+    if (round + 1 >= ks) {
+      // unconverged after ks updates: on to the queue kernel
+      if (go) {
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+          P[a * N + z] = Pz[a];
+          if (rq) rq[a * N + z] = rz[a];
+        }
+        iters[z] = (uint8_t)k;
+      }
+      enqueue(queue, qcount, go, z);
+      break;
+    }
+    if (n > BS - 32) {
+      // packing would free no warp: every zone stays with its thread
+      own = go;
+      continue;
+    }
+    if (go) stg.put<BS>(rank, Pz, rz, sl, k);
+    __syncthreads();
+    own = t < n;
+    if (own) stg.get<BS>(t, Pz, rz, sl, k);
+    __syncthreads();
+  }
+  tl.flush(cnt);
 }
 
 // The zones queued by newton_dense, packed densely into warps: a persistent
@@ -681,6 +854,8 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
         [](int* grid) {
           cudaError_t e = cudaFuncSetAttribute(newton_dense<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
           if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(newton_rounds<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+          if (e == cudaSuccess)
             e = cudaFuncSetAttribute(newton_queue<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
           int dev = 0, sms = 0, per_sm = 0;
           if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -692,8 +867,8 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
         &qgrid);
   }
   static cudaError_t launch(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
-                            Counters* cnt, const double* Pfb, double accept, int kcut, int* queue, int* qcount,
-                            double* rq, const Rescue& rs, cudaStream_t st) {
+                            Counters* cnt, const double* Pfb, double accept, int kcut, bool rounds, int* queue,
+                            int* qcount, double* rq, const Rescue& rs, cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
@@ -703,9 +878,16 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
     if (rescue && (e = cudaMemsetAsync(rs.count, 0, sizeof(int), st)) != cudaSuccess) return e;
     int* rqueue = rescue ? rs.queue : nullptr;
     const long long nb = (p.N + BS - 1) / BS;
-    newton_dense<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
-                                                                 compact ? kcut : p.kmax, compact ? queue : nullptr,
-                                                                 qcount, rq, rqueue, rs.count);
+    if (rounds)
+      newton_rounds<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
+                                                                    compact ? kcut : p.kmax,
+                                                                    compact ? queue : nullptr, qcount, rq, rqueue,
+                                                                    rs.count);
+    else
+      newton_dense<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
+                                                                   compact ? kcut : p.kmax,
+                                                                   compact ? queue : nullptr, qcount, rq, rqueue,
+                                                                   rs.count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (compact) {
       newton_queue<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue,
@@ -723,13 +905,13 @@ static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P,
                                    int* qcount, double* rq, const Rescue& rs, cudaStream_t st) {
   switch (cfg.bs) {
     case 32:
-      return NewtonKernels<MIXED, 32, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
+      return NewtonKernels<MIXED, 32, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, cfg.rounds, queue,
                                                      qcount, rq, rs, st);
     case 64:
-      return NewtonKernels<MIXED, 64, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
+      return NewtonKernels<MIXED, 64, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, cfg.rounds, queue,
                                                      qcount, rq, rs, st);
     case 128:
-      return NewtonKernels<MIXED, 128, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, queue,
+      return NewtonKernels<MIXED, 128, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, cfg.rounds, queue,
                                                       qcount, rq, rs, st);
     default: return cudaErrorInvalidValue;
   }
@@ -756,7 +938,7 @@ cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                           Counters* cnt, cudaStream_t st) {
-  const NewtonCfg cfg{64, 1 << 30};
+  const NewtonCfg cfg{64, 1 << 30, false};
   return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, nullptr, Rescue{},
                           st);
 }
@@ -1100,6 +1282,91 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
   accumulate(cnt, o, active, fellback);
 }
 
+// newton_dense_gr in rounds of one update with the block's unconverged
+// zones packed between rounds (see newton_rounds); the metric of a zone
+// stays in its column of shared memory like its constants.
+template <bool MIXED, int BS, bool IDEAL>
+__global__ void __launch_bounds__(BS) newton_rounds_gr(const __grid_constant__ Params p, const double* __restrict__ K,
+                                                       const double* __restrict__ gc, double* __restrict__ P,
+                                                       uint8_t* __restrict__ iters, uint8_t* __restrict__ status,
+                                                       Counters* __restrict__ cnt, int kstop, int* __restrict__ queue,
+                                                       int* __restrict__ qcount, double* __restrict__ rq,
+                                                       const double* __restrict__ Pfb, double accept,
+                                                       int* __restrict__ rqueue, int* __restrict__ rcount) {
+  using S = NewtonSmemGr<MIXED, BS>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int wsum[BS / 32];
+  double* kd = (double*)smem_raw;
+  double* md = (double*)(smem_raw + S::kd);
+  float* kf = (float*)(smem_raw + S::kd + S::md);
+  void* jac = smem_raw + S::kd + S::md + S::kf;
+  const Staging stg = Staging::at<BS>(jac);
+  const long long N = p.N;
+  const long long z0 = (long long)blockIdx.x * BS;
+  const int t = threadIdx.x;
+  const int ks = kstop < p.kmax ? kstop : p.kmax;
+  const unsigned long long acc = abits(accept);
+  bool own = z0 + t < N;
+  int sl = t, k = 0;
+  double Pz[NV], rz[NV];
+  if (own) {
+    load_zone_gr<MIXED, BS>(p, K, gc, z0 + t, kd + t, kf + t, md + t);
+#pragma unroll
+    for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z0 + t];
+  }
+  Tally tl;
+  for (int round = 0;; round++) {
+    const long long z = z0 + sl;
+    bool go = false, resc = false;
+    if (own) {
+      bool fb = false;
+      ZoneResult o = newton_zone_gr<MIXED, BS, IDEAL>(p, kd + sl, kf + sl, md + sl, Pz, jac, k, k + 1, rz, 1,
+                                                      round == 0 && Pfb ? Pfb + z : nullptr, N, acc, fb);
+      tl.work(o);
+      tl.fb += fb;
+      k = o.iters;
+      go = o.pending;
+      if (!go) {
+        if (p.floors && o.status == 0) floors_converged(p, gc, z, o, Pz);
+#pragma unroll
+        for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
+        iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
+        status[z] = (uint8_t)o.status;
+        if (MIXED && rqueue && o.status != 0) resc = true;  // finished by the rescue kernel
+        else tl.finish(cnt, o);
+      }
+    }
+    if (MIXED && rqueue) enqueue(rqueue, rcount, resc, z);
+    int n = 0;
+    const int rank = block_rank<BS>(go, wsum, n);
+    if (n == 0) break;
+    if (round + 1 >= ks) {
+      // unconverged after ks updates: on to the queue kernel
+      if (go) {
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+          P[a * N + z] = Pz[a];
+          if (rq) rq[a * N + z] = rz[a];
+        }
+        iters[z] = (uint8_t)k;
+      }
+      enqueue(queue, qcount, go, z);
+      break;
+    }
+    if (n > BS - 32) {
+      // packing would free no warp: every zone stays with its thread
+      own = go;
+      continue;
+    }
+    if (go) stg.put<BS>(rank, Pz, rz, sl, k);
+    __syncthreads();
+    own = t < n;
+    if (own) stg.get<BS>(t, Pz, rz, sl, k);
+    __syncthreads();
+  }
+  tl.flush(cnt);
+}
+
 template <bool MIXED, int BS, bool IDEAL>
 __global__ void __launch_bounds__(BS) newton_queue_gr(const __grid_constant__ Params p, const double* __restrict__ K,
                                                       const double* __restrict__ gc, double* __restrict__ P,
@@ -1246,6 +1513,8 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernelsGr {
         [](int* grid) {
           cudaError_t e = cudaFuncSetAttribute(newton_dense_gr<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
           if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(newton_rounds_gr<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+          if (e == cudaSuccess)
             e = cudaFuncSetAttribute(newton_queue_gr<MIXED, BS, IDEAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
           int dev = 0, sms = 0, per_sm = 0;
           if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -1257,8 +1526,8 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernelsGr {
         &qgrid);
   }
   static cudaError_t launch(const Params& p, const double* K, const double* gc, double* P, uint8_t* iters,
-                            uint8_t* status, Counters* cnt, int kcut, int* queue, int* qcount, double* rq,
-                            const double* Pfb, double accept, const Rescue& rs, cudaStream_t st) {
+                            uint8_t* status, Counters* cnt, int kcut, bool rounds, int* queue, int* qcount,
+                            double* rq, const double* Pfb, double accept, const Rescue& rs, cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
@@ -1268,10 +1537,16 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernelsGr {
     if (rescue && (e = cudaMemsetAsync(rs.count, 0, sizeof(int), st)) != cudaSuccess) return e;
     int* rqueue = rescue ? rs.queue : nullptr;
     const long long nb = (p.N + BS - 1) / BS;
-    newton_dense_gr<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
-                                                                    compact ? kcut : p.kmax,
-                                                                    compact ? queue : nullptr, qcount, rq, Pfb, accept,
-                                                                    rqueue, rs.count);
+    if (rounds)
+      newton_rounds_gr<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
+                                                                       compact ? kcut : p.kmax,
+                                                                       compact ? queue : nullptr, qcount, rq, Pfb,
+                                                                       accept, rqueue, rs.count);
+    else
+      newton_dense_gr<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
+                                                                      compact ? kcut : p.kmax,
+                                                                      compact ? queue : nullptr, qcount, rq, Pfb,
+                                                                      accept, rqueue, rs.count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (compact) {
       newton_queue_gr<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
@@ -1293,15 +1568,15 @@ static cudaError_t launch_newton_gr_i(const Params& p, int mixed, const double* 
   const bool b32 = cfg.bs == 32;
   if (mixed) {
     if (b32)
-      return NewtonKernelsGr<true, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+      return NewtonKernelsGr<true, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
                                                       Pfb, accept, rs, st);
-    return NewtonKernelsGr<true, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+    return NewtonKernelsGr<true, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
                                                     Pfb, accept, rs, st);
   }
   if (b32)
-    return NewtonKernelsGr<false, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+    return NewtonKernelsGr<false, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
                                                      Pfb, accept, rs, st);
-  return NewtonKernelsGr<false, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, queue, qcount, rq,
+  return NewtonKernelsGr<false, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
                                                    Pfb, accept, rs, st);
 }
 

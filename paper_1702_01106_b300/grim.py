@@ -58,7 +58,7 @@ class GrimSolver(ctypes.Structure):
 
 class GrimTuning(ctypes.Structure):
     _fields_ = [("newton_bs", ctypes.c_int), ("newton_kcut", ctypes.c_int), ("faces_bs", ctypes.c_int),
-                ("zone_bs", ctypes.c_int)]
+                ("zone_bs", ctypes.c_int), ("newton_rounds", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -271,7 +271,7 @@ class Grim:
         return t.as_dict()
 
     def set_tuning(self, **kw):
-        """Change fields of the launch shape (newton_bs, newton_kcut, faces_bs, zone_bs)."""
+        """Change fields of the launch shape (newton_bs, newton_kcut, faces_bs, zone_bs, newton_rounds)."""
         t = GrimTuning(**{**self.tuning(), **kw})
         self._check(self.lib.grim_set_tuning(self.h, ctypes.byref(t)), "grim_set_tuning")
 
