@@ -36,10 +36,11 @@ MLP_TRAIN_STEPS = 24000   # Adam steps of the learned start (untimed, about 20 s
 MLP_SAMPLE_STRIDE = 6     # training stages from every 6th of the first 48 steps (the timed stretch)
 # DRAM bytes read + written per launch at 1024^2 (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of each kernel on this workload;
-# newton32 captured on the plain-start arm; None while a kernel has changed
-# since its capture).
-NCU_TRAFFIC_BYTES = {"faces": 296.6e6, "zone_const": None, "newton64": 428.1e6, "newton32": 424.4e6,
-                     "mlp": None}
+# newton32 captured on the learned arm, the metric's, its in-order kernel;
+# mlp the tcgen05 inference kernel; None while a kernel has changed since
+# its capture).
+NCU_TRAFFIC_BYTES = {"faces": 296.6e6, "zone_const": None, "newton64": 428.1e6, "newton32": 472.3e6,
+                     "mlp": 162.5e6}
 TOL = 1e-10
 KERR_OUTLIER_LIMIT = 10.0  # training rows of the torus kept within this many central-99.8% spans of each median
 
