@@ -26,7 +26,7 @@ cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* P
 long long pn_cache_doubles(long long N);
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, const Rescue& rs, cudaStream_t st);
+                             int* qcount, double* rq, const Rescue& rs, const float* rn, cudaStream_t st);
 cudaError_t launch_mlp_features(const Params& p, const double* K, const double* Pn, const double* Pc, float* X,
                                 float* Y, cudaStream_t st);
 cudaError_t launch_mlp_guess(const Params& p, const float* feat, const double* Pn, const grim_mlp* m, double* P0,
@@ -49,7 +49,7 @@ cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
                              int* qcount, double* rq, const double* Pfb, double accept, const Rescue& rs,
-                             cudaStream_t st);
+                             const float* rn, cudaStream_t st);
 cudaError_t launch_residual_gr(const Params& p, const double* K, const double* gc, const double* Pk, int scaled,
                                double dts, double* R, cudaStream_t st);
 }  // namespace grim
@@ -331,7 +331,8 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
                    (cfg.kcut < ctx->p.kmax ? 2 : 1) + (rescue(ctx, Pn, PE, Pout).queue ? 1 : 0));
       GRIM_CUDA(grim::launch_newton_gr(ctx->p, ctx->precision, ctx->K, ctx->geo, Pout, iters ? iters : ctx->iters,
                                        status ? status : ctx->status, ctx->cnt, cfg, ctx->queue, ctx->qcount,
-                                       ctx->faces, learned ? Pn : nullptr, ctx->accept, rescue(ctx, Pn, PE, Pout), ctx->cur),
+                                       ctx->faces, learned ? Pn : nullptr, ctx->accept, rescue(ctx, Pn, PE, Pout),
+                                       learned ? ctx->feat : nullptr, ctx->cur),
                 "newton kernel");
     }
     if (ctx->p.floors) {
@@ -347,7 +348,8 @@ static int run_stage(grim_ctx* ctx, const double* Pn, const double* PE, double d
                  (cfg.kcut < ctx->p.kmax ? 2 : 1) + (rescue(ctx, Pn, PE, Pout).queue ? 1 : 0));
     GRIM_CUDA(grim::launch_newton_fb(ctx->p, ctx->precision, ctx->K, Pout, iters ? iters : ctx->iters,
                                      status ? status : ctx->status, ctx->cnt, learned ? Pn : nullptr, ctx->accept,
-                                     cfg, ctx->queue, ctx->qcount, ctx->faces, rescue(ctx, Pn, PE, Pout), ctx->cur),
+                                     cfg, ctx->queue, ctx->qcount, ctx->faces, rescue(ctx, Pn, PE, Pout),
+                                     learned ? ctx->feat : nullptr, ctx->cur),
               "newton kernel");
   }
   return GRIM_OK;

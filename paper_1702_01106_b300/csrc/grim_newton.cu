@@ -270,6 +270,26 @@ __device__ __forceinline__ double sum_sq10(const double* r) {
   return f;
 }
 
+// The learned start's fallback test without a float64 evaluation of the
+// plain start: rn (stride `stride`, may be NULL) holds the increment
+// features -r_a(P_n), the plain start's scaled residual in float (its
+// magnetic rows are those of P_n's field, which the plain start replaces
+// by the flux-CT update, so they are left out).  The learned start is kept
+// when its |r|^2 does not exceed theirs; otherwise the plain start is
+// evaluated and the two compared as before (it is needed in float64 then
+// anyway, as the solve's first residual).
+__device__ __forceinline__ bool learned_wins(double f, const float* rn, long long stride) {
+  if (!rn) return false;
+  double fp = 0.0;
+#pragma unroll
+  for (int a = 0; a < NV; a++)
+    if (a < 5 || a > 7) {
+      const double x = (double)__ldg(rn + a * stride);
+      fp = fma(x, x, fp);
+    }
+  return f <= fp;
+}
+
 struct ZoneResult {
   int iters, status, evals64, evals32, lu64, lu32;
   int done;       // Newton updates made by this call (iters counts from the zone's first)
@@ -292,7 +312,7 @@ template <bool MIXED, int BS, bool IDEAL>
 __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double* kd, const float* kf, double P[NV],
                                                   void* jac, const double* Pfb, long long fb_stride,
                                                   unsigned long long accept_bits, bool& fellback, int k0,
-                                                  int kstop, double* rq, long long rs) {
+                                                  int kstop, double* rq, long long rs, const float* rn = nullptr) {
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
   const RC<double> c64 = make_rc<double>(p);
   const KSm<double, BS> k64{kd};
@@ -310,7 +330,7 @@ __device__ __forceinline__ ZoneResult newton_zone(const Params& p, const double*
   }
   double f = sum_sq10(r);
   fellback = false;
-  if (Pfb && !(max_abits10(r) <= accept_bits)) {
+  if (Pfb && !(max_abits10(r) <= accept_bits) && !learned_wins(f, rn, fb_stride)) {
     double Pp[NV], rp[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pp[a] = (a >= 5 && a <= 7) ? P[a] : Pfb[a * fb_stride];
@@ -564,13 +584,14 @@ template <bool MIXED, int BS> struct NewtonSmem {
 // kstop updates, after which it is appended to the queue (kstop >= k_max:
 // no queue).
 template <bool MIXED, int BS, bool IDEAL>
-__global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Params p, const double* __restrict__ K,
+__global__ void __launch_bounds__(BS, 1) newton_dense(const __grid_constant__ Params p, const double* __restrict__ K,
                                                    double* __restrict__ P, uint8_t* __restrict__ iters,
                                                    uint8_t* __restrict__ status, Counters* __restrict__ cnt,
                                                    const double* __restrict__ Pfb, double accept, int kstop,
                                                    int* __restrict__ queue, int* __restrict__ qcount,
                                                    double* __restrict__ rq, int* __restrict__ rqueue,
-                                                   int* __restrict__ rcount) {
+                                                   int* __restrict__ rcount,
+                                                   const float* __restrict__ rn) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -592,7 +613,8 @@ __global__ void __launch_bounds__(BS) newton_dense(const __grid_constant__ Param
 #pragma unroll
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
     o = newton_zone<MIXED, BS, IDEAL>(p, kd, kf, Pz, jac, Pfb ? Pfb + z : nullptr, N, abits(accept), fellback, 0,
-                               kstop < p.kmax ? kstop : p.kmax, queue && rq ? rq + z : nullptr, N);
+                               kstop < p.kmax ? kstop : p.kmax, queue && rq ? rq + z : nullptr, N,
+                               Pfb && rn ? rn + z : nullptr);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
     iters[z] = (uint8_t)(o.iters < 255 ? o.iters : 255);
@@ -616,7 +638,8 @@ __global__ void __launch_bounds__(BS) newton_rounds(const __grid_constant__ Para
                                                     const double* __restrict__ Pfb, double accept, int kstop,
                                                     int* __restrict__ queue, int* __restrict__ qcount,
                                                     double* __restrict__ rq, int* __restrict__ rqueue,
-                                                    int* __restrict__ rcount) {
+                                                    int* __restrict__ rcount,
+                                                    const float* __restrict__ rn) {
   using S = NewtonSmem<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int wsum[BS / 32];
@@ -650,7 +673,7 @@ __global__ void __launch_bounds__(BS) newton_rounds(const __grid_constant__ Para
       bool fb = false;
       const ZoneResult o = newton_zone<MIXED, BS, IDEAL>(p, kd + sl, kf + sl, Pz, jac,
                                                          round == 0 && Pfb ? Pfb + z : nullptr, N, acc, fb, k,
-                                                         k + 1, rz, 1);
+                                                         k + 1, rz, 1, round == 0 && Pfb && rn ? rn + z : nullptr);
       tl.work(o);
       tl.fb += fb;
       k = o.iters;
@@ -868,7 +891,7 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
   }
   static cudaError_t launch(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                             Counters* cnt, const double* Pfb, double accept, int kcut, bool rounds, int* queue,
-                            int* qcount, double* rq, const Rescue& rs, cudaStream_t st) {
+                            int* qcount, double* rq, const Rescue& rs, const float* rn, cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
@@ -882,12 +905,12 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
       newton_rounds<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
                                                                     compact ? kcut : p.kmax,
                                                                     compact ? queue : nullptr, qcount, rq, rqueue,
-                                                                    rs.count);
+                                                                    rs.count, rn);
     else
       newton_dense<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, Pfb, accept,
                                                                    compact ? kcut : p.kmax,
                                                                    compact ? queue : nullptr, qcount, rq, rqueue,
-                                                                   rs.count);
+                                                                   rs.count, rn);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (compact) {
       newton_queue<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, P, iters, status, cnt, queue,
@@ -902,17 +925,17 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
 template <bool MIXED, bool IDEAL>
 static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P, uint8_t* iters, uint8_t* status,
                                    Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                                   int* qcount, double* rq, const Rescue& rs, cudaStream_t st) {
+                                   int* qcount, double* rq, const Rescue& rs, const float* rn, cudaStream_t st) {
   switch (cfg.bs) {
     case 32:
       return NewtonKernels<MIXED, 32, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, cfg.rounds, queue,
-                                                     qcount, rq, rs, st);
+                                                     qcount, rq, rs, rn, st);
     case 64:
       return NewtonKernels<MIXED, 64, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, cfg.rounds, queue,
-                                                     qcount, rq, rs, st);
+                                                     qcount, rq, rs, rn, st);
     case 128:
       return NewtonKernels<MIXED, 128, IDEAL>::launch(p, K, P, iters, status, cnt, Pfb, accept, cfg.kcut, cfg.rounds, queue,
-                                                      qcount, rq, rs, st);
+                                                      qcount, rq, rs, rn, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -921,25 +944,28 @@ static cudaError_t launch_newton_bs(const Params& p, const double* K, double* P,
 // the queue kernel over the zones still unconverged after kcut updates.
 // rq: scratch of NV x N doubles for the residuals of the zones handed to the
 // queue kernel (may be NULL: the queue kernel then re-evaluates them).
-// rs: the mixed solver's rescue (Rescue{} for none).
+// rs: the mixed solver's rescue (Rescue{} for none).  rn: with a learned
+// start (Pfb), the increment features -r_a(P_n) ([NV][N] floats, may be
+// NULL), which let the fallback test skip a float64 evaluation of the plain
+// start (learned_wins).
 cudaError_t launch_newton_fb(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                              Counters* cnt, const double* Pfb, double accept, const NewtonCfg& cfg, int* queue,
-                             int* qcount, double* rq, const Rescue& rs, cudaStream_t st) {
+                             int* qcount, double* rq, const Rescue& rs, const float* rn, cudaStream_t st) {
   // ideal MHD: the kernels that may take the 5x5 block (ideal_zone)
   if (!p.cond && !p.visc) {
     if (mixed)
-      return launch_newton_bs<true, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
-    return launch_newton_bs<false, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
+      return launch_newton_bs<true, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, rn, st);
+    return launch_newton_bs<false, true>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, rn, st);
   }
   if (mixed)
-    return launch_newton_bs<true, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
-  return launch_newton_bs<false, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, st);
+    return launch_newton_bs<true, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, rn, st);
+  return launch_newton_bs<false, false>(p, K, P, iters, status, cnt, Pfb, accept, cfg, queue, qcount, rq, rs, rn, st);
 }
 
 cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P, uint8_t* iters, uint8_t* status,
                           Counters* cnt, cudaStream_t st) {
   const NewtonCfg cfg{64, 1 << 30, false};
-  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, nullptr, Rescue{},
+  return launch_newton_fb(p, mixed, K, P, iters, status, cnt, nullptr, 0.0, cfg, nullptr, nullptr, nullptr, Rescue{}, nullptr,
                           st);
 }
 
@@ -1057,7 +1083,7 @@ template <bool MIXED, int BS, bool IDEAL>
 __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const float* kf, const double* md,
                                      double P[NV], void* jac, int k0, int kstop, double* rq, long long rs,
                                      const double* Pfb, long long fb_stride, unsigned long long accept_bits,
-                                     bool& fellback) {
+                                     bool& fellback, const float* rn = nullptr) {
   ZoneResult o = {0, 0, 0, 0, 0, 0, 0, false, 0.0};
   const RC<double> c64 = make_rc<double>(p);
   const KSm<double, BS> k64{kd};
@@ -1077,7 +1103,7 @@ __device__ ZoneResult newton_zone_gr(const Params& p, const double* kd, const fl
   }
   double f = sum_sq10(r);
   fellback = false;
-  if (Pfb && !(max_abits10(r) <= accept_bits)) {
+  if (Pfb && !(max_abits10(r) <= accept_bits) && !learned_wins(f, rn, fb_stride)) {
     double Pp[NV], rp[NV];
 #pragma unroll
     for (int a = 0; a < NV; a++) Pp[a] = (a >= 5 && a <= 7) ? P[a] : Pfb[a * fb_stride];
@@ -1251,7 +1277,8 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
                                                       Counters* __restrict__ cnt, int kstop, int* __restrict__ queue,
                                                       int* __restrict__ qcount, double* __restrict__ rq,
                                                       const double* __restrict__ Pfb, double accept,
-                                                      int* __restrict__ rqueue, int* __restrict__ rcount) {
+                                                      int* __restrict__ rqueue, int* __restrict__ rcount,
+                                                      const float* __restrict__ rn) {
   using S = NewtonSmemGr<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* kd = (double*)smem_raw + threadIdx.x;
@@ -1270,7 +1297,7 @@ __global__ void __launch_bounds__(BS) newton_dense_gr(const __grid_constant__ Pa
     for (int a = 0; a < NV; a++) Pz[a] = P[a * N + z];
     o = newton_zone_gr<MIXED, BS, IDEAL>(p, kd, kf, md, Pz, jac, 0, kstop < p.kmax ? kstop : p.kmax,
                                   queue && rq ? rq + z : nullptr, N, Pfb ? Pfb + z : nullptr, N, abits(accept),
-                                  fellback);
+                                  fellback, Pfb && rn ? rn + z : nullptr);
     if (p.floors && !o.pending && o.status == 0) floors_converged(p, gc, z, o, Pz);
 #pragma unroll
     for (int a = 0; a < NV; a++) P[a * N + z] = Pz[a];
@@ -1292,7 +1319,8 @@ __global__ void __launch_bounds__(BS) newton_rounds_gr(const __grid_constant__ P
                                                        Counters* __restrict__ cnt, int kstop, int* __restrict__ queue,
                                                        int* __restrict__ qcount, double* __restrict__ rq,
                                                        const double* __restrict__ Pfb, double accept,
-                                                       int* __restrict__ rqueue, int* __restrict__ rcount) {
+                                                       int* __restrict__ rqueue, int* __restrict__ rcount,
+                                                       const float* __restrict__ rn) {
   using S = NewtonSmemGr<MIXED, BS>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int wsum[BS / 32];
@@ -1321,7 +1349,8 @@ __global__ void __launch_bounds__(BS) newton_rounds_gr(const __grid_constant__ P
     if (own) {
       bool fb = false;
       ZoneResult o = newton_zone_gr<MIXED, BS, IDEAL>(p, kd + sl, kf + sl, md + sl, Pz, jac, k, k + 1, rz, 1,
-                                                      round == 0 && Pfb ? Pfb + z : nullptr, N, acc, fb);
+                                                      round == 0 && Pfb ? Pfb + z : nullptr, N, acc, fb,
+                                                      round == 0 && Pfb && rn ? rn + z : nullptr);
       tl.work(o);
       tl.fb += fb;
       k = o.iters;
@@ -1527,7 +1556,8 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernelsGr {
   }
   static cudaError_t launch(const Params& p, const double* K, const double* gc, double* P, uint8_t* iters,
                             uint8_t* status, Counters* cnt, int kcut, bool rounds, int* queue, int* qcount,
-                            double* rq, const double* Pfb, double accept, const Rescue& rs, cudaStream_t st) {
+                            double* rq, const double* Pfb, double accept, const Rescue& rs, const float* rn,
+                            cudaStream_t st) {
     int qgrid = 0;
     cudaError_t e = configure(qgrid);
     if (e != cudaSuccess) return e;
@@ -1541,12 +1571,12 @@ template <bool MIXED, int BS, bool IDEAL> struct NewtonKernelsGr {
       newton_rounds_gr<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
                                                                        compact ? kcut : p.kmax,
                                                                        compact ? queue : nullptr, qcount, rq, Pfb,
-                                                                       accept, rqueue, rs.count);
+                                                                       accept, rqueue, rs.count, rn);
     else
       newton_dense_gr<MIXED, BS, IDEAL><<<(unsigned)nb, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
                                                                       compact ? kcut : p.kmax,
                                                                       compact ? queue : nullptr, qcount, rq, Pfb,
-                                                                      accept, rqueue, rs.count);
+                                                                      accept, rqueue, rs.count, rn);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (compact) {
       newton_queue_gr<MIXED, BS, IDEAL><<<(unsigned)qgrid, BS, S::bytes, st>>>(p, K, gc, P, iters, status, cnt,
@@ -1564,30 +1594,32 @@ template <bool IDEAL>
 static cudaError_t launch_newton_gr_i(const Params& p, int mixed, const double* K, const double* gc, double* P,
                                      uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg,
                                      int* queue, int* qcount, double* rq, const double* Pfb, double accept,
-                                     const Rescue& rs, cudaStream_t st) {
+                                     const Rescue& rs, const float* rn, cudaStream_t st) {
   const bool b32 = cfg.bs == 32;
   if (mixed) {
     if (b32)
       return NewtonKernelsGr<true, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
-                                                      Pfb, accept, rs, st);
+                                                      Pfb, accept, rs, rn, st);
     return NewtonKernelsGr<true, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
-                                                    Pfb, accept, rs, st);
+                                                    Pfb, accept, rs, rn, st);
   }
   if (b32)
     return NewtonKernelsGr<false, 32, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
-                                                     Pfb, accept, rs, st);
+                                                     Pfb, accept, rs, rn, st);
   return NewtonKernelsGr<false, 64, IDEAL>::launch(p, K, gc, P, iters, status, cnt, cfg.kcut, cfg.rounds, queue, qcount, rq,
-                                                   Pfb, accept, rs, st);
+                                                   Pfb, accept, rs, rn, st);
 }
 
 cudaError_t launch_newton_gr(const Params& p, int mixed, const double* K, const double* gc, double* P,
                              uint8_t* iters, uint8_t* status, Counters* cnt, const NewtonCfg& cfg, int* queue,
                              int* qcount, double* rq, const double* Pfb, double accept, const Rescue& rs,
-                             cudaStream_t st) {
+                             const float* rn, cudaStream_t st) {
   // ideal MHD: the kernels that may take the 5x5 block (ideal_zone)
   if (!p.cond && !p.visc)
-    return launch_newton_gr_i<true>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, rs, st);
-  return launch_newton_gr_i<false>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, rs, st);
+    return launch_newton_gr_i<true>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, rs, rn,
+                                    st);
+  return launch_newton_gr_i<false>(p, mixed, K, gc, P, iters, status, cnt, cfg, queue, qcount, rq, Pfb, accept, rs, rn,
+                                   st);
 }
 
 // Learned-start features in a general metric, in the flat path's layout:
