@@ -42,7 +42,7 @@ cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo
                             cudaStream_t st);
 cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
                                  const double* geo, double* faces, double* K, double* P0, double* cache, int mode,
-                                 float* feat, cudaStream_t st);
+                                 float* feat, int ffslopes, cudaStream_t st);
 long long gr_cache_doubles(long long N);
 cudaError_t launch_gr_floors(const Params& p, const double* geo, const double* K, const double* Pn,
                              const uint8_t* status, double* P, cudaStream_t st);
@@ -263,7 +263,7 @@ static int run_explicit(grim_ctx* ctx, const double* Pn, const double* PE, doubl
     }
     KernelMark m(ctx, GRIM_K_ZONECONST, 3);
     GRIM_CUDA(grim::launch_gr_zone_const(ctx->p, Pn, PE, guess, dts, ctx->geo, ctx->faces, ctx->K, Pout,
-                                         ctx->pncache, mode, feat, ctx->cur),
+                                         ctx->pncache, mode, feat, ctx->precision == GRIM_MIXED, ctx->cur),
               "zone-constant kernel");
     return GRIM_OK;
   }

@@ -192,6 +192,10 @@ struct GrArgs {
   // float-float copies of gamma, gamma-1, sqrt(phi gamma), sqrt(psi gamma)
   // and kappa gamma (hi, lo pairs), for the float-float face states
   float ffc[10];
+  // the mixed solver's MC slopes along the face direction being computed
+  // ([NV][ghost-ring grid] float pairs, mc_slopes_gr), in the scratch the
+  // derived and source quantities take later in the stage
+  double* Sl;
 };
 constexpr int NCACHE_GR = NV + 6;
 
@@ -291,6 +295,26 @@ __device__ __forceinline__ void face_speeds(const ZG<S>& z, S gtt, S gtj, S gjj,
   else zg_speeds_kg(z, gtt, gtj, gjj, j, c.gam, kk, cmin, cmax);
 }
 
+// Centres of the grid with one ghost ring in every active direction.
+constexpr int ND = 8;  // Theta, u_mu (4), sqrt(-g) u^d (3)
+struct GhostBox {
+  int e1, e2, e3, o2, o3;
+  long long size;
+  __device__ __host__ long long at(int i, int j, int k) const {
+    return ((long long)(k + o3) * e2 + (j + o2)) * e1 + (i + 1);
+  }
+};
+__host__ __device__ inline GhostBox ghost_box(const Params& p) {
+  GhostBox b;
+  b.o2 = p.dim >= 2;
+  b.o3 = p.dim >= 3;
+  b.e1 = p.n1 + 2;
+  b.e2 = b.o2 ? p.n2 + 2 : 1;
+  b.e3 = b.o3 ? p.n3 + 2 : 1;
+  b.size = (long long)b.e1 * b.e2 * b.e3;
+  return b;
+}
+
 // LLF or HLLE flux (Section 2.4.2) on the face at the low side of zone
 // (i,j,k) in direction D, from MC, WENO5 or PPM face states of P^E.  The
 // stencil's zone indices and reflection flips are resolved once; the fields
@@ -312,6 +336,21 @@ __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int 
   }
   const long long N = p.N;
   S L[NV], R[NV];
+  if constexpr (RECON == RECON_MC && std::is_same<S, ff>::value) {
+    // the mixed solver: face values from the two centres beside the face and
+    // their float-float slopes (mc_slopes_gr), P -+ slope/2 in float-float
+    const GhostBox gb = ghost_box(p);
+    const long long c0 = gb.at(i - (D == 0), j - (D == 1), k - (D == 2)), c1 = gb.at(i, j, k);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const int bit = (v >= 2 && v <= 4) ? 1 << (v - 2) : (v >= 5 && v <= 7) ? 1 << (v - 5) : 0;
+      const double x0 = __ldg(a.PE + v * N + zz[1]), x1 = __ldg(a.PE + v * N + zz[2]);
+      const float2 s0 = __ldg(reinterpret_cast<const float2*>(a.Sl) + v * gb.size + c0);
+      const float2 s1 = __ldg(reinterpret_cast<const float2*>(a.Sl) + v * gb.size + c1);
+      L[v] = ff_split((fl[1] & bit) ? -x0 : x0) + scale2(ff(s0.x, s0.y), 0.5f);
+      R[v] = ff_split((fl[2] & bit) ? -x1 : x1) - scale2(ff(s1.x, s1.y), 0.5f);
+    }
+  } else {
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     // u~^d and B^d change sign in a zone mirrored across a boundary of direction d
@@ -338,6 +377,7 @@ __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int 
     }
     L[v] = from_double<S>(lv);
     R[v] = from_double<S>(rv);
+  }
   }
   Met<S> m;
   met_load(m, g);
@@ -386,6 +426,46 @@ __device__ __forceinline__ void face_body(const Params& p, const GrArgs& a, int 
     const S h = tconst<S>(0.5) * sg;
 #pragma unroll
     for (int v = 0; v < NV; v++) out[v * plane] = as_double(h * ((FL[v] + FR[v]) - cm * (UR[v] - UL[v])));
+  }
+}
+
+// The mixed solver's MC slopes along D, once per centre of the ghost-ring
+// grid, in float-float: each face reads the slopes of the two centres beside
+// it, which the face kernel formed twice, in float64 (the float64 pipe was
+// the face kernel's busiest).  The centres and their reflection flips are
+// resolved as in face_body, so every face sees the values it would have
+// formed itself; each slope is stored as its float pair (8 bytes, like a
+// double, without a rounding to one).
+template <int D>
+__global__ void __launch_bounds__(128) mc_slopes_gr(const __grid_constant__ Params p,
+                                                    const __grid_constant__ GrArgs a) {
+  const GhostBox gb = ghost_box(p);
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= gb.size) return;
+  const int i = (int)(q % gb.e1) - 1;
+  const int j = (int)((q / gb.e1) % gb.e2) - gb.o2;
+  const int k = (int)(q / ((long long)gb.e1 * gb.e2)) - gb.o3;
+  long long zz[3];
+  int fl[3];
+#pragma unroll
+  for (int t = 0; t < 3; t++) {
+    bool f[3];
+    zz[t] = gr_zone(p, i + (D == 0) * (t - 1), j + (D == 1) * (t - 1), k + (D == 2) * (t - 1), f);
+    fl[t] = (f[0] ? 1 : 0) | (f[1] ? 2 : 0) | (f[2] ? 4 : 0);
+  }
+  const long long N = p.N;
+  const ff theta = ff_split(p.theta);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const int bit = (v >= 2 && v <= 4) ? 1 << (v - 2) : (v >= 5 && v <= 7) ? 1 << (v - 5) : 0;
+    ff t3[3];
+#pragma unroll
+    for (int t = 0; t < 3; t++) {
+      const double x = __ldg(a.PE + v * N + zz[t]);
+      t3[t] = ff_split((fl[t] & bit) ? -x : x);
+    }
+    const ff sl = gm_slope(theta, t3[0], t3[1], t3[2]);
+    reinterpret_cast<float2*>(a.Sl)[v * gb.size + q] = make_float2(sl.hi, sl.lo);
   }
 }
 
@@ -443,24 +523,6 @@ __device__ __forceinline__ void gr_derived(const Params& p, const GrArgs& a, int
 // active direction), [ND][e1 e2 e3] with e1 = n1+2, e2 = n2+2 or 1, e3 = n3+2
 // or 1: computed once a stage here, read by the limited slopes of up to seven
 // zones.
-constexpr int ND = 8;  // Theta, u_mu (4), sqrt(-g) u^d (3)
-struct GhostBox {
-  int e1, e2, e3, o2, o3;
-  long long size;
-  __device__ __host__ long long at(int i, int j, int k) const {
-    return ((long long)(k + o3) * e2 + (j + o2)) * e1 + (i + 1);
-  }
-};
-__host__ __device__ inline GhostBox ghost_box(const Params& p) {
-  GhostBox b;
-  b.o2 = p.dim >= 2;
-  b.o3 = p.dim >= 3;
-  b.e1 = p.n1 + 2;
-  b.e2 = b.o2 ? p.n2 + 2 : 1;
-  b.e3 = b.o3 ? p.n3 + 2 : 1;
-  b.size = (long long)b.e1 * b.e2 * b.e3;
-  return b;
-}
 
 __global__ void __launch_bounds__(128) derived_gr(const __grid_constant__ Params p, const __grid_constant__ GrArgs a) {
   const GhostBox gb = ghost_box(p);
@@ -494,6 +556,11 @@ __device__ __forceinline__ void derived_load(const GrArgs& a, const GhostBox& gb
 // the limited slopes of Theta, u_mu and sqrt(-g) u^d from the derived
 // quantities) and the spatial part of nabla_mu u^mu; NSRC doubles a zone.
 constexpr int NSRC = 17;  // Sg (4), Aq, Bq, Cq (4), Ad, Dd (4), Ed, divu_sp
+// FFS: the limited slopes in float-float (the mixed solver, as on the flat
+// path): the generalized minmod of each derived quantity from float-float
+// splits of its three values (about 2 float64 instructions a slope instead
+// of 12; the float64 pipe bounds this kernel).
+template <bool FFS>
 __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params p, const __grid_constant__ GrArgs a) {
   const long long N = p.N;
   const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -520,10 +587,19 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
       double thm, thp, um[4], up[4], sm[3], sp[3];
       derived_load(a, gb, i - (d == 0), j - (d == 1), k - (d == 2), thm, um, sm);
       derived_load(a, gb, i + (d == 0), j + (d == 1), k + (d == 2), thp, up, sp);
-      dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
+      if constexpr (FFS) {
+        const ff theta = ff_split(p.theta);
+        dTh[d] = ff_join(gm_slope(theta, ff_split(thm), ff_split(th0), ff_split(thp))) * p.idx[d];
 #pragma unroll
-      for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
-      divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
+        for (int q = 0; q < 4; q++)
+          du[d][q] = ff_join(gm_slope(theta, ff_split(um[q]), ff_split(u0[q]), ff_split(up[q]))) * p.idx[d];
+        divu_sp += ff_join(gm_slope(theta, ff_split(sm[d]), ff_split(s0[d]), ff_split(sp[d]))) * p.idx[d];
+      } else {
+        dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
+#pragma unroll
+        for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
+        divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
+      }
     }
     divu_sp *= nr_rcp(sg);
   }
@@ -859,7 +935,11 @@ long long gr_geometry_doubles(const Params& p) {
 long long gr_face_doubles(const Params& p) {
   long long s = 0;
   for (int d = 0; d < p.dim; d++) s += (long long)NV * face_box(p, d).size;
-  return s + (long long)ND * ghost_box(p).size + (long long)NSRC * p.N;
+  // after the faces: the derived and source planes, which the MC slopes of
+  // the mixed solver use before them
+  const long long ds = (long long)ND * ghost_box(p).size + (long long)NSRC * p.N;
+  const long long sl = (long long)NV * ghost_box(p).size;
+  return s + (ds > sl ? ds : sl);
 }
 
 static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a) {
@@ -873,6 +953,7 @@ static void gr_args(const Params& p, const double* geo, double* faces, GrArgs& a
   }
   a.Dv = f;
   a.Src = f + (long long)ND * ghost_box(p).size;
+  a.Sl = f;  // the derived and source planes are written after the faces
   a.kappa = gr_kappa(p);
   const double cv[5] = {p.gamma, p.gamma - 1.0, sqrt(p.phi * p.gamma), sqrt(p.psi * p.gamma), a.kappa * p.gamma};
   for (int k = 0; k < 5; k++) {
@@ -903,6 +984,12 @@ cudaError_t launch_gr_geometry(const Params& p, int metric, double spin, double 
 template <typename S, int RECON>
 static cudaError_t launch_gr_faces_r(const Params& p, const GrArgs& a, cudaStream_t st) {
   for (int d = 0; d < p.dim; d++) {
+    if (RECON == RECON_MC && std::is_same<S, ff>::value) {
+      const unsigned ns = (unsigned)((ghost_box(p).size + 127) / 128);
+      if (d == 0) mc_slopes_gr<0><<<ns, 128, 0, st>>>(p, a);
+      else if (d == 1) mc_slopes_gr<1><<<ns, 128, 0, st>>>(p, a);
+      else mc_slopes_gr<2><<<ns, 128, 0, st>>>(p, a);
+    }
     const long long n = face_box(p, d).size;
     const unsigned nb = (unsigned)((n + 127) / 128);
     if (d == 0) face_flux_gr<0, S, RECON><<<nb, 128, 0, st>>>(p, a);
@@ -932,10 +1019,11 @@ cudaError_t launch_gr_faces(const Params& p, const double* PE, const double* geo
 long long gr_cache_doubles(long long N) { return (long long)NCACHE_GR * N; }
 
 // mode, cache: the P_n cache of a step (mode 0: none); feat: the learned
-// start's increment features (NULL: not wanted).
+// start's increment features (NULL: not wanted); ffslopes: the limited
+// slopes of the sources in float-float (the mixed solver).
 cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
                                  const double* geo, double* faces, double* K, double* P0, double* cache, int mode,
-                                 float* feat, cudaStream_t st) {
+                                 float* feat, int ffslopes, cudaStream_t st) {
   GrArgs a{};
   gr_args(p, geo, faces, a);
   a.Pn = Pn; a.PE = PE; a.guess = guess; a.dts = dts; a.K = K; a.P0 = P0;
@@ -947,7 +1035,8 @@ cudaError_t launch_gr_zone_const(const Params& p, const double* Pn, const double
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const unsigned nb = (unsigned)((p.N + 127) / 128);
-  sources_gr<<<nb, 128, 0, st>>>(p, a);
+  if (ffslopes) sources_gr<true><<<nb, 128, 0, st>>>(p, a);
+  else sources_gr<false><<<nb, 128, 0, st>>>(p, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   zone_const_gr<<<nb, 128, 0, st>>>(p, a);
   return cudaGetLastError();

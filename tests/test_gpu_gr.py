@@ -40,9 +40,13 @@ def _torus(n1, n2, n3, tol=1e-14):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_gr_residual_parity_kerr(dev, orc, precision):
-    """The stage residual on the torus against the oracle's; the mixed
-    solver's float-float face states and fluxes (about 48 significant bits)
-    meet the same bound as float64."""
+    """The stage residual on the torus against the oracle's, per row relative
+    to |r| + 1.  Float64 within 1e-11.  The mixed solver forms its face
+    states (the MC values from float-float slopes) and fluxes in float-float,
+    about 48 significant bits: at the torus surface, where the flux
+    divergence is ~1e3 times what a zone holds, a rounding of 2^-47 of the
+    face values is ~1e3 x 2^-47 ~ 1e-11 of the scaled residual, so its bound
+    is 2e-11."""
     from paper_1702_01106_b300.grim import Grim
     prob, Pn = _torus(20, 16, 1)
     rng = np.random.default_rng(5)
@@ -54,7 +58,8 @@ def test_gr_residual_parity_kerr(dev, orc, precision):
     g.residual(_t(Pn, dev), _t(PE, dev), dts, _t(Pk, dev), R)
     ref = orc.residual(prob, Pn, PE, dts, Pk)
     # torus-surface zones carry scaled residuals up to ~1e3 at P_n
-    assert (np.abs(R.cpu().numpy() - ref) / (np.abs(ref) + 1.0)).max() < 1e-11
+    bound = 1e-11 if precision == 0 else 2e-11
+    assert (np.abs(R.cpu().numpy() - ref) / (np.abs(ref) + 1.0)).max() < bound
     g.close()
 
 
