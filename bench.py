@@ -656,13 +656,19 @@ def main():
                        "l2": "no flush: per-step working set ~0.6 GB (states, stage constants) > 126 MB L2"},
             "fp64_plain": {"value": fp64_value, "ms_per_step": ms_d, "dtype": "f64",
                            "newton_iters_per_zone_stage": st_d["iters"] / max(1, st_d["zones"]),
+                           "fp64_residuals_per_zone_stage": st_d["evals64"] / max(1, st_d["zones"]),
+                           "fp32_residuals_per_zone_stage": st_d["evals32"] / max(1, st_d["zones"]),
                            "newton_iters_p99": iters_p99(st_d["hist"]),
                            "failed": st_d["failed"], "max_res": st_d["max_res"]},
             "mixed_plain_start": {"value": mixed_plain_value, "ms_per_step": ms_mp,
                                   "newton_iters_per_zone_stage": st_mp["iters"] / max(1, st_mp["zones"]),
+                                  "fp64_residuals_per_zone_stage": st_mp["evals64"] / max(1, st_mp["zones"]),
+                                  "fp32_residuals_per_zone_stage": st_mp["evals32"] / max(1, st_mp["zones"]),
                                   "newton_iters_p99": iters_p99(st_mp["hist"]),
                                   "failed": st_mp["failed"], "max_res": st_mp["max_res"]},
             "mixed_learned": {"newton_iters_per_zone_stage": st_m["iters"] / max(1, st_m["zones"]),
+                              "fp64_residuals_per_zone_stage": st_m["evals64"] / max(1, st_m["zones"]),
+                              "fp32_residuals_per_zone_stage": st_m["evals32"] / max(1, st_m["zones"]),
                               "newton_iters_p99": iters_p99(st_m["hist"]),
                               "failed": st_m["failed"], "max_res": st_m["max_res"],
                               "fallback_rate": st_m["fallbacks"] / max(1, st_m["zones"]),
