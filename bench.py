@@ -55,6 +55,34 @@ def read_flop_counts():
     return out
 
 
+# bf16 multiply-add flops of one Adam step per training row: the forward
+# contractions (2 x 47 104), the weight gradients (the same) and the input
+# gradients of the three upper layers (2 x 43 008).
+MLP_STEP_FLOPS_PER_ROW = 2 * (2 * 47104 + 43008)
+
+
+def training_rate(X, Y, peaks, steps=400, batch=4096):
+    """Adam steps of a fresh network on the training rows, timed with CUDA
+    events on the stream they run on (the default stream): ms per step and
+    the bf16 rate of their contractions against the measured burst peak."""
+    import torch
+    from paper_1702_01106_b300.grim import MLP
+    m = MLP(seed=5)
+    m.fit_norm(X, Y)
+    m.train(X, Y, steps=20, batch=batch, lr=1e-3, seed=3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    m.train(X, Y, steps=steps, batch=batch, lr=1e-3, seed=4)
+    e1.record()
+    torch.cuda.synchronize()
+    m.close()
+    ms = e0.elapsed_time(e1) / steps
+    tf = MLP_STEP_FLOPS_PER_ROW * batch / (ms * 1e-3) / 1e12
+    return {"ms_per_step": ms, "batch": batch, "launches_per_step": 29, "bf16_tflops": tf,
+            "bf16_frac_of_burst": tf / peaks.get("bf16_tflops", 1800.0)}
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -509,6 +537,7 @@ def main():
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     n_samples = int(Xtr.shape[0])
+    train_rate = training_rate(Xtr, Ytr, peaks)
     del Xtr, Ytr
     torch.cuda.empty_cache()
 
@@ -674,7 +703,8 @@ def main():
                               "fallback_rate": st_m["fallbacks"] / max(1, st_m["zones"]),
                               "one_step_max_rel_diff_vs_fp64": learned_err,
                               "training": {"samples": n_samples, "adam_steps": MLP_TRAIN_STEPS, "batch": 4096,
-                                           "loss_per_quarter": losses, "seconds": train_s}},
+                                           "loss_per_quarter": losses, "seconds_with_sampling": train_s,
+                                           "step": train_rate}},
             "tuning": tunings,
             "speedup_mixed_learned_vs_fp64": ms_d / ms_m,
             "speedup_mixed_plain_vs_fp64": ms_d / ms_mp,

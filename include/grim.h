@@ -387,6 +387,19 @@ int grim_mlp_train(grim_mlp* mlp, const float* X, const float* Y, long long M, i
 /* Gradient of the loss over all M rows (M a multiple of 64, one batch) with
  * respect to the parameters, to host float32 [param_count]; *loss its value. */
 int grim_mlp_gradient(grim_mlp* mlp, const float* X, const float* Y, long long M, float* grad, double* loss);
+/* The training contraction on its own: C[M][N] = A[M][K] B[N][K]^T with A
+ * and B bfloat16 device matrices, row-major with K contiguous (row strides
+ * lda, ldb elements), accumulated in float32 by the tensor cores (tcgen05,
+ * operands copied by TMA) into the float32 device matrix C (row stride
+ * ldc).  splits: the number of slices of K summed in a fixed order after the
+ * tensor-core pass (1..16; 0 = 1).  Requirements: M, K >= 1; N >= 16 and a
+ * multiple of 16; lda, ldb multiples of 8 and >= K; ldc a multiple of 4 and
+ * >= N; A, B, C 16-byte aligned (else GRIM_EINVAL).  Synchronous: allocates
+ * and frees a small device workspace (GRIM_ENOMEM); GRIM_ECUDA when a
+ * launch failed or a CTA gave up waiting for its copies or MMAs (C is then
+ * incomplete). */
+int grim_gemm_nt_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+                      int splits);
 /* Features (and, when P_conv and Y are non-NULL, targets) of every zone of
  * the stage whose explicit kernels ran last on ctx (grim_stage,
  * grim_residual or the full step of grim_step), with start-of-step state P_n

@@ -34,6 +34,8 @@
 #include <cstring>
 #include <cmath>
 #include <vector>
+#include <algorithm>
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "grim_tc.cuh"
@@ -80,6 +82,8 @@ struct grim_mlp {
   float* dA = nullptr;                                   // input-side gradient [B][128]
   float* grad = nullptr;                                 // parameter gradients [MLP_NPARAM]
   float* loss = nullptr;                                 // [1]
+  float* ws = nullptr;                                   // split-K partial tiles of the training GEMM
+  unsigned long long* stalls = nullptr;                  // training GEMM CTAs that gave up waiting
 };
 
 namespace grim {
@@ -102,97 +106,233 @@ __device__ __forceinline__ float silu_grad(float x) {
   return s * (1.0f + x * (1.0f - s));
 }
 
-// ---------------------------------------------------------------- tensor-core GEMM
-// C[M][N] (float32, ldc) = A[M][K] * B[N][K]^T, A and B bfloat16 row-major
-// with K contiguous (lda, ldb elements); M, N and K multiples of 16 (rows,
-// columns and k-chunks past the ends are read as zeros).
-// 64x64 output tile per CTA of 4 warps (2x2), each warp 32x32 = 2x4 mma
-// tiles of m16n8k16; operands staged through padded shared memory.
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+// ---------------------------------------------------------------- tensor-core GEMM (training)
+// C[M][N] (float32, ldc) = A[M][K] B[N][K]^T, A and B bfloat16 row-major
+// with K contiguous (lda, ldb elements).  One CTA of 128 threads per tile
+// of 128 rows x bn columns (bn <= 128, a multiple of 16): thread 0 has TMA
+// copy K-chunks of 64 columns of both operands into a four-stage ring in
+// shared memory and issues the tcgen05 MMAs (K = 16 each) that accumulate
+// the tile in float32 in 128 TMEM columns; then each warp reads its 32 TMEM
+// lanes (rows) back and stores them.  Rows, columns and K past the ends
+// arrive as zeros (the tensor maps' out-of-bounds fill).  A split along K
+// (blockIdx.z) stores its partial tile into its own slice of a workspace,
+// and gemm_splitk_sum adds the slices in a fixed order, so that results do
+// not depend on timing.
+//
+// An operand tile of R rows x 64 columns in shared memory: the eight groups
+// of 8 columns one after another, each R rows x 16 bytes (what one TMA box
+// of 8 x R elements writes), so element (r, k) lies at byte
+//   (k / 8) * R * 16 + r * 16 + (k % 8) * 2,
+// the no-swizzle K-major layout with LBO = R * 16 (core matrices adjacent
+// along K) and SBO = 128 (8-row groups).
+constexpr int GT_BM = 128, GT_BK = 64, GT_STAGES = 4, GT_THREADS = 128, GT_COLS = 128;
+constexpr int GT_A_BYTES = GT_BM * GT_BK * 2;   // 16 KB; B takes at most as much
+constexpr int GT_STAGE_BYTES = 2 * GT_A_BYTES;
+constexpr int GT_SMEM = GT_STAGES * GT_STAGE_BYTES + 1024 + 128;  // ring, alignment slack, barriers
+constexpr uint32_t GT_WAIT_LIMIT = 1u << 22;  // mbarrier polls before the kernel gives up
+constexpr int GT_MAX_SPLITS = 16;
+constexpr long long GT_WS_FLOATS = (long long)GT_MAX_SPLITS * 128 * 128;
 
-__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__global__ void __launch_bounds__(128) gemm_nt_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
-                                                    int lda, const __nv_bfloat16* __restrict__ B, int ldb,
-                                                    float* __restrict__ C, int ldc, int accumulate) {
-  __shared__ __align__(16) __nv_bfloat16 sA[GBM][GBK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 sB[GBN][GBK + GPAD];
+__global__ void __launch_bounds__(GT_THREADS, 1)
+    gemm_nt_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int K,
+                 int bn, int chunks_per_split, float* __restrict__ C, int ldc, long long split_stride,
+                 unsigned long long* __restrict__ stalls) {
+  extern __shared__ unsigned char gsm_raw[];
+  // the TMA destinations want 128-byte alignment: round the base up to 1 KB
+  unsigned char* gsm = gsm_raw + ((1024u - (tc::smem_addr(gsm_raw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(gsm + GT_STAGES * GT_STAGE_BYTES);
+  uint64_t* empty = full + GT_STAGES;
+  uint64_t* done = empty + GT_STAGES;
+  uint32_t* taddr = reinterpret_cast<uint32_t*>(done + 1);
+  int* abort = reinterpret_cast<int*>(taddr + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-#pragma unroll
-      for (int r = 0; r < 4; r++) acc[i][j][r] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GBK) {
-    // stage: 64 rows x 32 bf16 = 64 x 4 chunks of 16 bytes for each operand
-    for (int c = tid; c < GBM * 4; c += 128) {
-      const int r = c >> 2, q = (c & 3) * 8;
-      uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-      const bool kin = k0 + q + 8 <= K;
-      if (kin && m0 + r < M) va = *reinterpret_cast<const uint4*>(A + (long long)(m0 + r) * lda + k0 + q);
-      if (kin && n0 + r < N) vb = *reinterpret_cast<const uint4*>(B + (long long)(n0 + r) * ldb + k0 + q);
-      *reinterpret_cast<uint4*>(&sA[r][q]) = va;
-      *reinterpret_cast<uint4*>(&sB[r][q]) = vb;
+  const int m0 = blockIdx.y * GT_BM, n0 = blockIdx.x * bn;
+  const int nchunks = (K + GT_BK - 1) / GT_BK;
+  const int c0 = blockIdx.z * chunks_per_split;
+  const int nc = min(c0 + chunks_per_split, nchunks) - c0;  // >= 1 by the launcher's choice of splits
+  if (tid == 0) {
+    for (int s = 0; s < GT_STAGES; s++) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
     }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      unsigned af[2][4], bf[4][2];
-      const int ar = lane >> 2, ac = (lane & 3) * 2;
-#pragma unroll
-      for (int i = 0; i < 2; i++) {
-        const int r = wm + i * 16 + ar;
-        af[i][0] = *reinterpret_cast<const unsigned*>(&sA[r][kk + ac]);
-        af[i][1] = *reinterpret_cast<const unsigned*>(&sA[r + 8][kk + ac]);
-        af[i][2] = *reinterpret_cast<const unsigned*>(&sA[r][kk + ac + 8]);
-        af[i][3] = *reinterpret_cast<const unsigned*>(&sA[r + 8][kk + ac + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const int n = wn + j * 8 + ar;
-        bf[j][0] = *reinterpret_cast<const unsigned*>(&sB[n][kk + ac]);
-        bf[j][1] = *reinterpret_cast<const unsigned*>(&sB[n][kk + ac + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bf[j]);
-    }
-    __syncthreads();
+    tc::mbar_init(done, 1);
+    *abort = 0;
   }
-  // store: c0,c1 at (row lane/4, cols 2*(lane%4)+{0,1}); c2,c3 at row + 8
+  if (warp == 0) tc::tmem_alloc(taddr, GT_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tm = *taddr;
+  if (tid == 0) {
+    const uint32_t idesc = tc::idesc_bf16_f32(GT_BM, bn);
+    const uint32_t a_lbo = GT_BM * 16, b_lbo = bn * 16;
+    const uint32_t tx = (uint32_t)(GT_BK * 2) * (uint32_t)(GT_BM + bn);  // bytes of one chunk of A and B
+    int issued = 0, used = 0;
+    bool ok = true;
+    auto load = [&](int i) {
+      const int s = i % GT_STAGES;
+      unsigned char* sa = gsm + s * GT_STAGE_BYTES;
+      unsigned char* sb = sa + GT_A_BYTES;
+      tc::mbar_arrive_expect_tx(&full[s], tx);
+      const int k = (c0 + i) * GT_BK;
 #pragma unroll
-  for (int i = 0; i < 2; i++)
+      for (int j = 0; j < GT_BK / 8; j++) {
+        tc::tma_load_2d(sa + j * a_lbo, &ta, k + 8 * j, m0, &full[s]);
+        tc::tma_load_2d(sb + j * b_lbo, &tb, k + 8 * j, n0, &full[s]);
+      }
+    };
+    for (; issued < nc && issued < GT_STAGES; issued++) load(issued);
+    for (; used < nc; used++) {
+      const int s = used % GT_STAGES;
+      const uint32_t ph = (uint32_t)(used / GT_STAGES) & 1u;
+      if (!tc::mbar_wait(&full[s], ph, GT_WAIT_LIMIT)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_addr(gsm + s * GT_STAGE_BYTES), sb = sa + GT_A_BYTES;
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int r = m0 + wm + i * 16 + (lane >> 2);
-      const int cidx = n0 + wn + j * 8 + (lane & 3) * 2;
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const int rr = r + h * 8;
-        if (rr < M && cidx < N) {
-          float* p = C + (long long)rr * ldc + cidx;
-          if (accumulate) { p[0] += acc[i][j][2 * h]; p[1] += acc[i][j][2 * h + 1]; }
-          else { p[0] = acc[i][j][2 * h]; p[1] = acc[i][j][2 * h + 1]; }
+      for (int kk = 0; kk < GT_BK / 16; kk++)
+        tc::mma_bf16(tm, tc::smem_desc(sa + 2 * kk * a_lbo, a_lbo, 128), tc::smem_desc(sb + 2 * kk * b_lbo, b_lbo, 128),
+                     idesc, (uint32_t)(used | kk));
+      tc::commit(&empty[s]);
+      if (issued < nc) {
+        // refill the stage once the MMAs that read it have completed
+        if (!tc::mbar_wait(&empty[s], ph, GT_WAIT_LIMIT)) {
+          ok = false;
+          used++;
+          break;
         }
+        load(issued++);
       }
     }
+    tc::commit(done);  // one arrival when every MMA issued above has completed
+    if (!ok) {
+      // the copies still in flight land before the kernel gives up
+      for (int i = used; i < issued; i++)
+        tc::mbar_wait(&full[i % GT_STAGES], (uint32_t)(i / GT_STAGES) & 1u, GT_WAIT_LIMIT);
+      *abort = 1;
+    }
+  }
+  __syncwarp();
+  if (!tc::mbar_wait(done, 0, GT_WAIT_LIMIT)) *abort = 1;
+  __syncthreads();
+  if (*abort == 0) {
+    tc::fence_after_sync();
+    const int row = m0 + warp * 32 + lane;
+    float* out = C + blockIdx.z * split_stride + (long long)row * ldc + n0;
+    for (int c = 0; c < bn; c += 16) {
+      float v[16];
+      tc::ld_x16(tm + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      if (row < M && n0 + c < N) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4*>(out + c + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicAdd(stalls, 1ull);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tm, GT_COLS);
 }
 
+// C[r][c] = sum over the splits z, in order, of the partial tiles ws[z][r][c].
+__global__ void gemm_splitk_sum(const float* __restrict__ ws, int splits, long long slice, int M, int N,
+                                float* __restrict__ C, int ldc) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)M * N) return;
+  float s = 0.f;
+  for (int z = 0; z < splits; z++) s += ws[z * slice + i];
+  C[(i / N) * ldc + i % N] = s;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of a bfloat16 matrix [rows][K] with row stride ld elements,
+// copied in boxes of 8 columns x box_rows rows, zeros outside.
+static bool tmap_kmajor(CUtensorMap* t, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows) {
+  const EncodeTiledFn f = encode_tiled();
+  if (!f) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)ld * 2u};
+  const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1u, 1u};
+  return f(t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dim, stride, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launches C = A B^T (see gemm_nt_bf16).  Requirements, checked here:
+// N a multiple of 16; lda, ldb multiples of 8 and >= K (16-byte TMA
+// strides); ldc a multiple of 4 and >= N; A, B, C 16-byte aligned.
+// splits: the number of K-splits, or 0 to choose (only when K spans at
+// least 8 chunks of 64 and the tiles leave SMs idle; needs ws of
+// splits * M * N floats, else no split).  stalls: device counter raised when
+// a CTA gave up waiting for its copies or MMAs.
 static cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-                        float* C, int ldc, cudaStream_t st) {
-  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-  gemm_nt_bf16<<<grid, 128, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, 0);
+                        float* C, int ldc, float* ws, long long ws_floats, unsigned long long* stalls,
+                        cudaStream_t st, int splits = 0) {
+  auto misaligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
+  if (M < 1 || N < 16 || K < 1 || N % 16 || lda % 8 || ldb % 8 || lda < K || ldb < K || ldc % 4 || ldc < N ||
+      misaligned(A) || misaligned(B) || misaligned(C) || splits < 0 || !stalls)
+    return cudaErrorInvalidValue;
+  static PerDevice once;
+  int sms = 0;
+  cudaError_t e = once.get(
+      [](int* v) {
+        cudaError_t r = cudaFuncSetAttribute(gemm_nt_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, GT_SMEM);
+        int dev = 0;
+        if (r == cudaSuccess) r = cudaGetDevice(&dev);
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev);
+        return r;
+      },
+      &sms);
+  if (e != cudaSuccess) return e;
+  const int bn = N < 128 ? N : 128;
+  const int gx = (N + bn - 1) / bn, gy = (M + GT_BM - 1) / GT_BM;
+  const int nchunks = (K + GT_BK - 1) / GT_BK;
+  int s = splits;
+  if (s == 0) {
+    s = 1;
+    const int idle = sms / (gx * gy);
+    if (nchunks >= 8 && idle > 1) s = std::min(std::min(GT_MAX_SPLITS, nchunks / 4), idle);
+  }
+  s = std::min(s, nchunks);
+  const int cps = (nchunks + s - 1) / s;
+  s = (nchunks + cps - 1) / cps;  // every split gets at least one chunk
+  const long long slice = (long long)M * N;
+  if (s > 1 && (!ws || misaligned(ws) || (long long)s * slice > ws_floats)) {
+    if (splits) return cudaErrorInvalidValue;
+    s = 1;
+  }
+  const int cps_final = (nchunks + s - 1) / s;
+  CUtensorMap ta, tb;
+  if (!tmap_kmajor(&ta, A, M, K, lda, GT_BM) || !tmap_kmajor(&tb, B, N, K, ldb, bn)) return cudaErrorInvalidValue;
+  const dim3 grid(gx, gy, s);
+  if (s == 1) {
+    gemm_nt_bf16<<<grid, GT_THREADS, GT_SMEM, st>>>(ta, tb, M, N, K, bn, cps_final, C, ldc, 0, stalls);
+    return cudaGetLastError();
+  }
+  gemm_nt_bf16<<<grid, GT_THREADS, GT_SMEM, st>>>(ta, tb, M, N, K, bn, cps_final, ws, N, slice, stalls);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  gemm_splitk_sum<<<(unsigned)((slice + 255) / 256), 256, 0, st>>>(ws, s, slice, M, N, C, ldc);
   return cudaGetLastError();
 }
 
@@ -725,6 +865,15 @@ static int mlp_alloc_batch(grim_mlp* m, int B) {
   return GRIM_OK;
 }
 
+// Reads and clears the training GEMM's stall counter (synchronous); true
+// when a CTA gave up waiting (its tile was not written) or the read failed.
+static bool mlp_take_stalls(grim_mlp* m) {
+  unsigned long long n = 0;
+  if (cudaMemcpy(&n, m->stalls, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+  if (n) cudaMemset(m->stalls, 0, sizeof(n));
+  return n != 0;
+}
+
 // One forward + backward pass over the gathered batch; leaves the parameter
 // gradient in m->grad and adds the batch loss to *m->loss.
 static cudaError_t mlp_forward_backward(grim_mlp* m, int B, cudaStream_t st) {
@@ -738,7 +887,9 @@ static cudaError_t mlp_forward_backward(grim_mlp* m, int B, cudaStream_t st) {
   for (int l = 0; l < 4; l++) {
     wboffs[l] = wboff;
     const int no = mlp_nout(l);
-    if ((e = gemm(B, no, nin, in, nin, m->wb + wboff, nin, m->z[l], no, st)) != cudaSuccess) return e;
+    if ((e = gemm(B, no, nin, in, nin, m->wb + wboff, nin, m->z[l], no, m->ws, GT_WS_FLOATS, m->stalls, st)) !=
+        cudaSuccess)
+      return e;
     if (l < 3) {
       mlp_bias_silu<<<(unsigned)(((long long)B * no + T - 1) / T), T, 0, st>>>(m->z[l], m->params + mlp_boff(l), B, no,
                                                                               m->a[l], m->at[l]);
@@ -755,13 +906,17 @@ static cudaError_t mlp_forward_backward(grim_mlp* m, int B, cudaStream_t st) {
     const int no = mlp_nout(l), ni = mlp_nin(l);
     // dW_l [no][ni] = g^T [no][B] x a_{l-1} [B][ni]  ->  A = gt (K = B contiguous), B-operand = a_{l-1}^T [ni][B]
     const __nv_bfloat16* actT = (l == 0) ? m->xbt : m->at[l - 1];
-    if ((e = gemm(no, ni, B, m->gt, B, actT, B, m->grad + mlp_woff(l), ni, st)) != cudaSuccess) return e;
+    if ((e = gemm(no, ni, B, m->gt, B, actT, B, m->grad + mlp_woff(l), ni, m->ws, GT_WS_FLOATS, m->stalls, st)) !=
+        cudaSuccess)
+      return e;
     // db_l = column sums of the output-side gradient (float copy in dA)
     mlp_colsum<<<no, 256, 0, st>>>(m->dA, B, no, m->grad + mlp_boff(l));
     if (l == 0) break;
     // dA_{l-1} [B][ni] = g [B][no] x W_l [no][ni]  ->  B-operand = W_l^T [ni][no];
     // dA is reused: the bias gradient above has consumed it in stream order
-    if ((e = gemm(B, ni, no, m->g, no, m->wbt + wboffs[l], no, m->dA, ni, st)) != cudaSuccess) return e;
+    if ((e = gemm(B, ni, no, m->g, no, m->wbt + wboffs[l], no, m->dA, ni, m->ws, GT_WS_FLOATS, m->stalls, st)) !=
+        cudaSuccess)
+      return e;
     // dZ_{l-1} = dA * SiLU'(z_{l-1}) -> g, gt, and its float copy back into dA
     mlp_silu_back<<<(unsigned)(((long long)B * ni + T - 1) / T), T, 0, st>>>(m->dA, m->z[l - 1], B, ni, m->g, m->gt,
                                                                             m->dA);
@@ -782,13 +937,15 @@ int grim_mlp_create(unsigned long long seed, grim_mlp** out) {
             cudaMalloc(&m->v, 4 * np) == cudaSuccess && cudaMalloc(&m->grad, 4 * np) == cudaSuccess &&
             cudaMalloc(&m->wb, 2 * nw) == cudaSuccess && cudaMalloc(&m->wbt, 2 * nw) == cudaSuccess &&
             cudaMalloc(&m->norm, 4 * (2 * MLP_IN + 2 * MLP_Y)) == cudaSuccess &&
-            cudaMalloc(&m->loss, 4) == cudaSuccess;
+            cudaMalloc(&m->loss, 4) == cudaSuccess && cudaMalloc(&m->ws, 4 * GT_WS_FLOATS) == cudaSuccess &&
+            cudaMalloc(&m->stalls, sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) {
     grim_mlp_destroy(m);
     return GRIM_ENOMEM;
   }
   cudaMemset(m->m, 0, 4 * np);
   cudaMemset(m->v, 0, 4 * np);
+  cudaMemset(m->stalls, 0, sizeof(unsigned long long));
   std::vector<float> nrm(2 * MLP_IN + 2 * MLP_Y, 0.f);
   for (int i = 0; i < MLP_IN; i++) nrm[MLP_IN + i] = 1.f;
   for (int i = 0; i < MLP_Y; i++) nrm[2 * MLP_IN + MLP_Y + i] = 1.f;
@@ -806,9 +963,37 @@ int grim_mlp_create(unsigned long long seed, grim_mlp** out) {
 void grim_mlp_destroy(grim_mlp* m) {
   if (!m) return;
   void* ps[] = {m->params, m->m, m->v, m->wb, m->wbt, m->norm, m->xb, m->xbt, m->yb, m->xh, m->g, m->gt, m->dA, m->grad,
-                m->loss, m->z[0], m->z[1], m->z[2], m->z[3], m->a[0], m->a[1], m->a[2], m->at[0], m->at[1], m->at[2]};
+                m->loss, m->z[0], m->z[1], m->z[2], m->z[3], m->a[0], m->a[1], m->a[2], m->at[0], m->at[1], m->at[2],
+                m->ws, m->stalls};
   for (void* p : ps) cudaFree(p);
   delete m;
+}
+
+int grim_gemm_nt_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, float* C, int ldc,
+                      int splits) {
+  if (!A || !B || !C || splits < 0 || splits > GT_MAX_SPLITS) return GRIM_EINVAL;
+  float* ws = nullptr;
+  unsigned long long* stalls = nullptr;
+  const long long ws_floats = splits > 1 ? (long long)splits * M * N : 0;
+  if (cudaMalloc(&stalls, sizeof(unsigned long long)) != cudaSuccess ||
+      (ws_floats && cudaMalloc(&ws, 4 * ws_floats) != cudaSuccess)) {
+    cudaFree(stalls);
+    return GRIM_ENOMEM;
+  }
+  int rc = GRIM_OK;
+  unsigned long long n = 0;
+  if (cudaMemset(stalls, 0, sizeof(n)) != cudaSuccess) rc = GRIM_ECUDA;
+  if (!rc) {
+    const cudaError_t e = gemm(M, N, K, static_cast<const __nv_bfloat16*>(A), lda, static_cast<const __nv_bfloat16*>(B),
+                               ldb, C, ldc, ws, ws_floats, stalls, 0, splits ? splits : 1);
+    if (e == cudaErrorInvalidValue) rc = GRIM_EINVAL;
+    else if (e != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+             cudaMemcpy(&n, stalls, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess || n)
+      rc = GRIM_ECUDA;
+  }
+  cudaFree(ws);
+  cudaFree(stalls);
+  return rc;
 }
 
 int grim_mlp_param_count() { return MLP_NPARAM; }
@@ -890,6 +1075,7 @@ int grim_mlp_train(grim_mlp* m, const float* X, const float* Y, long long M, int
   }
   float l = 0.f;
   if (cudaMemcpy(&l, m->loss, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GRIM_ECUDA;
+  if (mlp_take_stalls(m)) return GRIM_ECUDA;
   if (mean_loss) *mean_loss = steps ? (double)l / steps : 0.0;
   return GRIM_OK;
 }
@@ -904,7 +1090,7 @@ int grim_mlp_gradient(grim_mlp* m, const float* X, const float* Y, long long M, 
   if (mlp_forward_backward(m, B, 0) != cudaSuccess) return GRIM_ECUDA;
   float l = 0.f;
   if (cudaMemcpy(grad_host, m->grad, 4 * MLP_NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(&l, m->loss, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      cudaMemcpy(&l, m->loss, 4, cudaMemcpyDeviceToHost) != cudaSuccess || mlp_take_stalls(m))
     return GRIM_ECUDA;
   if (loss) *loss = l;
   return GRIM_OK;

@@ -1,5 +1,6 @@
-// Fifth-generation tensor cores (tcgen05) on sm_103a: thin inline-PTX
-// wrappers for the learned start's inference kernel.
+// Fifth-generation tensor cores (tcgen05) and the tensor memory accelerator
+// (TMA) on sm_103a: thin inline-PTX wrappers for the learned start's
+// inference kernel and the network's training GEMM.
 //
 // One CTA-group-1 MMA computes D[M][N] (+)= A[M][K] B[N][K]^T with A and B
 // bfloat16 in shared memory and D float32 in tensor memory (TMEM): M = 128
@@ -88,6 +89,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
+// Arrival of one thread that also announces `bytes` of asynchronous copies
+// (TMA) whose completion the current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
 // Wait for the phase `parity` of the mbarrier to complete, giving up after
 // `limit` polls (each try_wait itself blocks for a bounded time).  Returns
 // false on giving up.
@@ -95,6 +102,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   for (uint32_t i = 0; i < limit; i++)
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
+}
+
+// ---- TMA: one 2-D tile of a tensor map (a __grid_constant__ kernel
+// parameter) into shared memory; the copy's bytes complete a transaction of
+// the mbarrier.  x is the innermost (contiguous) coordinate in elements,
+// y the row; x times the element size must be a multiple of 16 bytes.
+// Elements outside the tensor are written as zeros and still count towards
+// the transaction's bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+      : "memory");
 }
 
 // ---- TMEM to registers: 32 lanes x 32 bit, 16 consecutive columns per

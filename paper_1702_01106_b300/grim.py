@@ -25,6 +25,7 @@ EXPORTS = (
     "grim_profile", "grim_kernel_times", "grim_step_static", "grim_step_static_stats", "grim_math_selftest",
     "grim_mlp_create", "grim_mlp_destroy", "grim_mlp_param_count", "grim_mlp_get_params", "grim_mlp_set_params",
     "grim_mlp_fit_norm", "grim_mlp_train", "grim_mlp_gradient", "grim_mlp_sample", "grim_set_guess",
+    "grim_gemm_nt_bf16",
     "grim_get_tuning", "grim_set_tuning", "grim_autotune", "grim_use_graphs",
     "grim_batch_init", "grim_batch_destroy", "grim_batch_context", "grim_batch_step", "grim_batch_use_graphs",
     "grim_batch_get_stats", "grim_batch_reset_stats", "grim_batch_last_error",
@@ -117,6 +118,7 @@ def load():
     lib.grim_mlp_train.argtypes = [vp, vp, vp, ll, i, i, dp, ull, ctypes.POINTER(dp)]
     lib.grim_mlp_gradient.argtypes = [vp, vp, vp, ll, vp, ctypes.POINTER(dp)]
     lib.grim_mlp_sample.argtypes = [vp, vp, vp, vp, vp]
+    lib.grim_gemm_nt_bf16.argtypes = [i, i, i, vp, i, vp, i, vp, i, i]
     lib.grim_set_guess.argtypes = [vp, vp, dp]
     lib.grim_kernel_times.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.grim_get_tuning.argtypes = [vp, ctypes.POINTER(GrimTuning)]
@@ -383,6 +385,26 @@ def math_selftest(n: int = 1 << 20) -> float:
     if rc != 0:
         raise RuntimeError(f"grim_math_selftest failed: {lib.grim_strerror(rc).decode()}")
     return out.value
+
+
+def gemm_nt_bf16(A, B, splits: int = 0, out=None):
+    """C = A B^T on the tensor cores (grim_gemm_nt_bf16): A [M][K] and B [N][K]
+    bfloat16 CUDA tensors with unit column stride, C float32 [M][N]."""
+    import torch
+    lib = load()
+    for t in (A, B):
+        if not t.is_cuda or t.dtype != torch.bfloat16 or t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError("expected 2-D bfloat16 CUDA matrices with unit column stride")
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B differ in K")
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device) if out is None else out
+    rc = lib.grim_gemm_nt_bf16(M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(B.data_ptr()),
+                               B.stride(0), ctypes.c_void_p(C.data_ptr()), C.stride(0), splits)
+    if rc != 0:
+        raise RuntimeError(f"grim_gemm_nt_bf16 failed: {lib.grim_strerror(rc).decode()}")
+    return C
 
 
 class MLP:
