@@ -79,7 +79,7 @@ def training_rate(X, Y, peaks, steps=400, batch=4096):
     m.close()
     ms = e0.elapsed_time(e1) / steps
     tf = MLP_STEP_FLOPS_PER_ROW * batch / (ms * 1e-3) / 1e12
-    return {"ms_per_step": ms, "batch": batch, "launches_per_step": 29, "bf16_tflops": tf,
+    return {"ms_per_step": ms, "batch": batch, "launches_per_step": 33, "bf16_tflops": tf,
             "bf16_frac_of_burst": tf / peaks.get("bf16_tflops", 1800.0)}
 
 
@@ -294,9 +294,22 @@ def profile_case(args, dev, torch):
     for ncu captures of single kernels; prints one JSON line of timings.
     --case box: the turbulent box of side --side; --case box-learned: its
     mixed arm with a learned start; --case torus: the Kerr torus on a --side x
-    --side x --side/3 grid."""
+    --side x --side/3 grid; --case train: Adam steps of the learned start's
+    network at batch 4096 on 2^20 seeded rows (--steps steps inside the NVTX
+    range "timed")."""
     from paper_1702_01106_b300 import inputs
     from paper_1702_01106_b300.grim import Grim, GRIM_FP64, GRIM_MIXED
+    if args.case == "train":
+        gen = torch.Generator(device=dev).manual_seed(7)
+        X = torch.randn((1 << 20, 32), device=dev, generator=gen)
+        Y = torch.randn((1 << 20, 16), device=dev, generator=gen)
+        peaks, _ = read_peaks()
+        training_rate(X, Y, peaks, steps=max(3, args.warmup))
+        torch.cuda.nvtx.range_push("timed")
+        rate = training_rate(X, Y, peaks, steps=args.steps)
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"case": "MLP training, batch 4096", "steps": args.steps, "step": rate}))
+        return
     if args.case == "torus":
         prob = inputs.torus_problem(args.side, args.side, max(1, args.side // 3))
         P = inputs.torus_state(prob)
@@ -501,7 +514,7 @@ def main():
     ap.add_argument("--case-only", action="store_true",
                     help="only the float64 and mixed steps of a --side box (for ncu captures)")
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side for --case-only")
-    ap.add_argument("--case", default="box", choices=["box", "box-learned", "torus"],
+    ap.add_argument("--case", default="box", choices=["box", "box-learned", "torus", "train"],
                     help="workload of --case-only")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)

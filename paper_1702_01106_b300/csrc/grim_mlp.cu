@@ -82,7 +82,7 @@ struct grim_mlp {
   float* dA = nullptr;                                   // input-side gradient [B][128]
   float* grad = nullptr;                                 // parameter gradients [MLP_NPARAM]
   float* loss = nullptr;                                 // [1]
-  float* ws = nullptr;                                   // split-K partial tiles of the training GEMM
+  float* ws = nullptr;                                   // split-K partial tiles, partial bias sums
   unsigned long long* stalls = nullptr;                  // training GEMM CTAs that gave up waiting
 };
 
@@ -424,19 +424,34 @@ __global__ void mlp_silu_back(const float* __restrict__ dA, const float* __restr
 }
 
 // Bias gradient: column sums of a float32 [B][n] matrix.
-__global__ void mlp_colsum(const float* __restrict__ g, int B, int n, float* __restrict__ out) {
-  const int col = blockIdx.x;
+// Column sums of a float matrix g [B][n] (the bias gradient) in two passes
+// with coalesced reads: mlp_colsum_part sums slice s of MLP_CS_SLICES row
+// slices for 32 columns per block (threads (c, r): rows r, r + 8, ...),
+// mlp_colsum_final adds the slices in order, so the sum is reproducible.
+constexpr int MLP_CS_SLICES = 32;
+__global__ void mlp_colsum_part(const float* __restrict__ g, int B, int n, float* __restrict__ part) {
+  __shared__ float acc[8][33];
+  const int c = threadIdx.x, r = threadIdx.y, col = blockIdx.x * 32 + c, sl = blockIdx.y;
+  const int rows = (B + MLP_CS_SLICES - 1) / MLP_CS_SLICES;
+  const int r0 = sl * rows, r1 = min(B, r0 + rows);
   float s = 0.f;
-  for (int r = threadIdx.x; r < B; r += blockDim.x) s += g[(long long)r * n + col];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  __shared__ float part[32];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  if (col < n)
+    for (int i = r0 + r; i < r1; i += 8) s += g[(long long)i * n + col];
+  acc[r][c] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (r == 0 && col < n) {
     float t = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
-    out[col] = t;
+#pragma unroll
+    for (int k = 0; k < 8; k++) t += acc[k][c];
+    part[(long long)sl * n + col] = t;
   }
+}
+__global__ void mlp_colsum_final(const float* __restrict__ part, int n, float* __restrict__ out) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n) return;
+  float t = 0.f;
+  for (int sl = 0; sl < MLP_CS_SLICES; sl++) t += part[(long long)sl * n + col];
+  out[col] = t;
 }
 
 // Adam (Kingma & Ba 2015) on the float32 master parameters, then refresh the
@@ -899,7 +914,8 @@ static cudaError_t mlp_forward_backward(grim_mlp* m, int B, cudaStream_t st) {
     wboff += no * mlp_nin(l);
   }
   // loss and dL/d(head) -> g (bf16 [B][80]), gt ([80][B]), dA (float [B][80])
-  mlp_head_loss<<<(B + T - 1) / T, T, 0, st>>>(m->z[3], m->params + mlp_boff(3), m->yb, m->xh, B, m->g, m->gt, m->dA,
+  // one warp per block: a thread per row, spread over as many SMs as possible
+  mlp_head_loss<<<(B + 31) / 32, 32, 0, st>>>(m->z[3], m->params + mlp_boff(3), m->yb, m->xh, B, m->g, m->gt, m->dA,
                                                m->loss);
   // backward
   for (int l = 3; l >= 0; l--) {
@@ -910,7 +926,8 @@ static cudaError_t mlp_forward_backward(grim_mlp* m, int B, cudaStream_t st) {
         cudaSuccess)
       return e;
     // db_l = column sums of the output-side gradient (float copy in dA)
-    mlp_colsum<<<no, 256, 0, st>>>(m->dA, B, no, m->grad + mlp_boff(l));
+    mlp_colsum_part<<<dim3((no + 31) / 32, MLP_CS_SLICES), dim3(32, 8), 0, st>>>(m->dA, B, no, m->ws);
+    mlp_colsum_final<<<1, 128, 0, st>>>(m->ws, no, m->grad + mlp_boff(l));
     if (l == 0) break;
     // dA_{l-1} [B][ni] = g [B][no] x W_l [no][ni]  ->  B-operand = W_l^T [ni][no];
     // dA is reused: the bias gradient above has consumed it in stream order
@@ -1063,7 +1080,7 @@ int grim_mlp_train(grim_mlp* m, const float* X, const float* Y, long long M, int
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   long long off = (long long)(seed % (unsigned long long)M);
   for (int s = 0; s < steps; s++) {
-    mlp_gather<<<(batch + 255) / 256, 256>>>(X, Y, M, off, stride, batch, m->norm, m->xb, m->xbt, m->yb, m->xh);
+    mlp_gather<<<(batch + 31) / 32, 32>>>(X, Y, M, off, stride, batch, m->norm, m->xb, m->xbt, m->yb, m->xh);
     off = (off + (long long)batch * stride) % M;
     cudaError_t e = mlp_forward_backward(m, batch, 0);
     if (e != cudaSuccess) return GRIM_ECUDA;
@@ -1086,7 +1103,7 @@ int grim_mlp_gradient(grim_mlp* m, const float* X, const float* Y, long long M, 
   int rc = mlp_alloc_batch(m, B);
   if (rc) return rc;
   cudaMemset(m->loss, 0, 4);
-  mlp_gather<<<(B + 255) / 256, 256>>>(X, Y, M, 0, 1, B, m->norm, m->xb, m->xbt, m->yb, m->xh);
+  mlp_gather<<<(B + 31) / 32, 32>>>(X, Y, M, 0, 1, B, m->norm, m->xb, m->xbt, m->yb, m->xh);
   if (mlp_forward_backward(m, B, 0) != cudaSuccess) return GRIM_ECUDA;
   float l = 0.f;
   if (cudaMemcpy(grad_host, m->grad, 4 * MLP_NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess ||
