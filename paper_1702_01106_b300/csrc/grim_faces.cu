@@ -154,6 +154,9 @@ struct ExpArgs {
   // kappa gamma and the limiter theta (hi, lo pairs), for the float-float
   // face states and slopes
   float ffc[12];
+  // float-float copies of 1/dx^1, 1/dx^2, tau_R, phi, psi, 1/tau_R, 1/dt_s,
+  // 1/(dt_s tau_R) and dt_s, for the mixed solver's closure constants
+  float ffz[18];
 };
 constexpr int NCACHE = NV + 2;
 
@@ -299,22 +302,15 @@ __device__ __forceinline__ void derived_at_ff(const Params& p, const ExpArgs& a,
   u[1] = v1; u[2] = v2; u[3] = v3;
 }
 
-// FFS: the limited slopes of Theta and u_mu in float-float (the mixed
-// solver); everything else of the kernel is float64 either way.
-template <int BS, bool FFS>
-__global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Params p,
-                                                   const __grid_constant__ ExpArgs a) {
-  const long long N = p.N;
-  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (z >= N) return;
-  const int i = (int)(z % p.n1), j = (int)(z / p.n1);
+// Flux divergence of zone (i, j) from the face fluxes; flux-CT replaces
+// F^1[B^1], F^2[B^2] by 0 and the transverse B fluxes by averages of the
+// corner values
+// E(i', j') = (F^1[B^2](i',j') + F^1[B^2](i',j'-1) - F^2[B^1](i',j') - F^2[B^1](i'-1,j'))/4
+// (Section 4.2).
+__device__ __forceinline__ void flux_divergence_ct(const Params& p, const ExpArgs& a, int i, int j, double divF[NV]) {
   const long long w1 = p.n1 + 1, w2 = p.n1 + 2;
   const long long nf1 = w1 * (p.n2 + 2), nf2 = w2 * (p.n2 + 1);
   const double idx1 = p.idx[0], idx2 = p.idx[1];
-  // flux divergence; flux-CT replaces F^1[B^1], F^2[B^2] by 0 and the
-  // transverse B fluxes by averages of the corner values
-  // E(i', j') = (F^1[B^2](i',j') + F^1[B^2](i',j'-1) - F^2[B^1](i',j') - F^2[B^1](i'-1,j'))/4.
-  double divF[NV];
   const long long f1lo = (long long)(j + 1) * w1 + i, f2lo = (long long)j * w2 + (i + 1);
 #pragma unroll
   for (int v = 0; v < NV; v++) {
@@ -322,21 +318,53 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
     const double* F2 = a.F2 + v * nf2;
     divF[v] = (__ldg(F1 + f1lo + 1) - __ldg(F1 + f1lo)) * idx1 + (__ldg(F2 + f2lo + w2) - __ldg(F2 + f2lo)) * idx2;
   }
-  {
-    const double* F1b2 = a.F1 + 6 * nf1;
-    const double* F2b1 = a.F2 + 5 * nf2;
-    double E[2][2];
+  const double* F1b2 = a.F1 + 6 * nf1;
+  const double* F2b1 = a.F2 + 5 * nf2;
+  double E[2][2];
 #pragma unroll
-    for (int dj = 0; dj < 2; dj++)
+  for (int dj = 0; dj < 2; dj++)
 #pragma unroll
-      for (int di = 0; di < 2; di++) {
-        const int ii = i + di, jj = j + dj;
-        E[dj][di] = 0.25 * (__ldg(F1b2 + (long long)(jj + 1) * w1 + ii) + __ldg(F1b2 + (long long)jj * w1 + ii) -
-                            __ldg(F2b1 + (long long)jj * w2 + ii + 1) - __ldg(F2b1 + (long long)jj * w2 + ii));
-      }
-    divF[6] = (0.5 * (E[0][1] + E[1][1]) - 0.5 * (E[0][0] + E[1][0])) * idx1;
-    divF[5] = (-0.5 * (E[1][0] + E[1][1]) + 0.5 * (E[0][0] + E[0][1])) * idx2;
-  }
+    for (int di = 0; di < 2; di++) {
+      const int ii = i + di, jj = j + dj;
+      E[dj][di] = 0.25 * (__ldg(F1b2 + (long long)(jj + 1) * w1 + ii) + __ldg(F1b2 + (long long)jj * w1 + ii) -
+                          __ldg(F2b1 + (long long)jj * w2 + ii + 1) - __ldg(F2b1 + (long long)jj * w2 + ii));
+    }
+  divF[6] = (0.5 * (E[0][1] + E[1][1]) - 0.5 * (E[0][0] + E[1][0])) * idx1;
+  divF[5] = (-0.5 * (E[1][0] + E[1][1]) + 0.5 * (E[0][0] + E[0][1])) * idx2;
+}
+
+// The conserved variables U(P) of a float64 zone state in Minkowski space
+// (Section 4, Eqs. fullSEtens, divN_explicit, divT_explicit: rho u^t and
+// T^t_mu with the heat-flux and anisotropy terms), with B^i, q~ u^t and
+// dP~ u^t for the induction and closure rows.
+__device__ __forceinline__ void conserved_of(const Z<double>& zn, const double* P, double U[NV]) {
+  const double dp = zn.dpt * zn.ds, q = zn.qt * zn.qs;
+  const double third = dp * (1.0 / 3.0);
+  const double A = (zn.w0 + zn.bsq + third) * zn.ut;
+  const double qb = q * zn.bht, dpb = dp * zn.bht, qut = q * zn.ut;
+  U[0] = zn.rho * zn.ut;
+  U[1] = -A * zn.ut + zn.bt * zn.bt - 2.0 * qb * zn.ut + dpb * zn.bht + zn.pg + 0.5 * zn.bsq + third;
+#pragma unroll
+  for (int k = 0; k < 3; k++) U[2 + k] = A * zn.v[k] - zn.bt * zn.bc[k] + qb * zn.v[k] + qut * zn.bh[k] - dpb * zn.bh[k];
+  U[5] = P[5]; U[6] = P[6]; U[7] = P[7];
+  U[8] = zn.qt * zn.ut;
+  U[9] = zn.dpt * zn.ut;
+}
+
+// The stage constants of every zone in float64 (the float64 solver): the
+// flux divergence with flux-CT, U(P_n), the row scales, the heat-flux and
+// anisotropy rows' explicit parts (Eqs. q_evol_eqn_rescaled,
+// dP_evol_eqn_rescaled with q0def, dP0def at P^E), and the Newton start.
+template <int BS>
+__global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Params p,
+                                                   const __grid_constant__ ExpArgs a) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const int i = (int)(z % p.n1), j = (int)(z / p.n1);
+  const double idx1 = p.idx[0], idx2 = p.idx[1];
+  double divF[NV];
+  flux_divergence_ct(p, a, i, j, divF);
   // states at P^E and P_n
   double PEz[NV], Pnz[NV];
 #pragma unroll
@@ -358,18 +386,7 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
     Z<double> zn;
     if (a.mode == 1) zn = ze;
     else z_load(zn, Pnz, c);
-    const double dp = zn.dpt * zn.ds, q = zn.qt * zn.qs;
-    const double third = dp * (1.0 / 3.0);
-    const double A = (zn.w0 + zn.bsq + third) * zn.ut;
-    const double qb = q * zn.bht, dpb = dp * zn.bht, qut = q * zn.ut;
-    Un[0] = zn.rho * zn.ut;
-    Un[1] = -A * zn.ut + zn.bt * zn.bt - 2.0 * qb * zn.ut + dpb * zn.bht + zn.pg + 0.5 * zn.bsq + third;
-#pragma unroll
-    for (int k = 0; k < 3; k++)
-      Un[2 + k] = A * zn.v[k] - zn.bt * zn.bc[k] + qb * zn.v[k] + qut * zn.bh[k] - dpb * zn.bh[k];
-    Un[5] = Pnz[5]; Un[6] = Pnz[6]; Un[7] = Pnz[7];
-    Un[8] = zn.qt * zn.ut;
-    Un[9] = zn.dpt * zn.ut;
+    conserved_of(zn, Pnz, Un);
     th_n = zn.theta;
     ut_n = zn.ut;
     if (a.mode == 1) {
@@ -383,8 +400,8 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
 
   // limited slopes at P^E of Theta and u_mu; the spatial part of nabla_mu u^mu
   double dTh[2], du[2][4], divu_sp = 0.0;
-  if (!FFS) {
-    double th0 = ze.theta, u0[4] = {-ze.ut, ze.v[0], ze.v[1], ze.v[2]};
+  {
+    const double th0 = ze.theta, u0[4] = {-ze.ut, ze.v[0], ze.v[1], ze.v[2]};
 #pragma unroll
     for (int d = 0; d < 2; d++) {
       double thm, thp, um[4], up[4];
@@ -394,21 +411,6 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
       dTh[d] = gm_slope(p.theta, thm, th0, thp) * ih;
 #pragma unroll
       for (int m = 0; m < 4; m++) du[d][m] = gm_slope(p.theta, um[m], u0[m], up[m]) * ih;
-      divu_sp += du[d][1 + d];
-    }
-  } else {
-    const ff theta(a.ffc[10], a.ffc[11]);
-    const ff th0 = ff_split(ze.theta);
-    const ff u0[4] = {ff_split(-ze.ut), ff_split(ze.v[0]), ff_split(ze.v[1]), ff_split(ze.v[2])};
-#pragma unroll
-    for (int d = 0; d < 2; d++) {
-      ff thm, thp, um[4], up[4];
-      derived_at_ff(p, a, i - (d == 0), j - (d == 1), thm, um);
-      derived_at_ff(p, a, i + (d == 0), j + (d == 1), thp, up);
-      const double ih = (d == 0) ? idx1 : idx2;
-      dTh[d] = ff_join(gm_slope(theta, thm, th0, thp)) * ih;
-#pragma unroll
-      for (int m = 0; m < 4; m++) du[d][m] = ff_join(gm_slope(theta, um[m], u0[m], up[m])) * ih;
       divu_sp += du[d][1 + d];
     }
   }
@@ -516,6 +518,190 @@ __global__ void __launch_bounds__(BS) zone_const_2d(const __grid_constant__ Para
   }
 }
 
+// The same constants for the mixed solver.  What sets the conserved update
+// stays float64: the flux divergence with flux-CT, U(P_n), the constant
+// parts kU (dt_s div F - U(P_n)) and the flux-CT update of B.  The rest is
+// explicit source data evaluated at P^E, as the float-float face fluxes
+// are: the state at P^E, the limited slopes of Theta and u_mu, and the
+// heat-flux and anisotropy rows' coefficients are computed in float-float
+// (about 48 bits), and each stored coefficient is joined into a double once.
+// The row scales kU are refined in float-float as well.  The learned start's
+// features -r_a(P_n) follow from the same terms: for rows 0-7 they are
+// -kU dt_s div F, and for the closure rows the P_n parts of the constants
+// cancel, leaving -s (div F + (X_n - A)/tau_R - h div_i u^i) with
+// s = kU dt_s, X_n = q~_n or dP~_n, A the explicit target and h the
+// higher-order coefficient.
+template <int BS>
+__global__ void __launch_bounds__(BS, 512 / BS) zone_const_2d_mixed(const __grid_constant__ Params p,
+                                                         const __grid_constant__ ExpArgs a) {
+  const long long N = p.N;
+  const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= N) return;
+  const int i = (int)(z % p.n1), j = (int)(z / p.n1);
+  double divF[NV];
+  flux_divergence_ct(p, a, i, j, divF);
+  double PEz[NV], Pnz[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    PEz[v] = __ldg(a.PE + v * N + z);
+    Pnz[v] = (a.mode == 1) ? PEz[v] : __ldg(a.Pn + v * N + z);
+  }
+  // P_n quantities in float64: U(P_n), Theta_n, u^t_n (from the cache in the full step)
+  double Un[NV], th_n, ut_n;
+  if (a.mode == 2) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) Un[v] = __ldg(a.cache + v * N + z);
+    th_n = __ldg(a.cache + NV * N + z);
+    ut_n = __ldg(a.cache + (NV + 1) * N + z);
+  } else {
+    Z<double> zn;
+    z_load(zn, Pnz, make_rc<double>(p));
+    conserved_of(zn, Pnz, Un);
+    th_n = zn.theta;
+    ut_n = zn.ut;
+    if (a.mode == 1) {
+#pragma unroll
+      for (int v = 0; v < NV; v++) a.cache[v * N + z] = Un[v];
+      a.cache[NV * N + z] = th_n;
+      a.cache[(NV + 1) * N + z] = ut_n;
+    }
+  }
+  // the state at P^E in float-float
+  RC<ff> c;
+  c.gam = ff(a.ffc[0], a.ffc[1]);
+  c.gm1 = ff(a.ffc[2], a.ffc[3]);
+  c.sphig = ff(a.ffc[4], a.ffc[5]);
+  c.spsig = ff(a.ffc[6], a.ffc[7]);
+  c.cond = p.cond;
+  c.visc = p.visc;
+  // Of the field, only the direction b-hat enters here, and it does not
+  // depend on the field's scale: B^i is split at the power of two that
+  // brings its largest component near 1, so that a weak field keeps all its
+  // float-float bits (its low parts would otherwise be float denormals).
+  // b^2 and b^t of ze are then those of the scaled field and stay unused.
+  const int eb = max(max((int)((__double_as_longlong(PEz[5]) >> 52) & 0x7ff),
+                         (int)((__double_as_longlong(PEz[6]) >> 52) & 0x7ff)),
+                     (int)((__double_as_longlong(PEz[7]) >> 52) & 0x7ff));
+  const double sb = (eb > 0 && eb < 0x7ff) ? __longlong_as_double((long long)(2046 - eb) << 52) : 1.0;
+  ff PEf[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) PEf[v] = ff_split((v >= 5 && v <= 7) ? PEz[v] * sb : PEz[v]);
+  Z<ff> ze;
+  z_load(ze, PEf, c);
+  const ff idx1(a.ffz[0], a.ffz[1]), idx2(a.ffz[2], a.ffz[3]), tau(a.ffz[4], a.ffz[5]);
+  const ff phi(a.ffz[6], a.ffz[7]), psi(a.ffz[8], a.ffz[9]), it(a.ffz[10], a.ffz[11]);
+  const ff idts(a.ffz[12], a.ffz[13]), git(a.ffz[14], a.ffz[15]);
+  // limited slopes at P^E of Theta and u_mu; the spatial part of nabla_mu u^mu
+  ff dTh[2], du[2][4], divu_sp(0.f, 0.f);
+  {
+    const ff theta(a.ffc[10], a.ffc[11]);
+    const ff u0[4] = {-ze.ut, ze.v[0], ze.v[1], ze.v[2]};
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      ff thm, thp, um[4], up[4];
+      derived_at_ff(p, a, i - (d == 0), j - (d == 1), thm, um);
+      derived_at_ff(p, a, i + (d == 0), j + (d == 1), thp, up);
+      const ff ih = (d == 0) ? idx1 : idx2;
+      dTh[d] = gm_slope(theta, thm, ze.theta, thp) * ih;
+#pragma unroll
+      for (int m = 0; m < 4; m++) du[d][m] = gm_slope(theta, um[m], u0[m], up[m]) * ih;
+      divu_sp += du[d][1 + d];
+    }
+  }
+  const double dts = a.dts, idts_d = a.idts;
+  double* Kz = a.K + z;
+  float* feat = a.feat ? a.feat + z : nullptr;
+  const float fdts = a.ffz[16];
+  // row scales (they depend on P_n only) and the conserved rows' constants
+  double kU[NV];
+  const ff u0abs = fabs(ff_split(Un[0]));
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    if (a.mode == 2) {
+      kU[v] = Kz[(K_U + v) * N];
+    } else {
+      kU[v] = ff_join(nr_rcp(fabs(ff_split(Un[v])) + u0abs));
+      Kz[(K_U + v) * N] = kU[v];
+    }
+    if (v < 8) {
+      Kz[(K_C + v) * N] = kU[v] * (dts * divF[v] - Un[v]);
+      if (feat) feat[v * N] = -(d2f_jac(kU[v]) * fdts) * d2f_jac(divF[v]);
+    }
+  }
+  const ff bhu[4] = {ze.bht, ze.bh[0], ze.bh[1], ze.bh[2]};
+  const ff thn = ff_split(th_n), utn = ff_split(ut_n);
+  const ff ucovn[4] = {-utn, ff_split(Pnz[2]), ff_split(Pnz[3]), ff_split(Pnz[4])};
+  const ff zero(0.f, 0.f);
+  const ff hoq = p.ho ? scale2(ze.qt, 0.5f) : zero;
+  const ff hod = p.ho ? scale2(ze.dpt, 0.5f) : zero;
+  const ff cs2E = c.gam * ze.pg * ze.iden;
+  const ff third = tconst<ff>(1.0 / 3.0);
+  // heat flux row: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
+  ff Aq = zero, Bq = zero, Cq[4] = {zero, zero, zero, zero};
+  if (p.cond) {
+    const ff chi = phi * cs2E * tau;
+    const ff pre = -(sqr_root(tau * ze.rho * chi) * nr_rcp(ze.theta));  // -rho chi (tau/(chi rho Theta^2))^(1/2)
+    ff acc = zero;
+#pragma unroll
+    for (int m = 0; m < 4; m++) acc += bhu[m] * (ze.v[0] * du[0][m] + ze.v[1] * du[1][m]);
+    Aq = pre * (bhu[1] * dTh[0] + bhu[2] * dTh[1] + ze.theta * acc);
+    Bq = pre * bhu[0];
+    const ff pt = pre * ze.theta * ze.ut;
+#pragma unroll
+    for (int m = 0; m < 4; m++) Cq[m] = pt * bhu[m];
+  }
+  {
+    const ff qtn = ff_split(Pnz[8]);
+    ff src = scale2(qtn * it, 0.5f) - Aq * it + Bq * thn * git - hoq * (divu_sp - utn * idts);
+#pragma unroll
+    for (int m = 0; m < 4; m++) src += Cq[m] * ucovn[m] * git;
+    const double s8 = kU[8] * dts;
+    Kz[(K_C + 8) * N] = s8 * ((divF[8] - Un[8] * idts_d) + ff_join(src));
+    const ff s8f = ff_split(s8), sg = s8f * git;
+    Kz[(K_Q + 0) * N] = ff_join(scale2(s8f * it, 0.5f));
+    Kz[(K_Q + 1) * N] = ff_join(-(sg * Bq));
+#pragma unroll
+    for (int m = 0; m < 4; m++) Kz[(K_Q + 2 + m) * N] = ff_join(-(sg * Cq[m]));
+    Kz[(K_Q + 6) * N] = ff_join(-(s8f * hoq * idts));
+    if (feat) feat[8 * N] = -(s8f * (ff_split(divF[8]) + it * (qtn - Aq) - hoq * divu_sp)).hi;
+  }
+  // anisotropy row: dP~_0 = Ad + Dd^nu (u_nu - u_nu,n)/dt_s + Ed (u^t - u^t_n)/dt_s
+  ff Ad = zero, Dd[4] = {zero, zero, zero, zero}, Ed = zero;
+  if (p.visc) {
+    const ff nu = psi * cs2E * tau;
+    const ff pre = tconst<ff>(3.0) * sqr_root(tau * ze.rho * nu * nr_rcp(ze.theta));  // 3 rho nu (tau/(nu rho Theta))^(1/2)
+    ff sp = zero;
+#pragma unroll
+    for (int m = 0; m < 4; m++) sp += bhu[m] * (bhu[1] * du[0][m] + bhu[2] * du[1][m]);
+    Ad = pre * (sp - divu_sp * third);
+    const ff pb = pre * bhu[0];
+#pragma unroll
+    for (int m = 0; m < 4; m++) Dd[m] = pb * bhu[m];
+    Ed = -(pre * third);
+  }
+  {
+    const ff dptn = ff_split(Pnz[9]);
+    ff src = scale2(dptn * it, 0.5f) - Ad * it + Ed * utn * git - hod * (divu_sp - utn * idts);
+#pragma unroll
+    for (int m = 0; m < 4; m++) src += Dd[m] * ucovn[m] * git;
+    const double s9 = kU[9] * dts;
+    Kz[(K_C + 9) * N] = s9 * ((divF[9] - Un[9] * idts_d) + ff_join(src));
+    const ff s9f = ff_split(s9), sg = s9f * git;
+    Kz[(K_D + 0) * N] = ff_join(scale2(s9f * it, 0.5f));
+#pragma unroll
+    for (int m = 0; m < 4; m++) Kz[(K_D + 1 + m) * N] = ff_join(-(sg * Dd[m]));
+    Kz[(K_D + 5) * N] = ff_join(-(s9f * (Ed * git + hod * idts)));
+    if (feat) feat[9 * N] = -(s9f * (ff_split(divF[9]) + it * (dptn - Ad) - hod * divu_sp)).hi;
+  }
+  // initial guess: P_n (or the given guess) with B from the explicit flux-CT update
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    double x = a.guess ? __ldg(a.guess + v * N + z) : Pnz[v];
+    if (v >= 5 && v <= 7) x = Pnz[v] - dts * divF[v];
+    a.P0[v * N + z] = x;
+  }
+}
+
 // Explicit-stage scratch for an n1 x n2 grid, in doubles: the face arrays,
 // then Theta and u^t of every zone.
 long long face_scratch_doubles(int n1, int n2) {
@@ -542,6 +728,11 @@ void explicit_args(const Params& p, const double* Pn, const double* PE, const do
   for (int k = 0; k < 6; k++) {
     a.ffc[2 * k] = (float)cv[k];
     a.ffc[2 * k + 1] = (float)(cv[k] - (double)(float)cv[k]);
+  }
+  const double cz[9] = {p.idx[0], p.idx[1], p.tauR, p.phi, p.psi, a.itau, a.idts, a.idts * a.itau, dts};
+  for (int k = 0; k < 9; k++) {
+    a.ffz[2 * k] = (float)cz[k];
+    a.ffz[2 * k + 1] = (float)(cz[k] - (double)(float)cz[k]);
   }
   a.K = K; a.P0 = P0;
   a.F1 = faces;
@@ -582,18 +773,28 @@ long long pn_cache_doubles(long long N) { return (long long)NCACHE * N; }
 // of the same step (reads cache and K_U).
 // The float64 form first runs derived_2d; the float-float form recomputes
 // the neighbours' Theta and u^t itself.
-template <bool FFS>
+template <bool MIXED>
 static cudaError_t launch_zone_const_s(const Params& p, const ExpArgs& a, unsigned nb, int bs, cudaStream_t st) {
   switch (bs) {
-    case 64: if (!FFS) derived_2d<64><<<nb, 64, 0, st>>>(p, a); zone_const_2d<64, FFS><<<nb, 64, 0, st>>>(p, a); break;
-    case 128: if (!FFS) derived_2d<128><<<nb, 128, 0, st>>>(p, a); zone_const_2d<128, FFS><<<nb, 128, 0, st>>>(p, a); break;
-    case 256: if (!FFS) derived_2d<256><<<nb, 256, 0, st>>>(p, a); zone_const_2d<256, FFS><<<nb, 256, 0, st>>>(p, a); break;
+    case 64:
+      if (MIXED) zone_const_2d_mixed<64><<<nb, 64, 0, st>>>(p, a);
+      else { derived_2d<64><<<nb, 64, 0, st>>>(p, a); zone_const_2d<64><<<nb, 64, 0, st>>>(p, a); }
+      break;
+    case 128:
+      if (MIXED) zone_const_2d_mixed<128><<<nb, 128, 0, st>>>(p, a);
+      else { derived_2d<128><<<nb, 128, 0, st>>>(p, a); zone_const_2d<128><<<nb, 128, 0, st>>>(p, a); }
+      break;
+    case 256:
+      if (MIXED) zone_const_2d_mixed<256><<<nb, 256, 0, st>>>(p, a);
+      else { derived_2d<256><<<nb, 256, 0, st>>>(p, a); zone_const_2d<256><<<nb, 256, 0, st>>>(p, a); }
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-// ffslopes: the limited slopes in float-float (the mixed solver).
+// ffslopes: the mixed solver's form (zone_const_2d_mixed: the source terms at
+// P^E in float-float) instead of the float64 one.
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
                               double* K, double* P0, double* faces, double* cache, int mode, int bs, float* feat,
                               int ffslopes, cudaStream_t st) {

@@ -122,12 +122,15 @@ __device__ __forceinline__ ff scale2(ff a, float s) { return ff(a.hi * s, a.lo *
 // pipe): a double split into its leading 24 significant bits (hi, truncated)
 // and the float nearest to the remaining 29 (lo); a float widened exactly
 // to double.  Values outside the normal float range take the float64 route.
+// The float64 route, kept out of line so that the compiler cannot predicate
+// its float64 instructions into the common path.
+static __device__ __noinline__ ff ff_split_wide(double d) { return ff(d); }
 __device__ __forceinline__ ff ff_split(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const int e = (int)((b >> 52) & 0x7ff);
   if (e == 0) return ff(0.f, 0.f);
   // fast path for 2^-74 <= |d| < 2^100: every float below stays normal
-  if (e < 1075 - 126 || e > 1023 + 100) return ff(d);
+  if (e < 1075 - 126 || e > 1023 + 100) return ff_split_wide(d);
   const unsigned sign = (unsigned)(b >> 63);
   const unsigned long long m = b & 0xfffffffffffffull;
   const float hi = __uint_as_float((sign << 31) | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
