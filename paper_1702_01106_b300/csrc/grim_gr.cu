@@ -556,82 +556,91 @@ __device__ __forceinline__ void derived_load(const GrArgs& a, const GhostBox& gb
 // the limited slopes of Theta, u_mu and sqrt(-g) u^d from the derived
 // quantities) and the spatial part of nabla_mu u^mu; NSRC doubles a zone.
 constexpr int NSRC = 17;  // Sg (4), Aq, Bq, Cq (4), Ad, Dd (4), Ed, divu_sp
-// FFS: the limited slopes in float-float (the mixed solver, as on the flat
-// path): the generalized minmod of each derived quantity from float-float
-// splits of its three values (about 2 float64 instructions a slope instead
-// of 12; the float64 pipe bounds this kernel).
+// Square root in the sources' working precision: the library's in float64
+// (as before the float-float form existed), the float-float one otherwise.
+__device__ __forceinline__ double src_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ ff src_sqrt(ff x) { return sqr_root(x); }
+
+// FFS: the mixed solver's form.  The sources are explicit terms at P^E, the
+// class the mixed solver's float-float face fluxes belong to: the state in
+// the metric, the limited slopes, the connection contractions, the geometric
+// source and the closure coefficients are evaluated in float-float (T = ff)
+// and each stored source is joined into a double once.  The half step's
+// P_n cache (sqrt(-g) U(P_n) and the P_n quantities) stays float64.
+// Otherwise everything is float64 (T = double).
 template <bool FFS>
-__global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params p, const __grid_constant__ GrArgs a) {
+__global__ void __launch_bounds__(128, FFS ? 4 : 0) sources_gr(const __grid_constant__ Params p, const __grid_constant__ GrArgs a) {
+  using T = typename std::conditional<FFS, ff, double>::type;
   const long long N = p.N;
   const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= N) return;
   const int i = (int)(z % p.n1), j = (int)((z / p.n1) % p.n2), k = (int)(z / ((long long)p.n1 * p.n2));
   const GT g = centre_geo(p, a.gc, i, j);
-  const double sg = g(G_SQRTG), tau = g(G_TAUR);
+  const T sg = from_double<T>(g(G_SQRTG)), tau = from_double<T>(g(G_TAUR));
   double PEz[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) PEz[v] = __ldg(a.PE + v * N + z);
+  const T zero = T(0), third_c = tconst<T>(1.0 / 3.0);
   // --- limited slopes at P^E of Theta, u_mu and sqrt(-g) u^d
-  double dTh[3] = {0.0, 0.0, 0.0}, du[3][4], divu_sp = 0.0;
+  T dTh[3] = {zero, zero, zero}, du[3][4], divu_sp = zero;
 #pragma unroll
   for (int d = 0; d < 3; d++)
 #pragma unroll
-    for (int q = 0; q < 4; q++) du[d][q] = 0.0;
+    for (int q = 0; q < 4; q++) du[d][q] = zero;
   {
     const GhostBox gb = ghost_box(p);
     double th0, u0[4], s0[3];
     derived_load(a, gb, i, j, k, th0, u0, s0);
+    const T theta = from_double<T>(p.theta);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       if (d >= p.dim) continue;
       double thm, thp, um[4], up[4], sm[3], sp[3];
       derived_load(a, gb, i - (d == 0), j - (d == 1), k - (d == 2), thm, um, sm);
       derived_load(a, gb, i + (d == 0), j + (d == 1), k + (d == 2), thp, up, sp);
-      if constexpr (FFS) {
-        const ff theta = ff_split(p.theta);
-        dTh[d] = ff_join(gm_slope(theta, ff_split(thm), ff_split(th0), ff_split(thp))) * p.idx[d];
+      const T ih = from_double<T>(p.idx[d]);
+      dTh[d] = gm_slope(theta, from_double<T>(thm), from_double<T>(th0), from_double<T>(thp)) * ih;
 #pragma unroll
-        for (int q = 0; q < 4; q++)
-          du[d][q] = ff_join(gm_slope(theta, ff_split(um[q]), ff_split(u0[q]), ff_split(up[q]))) * p.idx[d];
-        divu_sp += ff_join(gm_slope(theta, ff_split(sm[d]), ff_split(s0[d]), ff_split(sp[d]))) * p.idx[d];
-      } else {
-        dTh[d] = gm_slope(p.theta, thm, th0, thp) * p.idx[d];
-#pragma unroll
-        for (int q = 0; q < 4; q++) du[d][q] = gm_slope(p.theta, um[q], u0[q], up[q]) * p.idx[d];
-        divu_sp += gm_slope(p.theta, sm[d], s0[d], sp[d]) * p.idx[d];
-      }
+      for (int q = 0; q < 4; q++)
+        du[d][q] = gm_slope(theta, from_double<T>(um[q]), from_double<T>(u0[q]), from_double<T>(up[q])) * ih;
+      divu_sp += gm_slope(theta, from_double<T>(sm[d]), from_double<T>(s0[d]), from_double<T>(sp[d])) * ih;
     }
     divu_sp *= nr_rcp(sg);
   }
   // --- sources at P^E
-  const RC<double> c = make_rc<double>(p);
-  Met<double> m;
+  RC<T> c;
+  T kk;
+  gr_consts(p, a, c, kk);
+  Met<T> m;
   met_load(m, g);
-  ZG<double> ze;
-  zg_load(ze, PEz, m, c);
-  const double cs2E = p.gamma * ze.pg * nr_rcp(ze.rho + p.gamma * ze.u);
-  const double ith = nr_rcp(ze.theta);
-  const double* bh = ze.bhcon;
+  T PEt[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) PEt[v] = from_double<T>(PEz[v]);
+  ZG<T> ze;
+  zg_load(ze, PEt, m, c);
+  const T cs2E = c.gam * ze.pg * nr_rcp(ze.rho + c.gam * ze.u);
+  const T ith = nr_rcp(ze.theta);
+  const T* bh = ze.bhcon;
   // Gl[sym(mu, nu)] = sum_l Gamma^l_{mu nu} u_l and Gb[sym(mu, nu)] = sum_l
   // Gamma^l_{mu nu} bhat_l at P^E (symmetric in mu, nu), and from Gl the sum
   // over nu, l of Gamma^l_{nu mu} u^nu u_l for each mu
-  double Gl[10], Gb[10];
+  T Gl[10], Gb[10];
 #pragma unroll
   for (int a = 0; a < 10; a++) {
-    double s = 0.0, t = 0.0;
+    T s = zero, t = zero;
 #pragma unroll
     for (int l = 0; l < 4; l++) {
-      const double G = g(G_GAM + 10 * l + a);
+      const T G = from_double<T>(g(G_GAM + 10 * l + a));
       s += G * ze.ucov[l];
       t += G * ze.bhcov[l];
     }
     Gl[a] = s;
     Gb[a] = t;
   }
-  double Gu[4];
+  T Gu[4];
 #pragma unroll
   for (int mu = 0; mu < 4; mu++) {
-    double s = 0.0;
+    T s = zero;
 #pragma unroll
     for (int nu = 0; nu < 4; nu++) s += Gl[sym(nu, mu)] * ze.ucon[nu];
     Gu[mu] = s;
@@ -640,77 +649,86 @@ __global__ void __launch_bounds__(128) sources_gr(const __grid_constant__ Params
   // with T^k_l of Eq. fullSEtens taken apart: (w + b^2 + dP/3) u^k u_l +
   // p_t delta^k_l - b^2 bhat^k bhat_l + q (bhat^k u_l + u^k bhat_l) - dP
   // bhat^k bhat_l, so that each part contracts Gamma with the vectors alone
-  double Sg[4];
+  T Sg[4];
   {
-    const double q = ze.qt * ze.qs, dp = ze.dpt * ze.ds, third = dp * (1.0 / 3.0);
-    const double A = ze.w0 + ze.bsq + third, pt = ze.pg + 0.5 * ze.bsq + third;
+    const T q = ze.qt * ze.qs, dp = ze.dpt * ze.ds, third = dp * third_c;
+    const T A = ze.w0 + ze.bsq + third, pt = ze.pg + tconst<T>(0.5) * ze.bsq + third;
 #pragma unroll
     for (int n = 0; n < 4; n++) {
-      double bGl = 0.0, uGb = 0.0, bGb = 0.0, tr = 0.0;
+      T bGl = zero, uGb = zero, bGb = zero, tr = zero;
 #pragma unroll
-      for (int kk = 0; kk < 4; kk++) {
-        bGl += bh[kk] * Gl[sym(n, kk)];
-        uGb += ze.ucon[kk] * Gb[sym(n, kk)];
-        bGb += bh[kk] * Gb[sym(n, kk)];
-        tr += g(G_GAM + 10 * kk + sym(n, kk));   // Gamma^k_{n k}
+      for (int kk2 = 0; kk2 < 4; kk2++) {
+        bGl += bh[kk2] * Gl[sym(n, kk2)];
+        uGb += ze.ucon[kk2] * Gb[sym(n, kk2)];
+        bGb += bh[kk2] * Gb[sym(n, kk2)];
+        tr += from_double<T>(g(G_GAM + 10 * kk2 + sym(n, kk2)));  // Gamma^k_{n k}
       }
       Sg[n] = sg * (A * Gu[n] + pt * tr + q * (bGl + uGb) - (ze.bsq + dp) * bGb);
     }
   }
   // heat flux: q~_0 = Aq + Bq (Theta - Theta_n)/dt_s + Cq^mu (u_mu - u_mu,n)/dt_s
-  double Aq = 0.0, Bq = 0.0, Cq[4] = {0.0, 0.0, 0.0, 0.0};
+  T Aq = zero, Bq = zero, Cq[4] = {zero, zero, zero, zero};
   if (p.cond) {
-    const double chi = p.phi * cs2E * tau;
-    const double pre = -sqrt(tau * ze.rho * chi) * ith;
-    double acc = 0.0;
-    #pragma unroll
+    const T chi = from_double<T>(p.phi) * cs2E * tau;
+    const T pre = -(src_sqrt(tau * ze.rho * chi) * ith);
+    T acc = zero;
+#pragma unroll
     for (int mu = 0; mu < 4; mu++) {
-      double a_sp = -Gu[mu];
-      #pragma unroll
+      T a_sp = -Gu[mu];
+#pragma unroll
       for (int d = 0; d < 3; d++) a_sp += ze.ucon[d + 1] * du[d][mu];
       acc += bh[mu] * a_sp;
     }
     Aq = pre * (bh[1] * dTh[0] + bh[2] * dTh[1] + bh[3] * dTh[2] + ze.theta * acc);
     Bq = pre * bh[0];
-    #pragma unroll
+#pragma unroll
     for (int mu = 0; mu < 4; mu++) Cq[mu] = pre * ze.theta * bh[mu] * ze.ucon[0];
   }
   // anisotropy: dP~_0 = Ad + Dd^nu (u_nu - u_nu,n)/dt_s + Ed (u^t - u^t_n)/dt_s
-  double Ad = 0.0, Dd[4] = {0.0, 0.0, 0.0, 0.0}, Ed = 0.0;
+  T Ad = zero, Dd[4] = {zero, zero, zero, zero}, Ed = zero;
   if (p.visc) {
-    const double nu = p.psi * cs2E * tau;
-    const double pre = 3.0 * sqrt(tau * ze.rho * nu * ith);
-    double sp = 0.0;
-    #pragma unroll
+    const T nu = from_double<T>(p.psi) * cs2E * tau;
+    const T pre = tconst<T>(3.0) * src_sqrt(tau * ze.rho * nu * ith);
+    T sp = zero;
+#pragma unroll
     for (int mu = 0; mu < 4; mu++)
-      #pragma unroll
+#pragma unroll
       for (int nn = 0; nn < 4; nn++) {
-        double nab = 0.0;
+        T nab = zero;
         if (mu >= 1) nab = du[mu - 1][nn];
         nab -= Gl[sym(mu, nn)];
         sp += bh[mu] * bh[nn] * nab;
       }
-    Ad = pre * (sp - divu_sp * (1.0 / 3.0));
-    #pragma unroll
+    Ad = pre * (sp - divu_sp * third_c);
+#pragma unroll
     for (int nn = 0; nn < 4; nn++) Dd[nn] = pre * bh[0] * bh[nn];
-    Ed = -pre * (1.0 / 3.0);
+    Ed = -(pre * third_c);
   }
   double* Sz = a.Src + z;
-  const double x[NSRC] = {Sg[0], Sg[1], Sg[2], Sg[3], Aq, Bq, Cq[0], Cq[1], Cq[2], Cq[3],
-                          Ad, Dd[0], Dd[1], Dd[2], Dd[3], Ed, divu_sp};
+  const T x[NSRC] = {Sg[0], Sg[1], Sg[2], Sg[3], Aq, Bq, Cq[0], Cq[1], Cq[2], Cq[3],
+                     Ad, Dd[0], Dd[1], Dd[2], Dd[3], Ed, divu_sp};
 #pragma unroll
-  for (int q = 0; q < NSRC; q++) Sz[q * N] = x[q];
+  for (int q = 0; q < NSRC; q++) Sz[q * N] = as_double(x[q]);
   if (a.mode == 1) {
     // the half step's P^E is P_n: its quantities go to the step's P_n cache
-    // for the zone-constant kernels of both stages
+    // for the zone-constant kernels of both stages, in float64
+    ZG<double> zn;
+    if constexpr (FFS) {
+      Met<double> m64;
+      met_load(m64, g);
+      zg_load(zn, PEz, m64, make_rc<double>(p));
+    } else {
+      zn = ze;
+    }
     double U[NV];
-    zg_conserved(ze, U);
+    zg_conserved(zn, U);
+    const double sgd = g(G_SQRTG);
 #pragma unroll
-    for (int v = 0; v < NV; v++) a.cache[v * N + z] = sg * U[v];
-    a.cache[NV * N + z] = ze.theta;
+    for (int v = 0; v < NV; v++) a.cache[v * N + z] = sgd * U[v];
+    a.cache[NV * N + z] = zn.theta;
 #pragma unroll
-    for (int q = 0; q < 4; q++) a.cache[(NV + 1 + q) * N + z] = ze.ucov[q];
-    a.cache[(NV + 5) * N + z] = ze.ucon[0];
+    for (int q = 0; q < 4; q++) a.cache[(NV + 1 + q) * N + z] = zn.ucov[q];
+    a.cache[(NV + 5) * N + z] = zn.ucon[0];
   }
 }
 
