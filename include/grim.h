@@ -422,16 +422,6 @@ int grim_set_guess(grim_ctx* ctx, grim_mlp* mlp, double accept);
  * *max_rel_err.  Allocates and frees a small device buffer; synchronises the
  * device. */
 int grim_math_selftest(int n, double* max_rel_err);
-/* Self-check of the float64 1/sqrt and sqrt the kernels use (a float
- * estimate refined by one second-order step of the binomial series, with
- * the library functions for zero, denormal, negative and non-finite
- * arguments): over n >= 8 seeded positive values spanning 2^-300..2^300,
- * the largest relative differences from IEEE division of 1 by IEEE sqrt
- * (*max_rel_rsq) and from IEEE sqrt (*max_rel_sqrt); and the number of
- * eight special arguments whose results differ from the library's bit for
- * bit (*special_mismatches).  Allocates and frees a small device buffer;
- * synchronises the device. */
-int grim_root_selftest(int n, double* max_rel_rsq, double* max_rel_sqrt, int* special_mismatches);
 
 #ifdef __cplusplus
 }

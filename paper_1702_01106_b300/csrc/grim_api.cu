@@ -18,7 +18,6 @@ cudaError_t launch_newton(const Params& p, int mixed, const double* K, double* P
 cudaError_t launch_residual(const Params& p, const double* K, const double* Pk, int scaled, double dts, double* R,
                             cudaStream_t st);
 cudaError_t launch_rcp_check(int n, unsigned long long seed, double* worst, cudaStream_t st);
-cudaError_t launch_root_check(int n, unsigned long long seed, unsigned long long* out, cudaStream_t st);
 long long face_scratch_doubles(int n1, int n2);
 cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, int ffstates, cudaStream_t st);
 cudaError_t launch_zone_const(const Params& p, const double* Pn, const double* PE, const double* guess, double dts,
@@ -693,22 +692,6 @@ int grim_kernel_times(grim_ctx* ctx, double* ms, unsigned long long* launches) {
 int grim_reset_stats(grim_ctx* ctx) {
   if (!ctx) return GRIM_EINVAL;
   GRIM_CUDA(cudaMemsetAsync(ctx->cnt, 0, sizeof(grim::Counters), ctx->stream), "stats reset");
-  return GRIM_OK;
-}
-
-int grim_root_selftest(int n, double* max_rel_rsq, double* max_rel_sqrt, int* special_mismatches) {
-  if (n < 8 || !max_rel_rsq || !max_rel_sqrt || !special_mismatches) return GRIM_EINVAL;
-  unsigned long long* d = nullptr;
-  if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return GRIM_ENOMEM;
-  unsigned long long h[3] = {0, 0, 0};
-  cudaError_t e = cudaMemset(d, 0, sizeof(h));
-  if (e == cudaSuccess) e = grim::launch_root_check(n, 6789ull, d, 0);
-  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  if (e != cudaSuccess) return GRIM_ECUDA;
-  std::memcpy(max_rel_rsq, &h[0], sizeof(double));
-  std::memcpy(max_rel_sqrt, &h[1], sizeof(double));
-  *special_mismatches = (int)h[2];
   return GRIM_OK;
 }
 

@@ -867,37 +867,6 @@ __global__ void rcp_check(int n, unsigned long long seed, double* worst) {
   atomicMax((unsigned long long*)worst, (unsigned long long)__double_as_longlong(rel));
 }
 
-// Float64 rsq and sqr_root against IEEE sqrt and division: n seeded
-// positive arguments spanning 2^-300..2^300 (largest relative differences
-// in out[0], out[1] as double bit patterns), and eight special arguments
-// (zero, denormals, a negative, infinity, NaN and two exact squares) that
-// must give the library's results bit for bit (mismatches counted in out[2]).
-__global__ void root_check(int n, unsigned long long seed, unsigned long long* out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 8) {
-    const double sp[8] = {0.0, 4.9e-324, 1e-310, -1.0, __longlong_as_double(0x7ff0000000000000ll),
-                          __longlong_as_double(0x7ff8000000000000ll), 1.0, 4.0};
-    const double x = sp[t];
-    const double a = rsq(x), b = rsqrt(x), c = sqr_root(x), d = sqrt(x);
-    const bool same = (a == b || (a != a && b != b)) && (c == d || (c != c && d != d));
-    if (!same) atomicAdd(out + 2, 1ull);
-  }
-  if (t >= n) return;
-  unsigned long long s = seed + 0x9e3779b97f4a7c15ull * (unsigned long long)(t + 1);
-  s ^= s >> 33; s *= 0xff51afd7ed558ccdull; s ^= s >> 33;
-  const double m = 1.0 + (double)(s >> 11) * (1.0 / 9007199254740992.0);
-  const int e = (int)((s >> 3) % 601) - 300;
-  const double x = ldexp(m, e);
-  const double rs = sqrt(x), rr = 1.0 / rs;
-  const double er = fabs(rsq(x) - rr) / rr, es = fabs(sqr_root(x) - rs) / rs;
-  atomicMax(out, (unsigned long long)__double_as_longlong(er));
-  atomicMax(out + 1, (unsigned long long)__double_as_longlong(es));
-}
-cudaError_t launch_root_check(int n, unsigned long long seed, unsigned long long* out, cudaStream_t st) {
-  root_check<<<(n + 255) / 256, 256, 0, st>>>(n, seed, out);
-  return cudaGetLastError();
-}
-
 template <bool MIXED, int BS, bool IDEAL> struct NewtonKernels {
   using S = NewtonSmem<MIXED, BS>;
   // the kernels' shared-memory limit and the queue kernel's persistent grid

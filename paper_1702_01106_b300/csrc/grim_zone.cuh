@@ -21,48 +21,9 @@ __device__ __forceinline__ double nr_rcp(double x) {
   return fma(r, e, r);
 }
 __device__ __forceinline__ float nr_rcp(float x) { return __frcp_rn(x); }
-// Float64 1/sqrt(x) and sqrt(x) for positive normal x, within about two
-// units in the last place: x = xs 2^(2k) with xs in [1, 4) (an exact shift
-// of the exponent), the float estimate y0 of 1/sqrt(xs), and one
-// second-order step of the binomial series
-//   1/sqrt(xs) = y0 (1 - r)^(-1/2) = y0 (1 + r/2 + 3 r^2/8 + O(r^3)),
-//   r = 1 - xs y0^2,
-// whose truncation (|r| ~ 2^-22, so r^3 ~ 2^-66) lies far below the float64
-// rounding; sqrt(xs) = xs/sqrt(xs) takes the same factor.  Five float64
-// instructions each; the scale 2^(-k) (or 2^k) goes back into the exponent
-// by integer arithmetic.  Zero, denormal, negative and non-finite arguments
-// take the library functions out of line (so that their float64 work is
-// never predicated into the common path).  Checked against IEEE sqrt and
-// division by grim_root_selftest.
-static __device__ __noinline__ double rsq_wide(double x) { return rsqrt(x); }
-static __device__ __noinline__ double sqrt_wide(double x) { return sqrt(x); }
-// xs, y0 and the correction factor c = r (1/2 + 3 r/8); returns false for
-// the arguments the fast form does not take.
-__device__ __forceinline__ bool root_core(double x, double& xs, double& y0, double& c, int& k) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff);
-  if (b < 0 || e == 0 || e == 0x7ff) return false;
-  k = (e - 1023) >> 1;  // floor((e - 1023) / 2)
-  xs = __longlong_as_double(b - ((long long)(2 * k) << 52));
-  y0 = f2d_jac(rsqrtf(d2f_jac(xs)));
-  const double r = fma(-(xs * y0), y0, 1.0);
-  c = r * fma(0.375, r, 0.5);
-  return true;
-}
-__device__ __forceinline__ double rsq(double x) {
-  double xs, y0, c;
-  int k;
-  if (!root_core(x, xs, y0, c, k)) return rsq_wide(x);
-  return __longlong_as_double(__double_as_longlong(fma(y0, c, y0)) - ((long long)k << 52));
-}
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double sqr_root(double x) {
-  double xs, y0, c;
-  int k;
-  if (!root_core(x, xs, y0, c, k)) return sqrt_wide(x);
-  const double s = xs * y0;
-  return __longlong_as_double(__double_as_longlong(fma(s, c, s)) + ((long long)k << 52));
-}
+__device__ __forceinline__ double sqr_root(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqr_root(float x) { return sqrtf(x); }
 // |x| as an unsigned integer: ordered like |x| for every non-NaN value.
 __device__ __forceinline__ unsigned long long abits(double x) {

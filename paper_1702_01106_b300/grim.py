@@ -25,7 +25,7 @@ EXPORTS = (
     "grim_profile", "grim_kernel_times", "grim_step_static", "grim_step_static_stats", "grim_math_selftest",
     "grim_mlp_create", "grim_mlp_destroy", "grim_mlp_param_count", "grim_mlp_get_params", "grim_mlp_set_params",
     "grim_mlp_fit_norm", "grim_mlp_train", "grim_mlp_gradient", "grim_mlp_sample", "grim_set_guess",
-    "grim_gemm_nt_bf16", "grim_root_selftest",
+    "grim_gemm_nt_bf16",
     "grim_get_tuning", "grim_set_tuning", "grim_autotune", "grim_use_graphs",
     "grim_batch_init", "grim_batch_destroy", "grim_batch_context", "grim_batch_step", "grim_batch_use_graphs",
     "grim_batch_get_stats", "grim_batch_reset_stats", "grim_batch_last_error",
@@ -108,7 +108,6 @@ def load():
     lib.grim_step_static_stats.argtypes = [vp, ctypes.POINTER(GrimStats)]
     lib.grim_profile.argtypes = [vp, i]
     lib.grim_math_selftest.argtypes = [i, ctypes.POINTER(dp)]
-    lib.grim_root_selftest.argtypes = [i, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(i)]
     ll, ull, fp = ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)
     lib.grim_mlp_create.argtypes = [ull, ctypes.POINTER(vp)]
     lib.grim_mlp_destroy.argtypes = [vp]
@@ -406,18 +405,6 @@ def gemm_nt_bf16(A, B, splits: int = 0, out=None):
     if rc != 0:
         raise RuntimeError(f"grim_gemm_nt_bf16 failed: {lib.grim_strerror(rc).decode()}")
     return C
-
-
-def root_selftest(n: int = 1 << 20):
-    """Largest relative differences of the kernels' float64 1/sqrt and sqrt
-    from IEEE, and the count of special arguments that differ from the
-    library's results."""
-    lib = load()
-    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
-    rc = lib.grim_root_selftest(n, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
-    if rc != 0:
-        raise RuntimeError(f"grim_root_selftest failed: {lib.grim_strerror(rc).decode()}")
-    return a.value, b.value, c.value
 
 
 class MLP:

@@ -177,18 +177,6 @@ def test_reciprocal_matches_ieee_division(dev):
     assert math_selftest(1 << 20) <= 2.0 ** -52
 
 
-def test_roots_match_ieee(dev):
-    """The float64 1/sqrt and sqrt of the zone state (a float estimate and one
-    second-order step of the binomial series, truncation ~2^-66) stay within
-    2^-51 of IEEE sqrt and of 1 divided by it (itself two roundings) over
-    2^-300..2^300; zero, denormal, negative and non-finite arguments give the
-    library's results exactly."""
-    from paper_1702_01106_b300.grim import root_selftest
-    er, es, bad = root_selftest(1 << 20)
-    assert er <= 2.0 ** -51 and es <= 2.0 ** -51, (er, es)
-    assert bad == 0
-
-
 @pytest.mark.parametrize("bc", [((1, 1), (2, 2), (0, 0)), ((2, 1), (0, 0), (0, 0)), ((0, 0), (1, 2), (0, 0))])
 def test_stage_parity_non_periodic_boundaries(dev, orc, bc):
     """Outflow (copy) and reflecting boundaries applied by the tile/face loaders."""
