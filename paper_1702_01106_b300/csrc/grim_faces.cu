@@ -175,8 +175,10 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   // reconstruction, then the face states in the state precision.  MC runs
   // in the state precision (the limiter is continuous in its arguments, so
   // a decision that differs from float64 at a near-tie moves the face value
-  // by no more than the rounding); WENO5 and PPM run in float64.
-  S Ls[NV], Rs[NV];
+  // by no more than the rounding); WENO5 and PPM run in float64.  The paired
+  // form (S = ff2) reconstructs in float-float and pairs the two states.
+  using SR = typename std::conditional<std::is_same<S, double>::value, double, ff>::type;
+  SR Ls[NV], Rs[NV];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     if constexpr (!std::is_same<S, double>::value && RECON == RECON_MC) {
@@ -206,10 +208,37 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
         L = fma(0.5, gm_slope(p.theta, s[1], s[2], s[3]), s[2]);
         R = fma(-0.5, gm_slope(p.theta, s[2], s[3], s[4]), s[3]);
       }
-      Ls[v] = from_double<S>(L);
-      Rs[v] = from_double<S>(R);
+      Ls[v] = from_double<SR>(L);
+      Rs[v] = from_double<SR>(R);
     }
   }
+  if constexpr (std::is_same<S, ff2>::value) {
+    // both face states in one paired instruction stream (lane x: left,
+    // lane y: right); the Riemann combination takes the lanes apart
+    RC<ff2> c;
+    c.gam = ff2(ff(a.ffc[0], a.ffc[1]), ff(a.ffc[0], a.ffc[1]));
+    c.gm1 = ff2(ff(a.ffc[2], a.ffc[3]), ff(a.ffc[2], a.ffc[3]));
+    c.sphig = ff2(ff(a.ffc[4], a.ffc[5]), ff(a.ffc[4], a.ffc[5]));
+    c.spsig = ff2(ff(a.ffc[6], a.ffc[7]), ff(a.ffc[6], a.ffc[7]));
+    c.cond = p.cond;
+    c.visc = p.visc;
+    const ff2 kg(ff(a.ffc[8], a.ffc[9]), ff(a.ffc[8], a.ffc[9]));
+    ff2 P2[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) P2[v] = ff2(Ls[v], Rs[v]);
+    Z<ff2> z2;
+    z_load(z2, P2, c);
+    ff2 U2[NV], F2[NV], cmin2, cmax2;
+    side_flux<D + 1>(z2, c.gam, kg, U2, F2, cmin2, cmax2);
+    ff UL[NV], FL[NV], UR[NV], FR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      UL[v] = U2[v].x(); UR[v] = U2[v].y();
+      FL[v] = F2[v].x(); FR[v] = F2[v].y();
+    }
+    riemann_flux<ff>(p.riemann, FL, FR, UL, UR, cmin2.x(), cmax2.x(), cmin2.y(), cmax2.y(), out, plane);
+    return;
+  } else {
   // face states and fluxes in the state precision S (float64, or
   // float-float for the mixed solver)
   RC<S> c;
@@ -236,13 +265,14 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   side_flux<D + 1>(zl, gam, kg, UL, FL, cminL, cmaxL);
   side_flux<D + 1>(zr, gam, kg, UR, FR, cminR, cmaxR);
   riemann_flux<S>(p.riemann, FL, FR, UL, UR, cminL, cmaxL, cminR, cmaxR, out, plane);
+  }
 }
 
 // One kernel per reconstruction, so that each holds only its own registers.
 // The float-float form is held to 128 registers a thread (16 warps per SM),
 // for the latency of its dependent float chains.
 template <int BS, typename S, int RECON>
-__global__ void __launch_bounds__(BS, std::is_same<S, ff>::value ? 65536 / (BS * 128) : 1) face_flux_2d(const __grid_constant__ Params p,
+__global__ void __launch_bounds__(BS, std::is_same<S, double>::value ? 1 : 65536 / (BS * 128)) face_flux_2d(const __grid_constant__ Params p,
                                                   const __grid_constant__ ExpArgs a) {
   const long long nf1 = (long long)(p.n1 + 1) * (p.n2 + 2);
   const long long nf2 = (long long)(p.n1 + 2) * (p.n2 + 1);
@@ -758,13 +788,14 @@ static cudaError_t launch_faces_s(const Params& p, const ExpArgs& a, unsigned nb
 }
 
 // bs: threads per block, 64, 128 or 256.  ffstates: face states and fluxes
-// in float-float (the mixed solver) instead of float64.
+// in float-float, both states of a face in paired lanes (the mixed solver),
+// instead of float64.
 cudaError_t launch_faces(const Params& p, const double* PE, double* faces, int bs, int ffstates, cudaStream_t st) {
   ExpArgs a;
   explicit_args(p, nullptr, PE, nullptr, 1.0, nullptr, nullptr, faces, a);
   const long long nf = (long long)(p.n1 + 1) * (p.n2 + 2) + (long long)(p.n1 + 2) * (p.n2 + 1);
   const unsigned nb = (unsigned)((nf + bs - 1) / bs);
-  return ffstates ? launch_faces_s<ff>(p, a, nb, bs, st) : launch_faces_s<double>(p, a, nb, bs, st);
+  return ffstates ? launch_faces_s<ff2>(p, a, nb, bs, st) : launch_faces_s<double>(p, a, nb, bs, st);
 }
 
 long long pn_cache_doubles(long long N) { return (long long)NCACHE * N; }

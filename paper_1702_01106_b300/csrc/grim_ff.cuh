@@ -198,4 +198,84 @@ __device__ __forceinline__ ff gm_slope(ff theta, ff vm, ff v0, ff vp) {
   return a.hi > 0.f ? m : -m;
 }
 
+// ---------------------------------------------------------------- paired lanes
+// Two float-float values evaluated together (lane x and lane y: the left and
+// right states of a face), on Blackwell's paired float32 instructions: FADD2,
+// FMUL2 and FFMA2 act on both lanes of a float2 at once, so the same
+// error-free transformations as ff above take one instruction stream for
+// two values.  Square roots, reciprocals and comparisons act lane by lane.
+struct ff2 {
+  float2 hi, lo;
+  ff2() = default;
+  __host__ __device__ constexpr ff2(float hx, float hy, float lx, float ly) : hi{hx, hy}, lo{lx, ly} {}
+  __device__ __forceinline__ ff2(float2 h, float2 l) : hi(h), lo(l) {}
+  __device__ __forceinline__ ff2(ff a, ff b) : hi(make_float2(a.hi, b.hi)), lo(make_float2(a.lo, b.lo)) {}
+  __device__ __forceinline__ explicit ff2(int i) : hi(make_float2((float)i, (float)i)), lo(make_float2(0.f, 0.f)) {}
+  __device__ __forceinline__ ff x() const { return ff(hi.x, lo.x); }
+  __device__ __forceinline__ ff y() const { return ff(hi.y, lo.y); }
+};
+template <> __host__ __device__ constexpr ff2 tconst<ff2>(double x) {
+  return ff2(static_cast<float>(x), static_cast<float>(x), static_cast<float>(x - static_cast<double>(static_cast<float>(x))),
+             static_cast<float>(x - static_cast<double>(static_cast<float>(x))));
+}
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// s + e with |s| >= |e| in each lane: the normalised pairs (ff_quick).
+__device__ __forceinline__ ff2 ff2_quick(float2 s, float2 e) {
+  const float2 h = add2(s, e);
+  return ff2(h, sub2(e, sub2(h, s)));
+}
+__device__ __forceinline__ ff2 operator-(ff2 a) { return ff2(neg2(a.hi), neg2(a.lo)); }
+// Dekker's sum as for ff: Knuth's two-sum of the leading parts, the low
+// parts added in plain float.
+__device__ __forceinline__ ff2 operator+(ff2 x, ff2 y) {
+  const float2 s = add2(x.hi, y.hi);
+  const float2 v = sub2(s, x.hi);
+  const float2 e = add2(sub2(x.hi, sub2(s, v)), sub2(y.hi, v));
+  return ff2_quick(s, add2(e, add2(x.lo, y.lo)));
+}
+__device__ __forceinline__ ff2 operator-(ff2 x, ff2 y) { return x + (-y); }
+__device__ __forceinline__ ff2 operator*(ff2 x, ff2 y) {
+  const float2 p = mul2(x.hi, y.hi);
+  float2 e = fma2(x.hi, y.hi, neg2(p));
+  e = fma2(x.hi, y.lo, e);
+  e = fma2(x.lo, y.hi, e);
+  return ff2_quick(p, e);
+}
+__device__ __forceinline__ ff2& operator+=(ff2& a, ff2 b) { a = a + b; return a; }
+__device__ __forceinline__ ff2& operator-=(ff2& a, ff2 b) { a = a - b; return a; }
+__device__ __forceinline__ ff2& operator*=(ff2& a, ff2 b) { a = a * b; return a; }
+
+__device__ __forceinline__ ff2 fmax(ff2 a, ff2 b) { return ff2(fmax(a.x(), b.x()), fmax(a.y(), b.y())); }
+__device__ __forceinline__ ff2 fmin(ff2 a, ff2 b) { return ff2(fmin(a.x(), b.x()), fmin(a.y(), b.y())); }
+__device__ __forceinline__ ff2 fabs(ff2 a) { return ff2(fabs(a.x()), fabs(a.y())); }
+// Lane by lane: keep lane x where kx, lane y where ky, zero elsewhere.
+__device__ __forceinline__ ff2 keep(ff2 a, bool kx, bool ky) {
+  return ff2(make_float2(kx ? a.hi.x : 0.f, ky ? a.hi.y : 0.f), make_float2(kx ? a.lo.x : 0.f, ky ? a.lo.y : 0.f));
+}
+__device__ __forceinline__ ff2 scale2(ff2 a, float2 s) { return ff2(mul2(a.hi, s), mul2(a.lo, s)); }
+
+// 1/y, sqrt(a) and a^(-1/2) as for ff, each lane's float estimate refined
+// by the paired float-float step.
+__device__ __forceinline__ ff2 nr_rcp(ff2 y) {
+  const ff2 x(make_float2(__frcp_rn(y.hi.x), __frcp_rn(y.hi.y)), make_float2(0.f, 0.f));
+  return x + x * (tconst<ff2>(1.0) - y * x);
+}
+__device__ __forceinline__ ff2 sqr_root(ff2 a) {
+  const bool px = a.hi.x > 0.f, py = a.hi.y > 0.f;
+  const float2 s = make_float2(px ? __fsqrt_rn(a.hi.x) : 1.f, py ? __fsqrt_rn(a.hi.y) : 1.f);
+  const ff2 S(s, make_float2(0.f, 0.f));
+  const ff2 r = a - S * S;
+  return keep(ff2_quick(s, mul2(r.hi, make_float2(0.5f / s.x, 0.5f / s.y))), px, py);
+}
+__device__ __forceinline__ ff2 rsq(ff2 a) {
+  const ff2 y(make_float2(rsqrtf(a.hi.x), rsqrtf(a.hi.y)), make_float2(0.f, 0.f));
+  return y + (y * tconst<ff2>(0.5)) * (tconst<ff2>(1.0) - (a * y) * y);
+}
+
 }  // namespace grim

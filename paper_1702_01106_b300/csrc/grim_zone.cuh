@@ -144,7 +144,24 @@ template <typename T> __device__ __forceinline__ void z_mag(Z<T>& z) {
   z.bt = z.B[0] * z.v[0] + z.B[1] * z.v[1] + z.B[2] * z.v[2];
 #pragma unroll
   for (int i = 0; i < 3; i++) z.bc[i] = (z.B[i] + z.bt * z.v[i]) * z.iut;
-  if constexpr (std::is_same<T, ff>::value) {
+  if constexpr (std::is_same<T, ff2>::value) {
+    // the same as for ff below, with a power of two for each lane
+    const float mx = fmaxf(fmaxf(fabsf(z.bt.hi.x), fabsf(z.bc[0].hi.x)), fmaxf(fabsf(z.bc[1].hi.x), fabsf(z.bc[2].hi.x)));
+    const float my = fmaxf(fmaxf(fabsf(z.bt.hi.y), fabsf(z.bc[0].hi.y)), fmaxf(fabsf(z.bc[1].hi.y), fabsf(z.bc[2].hi.y)));
+    float2 s, r;
+    pow2_scale(mx, s.x, r.x);
+    pow2_scale(my, s.y, r.y);
+    const ff2 t = scale2(z.bt, s), c0 = scale2(z.bc[0], s), c1 = scale2(z.bc[1], s), c2 = scale2(z.bc[2], s);
+    const ff2 q = c0 * c0 + c1 * c1 + c2 * c2 - t * t;
+    z.bsq = scale2(scale2(q, r), r);
+    const bool px = q.hi.x > 0.f, py = q.hi.y > 0.f;
+    const ff2 ib = rsq(ff2(make_float2(px ? q.hi.x : 1.f, py ? q.hi.y : 1.f),
+                           make_float2(px ? q.lo.x : 0.f, py ? q.lo.y : 0.f)));
+    z.bht = keep(t * ib, px, py);
+    z.bh[0] = keep(c0 * ib, px, py);
+    z.bh[1] = keep(c1 * ib, px, py);
+    z.bh[2] = keep(c2 * ib, px, py);
+  } else if constexpr (std::is_same<T, ff>::value) {
     // b^2 of a weak field leaves the float range: b^2 and bhat from b scaled
     // by a power of two
     const float m = fmaxf(fmaxf(fabsf(z.bt.hi), fabsf(z.bc[0].hi)), fmaxf(fabsf(z.bc[1].hi), fabsf(z.bc[2].hi)));
@@ -161,17 +178,17 @@ template <typename T> __device__ __forceinline__ void z_mag(Z<T>& z) {
       z.bht = T(0);
       z.bh[0] = z.bh[1] = z.bh[2] = T(0);
     }
-    return;
-  }
-  z.bsq = z.bc[0] * z.bc[0] + z.bc[1] * z.bc[1] + z.bc[2] * z.bc[2] - z.bt * z.bt;
-  if (z.bsq > T(0)) {
-    const T ib = rsq(z.bsq);
-    z.bht = z.bt * ib;
-#pragma unroll
-    for (int i = 0; i < 3; i++) z.bh[i] = z.bc[i] * ib;
   } else {
-    z.bht = T(0);
-    z.bh[0] = z.bh[1] = z.bh[2] = T(0);
+    z.bsq = z.bc[0] * z.bc[0] + z.bc[1] * z.bc[1] + z.bc[2] * z.bc[2] - z.bt * z.bt;
+    if (z.bsq > T(0)) {
+      const T ib = rsq(z.bsq);
+      z.bht = z.bt * ib;
+#pragma unroll
+      for (int i = 0; i < 3; i++) z.bh[i] = z.bc[i] * ib;
+    } else {
+      z.bht = T(0);
+      z.bh[0] = z.bh[1] = z.bh[2] = T(0);
+    }
   }
 }
 template <typename T> __device__ __forceinline__ void z_load(Z<T>& z, const T* P, const RC<T>& c) {
