@@ -179,9 +179,22 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
   // form (S = ff2) reconstructs in float-float and pairs the two states.
   using SR = typename std::conditional<std::is_same<S, double>::value, double, ff>::type;
   SR Ls[NV], Rs[NV];
+  ff2 P2mc[std::is_same<S, ff2>::value && RECON == RECON_MC ? NV : 1];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    if constexpr (!std::is_same<S, double>::value && RECON == RECON_MC) {
+    if constexpr (std::is_same<S, ff2>::value && RECON == RECON_MC) {
+      // both zones' limited slopes in paired lanes: P^- = t1 + s_1/2 (lane
+      // x), P^+ = t2 - s_2/2 (lane y)
+      const ff theta(a.ffc[10], a.ffc[11]);
+      ff t[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        t[k] = ff_split(__ldg(a.PE + v * N + zz[k + 1]));
+        if (comp_flips(v, fa[k + 1], fb[k + 1])) t[k] = -t[k];
+      }
+      const ff2 sl = gm_slope2(theta, ff2(t[0], t[1]), ff2(t[1], t[2]), ff2(t[2], t[3]));
+      P2mc[v] = ff2(t[1], t[2]) + scale2(sl, make_float2(0.5f, -0.5f));
+    } else if constexpr (!std::is_same<S, double>::value && RECON == RECON_MC) {
       const ff theta(a.ffc[10], a.ffc[11]);
       ff t[4];
 #pragma unroll
@@ -225,7 +238,10 @@ __device__ __forceinline__ void face_flux_dir(const Params& p, const ExpArgs& a,
     const ff2 kg(ff(a.ffc[8], a.ffc[9]), ff(a.ffc[8], a.ffc[9]));
     ff2 P2[NV];
 #pragma unroll
-    for (int v = 0; v < NV; v++) P2[v] = ff2(Ls[v], Rs[v]);
+    for (int v = 0; v < NV; v++) {
+      if constexpr (RECON == RECON_MC) P2[v] = P2mc[v];
+      else P2[v] = ff2(Ls[v], Rs[v]);
+    }
     Z<ff2> z2;
     z_load(z2, P2, c);
     ff2 U2[NV], F2[NV], cmin2, cmax2;

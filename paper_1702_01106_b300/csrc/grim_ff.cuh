@@ -260,6 +260,19 @@ __device__ __forceinline__ ff2 keep(ff2 a, bool kx, bool ky) {
 }
 __device__ __forceinline__ ff2 scale2(ff2 a, float2 s) { return ff2(mul2(a.hi, s), mul2(a.lo, s)); }
 
+// The generalized minmod of gm_slope above for two zones at once (lane x:
+// vm, v0, vp of one zone, lane y of the other): the differences, the
+// limiter's product and the sum on paired instructions, the sign tests and
+// the minimum lane by lane.
+__device__ __forceinline__ ff2 gm_slope2(ff theta, ff2 vm, ff2 v0, ff2 vp) {
+  const ff2 a = v0 - vm, c = vp - v0;
+  const bool kx = (a.hi.x > 0.f && c.hi.x > 0.f) || (a.hi.x < 0.f && c.hi.x < 0.f);
+  const bool ky = (a.hi.y > 0.f && c.hi.y > 0.f) || (a.hi.y < 0.f && c.hi.y < 0.f);
+  const ff2 m = fmin(ff2(theta, theta) * fmin(fabs(a), fabs(c)), tconst<ff2>(0.5) * fabs(a + c));
+  const ff mx = m.x(), my = m.y();
+  return keep(ff2(a.hi.x > 0.f ? mx : -mx, a.hi.y > 0.f ? my : -my), kx, ky);
+}
+
 // 1/y, sqrt(a) and a^(-1/2) as for ff, each lane's float estimate refined
 // by the paired float-float step.
 __device__ __forceinline__ ff2 nr_rcp(ff2 y) {
