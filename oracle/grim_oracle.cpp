@@ -683,9 +683,15 @@ static void compute_fluxes(Stage& S, const double* PE) {
       for (int j = 0; j < p.n[1]; j++)
         for (int i = 0; i < p.n[0]; i++) {
           if (!S.zmask[S.G.idx(i, j, k)]) continue;
+          // only indices inside the face arrays' extent -1..n (a zone on the
+          // high boundary would otherwise mark one past it)
           for (int c = -r[2]; c <= r[2] + (p.dim >= 3); c++)
             for (int b = -r[1]; b <= r[1] + (p.dim >= 2); b++)
-              for (int a = -r[0]; a <= r[0] + 1; a++) fm[S.eidx(i + a, j + b, k + c)] = 1;
+              for (int a = -r[0]; a <= r[0] + 1; a++) {
+                const int ii = i + a, jj = j + b, kk = k + c;
+                if (ii > p.n[0] || (p.dim >= 2 && jj > p.n[1]) || (p.dim >= 3 && kk > p.n[2])) continue;
+                fm[S.eidx(ii, jj, kk)] = 1;
+              }
         }
   }
   // Faces in direction d: 0..n_d along d; -1..n across it (flux-CT), in active dims.
