@@ -453,6 +453,15 @@ def bench_batched(dev, mlp, torch, world, steps=3):
         bt.close()
         del A, B
         torch.cuda.empty_cache()
+    ref = one["fp64"]
+    scale = np.abs(ref) + np.abs(ref).max(axis=1, keepdims=True)
+    scale[2:] += 1.0
+    bulk = ref[0] > 0.05 * ref[0].max()   # inside the torus, away from its surface and the atmosphere
+    for name in ("mixed", "mixed_learned"):
+        d = np.abs(one[name] - ref) / scale
+        out[name]["one_step_max_rel_diff_vs_fp64"] = float(d.max())
+        out[name]["one_step_max_rel_diff_vs_fp64_bulk"] = float(d[:, bulk].max())
+    del one, ref, scale, bulk
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
     out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed_learned"]["ms_per_step"]
     return out
@@ -464,6 +473,7 @@ def bench_kerr(dev, torch, world, steps=10, warmup=3, cpu=False):
     the light-speed bound: zone-updates/s of the float64 and mixed arms, and
     of the mixed arm with a learned start trained (untimed) on both stages
     of the first four float64 steps (8 stages of 4.7 M zones)."""
+    import numpy as np
     from paper_1702_01106_b300 import inputs, guess
     from paper_1702_01106_b300.grim import Grim, GRIM_FP64, GRIM_MIXED
     prob = inputs.torus_problem(192, 192, 128)
@@ -482,6 +492,7 @@ def bench_kerr(dev, torch, world, steps=10, warmup=3, cpu=False):
                                "loss_per_quarter": losses, "seconds": time.perf_counter() - t0}
     del X, Y
     torch.cuda.empty_cache()
+    one = {}
     for name, prec, learned in (("fp64", GRIM_FP64, False), ("mixed", GRIM_MIXED, False),
                                 ("mixed_learned", GRIM_MIXED, True)):
         g = Grim(prob, precision=prec)
@@ -492,6 +503,12 @@ def bench_kerr(dev, torch, world, steps=10, warmup=3, cpu=False):
         tuning = g.autotune(a, dt)[0]   # launch shapes, untimed
         ms, s, kt, _ = time_device(g, a, b, dt, steps, warmup, world, torch)
         ms = max_over_ranks(ms, world)
+        # one step from the initial state, untimed: the arms' agreement with float64
+        a1 = P.to(dev)
+        b1 = torch.empty_like(a1)
+        g.step(a1, b1, dt)
+        one[name] = b1.cpu().numpy().reshape(10, -1)
+        del a1, b1
         out[name] = {"value": aggregate_rate(prob.zones, ms * 1e-3, world), "ms_per_step": ms,
                      "newton_iters_per_zone_stage": s["iters"] / max(1, s["zones"]),
                      "fp64_residuals_per_zone_stage": s["evals64"] / max(1, s["zones"]),
@@ -503,6 +520,15 @@ def bench_kerr(dev, torch, world, steps=10, warmup=3, cpu=False):
         g.close()
         del a, b
         torch.cuda.empty_cache()
+    ref = one["fp64"]
+    scale = np.abs(ref) + np.abs(ref).max(axis=1, keepdims=True)
+    scale[2:] += 1.0
+    bulk = ref[0] > 0.05 * ref[0].max()   # inside the torus, away from its surface and the atmosphere
+    for name in ("mixed", "mixed_learned"):
+        d = np.abs(one[name] - ref) / scale
+        out[name]["one_step_max_rel_diff_vs_fp64"] = float(d.max())
+        out[name]["one_step_max_rel_diff_vs_fp64_bulk"] = float(d[:, bulk].max())
+    del one, ref, scale, bulk
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
     out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed_learned"]["ms_per_step"]
     if cpu:
