@@ -30,7 +30,15 @@
  *    kernels.
  *  - Reconstruction: generalized minmod (MC), WENO5 or PPM (Section 2.4.1);
  *    Riemann solver: LLF or HLLE (Section 2.4.2).
- *  - Precision: float64 throughout, or the mixed solver (GRIM_MIXED).
+ *  - Precision: float64 throughout, or the mixed solver (GRIM_MIXED): the
+ *    finite-difference Jacobian and its LU in float32; the residual, the
+ *    update, the line search and the convergence test in float64; the
+ *    explicit face fluxes and the source terms at P^E in float-float
+ *    (pairs of floats, about 48 bits), with U(P_n) and the flux divergence
+ *    in float64.
+ *  - Optionally, Newton starts from a small network's prediction
+ *    (grim_mlp_*, grim_set_guess; inference and training GEMMs on the
+ *    fifth-generation tensor cores), with the plain start P_n as fallback.
  */
 #ifndef GRIM_H
 #define GRIM_H
