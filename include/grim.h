@@ -298,8 +298,8 @@ int grim_set_tuning(grim_ctx* ctx, const grim_tuning* tuning);
 
 /* Choose the launch shape by timing grim_step from the device state P with
  * step dt (P is not modified): each field of grim_tuning in turn over its
- * allowed values, the others held, keeping the fastest (CUDA events, median
- * of 3 steps after one warm-up step).  With cache_path non-NULL, a line of
+ * allowed values, the others held, keeping the fastest, in two passes over
+ * the fields (CUDA events, median of 5 steps after one warm-up step).  With cache_path non-NULL, a line of
  * that text file (one JSON object per line, keyed by device name, grid,
  * precision, reconstruction, closures and whether a learned guess is set)
  * is used instead when present, and the result is written there otherwise.

@@ -515,9 +515,9 @@ static void write_cached_tuning(const char* path, const std::string& key, const 
 // Median of 3 timed steps after one warm-up step, eagerly launched.
 static int time_steps(grim_ctx* ctx, const double* P, double* out, double dt, double& ms) {
   cudaEvent_t a = ctx->event(), b = ctx->event();
-  float t[3];
+  float t[5];
   int rc = step_launches(ctx, P, out, dt);
-  for (int i = 0; i < 3 && !rc; i++) {
+  for (int i = 0; i < 5 && !rc; i++) {
     cudaEventRecord(a, ctx->stream);
     rc = step_launches(ctx, P, out, dt);
     cudaEventRecord(b, ctx->stream);
@@ -527,8 +527,8 @@ static int time_steps(grim_ctx* ctx, const double* P, double* out, double dt, do
   ctx->pool.push_back(a);
   ctx->pool.push_back(b);
   if (rc) return rc;
-  std::sort(t, t + 3);
-  ms = t[1];
+  std::sort(t, t + 5);
+  ms = t[2];
   return GRIM_OK;
 }
 
@@ -548,11 +548,14 @@ int grim_autotune(grim_ctx* ctx, const double* P, double dt, const char* cache_p
     const int kmax = ctx->p.kmax;
     const std::vector<int> sets[5] = {{32, 64, 128}, {0, 1}, {1, 2, 3, 4, kmax > 4 ? kmax : 5}, {64, 128, 256},
                                       {64, 128, 256}};
-    for (int f = 0; f < 5 && !rc; f++) {
-      for (int v : sets[f]) {
+    // two passes of coordinate descent: the second revisits each field
+    // after the others have moved
+    for (int f = 0; f < 10 && !rc; f++) {
+      for (int v : sets[f % 5]) {
         grim_tuning c = best;
-        int* field = f == 0 ? &c.newton_bs : f == 1 ? &c.newton_rounds : f == 2 ? &c.newton_kcut
-                   : f == 3 ? &c.faces_bs : &c.zone_bs;
+        const int fi = f % 5;
+        int* field = fi == 0 ? &c.newton_bs : fi == 1 ? &c.newton_rounds : fi == 2 ? &c.newton_kcut
+                   : fi == 3 ? &c.faces_bs : &c.zone_bs;
         if (*field == v) continue;
         *field = v;
         ctx->tune = c;
