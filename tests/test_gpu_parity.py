@@ -117,6 +117,39 @@ def test_many_steps_turbulent(dev, orc):
     assert sm["failed"] == 0 and sm["max_res"] <= 1e-12 and sm["evals32"] > 0
 
 
+def _corner_div_2d(prob, P):
+    """Corner divergence of B on a periodic 2-D grid (the quantity flux-CT
+    keeps, Section 4.2): at corner (i-1/2, j-1/2) the differences of B^1
+    along x^1 and of B^2 along x^2, each averaged over the two zones
+    adjacent along the other direction."""
+    B1, B2 = P[5, 0], P[6, 0]                       # [n2][n1]
+    d1 = B1 - np.roll(B1, 1, axis=1)
+    d1 = 0.5 * (d1 + np.roll(d1, 1, axis=0))
+    d2 = B2 - np.roll(B2, 1, axis=0)
+    d2 = 0.5 * (d2 + np.roll(d2, 1, axis=1))
+    return d1 / prob.dx[0] + d2 / prob.dx[1]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_flux_ct_keeps_divergence_100_steps(dev, precision):
+    """100 steps of the periodic ragged box, float64 and the mixed solver:
+    flux-CT leaves the corner divergence of B unchanged to round-off (each
+    step adds only float64 rounding: the edge EMFs are doubles also when the
+    mixed solver forms the face fluxes in float-float)."""
+    prob, P = _ragged_turbulent(40, 24, tol=1e-12)
+    dt = 0.5 / 40
+    g = _g(prob, precision=precision)
+    a = _t(P, dev)
+    d0 = _corner_div_2d(prob, P)
+    for _ in range(100):
+        g.step(a, a, dt)
+    d1 = _corner_div_2d(prob, a.cpu().numpy())
+    scale = np.abs(P[5:7]).max() / min(prob.dx[:2])
+    assert np.abs(d1 - d0).max() < 1e-12 * scale
+    assert g.stats()["failed"] == 0
+    g.close()
+
+
 def test_in_place_step(dev, orc):
     prob, P = _ragged_turbulent(24, 40)
     g = _g(prob)
