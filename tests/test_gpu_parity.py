@@ -150,6 +150,40 @@ def test_flux_ct_keeps_divergence_100_steps(dev, precision):
     g.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-14), (1, 1e-12)])
+def test_periodic_box_conserves_mass_energy_momentum(dev, orc, precision, tol):
+    """20 steps of the periodic 24^2 box, float64 and the mixed solver: the
+    totals of rho u^t, T^t_t and T^t_i (from the oracle's U(P)) move by no
+    more than the solver tolerance allows.  A full stage ends with every
+    zone's scaled residual |r_a| <= tol, r_a = (U_a(P) - U*_a) / (|U_a(P_n)|
+    + |U_0(P_n)|), and the totals of U* equal those of U(P_n) on a periodic
+    grid (the flux differences telescope), so a step moves total a by at
+    most tol sum(|U_a| + |U_0|); the bound takes twice that."""
+    prob = inputs.turbulent_box_problem(24, tol=tol)
+    P = inputs.turbulent_box_state(prob)
+    dt = 0.5 / 24
+    steps = 20
+
+    def totals(Q):
+        tot, mag = np.zeros(5), np.zeros(5)
+        for z in range(prob.zones):
+            U, _, _ = orc.point(prob, Q.reshape(10, -1)[:, z])
+            tot += U[:5]
+            mag += np.abs(U[:5])
+        return tot, mag
+
+    t0, m0 = totals(P)
+    g = _g(prob, precision=precision)
+    a = _t(P, dev)
+    for _ in range(steps):
+        g.step(a, a, dt)
+    assert g.stats()["failed"] == 0
+    t1, _ = totals(a.cpu().numpy())
+    bound = 2.0 * steps * tol * (m0 + m0[0])
+    assert np.all(np.abs(t1 - t0) <= bound), np.abs(t1 - t0) / bound
+    g.close()
+
+
 def test_in_place_step(dev, orc):
     prob, P = _ragged_turbulent(24, 40)
     g = _g(prob)
